@@ -1,0 +1,187 @@
+"""FP64 CPU oracle for per-element numerical integration (test infrastructure).
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its binding) never calls it.  The arithmetic lives in ``fem_oracle.c``, plain
+C with OpenMP over elements, which follows Algorithms 1/2 of the paper; this
+module compiles it with gcc on first use and wraps it with ctypes.
+
+Parity status of each function (what pins it is in tests/test_oracle_*.py):
+  rule, basis, integrate (constant coefficients), law_k, mlp_loss_grad: pinned;
+  integrate with law=2 (MLP coefficient): pinned through its parts (the MLP
+  forward is pinned by the finite-difference and closed-form tests, the
+  integration by the law=0 pins).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SRC = os.path.join(_HERE, "fem_oracle.c")
+_SO = os.path.join(_BUILD, "libfem_oracle.so")
+
+TET, PRISM = 0, 1
+ST_DET, ST_NONFINITE = 1, 2
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile fem_oracle.c into a shared library (gcc -O2 -fopenmp)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            d, i, i64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64
+            P = ctypes.c_void_p
+            lib.orc_ns.argtypes = [i, i]
+            lib.orc_nq.argtypes = [i, i]
+            lib.orc_jacobi.argtypes = [i, i, i, d]
+            lib.orc_jacobi.restype = d
+            lib.orc_djacobi.argtypes = [i, i, i, d]
+            lib.orc_djacobi.restype = d
+            lib.orc_gauss_jacobi.argtypes = [i, i, i, P, P]
+            lib.orc_rule.argtypes = [i, i, P, P]
+            lib.orc_basis.argtypes = [i, i, i, P, P]
+            lib.orc_law_k.argtypes = [d, d]
+            lib.orc_law_k.restype = d
+            lib.orc_law_residual.argtypes = [d, d, d]
+            lib.orc_law_residual.restype = d
+            lib.orc_mlp_nparams.argtypes = [i]
+            lib.orc_mlp_forward.argtypes = [i, P, P, i64, P, P, P]
+            lib.orc_mlp_loss_grad.argtypes = [i, P, P, i64, P, P, P, P]
+            lib.orc_mlp_loss_grad.restype = d
+            lib.orc_integrate_ex.argtypes = [i, i, i64, P, P, i64, i, P, i, P, P, P, P, P, i]
+            lib.orc_max_threads.argtypes = []
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def ns(elem: int, p: int) -> int:
+    return _load().orc_ns(elem, p)
+
+
+def nq(elem: int, p: int) -> int:
+    return _load().orc_nq(elem, p)
+
+
+def max_threads() -> int:
+    return _load().orc_max_threads()
+
+
+def jacobi(n, a, b, x):
+    return _load().orc_jacobi(n, a, b, float(x))
+
+
+def djacobi(n, a, b, x):
+    return _load().orc_djacobi(n, a, b, float(x))
+
+
+def gauss_jacobi(n: int, a: int, b: int):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    _load().orc_gauss_jacobi(n, a, b, _ptr(x), _ptr(w))
+    return x, w
+
+
+def rule(elem: int, p: int):
+    """Quadrature points [NQ][3] and weights [NQ] on the reference element."""
+    n = nq(elem, p)
+    if n < 0:
+        raise ValueError("unsupported element/degree")
+    xi = np.zeros((n, 3))
+    w = np.zeros(n)
+    _load().orc_rule(elem, p, _ptr(xi), _ptr(w))
+    return xi, w
+
+
+def basis(elem: int, p: int, pts) -> np.ndarray:
+    """Shape function values and reference derivatives [npts][4][NS]."""
+    pts = _f64(pts).reshape(-1, 3)
+    n = ns(elem, p)
+    out = np.zeros((pts.shape[0], 4, n))
+    _load().orc_basis(elem, p, pts.shape[0], _ptr(pts), _ptr(out))
+    return out
+
+
+def law_k(u: float, g: float) -> float:
+    return _load().orc_law_k(float(u), float(g))
+
+
+def law_residual(u: float, g: float, k: float) -> float:
+    return _load().orc_law_residual(float(u), float(g), float(k))
+
+
+def mlp_nparams(H: int) -> int:
+    return _load().orc_mlp_nparams(H)
+
+
+def mlp_forward(H, theta, box, u, g):
+    theta, box, u, g = _f64(theta), _f64(box), _f64(u), _f64(g)
+    y = np.zeros(u.shape[0])
+    _load().orc_mlp_forward(H, _ptr(theta), _ptr(box), u.shape[0], _ptr(u), _ptr(g), _ptr(y))
+    return y
+
+
+def mlp_loss_grad(H, theta, box, u, g, t):
+    theta, box, u, g, t = _f64(theta), _f64(box), _f64(u), _f64(g), _f64(t)
+    grad = np.zeros(mlp_nparams(H))
+    L = _load().orc_mlp_loss_grad(H, _ptr(theta), _ptr(box), u.shape[0], _ptr(u), _ptr(g),
+                                  _ptr(t), _ptr(grad))
+    return L, grad
+
+
+def integrate(elem: int, p: int, coords, coeffs, law: int = 0, ucoef=None, mlp=None,
+              nthreads: int = 0):
+    """Element matrices A [E][NS][NS], load vectors b [E][NS], status [E] (FP64).
+
+    coords [E][nv][3]; coeffs SoA [11][E]; law 0 constant, 1 exact nonlinear
+    law (ucoef [E][NS]), 2 MLP inside its box else the exact law
+    (mlp = (H, theta, box)).
+    """
+    coords = _f64(coords)
+    coeffs = _f64(coeffs)
+    E = coords.shape[0]
+    n = ns(elem, p)
+    if n < 0:
+        raise ValueError("unsupported element/degree")
+    A = np.zeros((E, n, n))
+    b = np.zeros((E, n))
+    st = np.zeros(E, dtype=np.int32)
+    uc = _f64(ucoef) if ucoef is not None else None
+    H, th, box = (0, None, None) if mlp is None else (mlp[0], _f64(mlp[1]), _f64(mlp[2]))
+    if law and uc is None:
+        raise ValueError("law needs ucoef")
+    if law == 2 and mlp is None:
+        raise ValueError("law 2 needs mlp")
+    rc = _load().orc_integrate_ex(elem, p, E, _ptr(coords), _ptr(coeffs), coeffs.shape[1], law,
+                                  _ptr(uc), H, _ptr(th), _ptr(box), _ptr(A), _ptr(b), _ptr(st),
+                                  nthreads)
+    if rc != 0:
+        raise RuntimeError("oracle integrate failed")
+    return A, b, st

@@ -1,0 +1,475 @@
+/*
+ * fem_oracle.c -- plain, slow FP64 CPU oracle for per-element numerical
+ * integration (Banas, Plaszewski, Maciol, "Numerical integration on GPUs for
+ * higher order finite elements", arXiv 1310.1191).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this code.  It shares no source with the
+ * CUDA library: quadrature comes from Newton iteration on Jacobi polynomials
+ * (the library uses Golub-Welsch), Jacobi polynomials come from their explicit
+ * finite sum (the library uses the three-term recurrence), and the element
+ * map derivatives come from the six vertex shape functions (the library uses
+ * edge vectors).
+ *
+ * What it computes (Section 2, Algorithms 1 and 2):
+ *   for each element, for each quadrature point iQ:
+ *     phi^Q[iQ][iD][i]   reference shape functions (iD=0) and their
+ *                        reference derivatives (iD=1..3),
+ *     J, det J, J^{-1}   Jacobian of the reference->real map,
+ *     psi^Q[iQ][iD][i]   physical derivatives by the chain rule (eq. sum_int):
+ *                        d phi/d x_m = sum_k d phi/d xi_k * (J^{-1})[k][m],
+ *     c^Q[iD][jD]        coefficients at the point,
+ *     A^e[i][j] += det * w^Q * c^Q[iD][jD] * psi[iD][i] * psi[jD][j]
+ *   for the non-zero entries of c (Algorithm 2 skips the zero ones).
+ * The generic second-order form is -div(D grad u) + b.grad u + c u = f, i.e.
+ *   c[0][0] = c, c[0][1+m] = b_m, c[1+l][1+m] = D[l][m], c[1+l][0] = 0,
+ * row i = test function, column j = trial function.  The load vector (not in
+ * the paper, which integrates only A^e) is b^e[i] = sum_Q det w f psi[0][i].
+ *
+ * Readings where the paper is silent (it names a prism with complete
+ * triangle polynomials times 1D polynomials and "Gaussian" quadrature,
+ * Section 2, Table 1):
+ *   - reference prism {xi,eta >= 0, xi+eta <= 1} x zeta in [-1,1], vertices
+ *     0..2 at zeta=-1 ((0,0),(1,0),(0,1)), 3..5 above them at zeta=+1;
+ *   - basis: Dubiner triangle functions in collapsed coordinates
+ *     (r=2xi-1, s=2eta-1, a=2(1+r)/(1-s)-1, b=s)
+ *       psi_ij = P_i^(0,0)(a) ((1-b)/2)^i P_j^(2i+1,0)(b), i+j <= p,
+ *     unnormalised, times Legendre L_k(zeta), k <= p; DOF index t + NT*k with
+ *     t running over n=i+j ascending, then i descending;
+ *   - quadrature: (p+1) points per direction, Gauss-Legendre in a,
+ *     Gauss-Jacobi(1,0) in b, Gauss-Legendre in zeta; xi=(1+a)(1-b)/4,
+ *     eta=(1+b)/2, w = wa wb wz / 8; point order q = iz*n*n + ia*n + ib;
+ *   - tetrahedron: P1 basis (barycentric), textbook 4-point degree-2 rule.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_TET 0
+#define ORC_PRISM 1
+
+#define ORC_ST_DET 1      /* det J <= 0 at some quadrature point */
+#define ORC_ST_NONFINITE 2 /* non-finite geometry or coefficient input */
+
+typedef long double ld;
+
+/* ------------------------------------------------------------------ sizes */
+int orc_ns(int elem, int p) {
+    if (elem == ORC_TET) return p == 1 ? 4 : -1;
+    if (p < 1 || p > 7) return -1;
+    return (p + 1) * (p + 1) * (p + 2) / 2;
+}
+
+int orc_nq(int elem, int p) {
+    if (elem == ORC_TET) return p == 1 ? 4 : -1;
+    if (p < 1 || p > 7) return -1;
+    return (p + 1) * (p + 1) * (p + 1);
+}
+
+/* -------------------------------------------------- Jacobi polynomials */
+static ld binom_l(int n, int k) {
+    if (k < 0 || k > n) return 0.0L;
+    ld r = 1.0L;
+    for (int i = 1; i <= k; i++) r = r * (ld)(n - k + i) / (ld)i;
+    return r;
+}
+
+static ld ipow_l(ld x, int k) {
+    ld r = 1.0L;
+    for (int i = 0; i < k; i++) r *= x;
+    return r;
+}
+
+/* P_n^(a,b)(x) by its explicit finite sum
+ *   sum_s C(n+a, n-s) C(n+b, s) ((x-1)/2)^s ((x+1)/2)^(n-s). */
+static ld jacobi_l(int n, int a, int b, ld x) {
+    if (n < 0) return 0.0L;
+    ld xm = (x - 1.0L) / 2.0L, xp = (x + 1.0L) / 2.0L, s = 0.0L;
+    for (int k = 0; k <= n; k++)
+        s += binom_l(n + a, n - k) * binom_l(n + b, k) * ipow_l(xm, k) * ipow_l(xp, n - k);
+    return s;
+}
+
+/* d/dx P_n^(a,b) = (n+a+b+1)/2 P_{n-1}^(a+1,b+1) */
+static ld djacobi_l(int n, int a, int b, ld x) {
+    if (n <= 0) return 0.0L;
+    return 0.5L * (ld)(n + a + b + 1) * jacobi_l(n - 1, a + 1, b + 1, x);
+}
+
+double orc_jacobi(int n, int a, int b, double x) { return (double)jacobi_l(n, a, b, x); }
+double orc_djacobi(int n, int a, int b, double x) { return (double)djacobi_l(n, a, b, x); }
+
+/* ---------------------------------------------- Gauss-Jacobi quadrature */
+/* Roots of P_n^(a,b) by Newton's method with deflation of the roots already
+ * found (Chebyshev points as first guesses), weights from
+ *   w_k = 2^(a+b+1) G(n+a+1) G(n+b+1) / (G(n+a+b+1) n!) / ((1-x_k^2) P_n'(x_k)^2).
+ * Nodes ascending.  Exact for polynomials of degree <= 2n-1 against
+ * (1-x)^a (1+x)^b on [-1,1]. */
+void orc_gauss_jacobi(int n, int a, int b, double *x, double *w) {
+    ld r[16];
+    const ld pi = 3.141592653589793238462643383279502884L;
+    for (int k = 0; k < n; k++) {
+        ld z = -cosl((2.0L * k + 1.0L) * pi / (2.0L * n));
+        if (k > 0) z = 0.5L * (z + r[k - 1]);
+        for (int it = 0; it < 200; it++) {
+            ld f = jacobi_l(n, a, b, z), fp = djacobi_l(n, a, b, z), s = 0.0L;
+            for (int i = 0; i < k; i++) s += 1.0L / (z - r[i]);
+            ld dz = -f / (fp - s * f);
+            z += dz;
+            if (fabsl(dz) < 1e-30L) break;
+        }
+        r[k] = z;
+    }
+    ld c = powl(2.0L, (ld)(a + b + 1)) * tgammal((ld)(n + a + 1)) * tgammal((ld)(n + b + 1)) /
+           (tgammal((ld)(n + a + b + 1)) * tgammal((ld)(n + 1)));
+    for (int k = 0; k < n; k++) {
+        ld d = djacobi_l(n, a, b, r[k]);
+        x[k] = (double)r[k];
+        w[k] = (double)(c / ((1.0L - r[k] * r[k]) * d * d));
+    }
+}
+
+/* Quadrature rule on the reference element; returns NQ or -1.
+ * xi: [NQ][3], w: [NQ]. */
+int orc_rule(int elem, int p, double *xi, double *w) {
+    if (elem == ORC_TET) {
+        if (p != 1) return -1;
+        /* barycentric (al, be, be, be) and permutations, weights 1/24 (volume 1/6) */
+        ld al = (5.0L + 3.0L * sqrtl(5.0L)) / 20.0L, be = (5.0L - sqrtl(5.0L)) / 20.0L;
+        ld pts[4][3] = {{be, be, be}, {al, be, be}, {be, al, be}, {be, be, al}};
+        for (int q = 0; q < 4; q++) {
+            for (int k = 0; k < 3; k++) xi[3 * q + k] = (double)pts[q][k];
+            w[q] = (double)(1.0L / 24.0L);
+        }
+        return 4;
+    }
+    if (p < 1 || p > 7) return -1;
+    int n = p + 1;
+    double xa[16], wa[16], xb[16], wb[16];
+    orc_gauss_jacobi(n, 0, 0, xa, wa);
+    orc_gauss_jacobi(n, 1, 0, xb, wb);
+    int q = 0;
+    for (int iz = 0; iz < n; iz++)
+        for (int ia = 0; ia < n; ia++)
+            for (int ib = 0; ib < n; ib++, q++) {
+                xi[3 * q + 0] = (1.0 + xa[ia]) * (1.0 - xb[ib]) / 4.0;
+                xi[3 * q + 1] = (1.0 + xb[ib]) / 2.0;
+                xi[3 * q + 2] = xa[iz];
+                w[q] = wa[ia] * wb[ib] * wa[iz] / 8.0;
+            }
+    return q;
+}
+
+/* ---------------------------------------------------------- basis */
+/* Values and reference derivatives of all shape functions at one point.
+ * phi: [4][NS]; row 0 values, rows 1..3 d/dxi, d/deta, d/dzeta. */
+static void basis_point(int elem, int p, const double *pt, double *phi) {
+    if (elem == ORC_TET) {
+        double x = pt[0], y = pt[1], z = pt[2];
+        double v[4] = {1.0 - x - y - z, x, y, z};
+        double d[3][4] = {{-1, 1, 0, 0}, {-1, 0, 1, 0}, {-1, 0, 0, 1}};
+        for (int i = 0; i < 4; i++) {
+            phi[i] = v[i];
+            for (int k = 0; k < 3; k++) phi[(1 + k) * 4 + i] = d[k][i];
+        }
+        return;
+    }
+    int NS = orc_ns(elem, p), NT = (p + 1) * (p + 2) / 2;
+    ld xi = pt[0], eta = pt[1], zeta = pt[2];
+    ld r = 2.0L * xi - 1.0L, s = 2.0L * eta - 1.0L;
+    ld a = 2.0L * (1.0L + r) / (1.0L - s) - 1.0L, bb = s;
+    ld tv[64], tx[64], ty[64];
+    int t = 0;
+    for (int nn = 0; nn <= p; nn++)
+        for (int i = nn; i >= 0; i--, t++) {
+            int j = nn - i;
+            ld fa = jacobi_l(i, 0, 0, a), dfa = djacobi_l(i, 0, 0, a);
+            ld hb = (1.0L - bb) / 2.0L;
+            ld pj = jacobi_l(j, 2 * i + 1, 0, bb), dpj = djacobi_l(j, 2 * i + 1, 0, bb);
+            ld gb = ipow_l(hb, i) * pj;
+            ld dgb = (i > 0 ? -0.5L * (ld)i * ipow_l(hb, i - 1) * pj : 0.0L) + ipow_l(hb, i) * dpj;
+            ld dpsi_da = dfa * gb, dpsi_db = fa * dgb;
+            ld dpsi_dr = dpsi_da * 2.0L / (1.0L - s);
+            ld dpsi_ds = dpsi_da * 2.0L * (1.0L + r) / ((1.0L - s) * (1.0L - s)) + dpsi_db;
+            tv[t] = fa * gb;
+            tx[t] = 2.0L * dpsi_dr;
+            ty[t] = 2.0L * dpsi_ds;
+        }
+    for (int k = 0; k <= p; k++) {
+        ld L = jacobi_l(k, 0, 0, zeta), dL = djacobi_l(k, 0, 0, zeta);
+        for (int tt = 0; tt < NT; tt++) {
+            int i = tt + NT * k;
+            phi[0 * NS + i] = (double)(tv[tt] * L);
+            phi[1 * NS + i] = (double)(tx[tt] * L);
+            phi[2 * NS + i] = (double)(ty[tt] * L);
+            phi[3 * NS + i] = (double)(tv[tt] * dL);
+        }
+    }
+}
+
+/* phi: [npts][4][NS] */
+int orc_basis(int elem, int p, int npts, const double *pts, double *phi) {
+    int NS = orc_ns(elem, p);
+    if (NS < 0) return -1;
+    for (int q = 0; q < npts; q++) basis_point(elem, p, pts + 3 * q, phi + (size_t)q * 4 * NS);
+    return NS;
+}
+
+/* ------------------------------------------------------ geometry map */
+/* Vertex shape functions N_v of the reference->real map and their
+ * reference derivatives dN[k][v] at one point. */
+static int map_derivs(int elem, const double *pt, double dN[3][6]) {
+    if (elem == ORC_TET) {
+        double d[3][4] = {{-1, 1, 0, 0}, {-1, 0, 1, 0}, {-1, 0, 0, 1}};
+        for (int k = 0; k < 3; k++)
+            for (int v = 0; v < 4; v++) dN[k][v] = d[k][v];
+        return 4;
+    }
+    double xi = pt[0], eta = pt[1], zeta = pt[2];
+    double lam[3] = {1.0 - xi - eta, xi, eta};
+    double dlx[3] = {-1.0, 1.0, 0.0}, dly[3] = {-1.0, 0.0, 1.0};
+    double lo = (1.0 - zeta) / 2.0, hi = (1.0 + zeta) / 2.0;
+    for (int a = 0; a < 3; a++) {
+        /* N_a = lam_a (1-zeta)/2 ; N_{a+3} = lam_a (1+zeta)/2 */
+        dN[0][a] = dlx[a] * lo;
+        dN[1][a] = dly[a] * lo;
+        dN[2][a] = -0.5 * lam[a];
+        dN[0][a + 3] = dlx[a] * hi;
+        dN[1][a + 3] = dly[a] * hi;
+        dN[2][a + 3] = 0.5 * lam[a];
+    }
+    return 6;
+}
+
+static double det3(const double J[3][3]) {
+    return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+/* inverse by cofactors: Ji[k][m] = cof(J)[m][k] / det */
+static void inv3(const double J[3][3], double det, double Ji[3][3]) {
+    for (int k = 0; k < 3; k++)
+        for (int m = 0; m < 3; m++) {
+            int r0 = (m + 1) % 3, r1 = (m + 2) % 3, c0 = (k + 1) % 3, c1 = (k + 2) % 3;
+            Ji[k][m] = (J[r0][c0] * J[r1][c1] - J[r0][c1] * J[r1][c0]) / det;
+        }
+}
+
+/* ------------------------------------------------ nonlinear coefficient law */
+/* k solves F(k) = k - 1 - 0.5 exp(-u^2) - 0.2 log(1 + k g) = 0; exactly 8
+ * Newton steps from k0 = 1 + 0.5 exp(-u^2), no early exit. */
+double orc_law_k(double u, double g) {
+    double e = 0.5 * exp(-u * u);
+    double k = 1.0 + e;
+    for (int it = 0; it < 8; it++) {
+        double F = k - 1.0 - e - 0.2 * log(1.0 + k * g);
+        double Fp = 1.0 - 0.2 * g / (1.0 + k * g);
+        k -= F / Fp;
+    }
+    return k;
+}
+
+double orc_law_residual(double u, double g, double k) {
+    return k - 1.0 - 0.5 * exp(-u * u) - 0.2 * log(1.0 + k * g);
+}
+
+/* -------------------------------------------------- MLP surrogate (FP64) */
+/* 2 -> H -> H -> 1 with tanh.  Parameter vector layout (row-major):
+ *   W1[H][2], b1[H], W2[H][H], b2[H], W3[1][H], b3[1].
+ * Inputs are normalised to [-1,1]^2 over the box [u0,u1]x[g0,g1]. */
+static double mlp_forward(int H, const double *th, const double *box, double u, double g,
+                          double *h1, double *h2) {
+    const double *W1 = th, *b1 = W1 + 2 * H, *W2 = b1 + H, *b2 = W2 + H * H, *W3 = b2 + H,
+                 *b3 = W3 + H;
+    double x0 = 2.0 * (u - box[0]) / (box[1] - box[0]) - 1.0;
+    double x1 = 2.0 * (g - box[2]) / (box[3] - box[2]) - 1.0;
+    for (int i = 0; i < H; i++) h1[i] = tanh(W1[2 * i] * x0 + W1[2 * i + 1] * x1 + b1[i]);
+    for (int i = 0; i < H; i++) {
+        double s = b2[i];
+        for (int j = 0; j < H; j++) s += W2[i * H + j] * h1[j];
+        h2[i] = tanh(s);
+    }
+    double y = b3[0];
+    for (int j = 0; j < H; j++) y += W3[j] * h2[j];
+    return y;
+}
+
+int orc_mlp_nparams(int H) { return 2 * H + H + H * H + H + H + 1; }
+
+/* y[n] = MLP(u[n], g[n]) */
+void orc_mlp_forward(int H, const double *th, const double *box, int64_t n, const double *u,
+                     const double *g, double *y) {
+    double h1[256], h2[256];
+    for (int64_t s = 0; s < n; s++) y[s] = mlp_forward(H, th, box, u[s], g[s], h1, h2);
+}
+
+/* Loss L = mean_s (y_s - t_s)^2 and its gradient dL/dtheta by backpropagation
+ * (reverse-mode chain rule through the three layers). */
+double orc_mlp_loss_grad(int H, const double *th, const double *box, int64_t n, const double *u,
+                         const double *g, const double *t, double *grad) {
+    const double *W2 = th + 3 * H, *W3 = th + 3 * H + H * H + H;
+    int P = orc_mlp_nparams(H);
+    double *gW1 = grad, *gb1 = gW1 + 2 * H, *gW2 = gb1 + H, *gb2 = gW2 + H * H, *gW3 = gb2 + H,
+           *gb3 = gW3 + H;
+    memset(grad, 0, sizeof(double) * P);
+    double h1[256], h2[256], d2[256], d1[256], L = 0.0;
+    for (int64_t s = 0; s < n; s++) {
+        double y = mlp_forward(H, th, box, u[s], g[s], h1, h2);
+        double x0 = 2.0 * (u[s] - box[0]) / (box[1] - box[0]) - 1.0;
+        double x1 = 2.0 * (g[s] - box[2]) / (box[3] - box[2]) - 1.0;
+        double r = y - t[s];
+        L += r * r;
+        double dy = 2.0 * r / (double)n;
+        gb3[0] += dy;
+        for (int j = 0; j < H; j++) {
+            gW3[j] += dy * h2[j];
+            d2[j] = dy * W3[j] * (1.0 - h2[j] * h2[j]);
+        }
+        for (int i = 0; i < H; i++) {
+            gb2[i] += d2[i];
+            for (int j = 0; j < H; j++) gW2[i * H + j] += d2[i] * h1[j];
+        }
+        for (int j = 0; j < H; j++) {
+            double s2 = 0.0;
+            for (int i = 0; i < H; i++) s2 += W2[i * H + j] * d2[i];
+            d1[j] = s2 * (1.0 - h1[j] * h1[j]);
+        }
+        for (int i = 0; i < H; i++) {
+            gb1[i] += d1[i];
+            gW1[2 * i] += d1[i] * x0;
+            gW1[2 * i + 1] += d1[i] * x1;
+        }
+    }
+    return L / (double)n;
+}
+
+/* ------------------------------------------------ element integration */
+/* law: 0 constant coefficients; 1 exact nonlinear law with D = k(u,|grad u|^2) I;
+ *      2 same with k from the MLP (mlp_theta, box, H) inside the box and the
+ *        exact law outside.
+ * coords [E][nv][3]; coeffs SoA [11][cstride]: Dxx Dyy Dzz Dxy Dxz Dyz bx by bz c f;
+ * ucoef [E][NS] (law != 0); A [E][NS][NS]; b [E][NS]; status [E] (nullable). */
+int orc_integrate_ex(int elem, int p, int64_t E, const double *coords, const double *coeffs,
+                     int64_t cstride, int law, const double *ucoef, int H, const double *theta,
+                     const double *box, double *A, double *bvec, int32_t *status, int nthreads) {
+    int NS = orc_ns(elem, p), NQ = orc_nq(elem, p);
+    if (NS < 0 || NQ < 0) return -1;
+    int nv = elem == ORC_TET ? 4 : 6;
+    double *xq = (double *)malloc(sizeof(double) * 3 * NQ);
+    double *wq = (double *)malloc(sizeof(double) * NQ);
+    double *phiQ = (double *)malloc(sizeof(double) * (size_t)NQ * 4 * NS);
+    orc_rule(elem, p, xq, wq);
+    orc_basis(elem, p, NQ, xq, phiQ);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel
+    {
+        double *psi = (double *)malloc(sizeof(double) * 4 * NS);
+        double h1[256], h2[256];
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t e = 0; e < E; e++) {
+            /* Algorithm 1, lines 1-5: coefficients, geometry, old DOFs, init */
+            const double *X = coords + (size_t)e * nv * 3;
+            double cf[11];
+            for (int k = 0; k < 11; k++) cf[k] = coeffs[(size_t)k * cstride + e];
+            int32_t st = 0;
+            for (int k = 0; k < 11; k++)
+                if (!isfinite(cf[k])) st |= ORC_ST_NONFINITE;
+            for (int k = 0; k < nv * 3; k++)
+                if (!isfinite(X[k])) st |= ORC_ST_NONFINITE;
+            const double *U = law ? ucoef + (size_t)e * NS : NULL;
+            double *Ae = A + (size_t)e * NS * NS, *be = bvec + (size_t)e * NS;
+            memset(Ae, 0, sizeof(double) * NS * NS);
+            memset(be, 0, sizeof(double) * NS);
+            for (int q = 0; q < NQ; q++) {
+                /* lines 7-8: shape functions at iQ; Jacobian, det, inverse */
+                const double *phi = phiQ + (size_t)q * 4 * NS;
+                double dN[3][6], J[3][3], Ji[3][3];
+                map_derivs(elem, xq + 3 * q, dN);
+                for (int i = 0; i < 3; i++)
+                    for (int k = 0; k < 3; k++) {
+                        double s = 0.0;
+                        for (int v = 0; v < nv; v++) s += X[3 * v + i] * dN[k][v];
+                        J[i][k] = s;
+                    }
+                double det = det3(J);
+                if (!(det > 0.0)) st |= ORC_ST_DET;
+                inv3(J, det, Ji);
+                /* line 9: physical derivatives psi = J^{-T} grad_ref phi */
+                for (int i = 0; i < NS; i++) {
+                    psi[i] = phi[i];
+                    for (int m = 0; m < 3; m++) {
+                        double s = 0.0;
+                        for (int k = 0; k < 3; k++) s += Ji[k][m] * phi[(1 + k) * NS + i];
+                        psi[(1 + m) * NS + i] = s;
+                    }
+                }
+                /* line 10: coefficients at the point */
+                double c[4][4] = {{0}};
+                c[0][0] = cf[9];
+                c[0][1] = cf[6];
+                c[0][2] = cf[7];
+                c[0][3] = cf[8];
+                if (law == 0) {
+                    c[1][1] = cf[0];
+                    c[2][2] = cf[1];
+                    c[3][3] = cf[2];
+                    c[1][2] = c[2][1] = cf[3];
+                    c[1][3] = c[3][1] = cf[4];
+                    c[2][3] = c[3][2] = cf[5];
+                } else {
+                    double u = 0.0, gu[3] = {0, 0, 0};
+                    for (int i = 0; i < NS; i++) {
+                        u += U[i] * psi[i];
+                        for (int m = 0; m < 3; m++) gu[m] += U[i] * psi[(1 + m) * NS + i];
+                    }
+                    double g = gu[0] * gu[0] + gu[1] * gu[1] + gu[2] * gu[2];
+                    double k;
+                    if (law == 2 && u >= box[0] && u <= box[1] && g >= box[2] && g <= box[3])
+                        k = mlp_forward(H, theta, box, u, g, h1, h2);
+                    else
+                        k = orc_law_k(u, g);
+                    c[1][1] = c[2][2] = c[3][3] = k;
+                }
+                double dw = det * wq[q];
+                /* lines 11-15: update A^e for every DOF pair, non-zero c only */
+                for (int i = 0; i < NS; i++)
+                    for (int j = 0; j < NS; j++) {
+                        double s = 0.0;
+                        for (int iD = 0; iD < 4; iD++)
+                            for (int jD = 0; jD < 4; jD++)
+                                if (c[iD][jD] != 0.0)
+                                    s += dw * c[iD][jD] * psi[iD * NS + i] * psi[jD * NS + j];
+                        Ae[i * NS + j] += s;
+                    }
+                for (int i = 0; i < NS; i++) be[i] += dw * cf[10] * psi[i];
+            }
+            if (status) status[e] = st;
+        }
+        free(psi);
+    }
+    free(xq);
+    free(wq);
+    free(phiQ);
+    return 0;
+}
+
+int orc_integrate(int elem, int p, int64_t E, const double *coords, const double *coeffs,
+                  int64_t cstride, double *A, double *bvec, int32_t *status, int nthreads) {
+    return orc_integrate_ex(elem, p, E, coords, coeffs, cstride, 0, NULL, 0, NULL, NULL, A, bvec,
+                            status, nthreads);
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
