@@ -1,0 +1,128 @@
+/*
+ * fem.h -- C ABI of the GB300 per-element numerical integration library.
+ *
+ * The operation (Section 2 of Banas, Plaszewski, Maciol, arXiv 1310.1191,
+ * Algorithms 1 and 2): given the geometry of each element, problem dependent
+ * coefficients and (for nonlinear problems) old degrees of freedom, create the
+ * element stiffness matrix
+ *     A^e[i][j] = sum_Q det J_Q w_Q sum_{iD,jD} c^Q[iD][jD] psi^Q[iD][i] psi^Q[jD][j]
+ * where psi^Q are the shape functions (iD = 0) and their physical derivatives
+ * (iD = 1..3) at quadrature point Q (eq. sum_int, Section 5.1).  The weak form
+ * is the generic scalar second-order one,
+ *     a(u, v) = int grad v . D grad u + v b . grad u + c u v,   l(v) = int f v,
+ * so c[0][0] = c, c[0][1+m] = b_m, c[1+l][1+m] = D[l][m], c[1+l][0] = 0.
+ * Row i of A^e is the test function, column j the trial function.  The load
+ * vector b^e[i] = sum_Q det J_Q w_Q f psi^Q[0][i] is produced beside A^e.
+ *
+ * Elements: P1 tetrahedra (4 nodes, 4-point degree-2 rule) and straight-edged
+ * 6-node prisms of degree p = 1..7 (Dubiner triangle x Legendre basis,
+ * NS = (p+1)^2 (p+2)/2 shape functions, collapsed Gauss-Jacobi x Gauss-Legendre
+ * rule with NQ = (p+1)^3 points, exact to degree 2p).
+ *
+ * Conventions for every entry point:
+ *   - all functions return a status code (FEM_OK = 0) and never abort;
+ *   - argument errors are detected on the host before anything is enqueued;
+ *   - device pointers are caller-owned; the library owns only table handles
+ *     and the objects it creates (plans, surrogates);
+ *   - compute entry points are asynchronous on the given CUDA stream
+ *     (cudaStream_t passed as void*, NULL = legacy default stream).
+ */
+#ifndef FEM_GB300_H
+#define FEM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define FEM_OK 0
+#define FEM_EINVAL 1        /* bad argument (null, size, alignment, range) */
+#define FEM_ENOMEM 2        /* library-owned allocation failed */
+#define FEM_ECUDA 3         /* a CUDA runtime call failed (see fem_last_error) */
+#define FEM_EUNSUPPORTED 4  /* valid but not provided combination */
+#define FEM_EELEMENT 5      /* at least one element flagged in status[] */
+#define FEM_ETIMEOUT 6      /* a bounded device wait gave up */
+
+/* ---- element types ---- */
+#define FEM_TET4 0
+#define FEM_PRISM6 1
+
+/* ---- arithmetic of the contraction (geometry is always FP64) ---- */
+#define FEM_F64 0     /* FP64 FMA; outputs double */
+#define FEM_F32 1     /* FP32 FMA, G rounded from FP64; outputs float */
+#define FEM_BF16X3 2  /* tensor cores, bf16 hi+lo split, FP32 accumulate; float */
+#define FEM_F16X3 3   /* tensor cores, fp16 hi+lo split, FP32 accumulate; float */
+
+/* ---- output layouts ---- */
+#define FEM_OUT_FULL 0       /* A [E][NS][NS] row-major, unpadded */
+#define FEM_OUT_SYMPACKED 1  /* upper triangle row by row, NS(NS+1)/2 per element */
+
+/* ---- per-element status bits (int32 status[e]) ---- */
+#define FEM_ST_DET 1        /* det J <= 0 at some quadrature point */
+#define FEM_ST_NONFINITE 2  /* non-finite coordinate or coefficient */
+#define FEM_ST_NONSYM 4     /* symmetric-packed output requested but b != 0 */
+#define FEM_ST_FALLBACK 8   /* surrogate input left its box: exact law used (info) */
+
+typedef struct fem_tables_s *fem_tables;
+
+/* Reference data on the host, no GPU needed (Section 2: xi^Q, w^Q and
+ * phi^Q[iQ][iD][iDOF] of one element type and degree).
+ *   nq, ns  : out, number of points and shape functions (may be NULL);
+ *   xi      : out [nq][3] reference coordinates, or NULL;
+ *   w       : out [nq] weights (sum = reference volume: 1 prism, 1/6 tet), or NULL;
+ *   phi     : out [nq][4][ns] values (row 0) and reference derivatives
+ *             d/dxi, d/deta, d/dzeta (rows 1..3), or NULL.
+ * Returns FEM_EINVAL for an unknown element or p outside 1..7 (tet: p = 1). */
+int fem_reference_rule(int elem, int p, int *nq, int *ns, double *xi, double *w, double *phi);
+
+/* Build the device tables (quadrature points and weights, shape functions
+ * and reference derivatives at all points, in FP64 and in the reduced
+ * formats the contraction kernels read) for degrees p_min..p_max of one
+ * element type, on the current CUDA device.  Synchronous.  "These values are
+ * the same for all elements of a given approximation order" (Section 4.1):
+ * they are built once and kept resident in HBM.
+ *   out : receives a library-owned handle; release with fem_tables_destroy. */
+int fem_tables_build(int elem, int p_min, int p_max, fem_tables *out);
+int fem_tables_destroy(fem_tables t);
+
+/* Per-element integration of a uniform-degree batch (Algorithms 3/4 of
+ * Section 4.1 re-designed for sm_103a).
+ *   t            : tables holding degree p of the element type;
+ *   p            : polynomial degree (1..7; 1 for FEM_TET4);
+ *   n_elem       : number of elements (0 is a no-op);
+ *   coords       : device, double [n_elem][nv][3], nv = 4 (tet) or 6 (prism),
+ *                  8-byte aligned; vertex order as in the reference element;
+ *   coeffs       : device, double SoA [11][coeff_stride]: Dxx Dyy Dzz Dxy Dxz
+ *                  Dyz bx by bz c f, element e at column e; coeff_stride >= n_elem;
+ *   prec         : FEM_F64 / FEM_F32 / FEM_BF16X3 / FEM_F16X3;
+ *   layout       : FEM_OUT_FULL or FEM_OUT_SYMPACKED;
+ *   A_out        : device, [n_elem][NS*NS] (full) or [n_elem][NS(NS+1)/2]
+ *                  (packed) of double (FEM_F64) or float (others), 16-byte aligned;
+ *   b_out        : device, [n_elem][NS] of the same type, or NULL to skip;
+ *   status       : device int32 [n_elem] of FEM_ST_* bits, or NULL;
+ *   stream       : cudaStream_t.
+ * Returns FEM_EINVAL for null/misaligned pointers, n_elem < 0, p outside the
+ * tables, unknown prec/layout; FEM_EUNSUPPORTED for a tensor-core precision
+ * where no tensor-core kernel exists for (elem, p); FEM_ECUDA if a launch
+ * fails.  Numerical problems of single elements never fail the call: they are
+ * reported in status[]. */
+int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
+                  int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out,
+                  int32_t *status, void *stream);
+
+/* Number of output values per element for (elem, p, layout): NS*NS or NS(NS+1)/2;
+ * -1 if invalid.  */
+int64_t fem_matrix_size(int elem, int p, int layout);
+
+/* Human-readable text of a status code, and of the last error raised on the
+ * calling host thread (empty if none). */
+const char *fem_status_str(int status);
+const char *fem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEM_GB300_H */

@@ -1,0 +1,155 @@
+"""ctypes binding of the C ABI in include/fem.h (argument marshalling only).
+
+Function names match the C entry points.  Device buffers are passed as
+torch CUDA tensors (their data pointers are handed to the library) or as raw
+integer addresses; every computation runs in the library's CUDA kernels.
+If the shared library has not been built, loading fails loudly: there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfem_gb300.so")
+
+FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_ECUDA, FEM_EUNSUPPORTED, FEM_EELEMENT, FEM_ETIMEOUT = range(7)
+FEM_TET4, FEM_PRISM6 = 0, 1
+FEM_F64, FEM_F32, FEM_BF16X3, FEM_F16X3 = 0, 1, 2, 3
+FEM_OUT_FULL, FEM_OUT_SYMPACKED = 0, 1
+FEM_ST_DET, FEM_ST_NONFINITE, FEM_ST_NONSYM, FEM_ST_FALLBACK = 1, 2, 4, 8
+
+# every symbol include/fem.h declares (checked by the CPU tests)
+EXPORTS = (
+    "fem_reference_rule", "fem_tables_build", "fem_tables_destroy", "fem_integrate",
+    "fem_matrix_size", "fem_status_str", "fem_last_error",
+)
+
+_lib = None
+
+
+class FemError(RuntimeError):
+    def __init__(self, fn, code, msg):
+        super().__init__("%s failed: %s (%d): %s" % (fn, status_str(code), code, msg))
+        self.code = code
+
+
+def load():
+    """Load libfem_gb300.so; raises if it was not built (no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libfem_gb300.so is not built: run paper_1310_1191_gb300.build.build() "
+                           "(or __graft_entry__.build()) first")
+    lib = ctypes.CDLL(LIB_PATH)
+    i, i64, P = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+    lib.fem_reference_rule.argtypes = [i, i, P, P, P, P, P]
+    lib.fem_tables_build.argtypes = [i, i, i, P]
+    lib.fem_tables_destroy.argtypes = [P]
+    lib.fem_integrate.argtypes = [P, i, i64, P, P, i64, i, i, P, P, P, P]
+    lib.fem_matrix_size.argtypes = [i, i, i]
+    lib.fem_matrix_size.restype = i64
+    lib.fem_status_str.argtypes = [i]
+    lib.fem_status_str.restype = ctypes.c_char_p
+    lib.fem_last_error.argtypes = []
+    lib.fem_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_str(code: int) -> str:
+    return load().fem_status_str(code).decode()
+
+
+def last_error() -> str:
+    return load().fem_last_error().decode()
+
+
+def _check(fn, code):
+    if code != FEM_OK:
+        raise FemError(fn, code, last_error())
+    return code
+
+
+def _addr(x):
+    """Device/host address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return stream
+
+
+def fem_reference_rule(elem: int, p: int):
+    """(xi [nq][3], w [nq], phi [nq][4][ns]) from the library's host tables."""
+    lib = load()
+    nq, ns = ctypes.c_int(), ctypes.c_int()
+    _check("fem_reference_rule", lib.fem_reference_rule(elem, p, ctypes.byref(nq),
+                                                        ctypes.byref(ns), None, None, None))
+    xi = np.zeros((nq.value, 3))
+    w = np.zeros(nq.value)
+    phi = np.zeros((nq.value, 4, ns.value))
+    _check("fem_reference_rule", lib.fem_reference_rule(elem, p, None, None, xi.ctypes.data,
+                                                        w.ctypes.data, phi.ctypes.data))
+    return xi, w, phi
+
+
+def fem_matrix_size(elem: int, p: int, layout: int) -> int:
+    return load().fem_matrix_size(elem, p, layout)
+
+
+class Tables:
+    """Owning wrapper of a fem_tables handle."""
+
+    def __init__(self, elem: int, p_min: int, p_max: int):
+        self.elem, self.p_min, self.p_max = elem, p_min, p_max
+        h = ctypes.c_void_p()
+        _check("fem_tables_build", load().fem_tables_build(elem, p_min, p_max, ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().fem_tables_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fem_tables_build(elem: int, p_min: int, p_max: int) -> Tables:
+    return Tables(elem, p_min, p_max)
+
+
+def fem_tables_destroy(t: Tables) -> None:
+    t.close()
+
+
+def fem_integrate(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_stride: int, prec: int,
+                  layout: int, A_out, b_out=None, status=None, stream=None) -> int:
+    """Enqueue the integration of n_elem elements of degree p (see fem.h)."""
+    return _check("fem_integrate", load().fem_integrate(
+        t.handle, p, n_elem, _addr(coords), _addr(coeffs), coeff_stride, prec, layout,
+        _addr(A_out), _addr(b_out), _addr(status), _stream(stream)))

@@ -1,0 +1,187 @@
+// C ABI entry points: argument validation, table management and dispatch.
+//
+// Host-side responsibilities follow the paper's host code (Section 4.2): the
+// element data stay in caller-owned device memory, the reference tables are
+// built once per degree and kept resident, the launch shape is derived from
+// the degree, and the output is left on the device for the caller (the
+// "second alternative" of Section 4.2).
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fem_internal.h"
+
+namespace fem {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+static int cuda_fail(const char *what, cudaError_t e) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return FEM_ECUDA;
+}
+
+static int invalid(const char *what) {
+  set_error(what);
+  return FEM_EINVAL;
+}
+
+static void free_table(DevTable &d) {
+  if (d.qp) cudaFree(d.qp);
+  if (d.phi64) cudaFree(d.phi64);
+  if (d.phi32) cudaFree(d.phi32);
+  d = DevTable();
+}
+
+template <class T>
+static int upload(T **dst, const T *src, size_t n) {
+  cudaError_t e = cudaMalloc((void **)dst, n * sizeof(T));
+  if (e != cudaSuccess) {
+    *dst = nullptr;
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return FEM_ENOMEM;
+  }
+  e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail("cudaMemcpy", e);
+  return FEM_OK;
+}
+
+}  // namespace fem
+
+using namespace fem;
+
+extern "C" {
+
+const char *fem_status_str(int s) {
+  switch (s) {
+    case FEM_OK: return "ok";
+    case FEM_EINVAL: return "invalid argument";
+    case FEM_ENOMEM: return "out of memory";
+    case FEM_ECUDA: return "CUDA error";
+    case FEM_EUNSUPPORTED: return "unsupported combination";
+    case FEM_EELEMENT: return "element flagged";
+    case FEM_ETIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char *fem_last_error(void) { return g_last_error.c_str(); }
+
+int64_t fem_matrix_size(int elem, int p, int layout) {
+  if (elem == FEM_TET4 ? p != 1 : (elem != FEM_PRISM6 || p < 1 || p > kMaxP)) return -1;
+  const int64_t ns = ns_of(elem, p);
+  if (layout == FEM_OUT_FULL) return ns * ns;
+  if (layout == FEM_OUT_SYMPACKED) return ns * (ns + 1) / 2;
+  return -1;
+}
+
+int fem_reference_rule(int elem, int p, int *nq, int *ns, double *xi, double *w, double *phi) {
+  HostRule r;
+  if (!build_host_rule(elem, p, &r)) return invalid("fem_reference_rule: unknown element or degree");
+  if (nq) *nq = r.nq;
+  if (ns) *ns = r.ns;
+  if (xi) std::memcpy(xi, r.xi.data(), r.xi.size() * sizeof(double));
+  if (w) std::memcpy(w, r.w.data(), r.w.size() * sizeof(double));
+  if (phi) std::memcpy(phi, r.phi.data(), r.phi.size() * sizeof(double));
+  return FEM_OK;
+}
+
+int fem_tables_build(int elem, int p_min, int p_max, fem_tables *out) {
+  if (!out) return invalid("fem_tables_build: out is NULL");
+  *out = nullptr;
+  if (elem == FEM_TET4) {
+    if (p_min != 1 || p_max != 1) return invalid("fem_tables_build: tetrahedra have p = 1 only");
+  } else if (elem != FEM_PRISM6 || p_min < 1 || p_max > kMaxP || p_min > p_max) {
+    return invalid("fem_tables_build: bad element type or degree range");
+  }
+  fem_tables t = new (std::nothrow) fem_tables_s();
+  if (!t) return FEM_ENOMEM;
+  t->elem = elem;
+  t->p_min = p_min;
+  t->p_max = p_max;
+  cudaGetDevice(&t->device);
+  int rc = FEM_OK;
+  for (int p = p_min; p <= p_max && rc == FEM_OK; p++) {
+    HostRule r;
+    build_host_rule(elem, p, &r);
+    DevTable &d = t->tab[p];
+    d.p = p;
+    d.ns = r.ns;
+    d.nq = r.nq;
+    std::vector<double> qp(4 * (size_t)r.nq);
+    for (int q = 0; q < r.nq; q++) {
+      qp[4 * q + 0] = r.xi[3 * q + 0];
+      qp[4 * q + 1] = r.xi[3 * q + 1];
+      qp[4 * q + 2] = r.xi[3 * q + 2];
+      qp[4 * q + 3] = r.w[q];
+    }
+    std::vector<float> phi32(r.phi.size());
+    for (size_t i = 0; i < r.phi.size(); i++) phi32[i] = (float)r.phi[i];
+    rc = upload(&d.qp, qp.data(), qp.size());
+    if (rc == FEM_OK) rc = upload(&d.phi64, r.phi.data(), r.phi.size());
+    if (rc == FEM_OK) rc = upload(&d.phi32, phi32.data(), phi32.size());
+  }
+  if (rc != FEM_OK) {
+    for (int p = 0; p <= kMaxP; p++) free_table(t->tab[p]);
+    delete t;
+    return rc;
+  }
+  *out = t;
+  return FEM_OK;
+}
+
+int fem_tables_destroy(fem_tables t) {
+  if (!t) return FEM_OK;
+  for (int p = 0; p <= kMaxP; p++) free_table(t->tab[p]);
+  delete t;
+  return FEM_OK;
+}
+
+int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
+                  int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out,
+                  int32_t *status, void *stream) {
+  if (!t) return invalid("fem_integrate: tables handle is NULL");
+  if (p < t->p_min || p > t->p_max) return invalid("fem_integrate: degree not in the tables");
+  if (n_elem < 0) return invalid("fem_integrate: n_elem < 0");
+  if (prec < FEM_F64 || prec > FEM_F16X3) return invalid("fem_integrate: unknown precision");
+  if (layout != FEM_OUT_FULL && layout != FEM_OUT_SYMPACKED) return invalid("fem_integrate: unknown layout");
+  if (n_elem == 0) return FEM_OK;
+  if (!coords || !coeffs || !A_out) return invalid("fem_integrate: NULL coords, coeffs or A_out");
+  if (coeff_stride < n_elem) return invalid("fem_integrate: coeff_stride < n_elem");
+  if (((uintptr_t)coords | (uintptr_t)coeffs) & 7) return invalid("fem_integrate: coords/coeffs not 8-byte aligned");
+  if ((uintptr_t)A_out & 15) return invalid("fem_integrate: A_out not 16-byte aligned");
+  const size_t osz = prec == FEM_F64 ? 8 : 4;
+  if (b_out && ((uintptr_t)b_out & (osz - 1))) return invalid("fem_integrate: b_out misaligned");
+  if (status && ((uintptr_t)status & 3)) return invalid("fem_integrate: status misaligned");
+  const DevTable &d = t->tab[p];
+  FmaArgs a;
+  a.n = n_elem;
+  a.coords = coords;
+  a.coeffs = coeffs;
+  a.cstride = coeff_stride;
+  a.qp = d.qp;
+  a.A = A_out;
+  a.b = b_out;
+  a.status = status;
+  a.layout = layout;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return invalid("fem_integrate: tables live on another device");
+  switch (prec) {
+    case FEM_F64:
+      a.phi = d.phi64;
+      return launch_fma_f64(t->elem, p, a, stream);
+    case FEM_F32:
+      a.phi = d.phi32;
+      return launch_fma_f32(t->elem, p, a, stream);
+    default:
+      set_error("fem_integrate: tensor-core precisions are not available for this element/degree");
+      return FEM_EUNSUPPORTED;
+  }
+}
+
+}  // extern "C"

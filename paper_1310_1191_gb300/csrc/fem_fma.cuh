@@ -1,0 +1,257 @@
+// CUDA-core contraction kernels (FP64 and FP32 FMA) for the element matrices.
+//
+// Per element the weak form reduces to (Algorithm 2 with the sparse c):
+//     A[i][j] = sum_Q sum_{d,d'} phi[Q][d][i] G_Q[d][d'] phi[Q][d'][j]
+//             = sum_k Phi[k][i] T[k][j],   k = 4 Q + d,  K = 4 NQ,
+// with the weighted tile T[4Q+d][j] = sum_{d'} G_Q[d][d'] phi[Q][d'][j]
+// (13 FMAs per (Q, j) thanks to the zero block G[1..3][0] and the symmetric
+// diffusion block).  Phi (the reference table, the same for every element) is
+// the left operand, so one CTA can share it between several elements.
+//
+// Work decomposition (the paper's two-level parallelism, Section 4): a CTA
+// owns a group of EPB elements and one BM x BM output tile of each (the
+// "part" of A^e of Algorithms 3/4 when NS > BM); every thread owns a TM x TN
+// register micro-tile of one element ("owner computes").  Per CTA:
+//   0. stage coordinates and coefficients of its elements in shared memory;
+//   1. geometry of every (element, point) in FP64 -> G records in shared memory;
+//   2. per chunk of QC points: stage the Phi rows of the tile and build the
+//      weighted T columns of the tile for each element, then accumulate the
+//      outer products in registers;
+//   3. the column-0 tiles also form the load vector b = sum_Q S_Q phi[Q][0];
+//   4. write the unpadded micro-tiles (full or upper-packed rows).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fem_geometry.cuh"
+
+namespace fem {
+
+template <int ELEM_, int P_, int BM_, int TM_, int TN_, int EPB_, int QC_>
+struct FmaCfg {
+  static constexpr int ELEM = ELEM_, P = P_;
+  static constexpr int NS = ns_of(ELEM_, P_), NQ = nq_of(ELEM_, P_), NV = nv_of(ELEM_);
+  static constexpr int BM = BM_, BN = BM_, TM = TM_, TN = TN_;
+  static constexpr int TY = BM / TM, TX = BN / TN, TPE = TX * TY;
+  static constexpr int EPB = EPB_, NT = EPB * TPE;
+  static constexpr int TILES = (NS + BM - 1) / BM;
+  static constexpr int QC = QC_, KC = 4 * QC, NCH = (NQ + QC - 1) / QC;
+  static constexpr int NREC = NV * 3 + 11;  // coords + coefficients per element
+  static_assert(BM % TM == 0 && BN % TN == 0, "tile must split into micro-tiles");
+  static_assert(NT <= 1024, "too many threads");
+
+  template <class T>
+  static constexpr size_t smem_bytes() {
+    return sizeof(T) * ((size_t)KC * BM + (size_t)EPB * KC * BN + (size_t)EPB * NQ * kGStride) +
+           sizeof(double) * (size_t)EPB * NREC + sizeof(int) * (size_t)EPB + 64;
+  }
+};
+
+template <class T, class C>
+__global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *sPA = reinterpret_cast<T *>(smem);                 // [KC][BM]
+  T *sT = sPA + C::KC * C::BM;                          // [EPB][KC][BN]
+  T *sG = sT + C::EPB * C::KC * C::BN;                  // [EPB][NQ][kGStride]
+  double *sX = reinterpret_cast<double *>(sG + C::EPB * C::NQ * kGStride);  // [EPB][NREC]
+  int *sSt = reinterpret_cast<int *>(sX + C::EPB * C::NREC);               // [EPB]
+
+  const T *phi = static_cast<const T *>(a.phi);
+  const int tid = threadIdx.x;
+  long long blk = blockIdx.x;
+  const int tj = (int)(blk % C::TILES);
+  blk /= C::TILES;
+  const int ti = (int)(blk % C::TILES);
+  blk /= C::TILES;
+  const int64_t e0 = blk * (int64_t)C::EPB;
+
+  // 0. element records
+  for (int idx = tid; idx < C::EPB * C::NREC; idx += C::NT) {
+    const int le = idx / C::NREC, k = idx % C::NREC;
+    const int64_t e = e0 + le;
+    double v = 0.0;
+    if (e < a.n) v = k < C::NV * 3 ? a.coords[e * (C::NV * 3) + k] : a.coeffs[(k - C::NV * 3) * a.cstride + e];
+    sX[idx] = v;
+  }
+  if (tid < C::EPB) sSt[tid] = 0;
+  __syncthreads();
+  for (int idx = tid; idx < C::EPB * C::NREC; idx += C::NT)
+    if (!isfinite(sX[idx])) atomicOr(&sSt[idx / C::NREC], FEM_ST_NONFINITE);
+  if (a.layout == FEM_OUT_SYMPACKED && tid < C::EPB) {
+    const double *cf = sX + tid * C::NREC + C::NV * 3;
+    if (cf[6] != 0.0 || cf[7] != 0.0 || cf[8] != 0.0) atomicOr(&sSt[tid], FEM_ST_NONSYM);
+  }
+
+  // 1. geometry (FP64) -> point records
+  for (int idx = tid; idx < C::EPB * C::NQ; idx += C::NT) {
+    const int le = idx / C::NQ, q = idx % C::NQ;
+    double g[11];
+    const double *rec = sX + le * C::NREC;
+    int st = point_matrix<C::ELEM>(rec, rec + C::NV * 3, a.qp + 4 * q, g);
+    T *dst = sG + (size_t)idx * kGStride;
+    if (e0 + le < a.n) {
+#pragma unroll
+      for (int k = 0; k < 11; k++) dst[k] = (T)g[k];
+      if (st) atomicOr(&sSt[le], st);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 11; k++) dst[k] = (T)0;
+    }
+  }
+  __syncthreads();
+
+  // 2. contraction over chunks of points
+  const int le = tid / C::TPE, r = tid % C::TPE, tx = r % C::TX, ty = r / C::TX;
+  T acc[C::TM][C::TN];
+#pragma unroll
+  for (int i = 0; i < C::TM; i++)
+#pragma unroll
+    for (int j = 0; j < C::TN; j++) acc[i][j] = (T)0;
+
+  for (int ch = 0; ch < C::NCH; ch++) {
+    const int q0 = ch * C::QC;
+    for (int idx = tid; idx < C::KC * C::BM; idx += C::NT) {
+      const int k = idx / C::BM, i = idx % C::BM;
+      const int row = ti * C::BM + i, kg = 4 * q0 + k;
+      sPA[idx] = (row < C::NS && kg < 4 * C::NQ) ? phi[(size_t)kg * C::NS + row] : (T)0;
+    }
+    for (int idx = tid; idx < C::EPB * C::QC * C::BN; idx += C::NT) {
+      const int l2 = idx / (C::QC * C::BN), rem = idx % (C::QC * C::BN);
+      const int qq = rem / C::BN, j = rem % C::BN;
+      const int q = q0 + qq, col = tj * C::BN + j;
+      T t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+      if (q < C::NQ && col < C::NS) {
+        const T *ph = phi + (size_t)(4 * q) * C::NS + col;
+        const T f0 = ph[0], f1 = ph[C::NS], f2 = ph[2 * C::NS], f3 = ph[3 * C::NS];
+        const T *g = sG + ((size_t)l2 * C::NQ + q) * kGStride;
+        t0 = g[G00] * f0 + g[G01] * f1 + g[G02] * f2 + g[G03] * f3;
+        t1 = g[G11] * f1 + g[G12] * f2 + g[G13] * f3;
+        t2 = g[G12] * f1 + g[G22] * f2 + g[G23] * f3;
+        t3 = g[G13] * f1 + g[G23] * f2 + g[G33] * f3;
+      }
+      T *tt = sT + ((size_t)l2 * C::KC + 4 * qq) * C::BN + j;
+      tt[0] = t0;
+      tt[C::BN] = t1;
+      tt[2 * C::BN] = t2;
+      tt[3 * C::BN] = t3;
+    }
+    __syncthreads();
+    const T *pa = sPA + ty * C::TM;
+    const T *pb = sT + (size_t)le * C::KC * C::BN + tx * C::TN;
+#pragma unroll 4
+    for (int k = 0; k < C::KC; k++) {
+      T av[C::TM], bv[C::TN];
+#pragma unroll
+      for (int i = 0; i < C::TM; i++) av[i] = pa[k * C::BM + i];
+#pragma unroll
+      for (int j = 0; j < C::TN; j++) bv[j] = pb[k * C::BN + j];
+#pragma unroll
+      for (int i = 0; i < C::TM; i++)
+#pragma unroll
+        for (int j = 0; j < C::TN; j++) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+  // 3. load vector rows of this tile
+  if (tj == 0 && a.b != nullptr) {
+    T *bo = static_cast<T *>(a.b);
+    for (int idx = tid; idx < C::EPB * C::BM; idx += C::NT) {
+      const int l2 = idx / C::BM, i = idx % C::BM, row = ti * C::BM + i;
+      const int64_t e = e0 + l2;
+      if (row < C::NS && e < a.n) {
+        T s = 0;
+        const T *g = sG + (size_t)l2 * C::NQ * kGStride + GS;
+        for (int q = 0; q < C::NQ; q++) s = fma(g[q * kGStride], phi[(size_t)(4 * q) * C::NS + row], s);
+        bo[e * C::NS + row] = s;
+      }
+    }
+  }
+
+  // 4. write the micro-tile
+  const int64_t e = e0 + le;
+  if (e < a.n) {
+    T *Ao = static_cast<T *>(a.A);
+    if (a.layout == FEM_OUT_FULL) {
+      T *Ae = Ao + e * (int64_t)(C::NS * C::NS);
+#pragma unroll
+      for (int i = 0; i < C::TM; i++) {
+        const int row = ti * C::BM + ty * C::TM + i;
+        if (row >= C::NS) continue;
+#pragma unroll
+        for (int j = 0; j < C::TN; j++) {
+          const int col = tj * C::BN + tx * C::TN + j;
+          if (col < C::NS) Ae[row * C::NS + col] = acc[i][j];
+        }
+      }
+    } else {
+      constexpr int NP = C::NS * (C::NS + 1) / 2;
+      T *Ae = Ao + e * (int64_t)NP;
+#pragma unroll
+      for (int i = 0; i < C::TM; i++) {
+        const int row = ti * C::BM + ty * C::TM + i;
+        if (row >= C::NS) continue;
+        const int base = row * C::NS - row * (row - 1) / 2 - row;
+#pragma unroll
+        for (int j = 0; j < C::TN; j++) {
+          const int col = tj * C::BN + tx * C::TN + j;
+          if (col < C::NS && col >= row) Ae[base + col] = acc[i][j];
+        }
+      }
+    }
+  }
+  if (a.status != nullptr && ti == 0 && tj == 0 && tid < C::EPB && e0 + tid < a.n)
+    a.status[e0 + tid] = sSt[tid];
+}
+
+template <class T, class C>
+int launch_fma_cfg(const FmaArgs &a, void *stream) {
+  if (a.n == 0) return FEM_OK;
+  const size_t smem = C::template smem_bytes<T>();
+  cudaError_t err = cudaFuncSetAttribute(fma_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) {
+    set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(err));
+    return FEM_ECUDA;
+  }
+  const int64_t groups = (a.n + C::EPB - 1) / C::EPB;
+  const int64_t grid = groups * C::TILES * C::TILES;
+  if (grid > 0x7fffffffLL) {
+    set_error("too many elements for one launch");
+    return FEM_EINVAL;
+  }
+  fma_kernel<T, C><<<(unsigned)grid, C::NT, smem, (cudaStream_t)stream>>>(a);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) {
+    set_error(std::string("fma_kernel launch: ") + cudaGetErrorString(err));
+    return FEM_ECUDA;
+  }
+  return FEM_OK;
+}
+
+// Tile shapes per degree (ELEM, P, BM, TM, TN, EPB, QC).
+template <int ELEM, int P> struct FmaShape;
+template <> struct FmaShape<FEM_TET4, 1> { using type = FmaCfg<FEM_TET4, 1, 4, 1, 4, 64, 4>; };
+template <> struct FmaShape<FEM_PRISM6, 1> { using type = FmaCfg<FEM_PRISM6, 1, 6, 1, 6, 42, 4>; };
+template <> struct FmaShape<FEM_PRISM6, 2> { using type = FmaCfg<FEM_PRISM6, 2, 18, 3, 6, 14, 3>; };
+template <> struct FmaShape<FEM_PRISM6, 3> { using type = FmaCfg<FEM_PRISM6, 3, 40, 4, 4, 2, 8>; };
+template <> struct FmaShape<FEM_PRISM6, 4> { using type = FmaCfg<FEM_PRISM6, 4, 75, 5, 5, 1, 5>; };
+template <> struct FmaShape<FEM_PRISM6, 5> { using type = FmaCfg<FEM_PRISM6, 5, 126, 6, 6, 1, 6>; };
+template <> struct FmaShape<FEM_PRISM6, 6> { using type = FmaCfg<FEM_PRISM6, 6, 98, 7, 7, 1, 7>; };
+template <> struct FmaShape<FEM_PRISM6, 7> { using type = FmaCfg<FEM_PRISM6, 7, 96, 6, 6, 1, 8>; };
+
+template <class T>
+int launch_fma_any(int elem, int p, const FmaArgs &a, void *stream) {
+  if (elem == FEM_TET4) return launch_fma_cfg<T, FmaShape<FEM_TET4, 1>::type>(a, stream);
+  switch (p) {
+    case 1: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 1>::type>(a, stream);
+    case 2: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 2>::type>(a, stream);
+    case 3: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 3>::type>(a, stream);
+    case 4: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 4>::type>(a, stream);
+    case 5: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 5>::type>(a, stream);
+    case 6: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 6>::type>(a, stream);
+    case 7: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 7>::type>(a, stream);
+  }
+  return FEM_EINVAL;
+}
+
+}  // namespace fem

@@ -1,0 +1,86 @@
+// Geometry stage (always FP64): Jacobian of the reference->real map at one
+// quadrature point, its determinant and adjugate, folded with the element's
+// coefficients into the 4x4 point matrix G_Q of the weak form.
+//
+// Section 2 / eq. sum_int: physical derivatives are psi = J^{-T} grad_ref phi,
+// so with c[iD][jD] as in fem.h the contribution of one point is
+//     sum_{d,d'} phi[d][i] G[d][d'] phi[d'][j]   (d = 0 value, 1..3 ref. derivs)
+// with
+//     G[1+k][1+l] = w det  (J^{-1} D J^{-T})[k][l] = (w / det) (adj D adj^T)[k][l]
+//     G[0][1+l]   = w det  (J^{-1} b)[l]           = w (adj b)[l]
+//     G[0][0]     = w det c,      G[1+k][0] = 0,
+// and the load vector weight S = w det f.  Using the adjugate leaves a single
+// division per point.
+#pragma once
+
+#include "fem_internal.h"
+
+namespace fem {
+
+// Slots of the packed point record (11 used, padded to 12).
+enum GSlot { G00 = 0, G01, G02, G03, G11, G12, G13, G22, G23, G33, GS, GPAD };
+constexpr int kGStride = 12;
+
+// X: vertex coordinates [nv][3]; cf: 11 coefficients (COEF order);
+// q4: xi, eta, zeta, w.  Writes 11 values to g; returns FEM_ST_DET if det <= 0.
+template <int ELEM>
+__device__ __forceinline__ int point_matrix(const double *X, const double *cf, const double *q4,
+                                            double *g) {
+  double J[3][3];
+  if (ELEM == FEM_PRISM6) {
+    // x(xi,eta,zeta) = sum_a lam_a(xi,eta) [ (1-zeta)/2 x_a + (1+zeta)/2 x_{a+3} ]
+    const double xi = q4[0], eta = q4[1], ze = q4[2];
+    const double lo = 0.5 * (1.0 - ze), hi = 0.5 * (1.0 + ze), l0 = 1.0 - xi - eta;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      const double b0 = X[0 + i], b1 = X[3 + i], b2 = X[6 + i];
+      const double t0 = X[9 + i], t1 = X[12 + i], t2 = X[15 + i];
+      J[i][0] = lo * (b1 - b0) + hi * (t1 - t0);
+      J[i][1] = lo * (b2 - b0) + hi * (t2 - t0);
+      J[i][2] = 0.5 * (l0 * (t0 - b0) + xi * (t1 - b1) + eta * (t2 - b2));
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      J[i][0] = X[3 + i] - X[i];
+      J[i][1] = X[6 + i] - X[i];
+      J[i][2] = X[9 + i] - X[i];
+    }
+  }
+  double adj[3][3];
+  adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  adj[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  adj[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  adj[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  const double det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+  const double w = q4[3];
+  const double D[3][3] = {{cf[0], cf[3], cf[4]}, {cf[3], cf[1], cf[5]}, {cf[4], cf[5], cf[2]}};
+  double M[3][3];  // adj D
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int n = 0; n < 3; n++) M[k][n] = adj[k][0] * D[0][n] + adj[k][1] * D[1][n] + adj[k][2] * D[2][n];
+  const double s = w / det;
+  auto Gd = [&](int k, int l) {
+    return s * (M[k][0] * adj[l][0] + M[k][1] * adj[l][1] + M[k][2] * adj[l][2]);
+  };
+  g[G11] = Gd(0, 0);
+  g[G12] = Gd(0, 1);
+  g[G13] = Gd(0, 2);
+  g[G22] = Gd(1, 1);
+  g[G23] = Gd(1, 2);
+  g[G33] = Gd(2, 2);
+#pragma unroll
+  for (int l = 0; l < 3; l++) g[G01 + l] = w * (adj[l][0] * cf[6] + adj[l][1] * cf[7] + adj[l][2] * cf[8]);
+  const double wd = w * det;
+  g[G00] = wd * cf[9];
+  g[GS] = wd * cf[10];
+  return det > 0.0 ? 0 : FEM_ST_DET;
+}
+
+}  // namespace fem

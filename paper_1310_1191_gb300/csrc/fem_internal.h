@@ -1,0 +1,72 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fem.h"
+
+namespace fem {
+
+constexpr int kMaxP = 7;
+
+__host__ __device__ constexpr int ns_of(int elem, int p) {
+  return elem == FEM_TET4 ? 4 : (p + 1) * (p + 1) * (p + 2) / 2;
+}
+__host__ __device__ constexpr int nq_of(int elem, int p) {
+  return elem == FEM_TET4 ? 4 : (p + 1) * (p + 1) * (p + 1);
+}
+__host__ __device__ constexpr int nv_of(int elem) { return elem == FEM_TET4 ? 4 : 6; }
+
+// Reference data of one (element, degree), built on the host in FP64.
+struct HostRule {
+  int nq = 0, ns = 0;
+  std::vector<double> xi;   // [nq][3]
+  std::vector<double> w;    // [nq]
+  std::vector<double> phi;  // [nq][4][ns]
+};
+
+// Builds the quadrature rule and shape-function table; false if (elem,p) invalid.
+bool build_host_rule(int elem, int p, HostRule *out);
+
+// Device copies of one degree's tables.
+struct DevTable {
+  int p = 0, ns = 0, nq = 0;
+  double *qp = nullptr;     // [nq][4]: xi, eta, zeta, w (FP64)
+  double *phi64 = nullptr;  // [4 nq][ns] row k = 4 q + d (FP64)
+  float *phi32 = nullptr;   // same, FP32
+};
+
+}  // namespace fem
+
+struct fem_tables_s {
+  int elem = 0, p_min = 0, p_max = 0, device = 0;
+  fem::DevTable tab[fem::kMaxP + 1];
+};
+
+namespace fem {
+
+// thread-local last-error text
+void set_error(const std::string &msg);
+
+// Kernel launch arguments of the FMA path.
+struct FmaArgs {
+  int64_t n;
+  const double *coords;
+  const double *coeffs;
+  int64_t cstride;
+  const double *qp;
+  const void *phi;  // FP64 or FP32 table by precision
+  void *A;
+  void *b;
+  int32_t *status;
+  int layout;
+};
+
+// Launch the FP64 / FP32 FMA kernels for (elem, p); returns a fem status code.
+int launch_fma_f64(int elem, int p, const FmaArgs &a, void *stream);
+int launch_fma_f32(int elem, int p, const FmaArgs &a, void *stream);
+
+}  // namespace fem

@@ -219,7 +219,7 @@ def coefficients(E: int, seed: int = SEED_COEF, kind: str = "random",
     R[:, 2, 1] = 2 * (qy * qz + qx * qw)
     R[:, 2, 2] = 1 - 2 * (qx * qx + qy * qy)
     L = np.stack(lam, axis=1)
-    D = np.einsum("eik,ek,ejk->eij", R, L, R)
+    D = np.matmul(R * L[:, None, :], R.transpose(0, 2, 1))
     out[0], out[1], out[2] = D[:, 0, 0], D[:, 1, 1], D[:, 2, 2]
     out[3], out[4], out[5] = D[:, 0, 1], D[:, 0, 2], D[:, 1, 2]
     if kind == "random":
