@@ -64,6 +64,7 @@ extern "C" {
 #define FEM_ST_NONFINITE 2  /* non-finite coordinate or coefficient */
 #define FEM_ST_NONSYM 4     /* symmetric-packed output requested but b != 0 */
 #define FEM_ST_FALLBACK 8   /* surrogate input left its box: exact law used (info) */
+#define FEM_ST_TIMEOUT 16   /* a bounded device wait expired: this element's output is invalid */
 
 typedef struct fem_tables_s *fem_tables;
 
@@ -111,6 +112,12 @@ int fem_tables_destroy(fem_tables t);
 int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
                   int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out,
                   int32_t *status, void *stream);
+
+/* Device error word of the tables' kernels: FEM_ETIMEOUT if a bounded wait
+ * inside a tensor-core launch expired since the last clear (the affected
+ * elements also carry FEM_ST_TIMEOUT), else FEM_OK.  Synchronises the device.
+ *   clear : non-zero resets the word. */
+int fem_error_flag(fem_tables t, int clear);
 
 /* Number of output values per element for (elem, p, layout): NS*NS or NS(NS+1)/2;
  * -1 if invalid.  */

@@ -20,12 +20,12 @@ FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_ECUDA, FEM_EUNSUPPORTED, FEM_EELEMENT, FEM_E
 FEM_TET4, FEM_PRISM6 = 0, 1
 FEM_F64, FEM_F32, FEM_BF16X3, FEM_F16X3 = 0, 1, 2, 3
 FEM_OUT_FULL, FEM_OUT_SYMPACKED = 0, 1
-FEM_ST_DET, FEM_ST_NONFINITE, FEM_ST_NONSYM, FEM_ST_FALLBACK = 1, 2, 4, 8
+FEM_ST_DET, FEM_ST_NONFINITE, FEM_ST_NONSYM, FEM_ST_FALLBACK, FEM_ST_TIMEOUT = 1, 2, 4, 8, 16
 
 # every symbol include/fem.h declares (checked by the CPU tests)
 EXPORTS = (
     "fem_reference_rule", "fem_tables_build", "fem_tables_destroy", "fem_integrate",
-    "fem_matrix_size", "fem_status_str", "fem_last_error",
+    "fem_matrix_size", "fem_status_str", "fem_last_error", "fem_error_flag",
 )
 
 _lib = None
@@ -57,6 +57,7 @@ def load():
     lib.fem_status_str.restype = ctypes.c_char_p
     lib.fem_last_error.argtypes = []
     lib.fem_last_error.restype = ctypes.c_char_p
+    lib.fem_error_flag.argtypes = [P, i]
     _lib = lib
     return lib
 
@@ -153,3 +154,8 @@ def fem_integrate(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_stride: 
     return _check("fem_integrate", load().fem_integrate(
         t.handle, p, n_elem, _addr(coords), _addr(coeffs), coeff_stride, prec, layout,
         _addr(A_out), _addr(b_out), _addr(status), _stream(stream)))
+
+
+def fem_error_flag(t: Tables, clear: bool = True) -> int:
+    """FEM_ETIMEOUT if a bounded device wait expired since the last clear (synchronises)."""
+    return load().fem_error_flag(t.handle, 1 if clear else 0)

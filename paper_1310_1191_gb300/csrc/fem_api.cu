@@ -7,6 +7,7 @@
 // "second alternative" of Section 4.2).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -34,7 +35,15 @@ static void free_table(DevTable &d) {
   if (d.qp) cudaFree(d.qp);
   if (d.phi64) cudaFree(d.phi64);
   if (d.phi32) cudaFree(d.phi32);
+  if (d.img_bf16) cudaFree(d.img_bf16);
+  if (d.img_f16) cudaFree(d.img_f16);
   d = DevTable();
+}
+
+static void free_tables(fem_tables t) {
+  for (int p = 0; p <= kMaxP; p++) free_table(t->tab[p]);
+  if (t->d_err) cudaFree(t->d_err);
+  t->d_err = nullptr;
 }
 
 template <class T>
@@ -124,9 +133,29 @@ int fem_tables_build(int elem, int p_min, int p_max, fem_tables *out) {
     rc = upload(&d.qp, qp.data(), qp.size());
     if (rc == FEM_OK) rc = upload(&d.phi64, r.phi.data(), r.phi.size());
     if (rc == FEM_OK) rc = upload(&d.phi32, phi32.data(), phi32.size());
+    if (rc == FEM_OK && elem == FEM_PRISM6) {
+      double mx = 0.0;
+      for (double v : r.phi) mx = std::fmax(mx, std::fabs(v));
+      int ex = 0;
+      std::frexp(mx, &ex);  // mx < 2^ex
+      d.phimax = (float)mx;
+      d.aphi_f16 = 14 - ex;  // scaled magnitudes below 2^14
+      std::vector<uint16_t> img;
+      build_tc_image(p, r.phi, false, 0, img);
+      rc = upload(&d.img_bf16, img.data(), img.size());
+      if (rc == FEM_OK) {
+        build_tc_image(p, r.phi, true, d.aphi_f16, img);
+        rc = upload(&d.img_f16, img.data(), img.size());
+      }
+    }
+  }
+  if (rc == FEM_OK) {
+    cudaError_t e = cudaMalloc((void **)&t->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(t->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) rc = cuda_fail("cudaMalloc(error word)", e);
   }
   if (rc != FEM_OK) {
-    for (int p = 0; p <= kMaxP; p++) free_table(t->tab[p]);
+    free_tables(t);
     delete t;
     return rc;
   }
@@ -136,9 +165,19 @@ int fem_tables_build(int elem, int p_min, int p_max, fem_tables *out) {
 
 int fem_tables_destroy(fem_tables t) {
   if (!t) return FEM_OK;
-  for (int p = 0; p <= kMaxP; p++) free_table(t->tab[p]);
+  free_tables(t);
   delete t;
   return FEM_OK;
+}
+
+int fem_error_flag(fem_tables t, int clear) {
+  if (!t || !t->d_err) return invalid("fem_error_flag: tables handle is NULL");
+  int h = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, t->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && clear) e = cudaMemset(t->d_err, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail("fem_error_flag", e);
+  return h ? FEM_ETIMEOUT : FEM_OK;
 }
 
 int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
@@ -178,9 +217,23 @@ int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, con
     case FEM_F32:
       a.phi = d.phi32;
       return launch_fma_f32(t->elem, p, a, stream);
-    default:
-      set_error("fem_integrate: tensor-core precisions are not available for this element/degree");
-      return FEM_EUNSUPPORTED;
+    default: {
+      if (t->elem != FEM_PRISM6) {
+        set_error("fem_integrate: tensor-core precisions are provided for prisms only");
+        return FEM_EUNSUPPORTED;
+      }
+      TcLaunch l;
+      l.n = n_elem;
+      l.coords = coords;
+      l.coeffs = coeffs;
+      l.cstride = coeff_stride;
+      l.A = A_out;
+      l.b = b_out;
+      l.status = status;
+      l.layout = layout;
+      l.err = t->d_err;
+      return launch_tc(p, prec == FEM_F16X3, d, l, stream);
+    }
   }
 }
 

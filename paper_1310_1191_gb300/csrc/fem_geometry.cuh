@@ -84,3 +84,75 @@ __device__ __forceinline__ int point_matrix(const double *X, const double *cf, c
 }
 
 }  // namespace fem
+
+namespace fem {
+
+// Same point record with J, adj J and det J in FP64 and the 3x3 products that
+// form G in FP32 (for the reduced-precision contractions, whose G is rounded
+// to FP32 anyway).  Returns FEM_ST_DET if det <= 0.
+template <int ELEM>
+__device__ __forceinline__ int point_matrix_f32(const double *X, const double *cf, const double *q4,
+                                                float *g) {
+  double J[3][3];
+  if (ELEM == FEM_PRISM6) {
+    const double xi = q4[0], eta = q4[1], ze = q4[2];
+    const double lo = 0.5 * (1.0 - ze), hi = 0.5 * (1.0 + ze), l0 = 1.0 - xi - eta;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      const double b0 = X[0 + i], b1 = X[3 + i], b2 = X[6 + i];
+      const double t0 = X[9 + i], t1 = X[12 + i], t2 = X[15 + i];
+      J[i][0] = lo * (b1 - b0) + hi * (t1 - t0);
+      J[i][1] = lo * (b2 - b0) + hi * (t2 - t0);
+      J[i][2] = 0.5 * (l0 * (t0 - b0) + xi * (t1 - b1) + eta * (t2 - b2));
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      J[i][0] = X[3 + i] - X[i];
+      J[i][1] = X[6 + i] - X[i];
+      J[i][2] = X[9 + i] - X[i];
+    }
+  }
+  double adj[3][3];
+  adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  adj[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  adj[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  adj[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  const double det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+  float a[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int m = 0; m < 3; m++) a[k][m] = (float)adj[k][m];
+  const float w = (float)q4[3];
+  const float D[3][3] = {{(float)cf[0], (float)cf[3], (float)cf[4]},
+                         {(float)cf[3], (float)cf[1], (float)cf[5]},
+                         {(float)cf[4], (float)cf[5], (float)cf[2]}};
+  float M[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int n = 0; n < 3; n++) M[k][n] = a[k][0] * D[0][n] + a[k][1] * D[1][n] + a[k][2] * D[2][n];
+  const float s = w / (float)det;
+  auto Gd = [&](int k, int l) { return s * (M[k][0] * a[l][0] + M[k][1] * a[l][1] + M[k][2] * a[l][2]); };
+  g[G11] = Gd(0, 0);
+  g[G12] = Gd(0, 1);
+  g[G13] = Gd(0, 2);
+  g[G22] = Gd(1, 1);
+  g[G23] = Gd(1, 2);
+  g[G33] = Gd(2, 2);
+  const float b0 = (float)cf[6], b1 = (float)cf[7], b2 = (float)cf[8];
+#pragma unroll
+  for (int l = 0; l < 3; l++) g[G01 + l] = w * (a[l][0] * b0 + a[l][1] * b1 + a[l][2] * b2);
+  const float wd = (float)(q4[3] * det);
+  g[G00] = wd * (float)cf[9];
+  g[GS] = wd * (float)cf[10];
+  return det > 0.0 ? 0 : FEM_ST_DET;
+}
+
+}  // namespace fem

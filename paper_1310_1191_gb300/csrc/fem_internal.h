@@ -37,12 +37,18 @@ struct DevTable {
   double *qp = nullptr;     // [nq][4]: xi, eta, zeta, w (FP64)
   double *phi64 = nullptr;  // [4 nq][ns] row k = 4 q + d (FP64)
   float *phi32 = nullptr;   // same, FP32
+  // tensor-core operand images of Phi^T (hi | lo per K chunk), prisms only
+  uint16_t *img_bf16 = nullptr;
+  uint16_t *img_f16 = nullptr;
+  float phimax = 0.f;  // max |Phi|
+  int aphi_f16 = 0;    // power-of-two scale applied to the FP16 image
 };
 
 }  // namespace fem
 
 struct fem_tables_s {
   int elem = 0, p_min = 0, p_max = 0, device = 0;
+  int *d_err = nullptr;  // device error word (bounded waits that expired)
   fem::DevTable tab[fem::kMaxP + 1];
 };
 
@@ -68,5 +74,20 @@ struct FmaArgs {
 // Launch the FP64 / FP32 FMA kernels for (elem, p); returns a fem status code.
 int launch_fma_f64(int elem, int p, const FmaArgs &a, void *stream);
 int launch_fma_f32(int elem, int p, const FmaArgs &a, void *stream);
+
+// Tensor-core path (prisms).
+struct TcLaunch {
+  int64_t n;
+  const double *coords;
+  const double *coeffs;
+  int64_t cstride;
+  void *A;
+  void *b;
+  int32_t *status;
+  int layout;
+  int *err;
+};
+int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *stream);
+void build_tc_image(int p, const std::vector<double> &phi, bool f16, int aphi, std::vector<uint16_t> &out);
 
 }  // namespace fem

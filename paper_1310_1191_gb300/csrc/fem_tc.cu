@@ -1,0 +1,545 @@
+// Tensor-core contraction of the element matrices on sm_103a (tcgen05, TMEM,
+// bulk TMA copies, mbarrier pipeline), BF16 or FP16 operands split hi + lo,
+// FP32 accumulation.
+//
+// Per element the weak form is A_e = Phi^T T_e (K = 4 NQ; Algorithm 2 with the
+// sparse c, see fem_fma.cuh).  Transposed, A_e^T[j][i] = sum_k T_e[k][j] Phi[k][i],
+// so the MMA rows are (element, j) pairs and the columns i:
+//     D[(e,j)][i] = sum_k A[(e,j)][k] B[i][k],  A = T_e^T (per element), B = Phi^T.
+// Rows of all elements are stacked densely, NS+1 rows per element: rows
+// j < NS give column j of A_e, and an extra row whose weighted tile is
+// (S_Q, 0, 0, 0) per point (S_Q = w det f) gives the load vector
+// b_e[i] = sum_Q S_Q phi[Q][0][i] from the same MMAs.  An M tile of 128 rows
+// therefore has no padding whatever NS is; N is NS rounded up to 16 (split in
+// two MMAs of N = 144 at p = 7).
+//
+// hi + lo split: x = hi(x) + lo(x) with hi, lo 16-bit; the product uses
+// hi*hi + hi*lo + lo*hi (three MMAs into one FP32 accumulator), dropping
+// lo*lo.  For FP16 both operands are scaled by powers of two (Phi per degree,
+// T per element from a bound on |G| |Phi|) so the largest magnitude sits near
+// 2^14; the epilogue removes the scale exactly.
+//
+// CTA roles (192 threads, persistent over M tiles):
+//   warp 0, lane 0 : bulk-copies the Phi^T hi/lo image of each K chunk (TMA);
+//   warp 1, lane 0 : issues tcgen05.mma and commits (warp 1 owns TMEM);
+//   warps 2..5     : FP64 geometry -> G records (shared), then build the A
+//                    tiles (T^T hi/lo) of each K chunk, then drain TMEM and
+//                    write A_e / b_e (epilogue); warp w drains TMEM lanes
+//                    32 (w % 4) .. + 31, so it builds those rows too.
+// Every mbarrier wait is bounded (about a second); a CTA whose wait expires
+// sets the library's device error word, marks its elements FEM_ST_TIMEOUT,
+// waits for its own copies and MMAs, frees TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "fem_geometry.cuh"
+#include "fem_internal.h"
+#include "fem_tc_ptx.cuh"
+
+namespace fem {
+
+template <int P>
+struct TcCfg {
+  static constexpr int NS = ns_of(FEM_PRISM6, P), NQ = nq_of(FEM_PRISM6, P);
+  static constexpr int L = NS + 1;  // MMA rows per element
+  static constexpr int BM = 128;
+  static constexpr int KC = 32;     // K per stage: 8 points x 4 derivatives
+  static constexpr int QC = KC / 4;
+  static constexpr int KP = (4 * NQ + KC - 1) / KC * KC;
+  static constexpr int NCH = KP / KC;
+  static constexpr int NQP = KP / 4;
+  static constexpr int NP = (NS + 15) / 16 * 16;
+  static constexpr int NSPLIT = NP > 256 ? 2 : 1;
+  static constexpr int NH = NP / NSPLIT;
+  static constexpr int MAXEL = (BM - 1 + L - 1) / L + 1;
+  static constexpr int TMEM_COLS = NP <= 32 ? 32 : NP <= 64 ? 64 : NP <= 128 ? 128 : NP <= 256 ? 256 : 512;
+  static constexpr int STAGES = 3;
+  static constexpr int A_BYTES = BM * KC * 2;  // one half (hi or lo)
+  static constexpr int B_BYTES = NP * KC * 2;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int SBO = (KC / 8) * 128;   // 8-row group stride in a stage tile
+  static constexpr int NREC = 18 + 11;
+  // shared layout (bytes from a 1024-aligned base)
+  static constexpr size_t OFF_G = (size_t)STAGES * STAGE_BYTES;
+  static constexpr size_t OFF_X = OFF_G + (size_t)MAXEL * NQP * 12 * 4;
+  static constexpr size_t OFF_BAR = (OFF_X + (size_t)MAXEL * NREC * 8 + 15) / 16 * 16;
+  static constexpr size_t OFF_MISC = OFF_BAR + 8 * (2 * STAGES + 3);
+  static constexpr size_t SMEM = OFF_MISC + 16 + 16 * MAXEL + 1024;
+  static_assert(NH % 16 == 0 && NH >= 16 && NH <= 256, "MMA N out of range");
+  static_assert(NQP >= NQ, "padding");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+struct TcArgs {
+  int64_t n;
+  const double *coords;
+  const double *coeffs;
+  int64_t cstride;
+  const double *qp;
+  const float *phi32;
+  const uint16_t *img;  // Phi^T hi/lo image per K chunk
+  float phimax;         // max |Phi| (FP32 table)
+  int aphi;             // power-of-two exponent applied to the image (FP16)
+  void *A;
+  void *b;
+  int32_t *status;
+  int layout;
+  int *err;
+};
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
+
+template <bool F16>
+__device__ __forceinline__ uint32_t split_pack(float x0, float x1, uint32_t &lo_word) {
+  uint16_t h0, h1, l0, l1;
+  if (F16) {
+    __half a = __float2half_rn(x0), b = __float2half_rn(x1);
+    __half c = __float2half_rn(x0 - __half2float(a)), d = __float2half_rn(x1 - __half2float(b));
+    h0 = __half_as_ushort(a);
+    h1 = __half_as_ushort(b);
+    l0 = __half_as_ushort(c);
+    l1 = __half_as_ushort(d);
+  } else {
+    __nv_bfloat16 a = __float2bfloat16_rn(x0), b = __float2bfloat16_rn(x1);
+    __nv_bfloat16 c = __float2bfloat16_rn(x0 - __bfloat162float(a));
+    __nv_bfloat16 d = __float2bfloat16_rn(x1 - __bfloat162float(b));
+    h0 = __bfloat16_as_ushort(a);
+    h1 = __bfloat16_as_ushort(b);
+    l0 = __bfloat16_as_ushort(c);
+    l1 = __bfloat16_as_ushort(d);
+  }
+  lo_word = (uint32_t)l0 | ((uint32_t)l1 << 16);
+  return (uint32_t)h0 | ((uint32_t)h1 << 16);
+}
+
+template <int P, bool F16>
+__global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
+  using C = TcCfg<P>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float *sG = reinterpret_cast<float *>(sm + C::OFF_G);
+  double *sX = reinterpret_cast<double *>(sm + C::OFF_X);
+  uint64_t *bar_full = reinterpret_cast<uint64_t *>(sm + C::OFF_BAR);
+  uint64_t *bar_empty = bar_full + C::STAGES;
+  uint64_t *bar_accf = bar_empty + C::STAGES;
+  uint64_t *bar_acce = bar_accf + 1;
+  uint64_t *bar_fin = bar_acce + 1;
+  uint32_t *sTmem = reinterpret_cast<uint32_t *>(sm + C::OFF_MISC);
+  volatile int *sAbort = reinterpret_cast<volatile int *>(sm + C::OFF_MISC + 4);
+  float *sScale = reinterpret_cast<float *>(sm + C::OFF_MISC + 16);          // [MAXEL]
+  float *sInv = sScale + C::MAXEL;                                            // [MAXEL]
+  int *sSt = reinterpret_cast<int *>(sInv + C::MAXEL);                        // [MAXEL]
+  unsigned *sBnd = reinterpret_cast<unsigned *>(sSt + C::MAXEL);              // [MAXEL]
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t nrows = a.n * C::L;
+  const int64_t ntiles = (nrows + C::BM - 1) / C::BM;
+
+  if (tid == 0) {
+    for (int s = 0; s < C::STAGES; s++) {
+      ptx::mbar_init(&bar_full[s], 129);
+      ptx::mbar_init(&bar_empty[s], 1);
+    }
+    ptx::mbar_init(bar_accf, 1);
+    ptx::mbar_init(bar_acce, 128);
+    ptx::mbar_init(bar_fin, 1);
+    *sAbort = 0;
+    ptx::fence_mbar_init();
+    ptx::fence_proxy_async();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(sTmem, C::TMEM_COLS);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *sTmem;
+  const uint32_t stage0 = ptx::smem_u32(sm);
+
+  auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+    if (*sAbort) return false;
+    if (ptx::mbar_wait(bar, parity, kWaitLimitNs)) return true;
+    *sAbort = 1;
+    return false;
+  };
+
+  if (warp == 0) {
+    // ---------------- Phi^T image loader ----------------
+    if (lane == 0) {
+      uint32_t g = 0;
+      for (int64_t t = blockIdx.x; t < ntiles && !*sAbort; t += gridDim.x) {
+        for (int c = 0; c < C::NCH; c++, g++) {
+          const int s = g % C::STAGES;
+          const uint32_t round = g / C::STAGES;
+          if (!wait(&bar_empty[s], (round & 1) ^ 1)) break;
+          unsigned char *dst = sm + (size_t)s * C::STAGE_BYTES + 2 * C::A_BYTES;
+          ptx::mbar_arrive_expect_tx(&bar_full[s], 2 * C::B_BYTES);
+          ptx::bulk_g2s(dst, reinterpret_cast<const unsigned char *>(a.img) + (size_t)c * 2 * C::B_BYTES,
+                        2 * C::B_BYTES, &bar_full[s]);
+        }
+      }
+      if (*sAbort) {  // let copies in flight land before the CTA leaves
+        const uint64_t t0 = ptx::globaltimer();
+        while (ptx::globaltimer() - t0 < 200000) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = ptx::idesc_f16(!F16, C::BM, C::NH);
+      uint32_t g = 0, tt = 0;
+      for (int64_t t = blockIdx.x; t < ntiles && !*sAbort; t += gridDim.x, tt++) {
+        if (!wait(bar_acce, (tt & 1) ^ 1)) break;
+        ptx::tc_fence_after();
+        bool ok = true;
+        for (int c = 0; c < C::NCH; c++, g++) {
+          const int s = g % C::STAGES;
+          const uint32_t round = g / C::STAGES;
+          if (!wait(&bar_full[s], round & 1)) {
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t aH = stage0 + s * C::STAGE_BYTES, aL = aH + C::A_BYTES;
+          const uint32_t bH = aL + C::A_BYTES, bL = bH + C::B_BYTES;
+#pragma unroll
+          for (int ks = 0; ks < C::KC / 16; ks++) {
+            const uint64_t adH = ptx::smem_desc(aH + ks * 256, 128, C::SBO);
+            const uint64_t adL = ptx::smem_desc(aL + ks * 256, 128, C::SBO);
+#pragma unroll
+            for (int h = 0; h < C::NSPLIT; h++) {
+              const uint32_t boff = h * (C::NH / 8) * C::SBO + ks * 256;
+              const uint64_t bdH = ptx::smem_desc(bH + boff, 128, C::SBO);
+              const uint64_t bdL = ptx::smem_desc(bL + boff, 128, C::SBO);
+              const uint32_t d = tmem + h * C::NH;
+              ptx::mma_f16(d, adH, bdH, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+              ptx::mma_f16(d, adH, bdL, idesc, 1u);
+              ptx::mma_f16(d, adL, bdH, idesc, 1u);
+            }
+          }
+          ptx::mma_commit(&bar_empty[s]);
+        }
+        if (!ok) break;
+        ptx::mma_commit(bar_accf);
+      }
+      // make sure no MMA is still running before TMEM is released
+      ptx::mma_commit(bar_fin);
+      ptx::mbar_wait(bar_fin, 0, kWaitLimitNs);
+    }
+  } else {
+    // ---------------- producers + epilogue (128 threads) ----------------
+    // Every producer runs every tile iteration and every named barrier; after
+    // an abort the work is skipped but the barrier sequence stays the same, so
+    // no thread can be left waiting on a named barrier.
+    const int pt = tid - 64;
+    const int lq = warp & 3;
+    const int rl = 32 * lq + lane;  // row of the tile this thread builds and drains
+    uint32_t tt = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tt++) {
+      const uint32_t g0 = tt * C::NCH;  // first K chunk of this tile in the CTA's sequence
+      const int64_t R0 = t * C::BM;
+      const int64_t e_first = R0 / C::L;
+      int64_t e_last = (R0 + C::BM - 1) / C::L;
+      if (e_last > a.n - 1) e_last = a.n - 1;
+      const int nel = (int)(e_last - e_first + 1);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (!*sAbort) {
+        for (int idx = pt; idx < nel * C::NREC; idx += 128) {  // element records
+          const int el = idx / C::NREC, k = idx % C::NREC;
+          const int64_t e = e_first + el;
+          sX[idx] = k < 18 ? a.coords[e * 18 + k] : a.coeffs[(k - 18) * a.cstride + e];
+        }
+        if (pt < C::MAXEL) {
+          sSt[pt] = 0;
+          sBnd[pt] = 0u;
+        }
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (!*sAbort) {
+        for (int idx = pt; idx < nel * C::NREC; idx += 128)
+          if (!isfinite(sX[idx])) atomicOr(&sSt[idx / C::NREC], FEM_ST_NONFINITE);
+        if (a.layout == FEM_OUT_SYMPACKED && pt < nel) {
+          const double *cf = sX + pt * C::NREC + 18;
+          if (cf[6] != 0.0 || cf[7] != 0.0 || cf[8] != 0.0) atomicOr(&sSt[pt], FEM_ST_NONSYM);
+        }
+        // geometry -> G records (FP64 J, adj, det; FP32 products)
+        for (int idx = pt; idx < nel * C::NQP; idx += 128) {
+          const int el = idx / C::NQP, q = idx % C::NQP;
+          float *gr = sG + (size_t)idx * 12;
+          if (q < C::NQ) {
+            float gv[11];
+            const double *rec = sX + el * C::NREC;
+            const int st = point_matrix_f32<FEM_PRISM6>(rec, rec + 18, a.qp + 4 * q, gv);
+#pragma unroll
+            for (int k = 0; k < 11; k++) gr[k] = gv[k];
+            if (st) atomicOr(&sSt[el], st);
+            if (F16) {
+              float b = fabsf(gv[G00]) + fabsf(gv[G01]) + fabsf(gv[G02]) + fabsf(gv[G03]);
+              b = fmaxf(b, fabsf(gv[G11]) + fabsf(gv[G12]) + fabsf(gv[G13]));
+              b = fmaxf(b, fabsf(gv[G12]) + fabsf(gv[G22]) + fabsf(gv[G23]));
+              b = fmaxf(b, fabsf(gv[G13]) + fabsf(gv[G23]) + fabsf(gv[G33]));
+              b = fmaxf(b, fabsf(gv[GS]));
+              if (isfinite(b)) atomicMax(&sBnd[el], __float_as_uint(b));
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < 11; k++) gr[k] = 0.f;
+          }
+        }
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (!*sAbort && pt < nel) {
+        float sc = 1.f, inv = 1.f;
+        if (F16) {
+          const float bnd = __uint_as_float(sBnd[pt]) * a.phimax;
+          int ex = 0;
+          if (bnd > 0.f) frexpf(bnd, &ex);
+          const int at = bnd > 0.f ? 14 - ex : 0;
+          sc = ldexpf(1.f, at);
+          inv = ldexpf(1.f, -(at + a.aphi));
+        }
+        sScale[pt] = sc;
+        sInv[pt] = inv;
+        const int64_t e = e_first + pt;
+        if (a.status && e * C::L >= R0) a.status[e] = sSt[pt];  // the tile holding row 0 reports
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (__any_sync(0xffffffffu, *sAbort != 0)) continue;  // warp-uniform
+
+      // K loop: build the A tiles (T^T, hi and lo) of this thread's row
+      const int64_t r = R0 + rl;
+      const bool valid = r < nrows;
+      const int64_t e = valid ? r / C::L : e_first;
+      const int j = valid ? (int)(r % C::L) : 0;
+      const int el = (int)(e - e_first);
+      const float sc = valid ? sScale[el] : 0.f;
+      const float *gbase = sG + (size_t)el * C::NQP * 12;
+      bool ok = true;
+      for (int c = 0; c < C::NCH; c++) {
+        const uint32_t g = g0 + c;
+        const int s = g % C::STAGES;
+        const uint32_t round = g / C::STAGES;
+        if (!wait(&bar_empty[s], (round & 1) ^ 1)) {
+          ok = false;
+          break;
+        }
+        uint32_t hw[C::KC / 2], lw[C::KC / 2];
+#pragma unroll
+        for (int qq = 0; qq < C::QC; qq++) {
+          const int q = c * C::QC + qq;
+          float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+          if (valid && q < C::NQ) {
+            const float *gr = gbase + q * 12;
+            if (j < C::NS) {
+              const float *ph = a.phi32 + (size_t)(4 * q) * C::NS + j;
+              const float f0 = __ldg(ph), f1 = __ldg(ph + C::NS), f2 = __ldg(ph + 2 * C::NS),
+                          f3 = __ldg(ph + 3 * C::NS);
+              t0 = gr[G00] * f0 + gr[G01] * f1 + gr[G02] * f2 + gr[G03] * f3;
+              t1 = gr[G11] * f1 + gr[G12] * f2 + gr[G13] * f3;
+              t2 = gr[G12] * f1 + gr[G22] * f2 + gr[G23] * f3;
+              t3 = gr[G13] * f1 + gr[G23] * f2 + gr[G33] * f3;
+            } else {
+              t0 = gr[GS];
+            }
+          }
+          hw[2 * qq] = split_pack<F16>(t0 * sc, t1 * sc, lw[2 * qq]);
+          hw[2 * qq + 1] = split_pack<F16>(t2 * sc, t3 * sc, lw[2 * qq + 1]);
+        }
+        unsigned char *aH = sm + (size_t)s * C::STAGE_BYTES;
+        unsigned char *aL = aH + C::A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < C::KC / 8; kk++) {
+          const size_t off = (size_t)((rl >> 3) * (C::KC / 8) + kk) * 128 + (rl & 7) * 16;
+          *reinterpret_cast<uint4 *>(aH + off) = make_uint4(hw[4 * kk], hw[4 * kk + 1], hw[4 * kk + 2], hw[4 * kk + 3]);
+          *reinterpret_cast<uint4 *>(aL + off) = make_uint4(lw[4 * kk], lw[4 * kk + 1], lw[4 * kk + 2], lw[4 * kk + 3]);
+        }
+        ptx::fence_proxy_async();
+        ptx::mbar_arrive(&bar_full[s]);
+      }
+
+      // epilogue: TMEM -> registers -> columns of A_e / b_e (warp-uniform decision,
+      // tcgen05.ld is collective over the warp)
+      if (ok) ok = wait(bar_accf, tt & 1);
+      __syncwarp();
+      if (!__all_sync(0xffffffffu, ok)) continue;
+      ptx::tc_fence_after();
+      const float inv = valid ? sInv[el] : 0.f;
+      const uint32_t tbase = tmem + ((uint32_t)(32 * lq) << 16);
+#pragma unroll 1
+      for (int c0 = 0; c0 < C::NP; c0 += 16) {
+        uint32_t v[16];
+        ptx::tmem_ld16(tbase + c0, v);
+        ptx::tmem_ld_wait();
+        if (valid) {
+          if (j < C::NS) {
+            if (a.layout == FEM_OUT_FULL) {
+              float *Ae = static_cast<float *>(a.A) + e * (int64_t)(C::NS * C::NS) + j;
+#pragma unroll
+              for (int u = 0; u < 16; u++) {
+                const int i = c0 + u;
+                if (i < C::NS) Ae[(size_t)i * C::NS] = __uint_as_float(v[u]) * inv;
+              }
+            } else {
+              constexpr int NPK = C::NS * (C::NS + 1) / 2;
+              float *Ae = static_cast<float *>(a.A) + e * (int64_t)NPK;
+#pragma unroll
+              for (int u = 0; u < 16; u++) {
+                const int i = c0 + u;
+                if (i < C::NS && i <= j) Ae[i * C::NS - i * (i - 1) / 2 + j - i] = __uint_as_float(v[u]) * inv;
+              }
+            }
+          } else if (a.b != nullptr) {
+            float *be = static_cast<float *>(a.b) + e * (int64_t)C::NS;
+#pragma unroll
+            for (int u = 0; u < 16; u++) {
+              const int i = c0 + u;
+              if (i < C::NS) be[i] = __uint_as_float(v[u]) * inv;
+            }
+          }
+        }
+      }
+      ptx::tc_fence_before();
+      ptx::mbar_arrive(bar_acce);
+    }
+  }
+
+  __syncthreads();
+  if (*sAbort) {
+    if (tid == 0 && a.err) atomicExch(a.err, 1);
+    // flag the elements of this CTA's tiles that may be incomplete
+    if (a.status) {
+      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t e0 = (t * C::BM) / C::L;
+        int64_t e1 = (t * C::BM + C::BM - 1) / C::L;
+        if (e1 > a.n - 1) e1 = a.n - 1;
+        for (int64_t e = e0 + tid; e <= e1; e += blockDim.x) atomicOr(&a.status[e], FEM_ST_TIMEOUT);
+      }
+    }
+  }
+  if (warp == 1) {
+    __syncwarp();
+    ptx::tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+template <int P, bool F16>
+static int launch_tc_p(const TcArgs &a, void *stream) {
+  using C = TcCfg<P>;
+  if (a.n == 0) return FEM_OK;
+  cudaError_t err = cudaFuncSetAttribute(tc_kernel<P, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  if (err != cudaSuccess) {
+    set_error(std::string("cudaFuncSetAttribute(tc_kernel): ") + cudaGetErrorString(err));
+    return FEM_ECUDA;
+  }
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_kernel<P, F16>, 192, C::SMEM);
+  // TMEM: every resident CTA holds TMEM_COLS of the SM's 512 columns
+  const int tmem_cap = 512 / C::TMEM_COLS;
+  if (per_sm > tmem_cap) per_sm = tmem_cap;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t ntiles = (a.n * C::L + C::BM - 1) / C::BM;
+  int64_t grid = (int64_t)nsm * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  tc_kernel<P, F16><<<(unsigned)grid, 192, C::SMEM, (cudaStream_t)stream>>>(a);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) {
+    set_error(std::string("tc_kernel launch: ") + cudaGetErrorString(err));
+    return FEM_ECUDA;
+  }
+  return FEM_OK;
+}
+
+template <bool F16>
+static int launch_tc_any(int p, const TcArgs &a, void *stream) {
+  switch (p) {
+    case 1: return launch_tc_p<1, F16>(a, stream);
+    case 2: return launch_tc_p<2, F16>(a, stream);
+    case 3: return launch_tc_p<3, F16>(a, stream);
+    case 4: return launch_tc_p<4, F16>(a, stream);
+    case 5: return launch_tc_p<5, F16>(a, stream);
+    case 6: return launch_tc_p<6, F16>(a, stream);
+    case 7: return launch_tc_p<7, F16>(a, stream);
+  }
+  return FEM_EINVAL;
+}
+
+int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *stream) {
+  TcArgs a;
+  a.n = l.n;
+  a.coords = l.coords;
+  a.coeffs = l.coeffs;
+  a.cstride = l.cstride;
+  a.qp = d.qp;
+  a.phi32 = d.phi32;
+  a.img = f16 ? d.img_f16 : d.img_bf16;
+  a.phimax = d.phimax;
+  a.aphi = f16 ? d.aphi_f16 : 0;
+  a.A = l.A;
+  a.b = l.b;
+  a.status = l.status;
+  a.layout = l.layout;
+  a.err = l.err;
+  if (!a.img) {
+    set_error("tensor-core tables missing for this degree");
+    return FEM_EUNSUPPORTED;
+  }
+  return f16 ? launch_tc_any<true>(p, a, stream) : launch_tc_any<false>(p, a, stream);
+}
+
+// Image of Phi^T for the B operand: per K chunk of 32, [hi | lo] blocks of
+// NP x 32 16-bit values in the canonical K-major core-matrix layout
+// (8 rows x 8 values = 128 bytes per core matrix; K-adjacent core matrices
+// 128 bytes apart, 8-row groups (KC/8)*128 bytes apart).  Rows i >= NS and
+// k >= 4 NQ are zero.
+template <int P>
+static void build_image_p(const std::vector<double> &phi, bool f16, int aphi, std::vector<uint16_t> &out) {
+  using C = TcCfg<P>;
+  out.assign((size_t)C::NCH * 2 * C::NP * C::KC, 0);
+  const double scale = std::ldexp(1.0, aphi);
+  for (int c = 0; c < C::NCH; c++) {
+    uint16_t *hi = out.data() + (size_t)c * 2 * C::NP * C::KC;
+    uint16_t *lo = hi + (size_t)C::NP * C::KC;
+    for (int i = 0; i < C::NS; i++)
+      for (int kl = 0; kl < C::KC; kl++) {
+        const int k = c * C::KC + kl;
+        if (k >= 4 * C::NQ) continue;
+        const double x = phi[(size_t)k * C::NS + i] * scale;
+        uint16_t h, l;
+        if (f16) {
+          __half hh = __double2half((double)x);
+          h = __half_as_ushort(hh);
+          l = __half_as_ushort(__double2half(x - (double)__half2float(hh)));
+        } else {
+          __nv_bfloat16 hh = __double2bfloat16(x);
+          h = __bfloat16_as_ushort(hh);
+          l = __bfloat16_as_ushort(__double2bfloat16(x - (double)__bfloat162float(hh)));
+        }
+        const size_t off = ((size_t)(i >> 3) * (C::KC / 8) + (kl >> 3)) * 64 + (i & 7) * 8 + (kl & 7);
+        hi[off] = h;
+        lo[off] = l;
+      }
+  }
+}
+
+void build_tc_image(int p, const std::vector<double> &phi, bool f16, int aphi, std::vector<uint16_t> &out) {
+  switch (p) {
+    case 1: build_image_p<1>(phi, f16, aphi, out); break;
+    case 2: build_image_p<2>(phi, f16, aphi, out); break;
+    case 3: build_image_p<3>(phi, f16, aphi, out); break;
+    case 4: build_image_p<4>(phi, f16, aphi, out); break;
+    case 5: build_image_p<5>(phi, f16, aphi, out); break;
+    case 6: build_image_p<6>(phi, f16, aphi, out); break;
+    case 7: build_image_p<7>(phi, f16, aphi, out); break;
+  }
+}
+
+}  // namespace fem

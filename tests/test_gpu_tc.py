@@ -1,0 +1,108 @@
+"""Tensor-core path (tcgen05, BF16/FP16 hi+lo split, FP32 accumulation) vs
+the FP64 oracle, through the C ABI.
+
+Tolerances (per-element relative Frobenius error of A_e and b_e), derived from
+the split arithmetic: a 16-bit hi + lo pair keeps 16 (BF16) or 22 (FP16)
+significant bits of each operand, and the dropped lo*lo term and the operand
+rounding leave a relative error of about 2^-15 (BF16) / 2^-20 (FP16) per
+product; with the mild cancellation of these sums (measured factor < 3) the
+bounds are 1e-4 (BF16x3) and 1e-5 (FP16x3).  The measured max / median are
+printed for the record."""
+import numpy as np
+import pytest
+
+from _util import PRISM, gpu_integrate, ns, rel_frob, unpack_upper, workload
+from paper_1310_1191_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_TC = {2: 1e-4, 3: 1e-5}
+# several M tiles of 128 rows (NS+1 rows per element) and a ragged last tile
+SMALL_E = {1: 300, 2: 70, 3: 37, 4: 23, 5: 9, 6: 5, 7: 4}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_1310_1191_gb300 import _lib, build
+    assert torch.cuda.is_available()
+    build.build()
+    _lib.load()
+    return _lib
+
+
+@pytest.fixture(scope="module")
+def tables(lib):
+    t = lib.fem_tables_build(lib.FEM_PRISM6, 1, 7)
+    yield t
+    t.close()
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("p", range(1, 8))
+def test_tc_parity_small(orc, lib, tables, p, prec):
+    E = SMALL_E[p]
+    X, C = workload(PRISM, p, E)
+    A, b, st = gpu_integrate(tables, PRISM, p, X, C, prec)
+    assert lib.fem_error_flag(tables) == lib.FEM_OK
+    RA, Rb, Rst = orc.integrate(PRISM, p, X, C)
+    n = ns(PRISM, p)
+    eA = rel_frob(A.reshape(E, n, n), RA)
+    eb = rel_frob(b, Rb)
+    print("p=%d prec=%d A max %.3e median %.3e  b max %.3e" % (p, prec, eA.max(), np.median(eA), eb.max()))
+    assert np.all(st == Rst)
+    assert eA.max() <= TOL_TC[prec] and eb.max() <= TOL_TC[prec]
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("p", [3, 7])
+def test_tc_sympacked_and_flags(orc, lib, tables, p, prec):
+    E = SMALL_E[p]
+    X, C = workload(PRISM, p, E, kind="symmetric")
+    X[1] = X[1][[1, 0, 2, 4, 3, 5]]  # mirrored element: det J < 0 (flagged, still integrated)
+    A, b, st = gpu_integrate(tables, PRISM, p, X, C, prec, layout=1)
+    RA, Rb, Rst = orc.integrate(PRISM, p, X, C)
+    n = ns(PRISM, p)
+    assert list(st) == list(Rst) and st[1] & 1
+    assert rel_frob(unpack_upper(A, n), np.triu(RA)).max() <= TOL_TC[prec]
+    assert rel_frob(b, Rb).max() <= TOL_TC[prec]
+
+
+def test_tc_tet_unsupported(lib):
+    import torch
+    t = lib.fem_tables_build(lib.FEM_TET4, 1, 1)
+    X = torch.zeros((2, 4, 3), dtype=torch.float64, device="cuda")
+    C = torch.zeros((11, 2), dtype=torch.float64, device="cuda")
+    A = torch.zeros((2, 16), dtype=torch.float32, device="cuda")
+    with pytest.raises(lib.FemError) as ei:
+        lib.fem_integrate(t, 1, 2, X, C, 2, lib.FEM_BF16X3, 0, A)
+    assert ei.value.code == lib.FEM_EUNSUPPORTED
+    t.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("p", [4, 5, 6, 7])
+def test_tc_parity_full_size_sampled(orc, lib, tables, p, prec):
+    """200,000 prisms per degree (the mixed-precision workload), full launch;
+    a seeded sample vs the oracle, all statuses clean, no NaN."""
+    import torch
+    E = 200000
+    X = inputs.prism_mesh(E)
+    C = inputs.coefficients(E)
+    A, b, st = gpu_integrate(tables, PRISM, p, X, C, prec, return_tensors=True)
+    assert lib.fem_error_flag(tables) == lib.FEM_OK
+    rng = np.random.default_rng(200 + p)
+    idx = np.array(sorted(set([0, E - 1]) | set(rng.choice(E, 6, replace=False).tolist())))
+    n = ns(PRISM, p)
+    ti = torch.from_numpy(idx).cuda()
+    Ai = A[ti].double().cpu().numpy().reshape(-1, n, n)
+    bi = b[ti].double().cpu().numpy()
+    assert int((st != 0).sum().item()) == 0
+    assert not bool(torch.isnan(A).any().item())
+    RA, Rb, _ = orc.integrate(PRISM, p, X[idx], C[:, idx])
+    eA = rel_frob(Ai, RA)
+    print("full p=%d prec=%d A max %.3e median %.3e" % (p, prec, eA.max(), np.median(eA)))
+    assert eA.max() <= TOL_TC[prec] and rel_frob(bi, Rb).max() <= TOL_TC[prec]
+    del A, b, st
+    torch.cuda.empty_cache()
