@@ -1,12 +1,14 @@
 """Tensor-core path (tcgen05, BF16/FP16 hi+lo split, FP32 accumulation) vs
 the FP64 oracle, through the C ABI.
 
-Tolerances (per-element relative Frobenius error of A_e and b_e), derived from
-the split arithmetic: a 16-bit hi + lo pair keeps 16 (BF16) or 22 (FP16)
-significant bits of each operand, and the dropped lo*lo term and the operand
-rounding leave a relative error of about 2^-15 (BF16) / 2^-20 (FP16) per
-product; with the mild cancellation of these sums (measured factor < 3) the
-bounds are 1e-4 (BF16x3) and 1e-5 (FP16x3).  The measured max / median are
+Tolerances (per-element relative Frobenius error of A_e and b_e), derived
+from the arithmetic: a 16-bit hi + lo pair keeps 16 (BF16) or 22 (FP16)
+significant bits of each operand (error about 2^-16 resp. 2^-21 per product
+after dropping lo*lo), and the tensor core's FP32 accumulator adds up to about
+one FP32 ulp (2^-24) of the running sum per accumulation step, 3 K/16 steps
+for K = 4 NQ (384 at p = 7: about 2.3e-5).  Measured, the accumulator term
+dominates for both types (the error grows linearly with K: ~2.5e-6 at p = 4,
+~9e-6 at p = 7).  Bound: 3e-5 for both.  The measured max / median are
 printed for the record."""
 import numpy as np
 import pytest
@@ -16,7 +18,7 @@ from paper_1310_1191_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL_TC = {2: 1e-4, 3: 1e-5}
+TOL_TC = {2: 3e-5, 3: 3e-5}
 # several M tiles of 128 rows (NS+1 rows per element) and a ragged last tile
 SMALL_E = {1: 300, 2: 70, 3: 37, 4: 23, 5: 9, 6: 5, 7: 4}
 
