@@ -119,6 +119,55 @@ int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, con
  *   clear : non-zero resets the word. */
 int fem_error_flag(fem_tables t, int clear);
 
+/* ---- mixed-degree meshes (p-binned persistent launch) ---- */
+typedef struct fem_plan_s *fem_plan;
+
+#define FEM_PLAN_AUTOTUNE 1  /* time the candidate tile shapes on the first execution */
+#define FEM_PLAN_LOOP 2      /* run one specialised launch per degree instead of one launch */
+#define FEM_PLAN_NOGRAPH 4   /* launch directly instead of replaying a captured CUDA graph */
+
+/* Per-element output offsets of a mixed-degree mesh, elements kept in their
+ * original order with unpadded variable-size blocks:
+ *   p_host : host int8 [n] degrees;
+ *   offA   : out host [n] offset (in values) of A_e in A_out, or NULL;
+ *   offb   : out host [n] offset of b_e in b_out, or NULL;
+ *   totals : out [2] total values of A_out and b_out, or NULL.
+ * FEM_EINVAL if a degree is invalid for elem. */
+int fem_output_offsets(int elem, const int8_t *p_host, int64_t n, int layout, int64_t *offA,
+                       int64_t *offb, int64_t *totals);
+
+/* Plan for a mixed-degree prism mesh (Section 4.2: the host classifies the
+ * elements by degree).  The elements are binned by degree on the host, the
+ * bins cut into work items (element group x output tile) ordered by cost, and
+ * executed by one persistent launch whose CTAs pull items from an atomic
+ * counter; the counter reset and the launch are captured in a CUDA graph on
+ * the first execution and replayed afterwards (re-captured when the buffers
+ * change).  With FEM_PLAN_AUTOTUNE the first execution times two candidate
+ * tile shapes per degree on the plan's own elements and keeps the faster;
+ * tune_cache (nullable) is a text file that stores and reuses the choices.
+ *   t      : prism tables covering every degree in p_host;
+ *   p_host : host int8 [n_elem] degrees (copied; not kept);
+ *   prec   : FEM_F64 or FEM_F32 (others FEM_EUNSUPPORTED);
+ *   layout : FEM_OUT_FULL / FEM_OUT_SYMPACKED.
+ * The plan owns device memory for the permutation, the offsets, the work
+ * list and the counter; release it with fem_plan_destroy. */
+int fem_plan_create(fem_tables t, int64_t n_elem, const int8_t *p_host, int prec, int layout, int flags,
+                    const char *tune_cache, fem_plan *out);
+
+/* Execute a plan: buffers as in fem_integrate, except that A_out and b_out
+ * are the flat variable-size arrays described by fem_output_offsets
+ * (elements in their original order).  Asynchronous on stream, except the
+ * first execution of an autotuning plan, which synchronises while timing.
+ * Executions of one plan must not overlap on the device (they share the
+ * work counter). */
+int fem_plan_execute(fem_plan plan, const double *coords, const double *coeffs, int64_t coeff_stride,
+                     void *A_out, void *b_out, int32_t *status, void *stream);
+
+/* Tile-shape variant chosen for degree p (0 or 1), and the autotuner's times
+ * of both candidates in ms (ms[2], nullable; 0 if not timed); -1 if invalid. */
+int fem_plan_variant(fem_plan plan, int p, double *ms);
+int fem_plan_destroy(fem_plan plan);
+
 /* Number of output values per element for (elem, p, layout): NS*NS or NS(NS+1)/2;
  * -1 if invalid.  */
 int64_t fem_matrix_size(int elem, int p, int layout);

@@ -26,7 +26,10 @@ FEM_ST_DET, FEM_ST_NONFINITE, FEM_ST_NONSYM, FEM_ST_FALLBACK, FEM_ST_TIMEOUT = 1
 EXPORTS = (
     "fem_reference_rule", "fem_tables_build", "fem_tables_destroy", "fem_integrate",
     "fem_matrix_size", "fem_status_str", "fem_last_error", "fem_error_flag",
+    "fem_output_offsets", "fem_plan_create", "fem_plan_execute", "fem_plan_variant",
+    "fem_plan_destroy",
 )
+FEM_PLAN_AUTOTUNE, FEM_PLAN_LOOP, FEM_PLAN_NOGRAPH = 1, 2, 4
 
 _lib = None
 
@@ -58,6 +61,11 @@ def load():
     lib.fem_last_error.argtypes = []
     lib.fem_last_error.restype = ctypes.c_char_p
     lib.fem_error_flag.argtypes = [P, i]
+    lib.fem_output_offsets.argtypes = [i, P, i64, i, P, P, P]
+    lib.fem_plan_create.argtypes = [P, i64, P, i, i, i, ctypes.c_char_p, P]
+    lib.fem_plan_execute.argtypes = [P, P, P, i64, P, P, P, P]
+    lib.fem_plan_variant.argtypes = [P, i, P]
+    lib.fem_plan_destroy.argtypes = [P]
     _lib = lib
     return lib
 
@@ -159,3 +167,67 @@ def fem_integrate(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_stride: 
 def fem_error_flag(t: Tables, clear: bool = True) -> int:
     """FEM_ETIMEOUT if a bounded device wait expired since the last clear (synchronises)."""
     return load().fem_error_flag(t.handle, 1 if clear else 0)
+
+
+def fem_output_offsets(elem: int, p_host, layout: int):
+    """(offA [n], offb [n], total_A, total_b) for a mixed-degree mesh (int8 degrees)."""
+    p_host = np.ascontiguousarray(p_host, dtype=np.int8)
+    n = p_host.shape[0]
+    offA = np.zeros(n, dtype=np.int64)
+    offb = np.zeros(n, dtype=np.int64)
+    tot = np.zeros(2, dtype=np.int64)
+    _check("fem_output_offsets", load().fem_output_offsets(elem, p_host.ctypes.data, n, layout,
+                                                           offA.ctypes.data, offb.ctypes.data,
+                                                           tot.ctypes.data))
+    return offA, offb, int(tot[0]), int(tot[1])
+
+
+class Plan:
+    """Owning wrapper of a fem_plan handle (mixed-degree prism mesh)."""
+
+    def __init__(self, t: Tables, p_host, prec: int, layout: int = FEM_OUT_FULL, flags: int = 0,
+                 tune_cache: str | None = None):
+        p_host = np.ascontiguousarray(p_host, dtype=np.int8)
+        self.n = p_host.shape[0]
+        self.tables = t
+        h = ctypes.c_void_p()
+        _check("fem_plan_create", load().fem_plan_create(
+            t.handle, self.n, p_host.ctypes.data, prec, layout, flags,
+            tune_cache.encode() if tune_cache else None, ctypes.byref(h)))
+        self.handle = h
+
+    def variant(self, p: int):
+        ms = np.zeros(2)
+        v = load().fem_plan_variant(self.handle, p, ms.ctypes.data)
+        return v, ms
+
+    def close(self):
+        if self.handle:
+            load().fem_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fem_plan_create(t: Tables, p_host, prec: int, layout: int = FEM_OUT_FULL, flags: int = 0,
+                    tune_cache: str | None = None) -> Plan:
+    return Plan(t, p_host, prec, layout, flags, tune_cache)
+
+
+def fem_plan_execute(plan: Plan, coords, coeffs, coeff_stride: int, A_out, b_out=None, status=None,
+                     stream=None) -> int:
+    return _check("fem_plan_execute", load().fem_plan_execute(
+        plan.handle, _addr(coords), _addr(coeffs), coeff_stride, _addr(A_out), _addr(b_out),
+        _addr(status), _stream(stream)))
+
+
+def fem_plan_variant(plan: Plan, p: int):
+    return plan.variant(p)
+
+
+def fem_plan_destroy(plan: Plan) -> None:
+    plan.close()

@@ -43,53 +43,61 @@ struct FmaCfg {
   template <class T>
   static constexpr size_t smem_bytes() {
     return sizeof(T) * ((size_t)KC * BM + (size_t)EPB * KC * BN + (size_t)EPB * NQ * kGStride) +
-           sizeof(double) * (size_t)EPB * NREC + sizeof(int) * (size_t)EPB + 64;
+           sizeof(double) * (size_t)EPB * NREC + sizeof(int) * (size_t)(EPB + 1) +
+           sizeof(int64_t) * (size_t)EPB + 64;
   }
 };
 
+// One work item: the group of EPB elements at sorted positions k0..k_end-1
+// (at most EPB; element id = perm[k] if a.perm, else k) and output tile (ti, tj).  Cooperative loops
+// stride over the whole block, so the body also runs inside kernels whose
+// block is larger than C::NT (the batched kernel); the register micro-tiles
+// belong to the first C::NT threads.
 template <class T, class C>
-__global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, const T *phi, int64_t k0,
+                                         int64_t k_end, int ti, int tj, unsigned char *smem) {
   T *sPA = reinterpret_cast<T *>(smem);                 // [KC][BM]
   T *sT = sPA + C::KC * C::BM;                          // [EPB][KC][BN]
   T *sG = sT + C::EPB * C::KC * C::BN;                  // [EPB][NQ][kGStride]
   double *sX = reinterpret_cast<double *>(sG + C::EPB * C::NQ * kGStride);  // [EPB][NREC]
   int *sSt = reinterpret_cast<int *>(sX + C::EPB * C::NREC);               // [EPB]
+  int64_t *sE = reinterpret_cast<int64_t *>(sSt + C::EPB + (C::EPB & 1));   // [EPB] element ids
 
-  const T *phi = static_cast<const T *>(a.phi);
-  const int tid = threadIdx.x;
-  long long blk = blockIdx.x;
-  const int tj = (int)(blk % C::TILES);
-  blk /= C::TILES;
-  const int ti = (int)(blk % C::TILES);
-  blk /= C::TILES;
-  const int64_t e0 = blk * (int64_t)C::EPB;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  constexpr int NSZ = C::NS * C::NS, NPK = C::NS * (C::NS + 1) / 2;
 
+  for (int le = tid; le < C::EPB; le += nthr) {
+    const int64_t k = k0 + le;
+    sE[le] = k < k_end ? (a.perm ? a.perm[k] : k) : -1;
+    sSt[le] = 0;
+  }
+  __syncthreads();
   // 0. element records
-  for (int idx = tid; idx < C::EPB * C::NREC; idx += C::NT) {
+  for (int idx = tid; idx < C::EPB * C::NREC; idx += nthr) {
     const int le = idx / C::NREC, k = idx % C::NREC;
-    const int64_t e = e0 + le;
+    const int64_t e = sE[le];
     double v = 0.0;
-    if (e < a.n) v = k < C::NV * 3 ? a.coords[e * (C::NV * 3) + k] : a.coeffs[(k - C::NV * 3) * a.cstride + e];
+    if (e >= 0) v = k < C::NV * 3 ? a.coords[e * (C::NV * 3) + k] : a.coeffs[(k - C::NV * 3) * a.cstride + e];
     sX[idx] = v;
   }
-  if (tid < C::EPB) sSt[tid] = 0;
   __syncthreads();
-  for (int idx = tid; idx < C::EPB * C::NREC; idx += C::NT)
+  for (int idx = tid; idx < C::EPB * C::NREC; idx += nthr)
     if (!isfinite(sX[idx])) atomicOr(&sSt[idx / C::NREC], FEM_ST_NONFINITE);
-  if (a.layout == FEM_OUT_SYMPACKED && tid < C::EPB) {
-    const double *cf = sX + tid * C::NREC + C::NV * 3;
-    if (cf[6] != 0.0 || cf[7] != 0.0 || cf[8] != 0.0) atomicOr(&sSt[tid], FEM_ST_NONSYM);
+  if (a.layout == FEM_OUT_SYMPACKED) {
+    for (int le = tid; le < C::EPB; le += nthr) {
+      const double *cf = sX + le * C::NREC + C::NV * 3;
+      if (cf[6] != 0.0 || cf[7] != 0.0 || cf[8] != 0.0) atomicOr(&sSt[le], FEM_ST_NONSYM);
+    }
   }
 
   // 1. geometry (FP64) -> point records
-  for (int idx = tid; idx < C::EPB * C::NQ; idx += C::NT) {
+  for (int idx = tid; idx < C::EPB * C::NQ; idx += nthr) {
     const int le = idx / C::NQ, q = idx % C::NQ;
     double g[11];
     const double *rec = sX + le * C::NREC;
-    int st = point_matrix<C::ELEM>(rec, rec + C::NV * 3, a.qp + 4 * q, g);
+    int st = point_matrix<C::ELEM>(rec, rec + C::NV * 3, qp + 4 * q, g);
     T *dst = sG + (size_t)idx * kGStride;
-    if (e0 + le < a.n) {
+    if (sE[le] >= 0) {
 #pragma unroll
       for (int k = 0; k < 11; k++) dst[k] = (T)g[k];
       if (st) atomicOr(&sSt[le], st);
@@ -101,7 +109,8 @@ __global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
   __syncthreads();
 
   // 2. contraction over chunks of points
-  const int le = tid / C::TPE, r = tid % C::TPE, tx = r % C::TX, ty = r / C::TX;
+  const bool owner = tid < C::NT;
+  const int le = owner ? tid / C::TPE : 0, r = tid % C::TPE, tx = r % C::TX, ty = r / C::TX;
   T acc[C::TM][C::TN];
 #pragma unroll
   for (int i = 0; i < C::TM; i++)
@@ -110,12 +119,12 @@ __global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
 
   for (int ch = 0; ch < C::NCH; ch++) {
     const int q0 = ch * C::QC;
-    for (int idx = tid; idx < C::KC * C::BM; idx += C::NT) {
+    for (int idx = tid; idx < C::KC * C::BM; idx += nthr) {
       const int k = idx / C::BM, i = idx % C::BM;
       const int row = ti * C::BM + i, kg = 4 * q0 + k;
       sPA[idx] = (row < C::NS && kg < 4 * C::NQ) ? phi[(size_t)kg * C::NS + row] : (T)0;
     }
-    for (int idx = tid; idx < C::EPB * C::QC * C::BN; idx += C::NT) {
+    for (int idx = tid; idx < C::EPB * C::QC * C::BN; idx += nthr) {
       const int l2 = idx / (C::QC * C::BN), rem = idx % (C::QC * C::BN);
       const int qq = rem / C::BN, j = rem % C::BN;
       const int q = q0 + qq, col = tj * C::BN + j;
@@ -136,19 +145,21 @@ __global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
       tt[3 * C::BN] = t3;
     }
     __syncthreads();
-    const T *pa = sPA + ty * C::TM;
-    const T *pb = sT + (size_t)le * C::KC * C::BN + tx * C::TN;
+    if (owner) {
+      const T *pa = sPA + ty * C::TM;
+      const T *pb = sT + (size_t)le * C::KC * C::BN + tx * C::TN;
 #pragma unroll 4
-    for (int k = 0; k < C::KC; k++) {
-      T av[C::TM], bv[C::TN];
+      for (int k = 0; k < C::KC; k++) {
+        T av[C::TM], bv[C::TN];
 #pragma unroll
-      for (int i = 0; i < C::TM; i++) av[i] = pa[k * C::BM + i];
+        for (int i = 0; i < C::TM; i++) av[i] = pa[k * C::BM + i];
 #pragma unroll
-      for (int j = 0; j < C::TN; j++) bv[j] = pb[k * C::BN + j];
+        for (int j = 0; j < C::TN; j++) bv[j] = pb[k * C::BN + j];
 #pragma unroll
-      for (int i = 0; i < C::TM; i++)
+        for (int i = 0; i < C::TM; i++)
 #pragma unroll
-        for (int j = 0; j < C::TN; j++) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+          for (int j = 0; j < C::TN; j++) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+      }
     }
     __syncthreads();
   }
@@ -156,24 +167,24 @@ __global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
   // 3. load vector rows of this tile
   if (tj == 0 && a.b != nullptr) {
     T *bo = static_cast<T *>(a.b);
-    for (int idx = tid; idx < C::EPB * C::BM; idx += C::NT) {
+    for (int idx = tid; idx < C::EPB * C::BM; idx += nthr) {
       const int l2 = idx / C::BM, i = idx % C::BM, row = ti * C::BM + i;
-      const int64_t e = e0 + l2;
-      if (row < C::NS && e < a.n) {
+      const int64_t e = sE[l2];
+      if (row < C::NS && e >= 0) {
         T s = 0;
         const T *g = sG + (size_t)l2 * C::NQ * kGStride + GS;
         for (int q = 0; q < C::NQ; q++) s = fma(g[q * kGStride], phi[(size_t)(4 * q) * C::NS + row], s);
-        bo[e * C::NS + row] = s;
+        bo[(a.offb ? a.offb[e] : e * (int64_t)C::NS) + row] = s;
       }
     }
   }
 
   // 4. write the micro-tile
-  const int64_t e = e0 + le;
-  if (e < a.n) {
+  const int64_t e = owner ? sE[le] : -1;
+  if (e >= 0) {
     T *Ao = static_cast<T *>(a.A);
     if (a.layout == FEM_OUT_FULL) {
-      T *Ae = Ao + e * (int64_t)(C::NS * C::NS);
+      T *Ae = Ao + (a.offA ? a.offA[e] : e * (int64_t)NSZ);
 #pragma unroll
       for (int i = 0; i < C::TM; i++) {
         const int row = ti * C::BM + ty * C::TM + i;
@@ -185,8 +196,7 @@ __global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
         }
       }
     } else {
-      constexpr int NP = C::NS * (C::NS + 1) / 2;
-      T *Ae = Ao + e * (int64_t)NP;
+      T *Ae = Ao + (a.offA ? a.offA[e] : e * (int64_t)NPK);
 #pragma unroll
       for (int i = 0; i < C::TM; i++) {
         const int row = ti * C::BM + ty * C::TM + i;
@@ -200,8 +210,21 @@ __global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
       }
     }
   }
-  if (a.status != nullptr && ti == 0 && tj == 0 && tid < C::EPB && e0 + tid < a.n)
-    a.status[e0 + tid] = sSt[tid];
+  if (a.status != nullptr && ti == 0 && tj == 0)
+    for (int l2 = tid; l2 < C::EPB; l2 += nthr)
+      if (sE[l2] >= 0) a.status[sE[l2]] = sSt[l2];
+  __syncthreads();  // shared memory is reused by the next work item
+}
+
+template <class T, class C>
+__global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  long long blk = blockIdx.x;
+  const int tj = (int)(blk % C::TILES);
+  blk /= C::TILES;
+  const int ti = (int)(blk % C::TILES);
+  blk /= C::TILES;
+  fma_body<T, C>(a, a.qp, static_cast<const T *>(a.phi), blk * (int64_t)C::EPB, a.n, ti, tj, smem);
 }
 
 template <class T, class C>

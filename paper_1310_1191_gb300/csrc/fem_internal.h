@@ -69,6 +69,9 @@ struct FmaArgs {
   void *b;
   int32_t *status;
   int layout;
+  const int64_t *perm = nullptr;  // sorted position -> element id (batched path), or NULL
+  const int64_t *offA = nullptr;  // per-element offset of A_e in A (values), or NULL
+  const int64_t *offb = nullptr;  // per-element offset of b_e in b (values), or NULL
 };
 
 // Launch the FP64 / FP32 FMA kernels for (elem, p); returns a fem status code.
