@@ -231,3 +231,4 @@ def fem_plan_variant(plan: Plan, p: int):
 
 def fem_plan_destroy(plan: Plan) -> None:
     plan.close()
+

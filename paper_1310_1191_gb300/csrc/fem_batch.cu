@@ -180,20 +180,22 @@ static double item_cost(int p) {  // relative cost of one element of degree p (c
   return 8.0 * nq * ns * ns + 150.0 * nq;
 }
 
-// Work items of all bins (or of one bin when only_p > 0) with the plan's variants.
-static void build_items(const fem_plan_s *pl, int only_p, std::vector<int4> &out) {
+// Work items of all bins (or of one bin when only_p > 0) for the given
+// per-degree variants; bin_off[p] .. bin_off[p+1] are the sorted positions of
+// degree p.  Appends to out (cleared first).
+static void build_items_raw(const int64_t *bin_off, const int *variant, int only_p, std::vector<int4> &out) {
   out.clear();
   std::vector<std::pair<double, int4>> v;
   for (int p = 1; p <= kMaxP; p++) {
     if (only_p > 0 && p != only_p) continue;
-    const int64_t k0 = pl->bin_off[p], k1 = pl->bin_off[p + 1];
+    const int64_t k0 = bin_off[p], k1 = bin_off[p + 1];
     if (k1 <= k0) continue;
-    const ShapeInfo si = shape_info(p, pl->variant[p]);
+    const ShapeInfo si = shape_info(p, variant[p]);
     for (int64_t k = k0; k < k1; k += si.epb) {
       const int64_t ke = std::min<int64_t>(k + si.epb, k1);
       for (int t = 0; t < si.tiles * si.tiles; t++) {
         int4 it;
-        it.x = (p << 4) | pl->variant[p];
+        it.x = (p << 4) | variant[p];
         it.y = t;
         it.z = (int)k;
         it.w = (int)ke;
@@ -206,6 +208,10 @@ static void build_items(const fem_plan_s *pl, int only_p, std::vector<int4> &out
     return a.first > b.first;
   });
   for (auto &x : v) out.push_back(x.second);
+}
+
+static void build_items(const fem_plan_s *pl, int only_p, std::vector<int4> &out) {
+  build_items_raw(pl->bin_off, pl->variant, only_p, out);
 }
 
 static int upload_items(fem_plan_s *pl, const std::vector<int4> &items) {
@@ -223,22 +229,27 @@ static int upload_items(fem_plan_s *pl, const std::vector<int4> &items) {
   return FEM_OK;
 }
 
-static BatchArgs batch_args(const fem_plan_s *pl, const FmaArgs &base) {
+static BatchArgs batch_args_raw(fem_tables t, int prec, const FmaArgs &base, const int4 *items, int nitems,
+                                unsigned *counter) {
   BatchArgs b;
   b.base = base;
   for (int p = 0; p <= kMaxP; p++) {
-    const DevTable &d = pl->t->tab[p];
+    const DevTable &d = t->tab[p];
     b.qp[p] = d.qp;
-    b.phi[p] = pl->prec == FEM_F64 ? (const void *)d.phi64 : (const void *)d.phi32;
+    b.phi[p] = prec == FEM_F64 ? (const void *)d.phi64 : (const void *)d.phi32;
   }
-  b.items = pl->items;
-  b.nitems = pl->nitems;
-  b.counter = pl->counter;
+  b.items = items;
+  b.nitems = nitems;
+  b.counter = counter;
   return b;
 }
 
-static int launch_batch(const fem_plan_s *pl, const BatchArgs &b, cudaStream_t s) {
-  const bool f64 = pl->prec == FEM_F64;
+static BatchArgs batch_args(const fem_plan_s *pl, const FmaArgs &base) {
+  return batch_args_raw(pl->t, pl->prec, base, pl->items, pl->nitems, pl->counter);
+}
+
+// Zero the work counter and launch the persistent kernel (no allocation).
+static int launch_batch_raw(bool f64, const BatchArgs &b, cudaStream_t s) {
   const size_t smem = batch_smem(f64);
   cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return plan_fail("cudaMemsetAsync(counter)", e);
@@ -262,6 +273,10 @@ static int launch_batch(const fem_plan_s *pl, const BatchArgs &b, cudaStream_t s
   e = cudaGetLastError();
   if (e != cudaSuccess) return plan_fail("batch_kernel launch", e);
   return FEM_OK;
+}
+
+static int launch_batch(const fem_plan_s *pl, const BatchArgs &b, cudaStream_t s) {
+  return launch_batch_raw(pl->prec == FEM_F64, b, s);
 }
 
 static int launch_per_p_loop(const fem_plan_s *pl, const FmaArgs &base, cudaStream_t s) {

@@ -67,7 +67,7 @@ struct TcCfg {
   static constexpr size_t OFF_X = OFF_G + (size_t)MAXEL * NQP * 12 * 4;
   static constexpr size_t OFF_BAR = (OFF_X + (size_t)MAXEL * NREC * 8 + 15) / 16 * 16;
   static constexpr size_t OFF_MISC = OFF_BAR + 8 * (2 * STAGES + 3);
-  static constexpr size_t SMEM = OFF_MISC + 16 + 16 * MAXEL + 1024;
+  static constexpr size_t SMEM = OFF_MISC + 16 + 28 * MAXEL + 1024;
   static_assert(NH % 16 == 0 && NH >= 16 && NH <= 256, "MMA N out of range");
   static_assert(NQP >= NQ, "padding");
   static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -133,6 +133,9 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
   float *sInv = sScale + C::MAXEL;                                            // [MAXEL]
   int *sSt = reinterpret_cast<int *>(sInv + C::MAXEL);                        // [MAXEL]
   unsigned *sBnd = reinterpret_cast<unsigned *>(sSt + C::MAXEL);              // [MAXEL]
+  unsigned *sBndB = sBnd + C::MAXEL;                                          // [MAXEL]
+  float *sScaleB = reinterpret_cast<float *>(sBndB + C::MAXEL);               // [MAXEL]
+  float *sInvB = sScaleB + C::MAXEL;                                          // [MAXEL]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nrows = a.n * C::L;
@@ -257,6 +260,7 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
         if (pt < C::MAXEL) {
           sSt[pt] = 0;
           sBnd[pt] = 0u;
+          sBndB[pt] = 0u;
         }
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -283,8 +287,11 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
               b = fmaxf(b, fabsf(gv[G11]) + fabsf(gv[G12]) + fabsf(gv[G13]));
               b = fmaxf(b, fabsf(gv[G12]) + fabsf(gv[G22]) + fabsf(gv[G23]));
               b = fmaxf(b, fabsf(gv[G13]) + fabsf(gv[G23]) + fabsf(gv[G33]));
-              b = fmaxf(b, fabsf(gv[GS]));
               if (isfinite(b)) atomicMax(&sBnd[el], __float_as_uint(b));
+              // the load-vector row (S_Q, 0, 0, 0) gets its own scale: a small
+              // source f must not fall into FP16 subnormals
+              const float bs = fabsf(gv[GS]);
+              if (isfinite(bs)) atomicMax(&sBndB[el], __float_as_uint(bs));
             }
           } else {
 #pragma unroll
@@ -294,17 +301,22 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (!*sAbort && pt < nel) {
-        float sc = 1.f, inv = 1.f;
+        float sc = 1.f, inv = 1.f, scb = 1.f, invb = 1.f;
         if (F16) {
-          const float bnd = __uint_as_float(sBnd[pt]) * a.phimax;
-          int ex = 0;
-          if (bnd > 0.f) frexpf(bnd, &ex);
-          const int at = bnd > 0.f ? 14 - ex : 0;
-          sc = ldexpf(1.f, at);
-          inv = ldexpf(1.f, -(at + a.aphi));
+          auto pow2_scale = [&](float bnd, float &s, float &is) {
+            int ex = 0;
+            if (bnd > 0.f) frexpf(bnd, &ex);  // bnd < 2^ex
+            const int at = bnd > 0.f ? 14 - ex : 0;
+            s = ldexpf(1.f, at);
+            is = ldexpf(1.f, -(at + a.aphi));
+          };
+          pow2_scale(__uint_as_float(sBnd[pt]) * a.phimax, sc, inv);
+          pow2_scale(__uint_as_float(sBndB[pt]) * a.phimax, scb, invb);
         }
         sScale[pt] = sc;
         sInv[pt] = inv;
+        sScaleB[pt] = scb;
+        sInvB[pt] = invb;
         const int64_t e = e_first + pt;
         if (a.status && e * C::L >= R0) a.status[e] = sSt[pt];  // the tile holding row 0 reports
       }
@@ -317,7 +329,7 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
       const int64_t e = valid ? r / C::L : e_first;
       const int j = valid ? (int)(r % C::L) : 0;
       const int el = (int)(e - e_first);
-      const float sc = valid ? sScale[el] : 0.f;
+      const float sc = valid ? (j < C::NS ? sScale[el] : sScaleB[el]) : 0.f;
       const float *gbase = sG + (size_t)el * C::NQP * 12;
       bool ok = true;
       for (int c = 0; c < C::NCH; c++) {
@@ -368,7 +380,7 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
       __syncwarp();
       if (!__all_sync(0xffffffffu, ok)) continue;
       ptx::tc_fence_after();
-      const float inv = valid ? sInv[el] : 0.f;
+      const float inv = valid ? (j < C::NS ? sInv[el] : sInvB[el]) : 0.f;
       const uint32_t tbase = tmem + ((uint32_t)(32 * lq) << 16);
 #pragma unroll 1
       for (int c0 = 0; c0 < C::NP; c0 += 16) {
