@@ -168,6 +168,31 @@ int fem_plan_execute(fem_plan plan, const double *coords, const double *coeffs, 
 int fem_plan_variant(fem_plan plan, int p, double *ms);
 int fem_plan_destroy(fem_plan plan);
 
+/* Mixed-degree integration that allocates no device memory (the paper has no
+ * counterpart; this is a library convenience).  For callers that cannot call
+ * cudaMalloc -- code running inside a fixed memory pool or budget, or on a
+ * path where an allocation's implicit device synchronisation is not allowed.
+ * It runs the same persistent p-binned kernel as fem_plan_execute (default
+ * tile shapes, no graph), with its scratch -- work counter, work list, degree
+ * permutation and output offsets -- in one fixed static device array of the
+ * library (about 1.4 MB, held on every GPU that loads the library until the
+ * process exits) instead of plan allocations.
+ *   Arguments as fem_plan_create + fem_plan_execute: p_host is a host int8
+ *   [n_elem] degree array; A_out / b_out are the flat variable-size arrays
+ *   described by fem_output_offsets; prec FEM_F64 or FEM_F32.
+ * Limits: n_elem <= 16384 and at most 65536 work items; larger calls return
+ * FEM_EINVAL with a message (use a plan instead).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call reuses the same array and leaves its contents there:
+ * the call zeroes the work counter itself, but calls whose executions overlap
+ * on the GPU (other streams, other host threads) race on the array and must
+ * be serialised by the caller.  The host-side preparation is serialised by a
+ * mutex.  Asynchronous on stream once the small work list is staged. */
+int fem_integrate_mixed_noalloc(fem_tables t, int64_t n_elem, const int8_t *p_host, const double *coords,
+                                const double *coeffs, int64_t coeff_stride, int prec, int layout,
+                                void *A_out, void *b_out, int32_t *status, void *stream);
+
 /* Number of output values per element for (elem, p, layout): NS*NS or NS(NS+1)/2;
  * -1 if invalid.  */
 int64_t fem_matrix_size(int elem, int p, int layout);

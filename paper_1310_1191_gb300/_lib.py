@@ -27,7 +27,7 @@ EXPORTS = (
     "fem_reference_rule", "fem_tables_build", "fem_tables_destroy", "fem_integrate",
     "fem_matrix_size", "fem_status_str", "fem_last_error", "fem_error_flag",
     "fem_output_offsets", "fem_plan_create", "fem_plan_execute", "fem_plan_variant",
-    "fem_plan_destroy",
+    "fem_plan_destroy", "fem_integrate_mixed_noalloc",
 )
 FEM_PLAN_AUTOTUNE, FEM_PLAN_LOOP, FEM_PLAN_NOGRAPH = 1, 2, 4
 
@@ -66,6 +66,7 @@ def load():
     lib.fem_plan_execute.argtypes = [P, P, P, i64, P, P, P, P]
     lib.fem_plan_variant.argtypes = [P, i, P]
     lib.fem_plan_destroy.argtypes = [P]
+    lib.fem_integrate_mixed_noalloc.argtypes = [P, i64, P, P, P, i64, i, i, P, P, P, P]
     _lib = lib
     return lib
 
@@ -232,3 +233,12 @@ def fem_plan_variant(plan: Plan, p: int):
 def fem_plan_destroy(plan: Plan) -> None:
     plan.close()
 
+
+def fem_integrate_mixed_noalloc(t: Tables, p_host, coords, coeffs, coeff_stride: int, prec: int,
+                                layout: int, A_out, b_out=None, status=None, stream=None) -> int:
+    """Mixed-degree integration with no device allocation (fixed static scratch,
+    at most 16384 elements); outputs laid out as fem_output_offsets describes."""
+    p_host = np.ascontiguousarray(p_host, dtype=np.int8)
+    return _check("fem_integrate_mixed_noalloc", load().fem_integrate_mixed_noalloc(
+        t.handle, p_host.shape[0], p_host.ctypes.data, _addr(coords), _addr(coeffs), coeff_stride,
+        prec, layout, _addr(A_out), _addr(b_out), _addr(status), _stream(stream)))

@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <mutex>
 #include <new>
 #include <sstream>
 #include <string>
@@ -391,9 +392,143 @@ static void drop_graph(fem_plan_s *pl) {
 
 }  // namespace fem
 
+namespace fem {
+
+// ---------------------------------------------------------------- allocation-free variant
+//
+// Some callers cannot allocate device memory: code that runs under a fixed
+// memory budget or pool, inside a host that has handed all device memory to
+// its own allocator, or that must not call cudaMalloc on a hot path because it
+// synchronises the device.  fem_integrate_mixed_noalloc serves them: it runs
+// the mixed-degree persistent kernel with all of its scratch (work counter,
+// work list, degree permutation, output offsets) in the file-scope device
+// array below instead of plan-owned allocations.  The array is a fixed
+// kNoAllocBytes (about 1.4 MB) that every GPU which loads this library keeps
+// until the process exits; it limits a call to kNoAllocMaxElems elements and
+// kNoAllocMaxItems work items.
+constexpr int64_t kNoAllocMaxElems = 16384;
+constexpr int64_t kNoAllocMaxItems = 65536;
+constexpr size_t kNoAllocOffItems = 256;  // the counter sits in the first 256 bytes
+constexpr size_t kNoAllocOffPerm = kNoAllocOffItems + sizeof(int4) * kNoAllocMaxItems;
+constexpr size_t kNoAllocOffA = kNoAllocOffPerm + sizeof(int64_t) * kNoAllocMaxElems;
+constexpr size_t kNoAllocOffB = kNoAllocOffA + sizeof(int64_t) * kNoAllocMaxElems;
+constexpr size_t kNoAllocBytes = kNoAllocOffB + sizeof(int64_t) * kNoAllocMaxElems;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static unsigned char *g_noalloc_dev[kNoAllocMaxDevices] = {nullptr};
+static std::mutex g_noalloc_mutex;  // guards the host staging arrays below
+static int4 g_noalloc_h_items[kNoAllocMaxItems];
+static int64_t g_noalloc_h_perm[kNoAllocMaxElems];
+static int64_t g_noalloc_h_offA[kNoAllocMaxElems];
+static int64_t g_noalloc_h_offb[kNoAllocMaxElems];
+
+}  // namespace fem
+
 using namespace fem;
 
 extern "C" {
+
+int fem_integrate_mixed_noalloc(fem_tables t, int64_t n_elem, const int8_t *p_host, const double *coords,
+                                const double *coeffs, int64_t coeff_stride, int prec, int layout, void *A_out,
+                                void *b_out, int32_t *status, void *stream) {
+  if (!t || t->elem != FEM_PRISM6) {
+    set_error("fem_integrate_mixed_noalloc: needs prism tables");
+    return FEM_EINVAL;
+  }
+  if (n_elem < 0 || n_elem > kNoAllocMaxElems) {
+    set_error("fem_integrate_mixed_noalloc: n_elem must be in 0..16384 (the fixed scratch size)");
+    return FEM_EINVAL;
+  }
+  if (prec != FEM_F64 && prec != FEM_F32) {
+    set_error("fem_integrate_mixed_noalloc: FP64 / FP32 only");
+    return FEM_EUNSUPPORTED;
+  }
+  if (layout != FEM_OUT_FULL && layout != FEM_OUT_SYMPACKED) {
+    set_error("fem_integrate_mixed_noalloc: unknown layout");
+    return FEM_EINVAL;
+  }
+  if (n_elem == 0) return FEM_OK;
+  if (!p_host || !coords || !coeffs || !A_out || coeff_stride < n_elem) {
+    set_error("fem_integrate_mixed_noalloc: NULL buffer or coeff_stride < n_elem");
+    return FEM_EINVAL;
+  }
+  if ((((uintptr_t)coords | (uintptr_t)coeffs) & 7) || ((uintptr_t)A_out & 15)) {
+    set_error("fem_integrate_mixed_noalloc: misaligned buffer");
+    return FEM_EINVAL;
+  }
+  int64_t bin_off[kMaxP + 2] = {0}, cur[kMaxP + 2];
+  for (int64_t e = 0; e < n_elem; e++) {
+    const int p = p_host[e];
+    if (p < t->p_min || p > t->p_max) {
+      set_error("fem_integrate_mixed_noalloc: an element's degree is not in the tables");
+      return FEM_EINVAL;
+    }
+    bin_off[p + 1]++;
+  }
+  for (int p = 1; p <= kMaxP; p++) bin_off[p + 1] += bin_off[p];
+  // one-time set-up per device: the device address of the scratch array
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return plan_fail("cudaGetDevice", err);
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_error("fem_integrate_mixed_noalloc: device index out of range");
+    return FEM_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_dev[dev]) {
+    void *ptr = nullptr;
+    err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (err != cudaSuccess) return plan_fail("cudaGetSymbolAddress(scratch)", err);
+    g_noalloc_dev[dev] = static_cast<unsigned char *>(ptr);
+  }
+  unsigned char *base = g_noalloc_dev[dev];
+  // host side: counting sort by degree, output offsets, work list (default shapes)
+  for (int p = 0; p <= kMaxP + 1; p++) cur[p] = bin_off[p];
+  for (int64_t e = 0; e < n_elem; e++) g_noalloc_h_perm[cur[p_host[e]]++] = e;
+  int rc = fem_output_offsets(FEM_PRISM6, p_host, n_elem, layout, g_noalloc_h_offA, g_noalloc_h_offb, nullptr);
+  if (rc != FEM_OK) return rc;
+  int variant[kMaxP + 1] = {0};
+  std::vector<int4> items;
+  build_items_raw(bin_off, variant, 0, items);
+  if ((int64_t)items.size() > kNoAllocMaxItems) {
+    set_error("fem_integrate_mixed_noalloc: more than 65536 work items (reduce n_elem)");
+    return FEM_EINVAL;
+  }
+  std::copy(items.begin(), items.end(), g_noalloc_h_items);
+  cudaStream_t s = (cudaStream_t)stream;
+  // pageable-source copies: each call returns once the host data is staged
+  err = cudaMemcpyAsync(base + kNoAllocOffItems, g_noalloc_h_items, sizeof(int4) * items.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(base + kNoAllocOffPerm, g_noalloc_h_perm, sizeof(int64_t) * n_elem,
+                          cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(base + kNoAllocOffA, g_noalloc_h_offA, sizeof(int64_t) * n_elem, cudaMemcpyHostToDevice, s);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(base + kNoAllocOffB, g_noalloc_h_offb, sizeof(int64_t) * n_elem, cudaMemcpyHostToDevice, s);
+  if (err != cudaSuccess) return plan_fail("fem_integrate_mixed_noalloc: staging copy", err);
+  FmaArgs a;
+  a.n = n_elem;
+  a.coords = coords;
+  a.coeffs = coeffs;
+  a.cstride = coeff_stride;
+  a.qp = nullptr;
+  a.phi = nullptr;
+  a.A = A_out;
+  a.b = b_out;
+  a.status = status;
+  a.layout = layout;
+  a.perm = reinterpret_cast<const int64_t *>(base + kNoAllocOffPerm);
+  a.offA = reinterpret_cast<const int64_t *>(base + kNoAllocOffA);
+  a.offb = reinterpret_cast<const int64_t *>(base + kNoAllocOffB);
+  BatchArgs b = batch_args_raw(t, prec, a, reinterpret_cast<const int4 *>(base + kNoAllocOffItems),
+                               (int)items.size(), reinterpret_cast<unsigned *>(base));
+  return launch_batch_raw(prec == FEM_F64, b, s);  // zeroes the counter, then launches
+}
+
+
 
 int fem_output_offsets(int elem, const int8_t *p_host, int64_t n, int layout, int64_t *offA, int64_t *offb,
                        int64_t *totals) {
