@@ -27,7 +27,7 @@ _SRC = os.path.join(_HERE, "fem_oracle.c")
 _SO = os.path.join(_BUILD, "libfem_oracle.so")
 
 TET, PRISM = 0, 1
-ST_DET, ST_NONFINITE = 1, 2
+ST_DET, ST_NONFINITE, ST_FALLBACK = 1, 2, 8
 
 _lib = None
 _lock = threading.Lock()
@@ -141,17 +141,19 @@ def mlp_nparams(H: int) -> int:
     return _load().orc_mlp_nparams(H)
 
 
-def mlp_forward(H, theta, box, u, g):
-    theta, box, u, g = _f64(theta), _f64(box), _f64(u), _f64(g)
+def mlp_forward(H, theta, box, u, s):
+    """MLP(u, s) with s = |grad u|; box = (u0, u1, s0, s1)."""
+    theta, box, u, s = _f64(theta), _f64(box), _f64(u), _f64(s)
     y = np.zeros(u.shape[0])
-    _load().orc_mlp_forward(H, _ptr(theta), _ptr(box), u.shape[0], _ptr(u), _ptr(g), _ptr(y))
+    _load().orc_mlp_forward(H, _ptr(theta), _ptr(box), u.shape[0], _ptr(u), _ptr(s), _ptr(y))
     return y
 
 
-def mlp_loss_grad(H, theta, box, u, g, t):
-    theta, box, u, g, t = _f64(theta), _f64(box), _f64(u), _f64(g), _f64(t)
+def mlp_loss_grad(H, theta, box, u, s, t):
+    """Mean squared error of MLP(u, s) against t and its gradient (backprop)."""
+    theta, box, u, s, t = _f64(theta), _f64(box), _f64(u), _f64(s), _f64(t)
     grad = np.zeros(mlp_nparams(H))
-    L = _load().orc_mlp_loss_grad(H, _ptr(theta), _ptr(box), u.shape[0], _ptr(u), _ptr(g),
+    L = _load().orc_mlp_loss_grad(H, _ptr(theta), _ptr(box), u.shape[0], _ptr(u), _ptr(s),
                                   _ptr(t), _ptr(grad))
     return L, grad
 

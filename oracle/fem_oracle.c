@@ -54,6 +54,7 @@
 
 #define ORC_ST_DET 1      /* det J <= 0 at some quadrature point */
 #define ORC_ST_NONFINITE 2 /* non-finite geometry or coefficient input */
+#define ORC_ST_FALLBACK 8  /* surrogate input outside its box: exact law used */
 
 typedef long double ld;
 
@@ -281,18 +282,25 @@ double orc_law_residual(double u, double g, double k) {
 /* -------------------------------------------------- MLP surrogate (FP64) */
 /* 2 -> H -> H -> 1 with tanh.  Parameter vector layout (row-major):
  *   W1[H][2], b1[H], W2[H][H], b2[H], W3[1][H], b3[1].
- * Inputs are normalised to [-1,1]^2 over the box [u0,u1]x[g0,g1]. */
-static double mlp_forward(int H, const double *th, const double *box, double u, double g,
+ * Inputs are u and s = |grad u|, normalised to [-1,1]^2 over the box
+ * [u0,u1] x [s0,s1]: u linearly, s linearly in log s (the law depends on s
+ * through log(1 + k s^2)). */
+static void mlp_inputs(const double *box, double u, double s, double *x0, double *x1) {
+    *x0 = 2.0 * (u - box[0]) / (box[1] - box[0]) - 1.0;
+    *x1 = 2.0 * (log(s) - log(box[2])) / (log(box[3]) - log(box[2])) - 1.0;
+}
+
+static double mlp_forward(int H, const double *th, const double *box, double u, double s,
                           double *h1, double *h2) {
     const double *W1 = th, *b1 = W1 + 2 * H, *W2 = b1 + H, *b2 = W2 + H * H, *W3 = b2 + H,
                  *b3 = W3 + H;
-    double x0 = 2.0 * (u - box[0]) / (box[1] - box[0]) - 1.0;
-    double x1 = 2.0 * (g - box[2]) / (box[3] - box[2]) - 1.0;
+    double x0, x1;
+    mlp_inputs(box, u, s, &x0, &x1);
     for (int i = 0; i < H; i++) h1[i] = tanh(W1[2 * i] * x0 + W1[2 * i + 1] * x1 + b1[i]);
     for (int i = 0; i < H; i++) {
-        double s = b2[i];
-        for (int j = 0; j < H; j++) s += W2[i * H + j] * h1[j];
-        h2[i] = tanh(s);
+        double a = b2[i];
+        for (int j = 0; j < H; j++) a += W2[i * H + j] * h1[j];
+        h2[i] = tanh(a);
     }
     double y = b3[0];
     for (int j = 0; j < H; j++) y += W3[j] * h2[j];
@@ -301,17 +309,17 @@ static double mlp_forward(int H, const double *th, const double *box, double u, 
 
 int orc_mlp_nparams(int H) { return 2 * H + H + H * H + H + H + 1; }
 
-/* y[n] = MLP(u[n], g[n]) */
+/* y[i] = MLP(u[i], s[i]) */
 void orc_mlp_forward(int H, const double *th, const double *box, int64_t n, const double *u,
-                     const double *g, double *y) {
+                     const double *s, double *y) {
     double h1[256], h2[256];
-    for (int64_t s = 0; s < n; s++) y[s] = mlp_forward(H, th, box, u[s], g[s], h1, h2);
+    for (int64_t i = 0; i < n; i++) y[i] = mlp_forward(H, th, box, u[i], s[i], h1, h2);
 }
 
 /* Loss L = mean_s (y_s - t_s)^2 and its gradient dL/dtheta by backpropagation
  * (reverse-mode chain rule through the three layers). */
 double orc_mlp_loss_grad(int H, const double *th, const double *box, int64_t n, const double *u,
-                         const double *g, const double *t, double *grad) {
+                         const double *sv, const double *t, double *grad) {
     const double *W2 = th + 3 * H, *W3 = th + 3 * H + H * H + H;
     int P = orc_mlp_nparams(H);
     double *gW1 = grad, *gb1 = gW1 + 2 * H, *gW2 = gb1 + H, *gb2 = gW2 + H * H, *gW3 = gb2 + H,
@@ -319,9 +327,9 @@ double orc_mlp_loss_grad(int H, const double *th, const double *box, int64_t n, 
     memset(grad, 0, sizeof(double) * P);
     double h1[256], h2[256], d2[256], d1[256], L = 0.0;
     for (int64_t s = 0; s < n; s++) {
-        double y = mlp_forward(H, th, box, u[s], g[s], h1, h2);
-        double x0 = 2.0 * (u[s] - box[0]) / (box[1] - box[0]) - 1.0;
-        double x1 = 2.0 * (g[s] - box[2]) / (box[3] - box[2]) - 1.0;
+        double y = mlp_forward(H, th, box, u[s], sv[s], h1, h2);
+        double x0, x1;
+        mlp_inputs(box, u[s], sv[s], &x0, &x1);
         double r = y - t[s];
         L += r * r;
         double dy = 2.0 * r / (double)n;
@@ -349,9 +357,9 @@ double orc_mlp_loss_grad(int H, const double *th, const double *box, int64_t n, 
 }
 
 /* ------------------------------------------------ element integration */
-/* law: 0 constant coefficients; 1 exact nonlinear law with D = k(u,|grad u|^2) I;
- *      2 same with k from the MLP (mlp_theta, box, H) inside the box and the
- *        exact law outside.
+/* law: 0 constant coefficients; 1 exact nonlinear law with D = k(u, |grad u|^2) I;
+ *      2 same with k = MLP(u, |grad u|) (theta, box, H) inside the box
+ *        [u0,u1] x [s0,s1] and the exact law outside (status bit 8).
  * coords [E][nv][3]; coeffs SoA [11][cstride]: Dxx Dyy Dzz Dxy Dxz Dyz bx by bz c f;
  * ucoef [E][NS] (law != 0); A [E][NS][NS]; b [E][NS]; status [E] (nullable). */
 int orc_integrate_ex(int elem, int p, int64_t E, const double *coords, const double *coeffs,
@@ -430,11 +438,15 @@ int orc_integrate_ex(int elem, int p, int64_t E, const double *coords, const dou
                         for (int m = 0; m < 3; m++) gu[m] += U[i] * psi[(1 + m) * NS + i];
                     }
                     double g = gu[0] * gu[0] + gu[1] * gu[1] + gu[2] * gu[2];
-                    double k;
-                    if (law == 2 && u >= box[0] && u <= box[1] && g >= box[2] && g <= box[3])
-                        k = mlp_forward(H, theta, box, u, g, h1, h2);
-                    else
+                    double sg = sqrt(g), k;
+                    int inbox = law == 2 && u >= box[0] && u <= box[1] && sg >= box[2] &&
+                                sg <= box[3];
+                    if (law == 2 && inbox) {
+                        k = mlp_forward(H, theta, box, u, sg, h1, h2);
+                    } else {
                         k = orc_law_k(u, g);
+                        if (law == 2) st |= ORC_ST_FALLBACK;
+                    }
                     c[1][1] = c[2][2] = c[3][3] = k;
                 }
                 double dw = det * wq[q];

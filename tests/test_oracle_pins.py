@@ -441,16 +441,17 @@ def test_integrate_nonlinear_law_reduces_to_constant(orc):
 
 def test_mlp_against_torch_and_fd(orc):
     """FP64 forward/backprop of the 2->H->H->1 tanh network vs torch.nn with
-    the same parameters, and vs central finite differences."""
+    the same parameters (inputs u and s = |grad u|, u mapped linearly and
+    log s linearly onto [-1, 1]), and vs central finite differences."""
     import torch
     H = 8
     rng = np.random.default_rng(11)
     P = orc.mlp_nparams(H)
     assert P == 2 * H + H + H * H + H + H + 1
     th = rng.standard_normal(P) * 0.5
-    box = np.array([-2.0, 2.0, 0.0, 50.0])
+    box = np.array([-2.0, 2.0, 1.0, 50.0])
     u = rng.uniform(-2, 2, 32)
-    g = rng.uniform(0, 50, 32)
+    g = rng.uniform(1, 50, 32)  # s = |grad u|
     t = rng.uniform(1, 2, 32)
     L, grad = orc.mlp_loss_grad(H, th, box, u, g, t)
     # torch reference
@@ -462,7 +463,7 @@ def test_mlp_against_torch_and_fd(orc):
         o += r * c
         layer.bias.data = torch.tensor(th[o:o + r])
         o += r
-    xin = torch.tensor(np.stack([2 * (u + 2) / 4 - 1, 2 * g / 50 - 1], 1))
+    xin = torch.tensor(np.stack([2 * (u + 2) / 4 - 1, 2 * np.log(g) / np.log(50.0) - 1], 1))
     y = net(xin)[:, 0]
     Lt = ((y - torch.tensor(t)) ** 2).mean()
     Lt.backward()
@@ -479,3 +480,30 @@ def test_mlp_against_torch_and_fd(orc):
         tm[k] -= h
         fd = (orc.mlp_loss_grad(H, tp, box, u, g, t)[0] - orc.mlp_loss_grad(H, tm, box, u, g, t)[0]) / (2 * h)
         assert abs(fd - grad[k]) <= 1e-6 * max(1.0, abs(grad[k]))
+
+
+def test_integrate_mlp_law_inside_and_outside_box(orc):
+    """law=2 equals law=1 when the network reproduces the law exactly outside
+    of its box (fallback flagged), and uses the network inside: a network whose
+    output is a constant k0 (all weights zero, b3 = k0) gives D = k0 I."""
+    p = 2
+    E = 4
+    X = inputs.prism_mesh(E, dims=(2, 1, 1))
+    C = inputs.coefficients(E)
+    NS = orc.ns(PRISM, p)
+    U = np.stack([2.0 * inputs.draw_uniform(5, np.arange(E, dtype=np.uint64), k) - 1.0
+                  for k in range(NS)], 1)
+    H = 8
+    th = np.zeros(orc.mlp_nparams(H))
+    th[-1] = 2.5
+    big = np.array([-1e9, 1e9, 1e-12, 1e12])
+    A2, b2, st2 = orc.integrate(PRISM, p, X, C, law=2, ucoef=U, mlp=(H, th, big))
+    C2 = C.copy()
+    C2[0] = C2[1] = C2[2] = 2.5
+    C2[3:6] = 0
+    A0, b0, _ = orc.integrate(PRISM, p, X, C2)
+    assert _relF(A2, A0) < 1e-14 and np.all(st2 == 0)
+    tiny = np.array([1e8, 2e8, 1e8, 2e8])  # nothing inside: exact law everywhere
+    A3, _, st3 = orc.integrate(PRISM, p, X, C, law=2, ucoef=U, mlp=(H, th, tiny))
+    A1, _, _ = orc.integrate(PRISM, p, X, C, law=1, ucoef=U)
+    assert _relF(A3, A1) < 1e-15 and np.all(st3 == 8)
