@@ -119,6 +119,68 @@ int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, con
  *   clear : non-zero resets the word. */
 int fem_error_flag(fem_tables t, int clear);
 
+/* ---- nonlinear coefficient law and its learned surrogate ---- */
+/* The law (coefficients at quadrature points computed from "old" degrees of
+ * freedom, Algorithm 1 line 10):
+ *     k = 1 + 0.5 exp(-u^2) + 0.2 log(1 + k |grad u|^2),  D = k I,
+ * solved per point by exactly 8 Newton steps from k0 = 1 + 0.5 exp(-u^2).
+ * The surrogate is a 2 -> 64 -> 64 -> 1 tanh network of (u, |grad u|) with
+ * BF16 weights and FP32 accumulation, used inside its training box
+ * [u0,u1] x [s0,s1] (u mapped linearly, log |grad u| linearly onto [-1,1]);
+ * outside the box the exact law is used and the element gets FEM_ST_FALLBACK. */
+#define FEM_LAW_EXACT 1
+#define FEM_LAW_MLP 2
+
+typedef struct fem_mlp_s *fem_mlp;
+
+/* Integration with the per-point law.  Arguments as fem_integrate, plus
+ *   ucoef : device float [n_elem][NS] coefficients of the scalar field u in
+ *           the element's shape functions (the "old" degrees of freedom);
+ *   law   : FEM_LAW_EXACT or FEM_LAW_MLP (then mlp must be a network);
+ *   prec  : FEM_F64 or FEM_F32 (the law in that precision; the network in FP32).
+ * The coefficient rows Dxx..Dyz are ignored (D = k I); b, c, f are used. */
+int fem_integrate_law(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
+                      int64_t coeff_stride, const float *ucoef, int law, fem_mlp mlp, int prec, int layout,
+                      void *A_out, void *b_out, int32_t *status, void *stream);
+
+/* u and |grad u| at every quadrature point of n prisms of degree p:
+ *   us : device float [n][NQ][2] out. */
+int fem_field_samples(fem_tables t, int p, int64_t n, const double *coords, const float *ucoef, float *us,
+                      void *stream);
+
+/* Training box from samples on the host: box[4] = percentiles lo_pct / hi_pct
+ * of u and of |grad u|; us_host float [n][2]. FEM_EINVAL if degenerate. */
+int fem_box_from_samples(int64_t n, const float *us_host, double lo_pct, double hi_pct, double *box);
+
+/* n training pairs drawn on the device: u uniform in [u0,u1], log |grad u|
+ * uniform in [log s0, log s1] (counter-based SplitMix64 draws of (seed, i)),
+ * target k from the exact law in FP64.  us: device float [n][2]; k: [n]. */
+int fem_law_samples(int64_t n, const double *box, uint64_t seed, float *us, float *k, void *stream);
+
+/* Network object: Glorot-uniform weights from seeded draws, zero biases. */
+int fem_mlp_create(const double *box, uint64_t seed, fem_mlp *out);
+int fem_mlp_destroy(fem_mlp m);
+int fem_mlp_nparams(void);
+/* y[i] = network(us[i][0], us[i][1]) on the device. */
+int fem_mlp_forward(fem_mlp m, int64_t n, const float *us, float *y, void *stream);
+/* Mean squared error over n samples and its gradient (hand-written backprop),
+ * computed with the BF16 compute weights: grad device float [P], loss [1]. */
+int fem_mlp_loss_grad(fem_mlp m, int64_t n, const float *us, const float *t, float *grad, float *loss,
+                      void *stream);
+/* steps Adam steps (beta 0.9 / 0.999, eps 1e-8) on minibatches of `batch`
+ * samples drawn with replacement from the n pairs (seeded); the first call
+ * sets the output bias to the mean target.  loss_host (nullable) receives the
+ * per-step minibatch losses (the call then synchronises). */
+int fem_mlp_train(fem_mlp m, int64_t n, const float *us, const float *t, int64_t steps, int batch, float lr,
+                  uint64_t seed, float *loss_host, void *stream);
+/* Host copies of the FP32 master and BF16-rounded compute parameters (each
+ * nullable, [P]) and the box (nullable, [4]); set replaces the master. */
+int fem_mlp_get(fem_mlp m, float *master_host, float *compute_host, double *box);
+int fem_mlp_set(fem_mlp m, const float *master_host);
+/* Checkpoint: "FEMMLP01", H, P, box, step, master, Adam m, Adam v. */
+int fem_mlp_save(fem_mlp m, const char *path);
+int fem_mlp_load(const char *path, fem_mlp *out);
+
 /* ---- mixed-degree meshes (p-binned persistent launch) ---- */
 typedef struct fem_plan_s *fem_plan;
 

@@ -28,7 +28,11 @@ EXPORTS = (
     "fem_matrix_size", "fem_status_str", "fem_last_error", "fem_error_flag",
     "fem_output_offsets", "fem_plan_create", "fem_plan_execute", "fem_plan_variant",
     "fem_plan_destroy", "fem_integrate_mixed_noalloc",
+    "fem_integrate_law", "fem_field_samples", "fem_box_from_samples", "fem_law_samples",
+    "fem_mlp_create", "fem_mlp_destroy", "fem_mlp_nparams", "fem_mlp_forward", "fem_mlp_loss_grad",
+    "fem_mlp_train", "fem_mlp_get", "fem_mlp_set", "fem_mlp_save", "fem_mlp_load",
 )
+FEM_LAW_EXACT, FEM_LAW_MLP = 1, 2
 FEM_PLAN_AUTOTUNE, FEM_PLAN_LOOP, FEM_PLAN_NOGRAPH = 1, 2, 4
 
 _lib = None
@@ -67,6 +71,21 @@ def load():
     lib.fem_plan_variant.argtypes = [P, i, P]
     lib.fem_plan_destroy.argtypes = [P]
     lib.fem_integrate_mixed_noalloc.argtypes = [P, i64, P, P, P, i64, i, i, P, P, P, P]
+    u64, f = ctypes.c_uint64, ctypes.c_float
+    lib.fem_integrate_law.argtypes = [P, i, i64, P, P, i64, P, i, P, i, i, P, P, P, P]
+    lib.fem_field_samples.argtypes = [P, i, i64, P, P, P, P]
+    lib.fem_box_from_samples.argtypes = [i64, P, ctypes.c_double, ctypes.c_double, P]
+    lib.fem_law_samples.argtypes = [i64, P, u64, P, P, P]
+    lib.fem_mlp_create.argtypes = [P, u64, P]
+    lib.fem_mlp_destroy.argtypes = [P]
+    lib.fem_mlp_nparams.argtypes = []
+    lib.fem_mlp_forward.argtypes = [P, i64, P, P, P]
+    lib.fem_mlp_loss_grad.argtypes = [P, i64, P, P, P, P, P]
+    lib.fem_mlp_train.argtypes = [P, i64, P, P, i64, i, f, u64, P, P]
+    lib.fem_mlp_get.argtypes = [P, P, P, P]
+    lib.fem_mlp_set.argtypes = [P, P]
+    lib.fem_mlp_save.argtypes = [P, ctypes.c_char_p]
+    lib.fem_mlp_load.argtypes = [ctypes.c_char_p, P]
     _lib = lib
     return lib
 
@@ -242,3 +261,127 @@ def fem_integrate_mixed_noalloc(t: Tables, p_host, coords, coeffs, coeff_stride:
     return _check("fem_integrate_mixed_noalloc", load().fem_integrate_mixed_noalloc(
         t.handle, p_host.shape[0], p_host.ctypes.data, _addr(coords), _addr(coeffs), coeff_stride,
         prec, layout, _addr(A_out), _addr(b_out), _addr(status), _stream(stream)))
+
+
+# ---------------------------------------------------------------- law and surrogate
+
+def _f64arr(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+class Mlp:
+    """Owning wrapper of a fem_mlp handle (2 -> 64 -> 64 -> 1 tanh surrogate)."""
+
+    def __init__(self, box=None, seed: int = 42, handle=None):
+        if handle is not None:
+            self.handle = handle
+            return
+        b = _f64arr(box)
+        h = ctypes.c_void_p()
+        _check("fem_mlp_create", load().fem_mlp_create(b.ctypes.data, seed, ctypes.byref(h)))
+        self.handle = h
+
+    @staticmethod
+    def nparams() -> int:
+        return load().fem_mlp_nparams()
+
+    def params(self):
+        """(master FP32 [P], compute BF16-rounded [P], box [4]) as numpy arrays."""
+        P = self.nparams()
+        a = np.zeros(P, dtype=np.float32)
+        c = np.zeros(P, dtype=np.float32)
+        box = np.zeros(4)
+        _check("fem_mlp_get", load().fem_mlp_get(self.handle, a.ctypes.data, c.ctypes.data, box.ctypes.data))
+        return a, c, box
+
+    def set_params(self, master):
+        m = np.ascontiguousarray(master, dtype=np.float32)
+        _check("fem_mlp_set", load().fem_mlp_set(self.handle, m.ctypes.data))
+
+    def close(self):
+        if self.handle:
+            load().fem_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fem_mlp_create(box, seed: int = 42) -> Mlp:
+    return Mlp(box, seed)
+
+
+def fem_mlp_destroy(m: Mlp) -> None:
+    m.close()
+
+
+def fem_mlp_nparams() -> int:
+    return Mlp.nparams()
+
+
+def fem_mlp_forward(m: Mlp, n: int, us, y, stream=None) -> int:
+    return _check("fem_mlp_forward", load().fem_mlp_forward(m.handle, n, _addr(us), _addr(y), _stream(stream)))
+
+
+def fem_mlp_loss_grad(m: Mlp, n: int, us, t, grad, loss, stream=None) -> int:
+    return _check("fem_mlp_loss_grad", load().fem_mlp_loss_grad(
+        m.handle, n, _addr(us), _addr(t), _addr(grad), _addr(loss), _stream(stream)))
+
+
+def fem_mlp_train(m: Mlp, n: int, us, t, steps: int, batch: int, lr: float, seed: int,
+                  losses: bool = True, stream=None):
+    """Run `steps` Adam steps; returns the per-step minibatch losses (numpy) or None."""
+    out = np.zeros(max(steps, 1), dtype=np.float32) if losses else None
+    _check("fem_mlp_train", load().fem_mlp_train(
+        m.handle, n, _addr(us), _addr(t), steps, batch, float(lr), seed,
+        out.ctypes.data if out is not None else None, _stream(stream)))
+    return out[:steps] if out is not None else None
+
+
+def fem_mlp_get(m: Mlp):
+    return m.params()
+
+
+def fem_mlp_set(m: Mlp, master) -> None:
+    m.set_params(master)
+
+
+def fem_mlp_save(m: Mlp, path: str) -> int:
+    return _check("fem_mlp_save", load().fem_mlp_save(m.handle, path.encode()))
+
+
+def fem_mlp_load(path: str) -> Mlp:
+    h = ctypes.c_void_p()
+    _check("fem_mlp_load", load().fem_mlp_load(path.encode(), ctypes.byref(h)))
+    return Mlp(handle=h)
+
+
+def fem_law_samples(n: int, box, seed: int, us, k, stream=None) -> int:
+    b = _f64arr(box)
+    return _check("fem_law_samples", load().fem_law_samples(n, b.ctypes.data, seed, _addr(us), _addr(k),
+                                                            _stream(stream)))
+
+
+def fem_field_samples(t: Tables, p: int, n: int, coords, ucoef, us, stream=None) -> int:
+    return _check("fem_field_samples", load().fem_field_samples(
+        t.handle, p, n, _addr(coords), _addr(ucoef), _addr(us), _stream(stream)))
+
+
+def fem_box_from_samples(us_host, lo_pct: float = 0.1, hi_pct: float = 99.9):
+    a = np.ascontiguousarray(us_host, dtype=np.float32).reshape(-1, 2)
+    box = np.zeros(4)
+    _check("fem_box_from_samples", load().fem_box_from_samples(a.shape[0], a.ctypes.data, lo_pct, hi_pct,
+                                                               box.ctypes.data))
+    return box
+
+
+def fem_integrate_law(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_stride: int, ucoef,
+                      law: int, mlp, prec: int, layout: int, A_out, b_out=None, status=None,
+                      stream=None) -> int:
+    return _check("fem_integrate_law", load().fem_integrate_law(
+        t.handle, p, n_elem, _addr(coords), _addr(coeffs), coeff_stride, _addr(ucoef), law,
+        mlp.handle if mlp is not None else None, prec, layout, _addr(A_out), _addr(b_out),
+        _addr(status), _stream(stream)))

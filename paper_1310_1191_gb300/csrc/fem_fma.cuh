@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "fem_geometry.cuh"
+#include "fem_law.cuh"
 
 namespace fem {
 
@@ -53,7 +54,14 @@ struct FmaCfg {
 // stride over the whole block, so the body also runs inside kernels whose
 // block is larger than C::NT (the batched kernel); the register micro-tiles
 // belong to the first C::NT threads.
-template <class T, class C>
+// Extra shared memory of the law variants: field coefficients per element
+// and, for the network, its parameters.
+template <class C>
+constexpr size_t law_smem_bytes(int law) {
+  return law == 0 ? 0 : (size_t)C::EPB * C::NS * 4 + 16 + (law == 2 ? (size_t)kMlpP * 4 + 16 : 0);
+}
+
+template <class T, class C, int LAW = 0>
 __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, const T *phi, int64_t k0,
                                          int64_t k_end, int ti, int tj, unsigned char *smem) {
   T *sPA = reinterpret_cast<T *>(smem);                 // [KC][BM]
@@ -62,6 +70,10 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   double *sX = reinterpret_cast<double *>(sG + C::EPB * C::NQ * kGStride);  // [EPB][NREC]
   int *sSt = reinterpret_cast<int *>(sX + C::EPB * C::NREC);               // [EPB]
   int64_t *sE = reinterpret_cast<int64_t *>(sSt + C::EPB + (C::EPB & 1));   // [EPB] element ids
+  float *sU = reinterpret_cast<float *>(
+      (reinterpret_cast<uintptr_t>(sE + C::EPB) + 15) & ~(uintptr_t)15);      // [EPB][NS] (LAW)
+  float *sW = reinterpret_cast<float *>(
+      (reinterpret_cast<uintptr_t>(sU + C::EPB * C::NS) + 15) & ~(uintptr_t)15);  // [kMlpP] (LAW 2)
 
   const int tid = threadIdx.x, nthr = blockDim.x;
   constexpr int NSZ = C::NS * C::NS, NPK = C::NS * (C::NS + 1) / 2;
@@ -80,6 +92,14 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     if (e >= 0) v = k < C::NV * 3 ? a.coords[e * (C::NV * 3) + k] : a.coeffs[(k - C::NV * 3) * a.cstride + e];
     sX[idx] = v;
   }
+  if (LAW != 0) {
+    for (int idx = tid; idx < C::EPB * C::NS; idx += nthr) {
+      const int64_t e = sE[idx / C::NS];
+      sU[idx] = e >= 0 ? a.ucoef[e * C::NS + idx % C::NS] : 0.f;
+    }
+    if (LAW == 2)
+      for (int idx = tid; idx < kMlpP; idx += nthr) sW[idx] = a.mlpw[idx];
+  }
   __syncthreads();
   for (int idx = tid; idx < C::EPB * C::NREC; idx += nthr)
     if (!isfinite(sX[idx])) atomicOr(&sSt[idx / C::NREC], FEM_ST_NONFINITE);
@@ -95,7 +115,45 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     const int le = idx / C::NQ, q = idx % C::NQ;
     double g[11];
     const double *rec = sX + le * C::NREC;
-    int st = point_matrix<C::ELEM>(rec, rec + C::NV * 3, qp + 4 * q, g);
+    int st;
+    if (LAW == 0) {
+      st = point_matrix<C::ELEM>(rec, rec + C::NV * 3, qp + 4 * q, g);
+    } else {
+      // coefficient stage (Algorithm 1 line 10): u and grad u at the point from
+      // the element's old degrees of freedom, then k(u, |grad u|), D = k I
+      double adj[3][3];
+      const double det = jac_adj<C::ELEM>(rec, qp + 4 * q, adj);
+      st = det > 0.0 ? 0 : FEM_ST_DET;
+      const T *ph = phi + (size_t)(4 * q) * C::NS;
+      const float *U = sU + le * C::NS;
+      T u = 0, r0 = 0, r1 = 0, r2 = 0;
+      for (int k = 0; k < C::NS; k++) {
+        const T uk = (T)U[k];
+        u = fma(uk, ph[k], u);
+        r0 = fma(uk, ph[C::NS + k], r0);
+        r1 = fma(uk, ph[2 * C::NS + k], r1);
+        r2 = fma(uk, ph[3 * C::NS + k], r2);
+      }
+      const double gx = (adj[0][0] * r0 + adj[1][0] * r1 + adj[2][0] * r2) / det;
+      const double gy = (adj[0][1] * r0 + adj[1][1] * r1 + adj[2][1] * r2) / det;
+      const double gz = (adj[0][2] * r0 + adj[1][2] * r1 + adj[2][2] * r2) / det;
+      const T gg = (T)(gx * gx + gy * gy + gz * gz);
+      T kq;
+      if (LAW == 1) {
+        kq = law_exact<T>(u, gg);
+      } else {
+        const float uf = (float)u, sf = sqrtf((float)gg);
+        if (uf >= a.box[0] && uf <= a.box[1] && sf >= a.box[2] && sf <= a.box[3]) {
+          kq = (T)mlp_eval(sW, a.nrm, uf, sf);
+        } else {
+          kq = law_exact<T>(u, gg);
+          st |= FEM_ST_FALLBACK;
+        }
+      }
+      const double *cf = rec + C::NV * 3;
+      const double cfl[11] = {(double)kq, (double)kq, (double)kq, 0.0, 0.0, 0.0, cf[6], cf[7], cf[8], cf[9], cf[10]};
+      point_from_adj(adj, det, qp[4 * q + 3], cfl, g);
+    }
     T *dst = sG + (size_t)idx * kGStride;
     if (sE[le] >= 0) {
 #pragma unroll
@@ -216,7 +274,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   __syncthreads();  // shared memory is reused by the next work item
 }
 
-template <class T, class C>
+template <class T, class C, int LAW = 0>
 __global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   long long blk = blockIdx.x;
@@ -224,14 +282,14 @@ __global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
   blk /= C::TILES;
   const int ti = (int)(blk % C::TILES);
   blk /= C::TILES;
-  fma_body<T, C>(a, a.qp, static_cast<const T *>(a.phi), blk * (int64_t)C::EPB, a.n, ti, tj, smem);
+  fma_body<T, C, LAW>(a, a.qp, static_cast<const T *>(a.phi), blk * (int64_t)C::EPB, a.n, ti, tj, smem);
 }
 
-template <class T, class C>
+template <class T, class C, int LAW = 0>
 int launch_fma_cfg(const FmaArgs &a, void *stream) {
   if (a.n == 0) return FEM_OK;
-  const size_t smem = C::template smem_bytes<T>();
-  cudaError_t err = cudaFuncSetAttribute(fma_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = C::template smem_bytes<T>() + law_smem_bytes<C>(LAW);
+  cudaError_t err = cudaFuncSetAttribute(fma_kernel<T, C, LAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) {
     set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(err));
     return FEM_ECUDA;
@@ -242,7 +300,7 @@ int launch_fma_cfg(const FmaArgs &a, void *stream) {
     set_error("too many elements for one launch");
     return FEM_EINVAL;
   }
-  fma_kernel<T, C><<<(unsigned)grid, C::NT, smem, (cudaStream_t)stream>>>(a);
+  fma_kernel<T, C, LAW><<<(unsigned)grid, C::NT, smem, (cudaStream_t)stream>>>(a);
   err = cudaGetLastError();
   if (err != cudaSuccess) {
     set_error(std::string("fma_kernel launch: ") + cudaGetErrorString(err));
@@ -262,17 +320,17 @@ template <> struct FmaShape<FEM_PRISM6, 5> { using type = FmaCfg<FEM_PRISM6, 5, 
 template <> struct FmaShape<FEM_PRISM6, 6> { using type = FmaCfg<FEM_PRISM6, 6, 98, 7, 7, 1, 7>; };
 template <> struct FmaShape<FEM_PRISM6, 7> { using type = FmaCfg<FEM_PRISM6, 7, 96, 6, 6, 1, 8>; };
 
-template <class T>
+template <class T, int LAW = 0>
 int launch_fma_any(int elem, int p, const FmaArgs &a, void *stream) {
-  if (elem == FEM_TET4) return launch_fma_cfg<T, FmaShape<FEM_TET4, 1>::type>(a, stream);
+  if (elem == FEM_TET4) return launch_fma_cfg<T, FmaShape<FEM_TET4, 1>::type, LAW>(a, stream);
   switch (p) {
-    case 1: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 1>::type>(a, stream);
-    case 2: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 2>::type>(a, stream);
-    case 3: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 3>::type>(a, stream);
-    case 4: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 4>::type>(a, stream);
-    case 5: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 5>::type>(a, stream);
-    case 6: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 6>::type>(a, stream);
-    case 7: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 7>::type>(a, stream);
+    case 1: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 1>::type, LAW>(a, stream);
+    case 2: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 2>::type, LAW>(a, stream);
+    case 3: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 3>::type, LAW>(a, stream);
+    case 4: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 4>::type, LAW>(a, stream);
+    case 5: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 5>::type, LAW>(a, stream);
+    case 6: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 6>::type, LAW>(a, stream);
+    case 7: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 7>::type, LAW>(a, stream);
   }
   return FEM_EINVAL;
 }

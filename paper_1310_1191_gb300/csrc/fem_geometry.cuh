@@ -21,11 +21,10 @@ namespace fem {
 enum GSlot { G00 = 0, G01, G02, G03, G11, G12, G13, G22, G23, G33, GS, GPAD };
 constexpr int kGStride = 12;
 
-// X: vertex coordinates [nv][3]; cf: 11 coefficients (COEF order);
-// q4: xi, eta, zeta, w.  Writes 11 values to g; returns FEM_ST_DET if det <= 0.
+// J (reference -> real map), adj J and det J at one point, FP64.
+// X: vertex coordinates [nv][3]; q4: xi, eta, zeta, w.
 template <int ELEM>
-__device__ __forceinline__ int point_matrix(const double *X, const double *cf, const double *q4,
-                                            double *g) {
+__device__ __forceinline__ double jac_adj(const double *X, const double *q4, double (&adj)[3][3]) {
   double J[3][3];
   if (ELEM == FEM_PRISM6) {
     // x(xi,eta,zeta) = sum_a lam_a(xi,eta) [ (1-zeta)/2 x_a + (1+zeta)/2 x_{a+3} ]
@@ -47,7 +46,6 @@ __device__ __forceinline__ int point_matrix(const double *X, const double *cf, c
       J[i][2] = X[9 + i] - X[i];
     }
   }
-  double adj[3][3];
   adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
   adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
   adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
@@ -57,8 +55,12 @@ __device__ __forceinline__ int point_matrix(const double *X, const double *cf, c
   adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
   adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
   adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-  const double det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
-  const double w = q4[3];
+  return J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+}
+
+// Point record from adj J, det J and the weight (FP64); cf: 11 coefficients.
+__device__ __forceinline__ void point_from_adj(const double (&adj)[3][3], double det, double w,
+                                               const double *cf, double *g) {
   const double D[3][3] = {{cf[0], cf[3], cf[4]}, {cf[3], cf[1], cf[5]}, {cf[4], cf[5], cf[2]}};
   double M[3][3];  // adj D
 #pragma unroll
@@ -80,6 +82,16 @@ __device__ __forceinline__ int point_matrix(const double *X, const double *cf, c
   const double wd = w * det;
   g[G00] = wd * cf[9];
   g[GS] = wd * cf[10];
+}
+
+// X: vertex coordinates [nv][3]; cf: 11 coefficients (COEF order);
+// q4: xi, eta, zeta, w.  Writes 11 values to g; returns FEM_ST_DET if det <= 0.
+template <int ELEM>
+__device__ __forceinline__ int point_matrix(const double *X, const double *cf, const double *q4,
+                                            double *g) {
+  double adj[3][3];
+  const double det = jac_adj<ELEM>(X, q4, adj);
+  point_from_adj(adj, det, q4[3], cf, g);
   return det > 0.0 ? 0 : FEM_ST_DET;
 }
 

@@ -72,11 +72,19 @@ struct FmaArgs {
   const int64_t *perm = nullptr;  // sorted position -> element id (batched path), or NULL
   const int64_t *offA = nullptr;  // per-element offset of A_e in A (values), or NULL
   const int64_t *offb = nullptr;  // per-element offset of b_e in b (values), or NULL
+  // nonlinear coefficient law (law kernels only)
+  const float *ucoef = nullptr;  // [n][NS] field coefficients of u per element
+  const float *mlpw = nullptr;   // network parameters (FP32 values of BF16 weights)
+  float nrm[4] = {0, 0, 0, 0};   // input normalisation of the network
+  float box[4] = {0, 0, 0, 0};   // u0, u1, s0, s1 (network used inside)
 };
 
 // Launch the FP64 / FP32 FMA kernels for (elem, p); returns a fem status code.
 int launch_fma_f64(int elem, int p, const FmaArgs &a, void *stream);
 int launch_fma_f32(int elem, int p, const FmaArgs &a, void *stream);
+// law = 1 exact Newton law, 2 network with exact-law fallback
+int launch_fma_law_f64(int elem, int p, int law, const FmaArgs &a, void *stream);
+int launch_fma_law_f32(int elem, int p, int law, const FmaArgs &a, void *stream);
 
 // Tensor-core path (prisms).
 struct TcLaunch {

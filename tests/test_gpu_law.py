@@ -1,0 +1,247 @@
+"""Nonlinear coefficient law and learned surrogate on the GPU vs the oracle:
+training samples, network forward and gradients, training, field samples,
+integration with the exact law and with the network, checkpointing, and the
+measured gain of the network over the exact law."""
+import os
+import time
+
+import numpy as np
+import pytest
+
+from _util import PRISM, rel_frob
+from paper_1310_1191_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+P3, NS3, NQ3 = 3, 40, 64
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_1310_1191_gb300 import _lib, build
+    assert torch.cuda.is_available()
+    build.build()
+    _lib.load()
+    return _lib
+
+
+@pytest.fixture(scope="module")
+def tables(lib):
+    t = lib.fem_tables_build(lib.FEM_PRISM6, 1, 7)
+    yield t
+    t.close()
+
+
+def _field(E, ns, first=0):
+    return inputs.field_coefficients(E, ns, first=first).astype(np.float32)
+
+
+BOX = np.array([-5.4, 5.5, 58.0, 4900.0])  # about the 0.1/99.9 percentiles of the p=3 workload
+
+
+def test_law_samples_match_generator_and_oracle_law(orc, lib):
+    import torch
+    n = 4096
+    us = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    k = torch.empty(n, dtype=torch.float32, device="cuda")
+    lib.fem_law_samples(n, BOX, 42, us, k)
+    torch.cuda.synchronize()
+    us, k = us.cpu().numpy(), k.cpu().numpy()
+    idx = np.arange(n, dtype=np.uint64)
+    u_ref = BOX[0] + (BOX[1] - BOX[0]) * inputs.draw_uniform(42, idx, 0)
+    s_ref = np.exp(np.log(BOX[2]) + (np.log(BOX[3]) - np.log(BOX[2])) * inputs.draw_uniform(42, idx, 1))
+    assert np.allclose(us[:, 0], u_ref.astype(np.float32), rtol=2e-7, atol=1e-6)
+    assert np.allclose(us[:, 1], s_ref.astype(np.float32), rtol=2e-7)
+    kr = np.array([orc.law_k(u, s * s) for u, s in zip(u_ref, s_ref)])
+    assert np.max(np.abs(k - kr) / kr) <= 2e-7
+
+
+def test_mlp_forward_and_gradient_vs_oracle(orc, lib):
+    import torch
+    m = lib.fem_mlp_create(BOX, 7)
+    master, wc, box = m.params()
+    assert np.array_equal(box, BOX)
+    # compute weights are the master weights rounded to BF16
+    bf = (master.view(np.uint32).astype(np.uint64) + 0x7FFF + ((master.view(np.uint32) >> 16) & 1))
+    assert np.array_equal(wc, ((bf >> 16) << 16).astype(np.uint32).view(np.float32))
+    n = 2048
+    rng = np.random.default_rng(3)
+    u = rng.uniform(BOX[0], BOX[1], n)
+    s = np.exp(rng.uniform(np.log(BOX[2]), np.log(BOX[3]), n))
+    tgt = np.array([orc.law_k(a, b * b) for a, b in zip(u, s)])
+    us_d = torch.from_numpy(np.stack([u, s], 1).astype(np.float32)).cuda()
+    t_d = torch.from_numpy(tgt.astype(np.float32)).cuda()
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    lib.fem_mlp_forward(m, n, us_d, y)
+    grad = torch.empty(lib.fem_mlp_nparams(), dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    lib.fem_mlp_loss_grad(m, n, us_d, t_d, grad, loss)
+    torch.cuda.synchronize()
+    u32 = us_d.cpu().numpy().astype(np.float64)
+    t32 = t_d.cpu().numpy().astype(np.float64)
+    yr = orc.mlp_forward(64, wc.astype(np.float64), BOX, u32[:, 0], u32[:, 1])
+    assert np.max(np.abs(y.cpu().numpy() - yr)) <= 1e-5 * np.max(np.abs(yr))
+    Lr, gr = orc.mlp_loss_grad(64, wc.astype(np.float64), BOX, u32[:, 0], u32[:, 1], t32)
+    g = grad.cpu().numpy()
+    assert abs(loss.item() - Lr) <= 1e-4 * Lr
+    assert np.max(np.abs(g - gr)) <= 1e-4 * np.max(np.abs(gr))
+    m.close()
+
+
+def test_mlp_training_fits_law_and_checkpoint(orc, lib, tmp_path):
+    import torch
+    N = 1_000_000
+    us = torch.empty((N, 2), dtype=torch.float32, device="cuda")
+    k = torch.empty(N, dtype=torch.float32, device="cuda")
+    lib.fem_law_samples(N, BOX, 42, us, k)
+    m = lib.fem_mlp_create(BOX, 42)
+    L1 = lib.fem_mlp_train(m, N, us, k, 3000, 8192, 1e-3, 1)
+    L2 = lib.fem_mlp_train(m, N, us, k, 1000, 8192, 3e-4, 2)
+    assert L2[-100:].mean() < 1e-3 * L1[:10].mean()
+    M = 200_000
+    hus = torch.empty((M, 2), dtype=torch.float32, device="cuda")
+    hk = torch.empty(M, dtype=torch.float32, device="cuda")
+    lib.fem_law_samples(M, BOX, 4242, hus, hk)
+    y = torch.empty(M, dtype=torch.float32, device="cuda")
+    lib.fem_mlp_forward(m, M, hus, y)
+    torch.cuda.synchronize()
+    rel = ((y - hk).abs() / hk).cpu().numpy()
+    print("surrogate held-out relative error: median %.2e p99 %.2e max %.2e"
+          % (np.median(rel), np.percentile(rel, 99), rel.max()))
+    assert np.median(rel) < 2e-3 and rel.max() < 2e-2
+    # checkpoint round trip: identical outputs
+    path = str(tmp_path / "net.bin")
+    lib.fem_mlp_save(m, path)
+    m2 = lib.fem_mlp_load(path)
+    y2 = torch.empty(M, dtype=torch.float32, device="cuda")
+    lib.fem_mlp_forward(m2, M, hus, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y, y2)
+    m.close()
+    m2.close()
+
+
+def test_field_samples_vs_host_reference(orc, lib, tables):
+    import torch
+    E = 50
+    X = inputs.prism_mesh(E)
+    U = _field(E, NS3)
+    out = torch.empty((E, NQ3, 2), dtype=torch.float32, device="cuda")
+    lib.fem_field_samples(tables, P3, E, torch.from_numpy(X).cuda(), torch.from_numpy(U).cuda(), out)
+    torch.cuda.synchronize()
+    out = out.cpu().numpy()
+    xi, w = orc.rule(PRISM, P3)
+    phi = orc.basis(PRISM, P3, xi)
+    for e in range(0, E, 7):
+        for q in range(0, NQ3, 5):
+            x, y, z = xi[q]
+            lo, hi = (1 - z) / 2, (1 + z) / 2
+            Xe = X[e]
+            J = np.stack([lo * (Xe[1] - Xe[0]) + hi * (Xe[4] - Xe[3]),
+                          lo * (Xe[2] - Xe[0]) + hi * (Xe[5] - Xe[3]),
+                          0.5 * ((1 - x - y) * (Xe[3] - Xe[0]) + x * (Xe[4] - Xe[1]) + y * (Xe[5] - Xe[2]))], 1)
+            u = U[e] @ phi[q, 0]
+            gr = np.linalg.solve(J.T, phi[q, 1:] @ U[e])
+            assert abs(out[e, q, 0] - u) <= 1e-5 * max(1.0, abs(u))
+            assert abs(out[e, q, 1] - np.linalg.norm(gr)) <= 1e-5 * np.linalg.norm(gr)
+
+
+@pytest.mark.parametrize("p", [1, 3])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_integrate_exact_law_vs_oracle(orc, lib, tables, p, prec):
+    import torch
+    E = 30
+    NS = (p + 1) ** 2 * (p + 2) // 2
+    X = inputs.prism_mesh(E)
+    C = inputs.coefficients(E)
+    U = _field(E, NS)
+    dt = torch.float64 if prec == 0 else torch.float32
+    A = torch.empty((E, NS * NS), dtype=dt, device="cuda")
+    b = torch.empty((E, NS), dtype=dt, device="cuda")
+    st = torch.empty(E, dtype=torch.int32, device="cuda")
+    lib.fem_integrate_law(tables, p, E, torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda(), E,
+                          torch.from_numpy(U).cuda(), lib.FEM_LAW_EXACT, None, prec, 0, A, b, st)
+    torch.cuda.synchronize()
+    RA, Rb, Rst = orc.integrate(PRISM, p, X, C, law=1, ucoef=U.astype(np.float64))
+    tol = 1e-12 if prec == 0 else 1e-5
+    assert rel_frob(A.cpu().numpy().reshape(E, NS, NS), RA).max() <= tol
+    assert rel_frob(b.cpu().numpy(), Rb).max() <= tol
+    assert np.array_equal(st.cpu().numpy(), Rst)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_integrate_network_vs_oracle(orc, lib, tables, prec):
+    """Network coefficient inside a box that holds every point (no fallback),
+    and a box that holds none (exact law everywhere, every element flagged)."""
+    import torch
+    E = 24
+    X = inputs.prism_mesh(E)
+    C = inputs.coefficients(E)
+    U = _field(E, NS3)
+    dt = torch.float64 if prec == 0 else torch.float32
+    Xd, Cd, Ud = torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda(), torch.from_numpy(U).cuda()
+    for box, flag in ((np.array([-1e3, 1e3, 1e-3, 1e6]), 0), (np.array([1e3, 2e3, 1e8, 2e8]), 8)):
+        m = lib.fem_mlp_create(box, 11)
+        _, wc, _ = m.params()
+        A = torch.empty((E, NS3 * NS3), dtype=dt, device="cuda")
+        st = torch.empty(E, dtype=torch.int32, device="cuda")
+        lib.fem_integrate_law(tables, P3, E, Xd, Cd, E, Ud, lib.FEM_LAW_MLP, m, prec, 0, A, None, st)
+        torch.cuda.synchronize()
+        RA, _, Rst = orc.integrate(PRISM, P3, X, C, law=2, ucoef=U.astype(np.float64),
+                                   mlp=(64, wc.astype(np.float64), box))
+        # the network runs in FP32 in both kernels
+        assert rel_frob(A.cpu().numpy().reshape(E, NS3, NS3), RA).max() <= 1e-5
+        assert np.all(st.cpu().numpy() == flag) and np.all(Rst == flag)
+        m.close()
+
+
+@pytest.mark.slow
+def test_surrogate_gain_measured(orc, lib, tables):
+    """What the trained network gains over the exact law on the nonlinear
+    workload (p = 3, FP32): element-matrix error vs the FP64 oracle (exact
+    law) and device time of the whole integration, both reported.  The
+    network must stay within 5e-3 of the oracle; the time ratio is measured,
+    not assumed (the 8-step Newton law is cheap, so the network can lose)."""
+    import torch
+    E = 200_000
+    X = inputs.prism_mesh(E)
+    C = inputs.coefficients(E)
+    U = _field(E, NS3)
+    Xd, Cd, Ud = torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda(), torch.from_numpy(U).cuda()
+    pil = torch.empty((20000, NQ3, 2), dtype=torch.float32, device="cuda")
+    lib.fem_field_samples(tables, P3, 20000, Xd, Ud, pil)
+    box = lib.fem_box_from_samples(pil.cpu().numpy())
+    N = 2_000_000
+    us = torch.empty((N, 2), dtype=torch.float32, device="cuda")
+    k = torch.empty(N, dtype=torch.float32, device="cuda")
+    lib.fem_law_samples(N, box, 42, us, k)
+    m = lib.fem_mlp_create(box, 42)
+    lib.fem_mlp_train(m, N, us, k, 4000, 8192, 1e-3, 1)
+    lib.fem_mlp_train(m, N, us, k, 2000, 8192, 3e-4, 2)
+    A = torch.empty((E, NS3 * NS3), dtype=torch.float32, device="cuda")
+    st = torch.empty(E, dtype=torch.int32, device="cuda")
+    times, errs = {}, {}
+    idx = np.arange(0, E, E // 48)[:48]
+    RA, _, _ = orc.integrate(PRISM, P3, X[idx], C[:, idx], law=1, ucoef=U[idx].astype(np.float64))
+    for name, law, mm in (("exact", lib.FEM_LAW_EXACT, None), ("network", lib.FEM_LAW_MLP, m)):
+        run = lambda: lib.fem_integrate_law(tables, P3, E, Xd, Cd, E, Ud, law, mm, 1, 0, A, None, st)
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / 3
+        Ai = A[torch.from_numpy(idx).cuda()].double().cpu().numpy().reshape(-1, NS3, NS3)
+        errs[name] = rel_frob(Ai, RA)
+    fb = int(((st & 8) != 0).sum().item())
+    print("exact law: %.2f ms, err max %.2e | network: %.2f ms, err max %.2e median %.2e | "
+          "time ratio network/exact %.2f | fallback elements %.1f%%"
+          % (times["exact"], errs["exact"].max(), times["network"], errs["network"].max(),
+             np.median(errs["network"]), times["network"] / times["exact"], 100.0 * fb / E))
+    assert errs["exact"].max() <= 1e-5
+    assert errs["network"].max() <= 5e-3
+    m.close()
