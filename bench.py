@@ -1,16 +1,24 @@
 """Benchmark: element matrices/s of the prism degree sweep (p = 1..7).
 
-One step integrates, for every degree p = 1..7, E_p jittered straight-edged
-prisms with random SPD diffusion, convection, reaction and source
-coefficients (E_p = round(2e9 / (8 (NS^2 + NS))), ~2 GB of FP64 output per
-degree), full non-symmetric A_e and b_e.  `value` is element matrices per
+Headline (`value`): one step integrates, for every degree p = 1..7, E_p
+jittered straight-edged prisms with random SPD diffusion, convection,
+reaction and source coefficients (E_p = round(2e9 / (8 (NS^2 + NS))), about
+2 GB of FP64 output per degree), full non-symmetric A_e and b_e, in FP64
+(--precision f32 for the FP32 kernels).  `value` is element matrices per
 second over the whole sweep (sum E_p / step time), device-timed with CUDA
-events, inputs resident in HBM; the L2 is flushed between timed steps.
+events on the launching stream, inputs resident in HBM, L2 flushed between
+timed steps.  `e2e` is the same sweep through the host-buffer entry point
+fem_integrate_host (pinned host inputs and outputs, copies inside the timed
+region).
 
-Lines printed (one JSON line from rank 0):
-  --impl ours (default): the CUDA library through its C ABI;
-  --impl reference: the FP64 CPU oracle on the host cores, on a bounded
-    per-degree sample of the same workload, extrapolated to the sweep.
+`workloads` (rank 0, unless --no-extras) reports the other workloads, each
+timed the same way: P1 tetrahedra, the FP32 sweep, the tensor-core BF16x3 /
+FP16x3 forms at p = 4..7 (errors against the GPU FP64 path), the 500k-prism
+mixed-degree mesh (graph + autotuned persistent launch vs per-degree loop),
+and the nonlinear-law workload with the exact law and the trained network.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+per-degree sample of the same sweep, extrapolated to the sweep.
 """
 from __future__ import annotations
 
@@ -33,9 +41,19 @@ from paper_1310_1191_gb300 import inputs  # noqa: E402
 SWEEP_E = {1: 5952381, 2: 730994, 3: 152439, 4: 43860, 5: 15623, 6: 6475, 7: 3004}
 # oracle sample per degree for the CPU baseline (~1-3 s of host work each)
 CPU_SAMPLE = {1: 400000, 2: 40000, 3: 4000, 4: 600, 5: 96, 6: 32, 7: 16}
-# nominal ALU peaks: 152 SMs x 2.07 GHz x lanes x 2 flops
-PEAK_F32 = 152 * 2.07e9 * 128 * 2 / 1e12   # 80.5 TFLOP/s
-PEAK_F64 = 1.25                            # TFLOP/s, GB300 FP64 (nominal)
+# ALU peaks derived from unit counts and clocks (152 SMs x 2.07 GHz):
+PEAK_F32 = 152 * 2.07e9 * 128 * 2 / 1e12   # 128 FP32 lanes per SM: 80.5 TFLOP/s
+PEAK_F64 = 152 * 2.07e9 * 2 * 2 / 1e12     # 2 FP64 FMA per SM per clock: 1.26 TFLOP/s
+HBM_FALLBACK, BF16_FALLBACK = 6800.0, 1900.0
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, BF16_FALLBACK, "fallback"
 
 
 def ns_of(p):
@@ -123,7 +141,7 @@ def cpu_baseline(sweep, sample=CPU_SAMPLE):
     t_total, desc = 0.0, []
     for p in sweep:
         n = min(sample[p], sweep[p])
-        X = inputs.prism_mesh(sweep[p])[:n] if n < sweep[p] else inputs.prism_mesh(sweep[p])
+        X = inputs.prism_mesh(sweep[p])[:n]
         C = inputs.coefficients(n)
         t0 = time.perf_counter()
         oracle.integrate(1, p, X, C)
@@ -142,11 +160,11 @@ def run_reference(args):
     if rank != 0:
         return
     sweep = dict(SWEEP_E)
-    samp = dict(CPU_SAMPLE)
     t0 = time.perf_counter()
     vals = []
+    cb = None
     for _ in range(max(1, args.steps)):
-        cb = cpu_baseline(sweep, samp)
+        cb = cpu_baseline(sweep)
         vals.append(cb["value"])
     el = time.perf_counter() - t0
     v = statistics.median(vals)
@@ -162,6 +180,252 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0},
             "wall_s": el}
     print(json.dumps(line), flush=True)
+
+
+def _timed(stream, fn, reps, warm=1):
+    """Device time (ms) per call of fn on stream: warm-up calls, then reps calls
+    bracketed by CUDA events."""
+    import torch
+    for _ in range(warm):
+        with torch.cuda.stream(stream):
+            fn()
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_sweep(lib, tables, sweep, data, prec, stream, steps, warmup, flush):
+    """Per-step and per-degree device times of the sweep."""
+    import torch
+
+    def step(events=None):
+        with torch.cuda.stream(stream):
+            for p, d in data.items():
+                if events is not None:
+                    events[p][0].record(stream)
+                lib.fem_integrate(tables, p, sweep[p], d["X"], d["C"], sweep[p], prec,
+                                  lib.FEM_OUT_FULL, d["A"], d["b"], d["st"], stream)
+                if events is not None:
+                    events[p][1].record(stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    per_p = {p: [] for p in sweep}
+    step_ms = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev = {p: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for p in sweep}
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        step(ev)
+        s1.record(stream)
+        s1.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+        for p in sweep:
+            per_p[p].append(ev[p][0].elapsed_time(ev[p][1]))
+    return step_ms, {p: statistics.mean(v) for p, v in per_p.items()}
+
+
+def per_degree_table(sweep, mean_p, osz, peak, hbm):
+    out = {}
+    for p in sweep:
+        t_s = mean_p[p] / 1e3
+        tf = flops_per_elem(p) * sweep[p] / t_s / 1e12
+        gbs = bytes_per_elem(p, osz) * sweep[p] / t_s / 1e9
+        t_roof = max(flops_per_elem(p) / (peak * 1e12), bytes_per_elem(p, osz) / (hbm * 1e9))
+        out[str(p)] = {"elements": sweep[p], "ms": round(mean_p[p], 4), "elem_per_s": sweep[p] / t_s,
+                       "tflops": round(tf, 3), "gbs": round(gbs, 1),
+                       "roofline_frac": round(t_roof * sweep[p] / t_s, 4)}
+    return out
+
+
+def make_sweep_data(sweep, dev, dt, host=None):
+    """Device inputs/outputs of the sweep; host arrays generated once and reused."""
+    import torch
+    data = {}
+    for p, E in sweep.items():
+        if host is not None and p in host:
+            X, C = host[p]
+        else:
+            X, C = inputs.prism_mesh(E), inputs.coefficients(E)
+            if host is not None:
+                host[p] = (X, C)
+        n = ns_of(p)
+        data[p] = dict(X=torch.from_numpy(X).to(dev), C=torch.from_numpy(C).to(dev),
+                       A=torch.empty((E, n * n), dtype=dt, device=dev),
+                       b=torch.empty((E, n), dtype=dt, device=dev),
+                       st=torch.empty((E,), dtype=torch.int32, device=dev), Xh=X, Ch=C)
+    return data
+
+
+def measure_e2e(lib, tables, sweep, data, prec, steps):
+    """The sweep through fem_integrate_host: pinned host inputs/outputs, copies
+    in the timed region."""
+    import torch
+    dt = torch.float64 if prec == lib.FEM_F64 else torch.float32
+    host = {}
+    h2d = d2h = 0
+    for p, d in data.items():
+        host[p] = dict(X=torch.from_numpy(d["Xh"]).pin_memory(),
+                       C=torch.from_numpy(d["Ch"]).pin_memory(),
+                       A=torch.empty(tuple(d["A"].shape), dtype=dt).pin_memory(),
+                       b=torch.empty(tuple(d["b"].shape), dtype=dt).pin_memory())
+        h2d += host[p]["X"].numel() * 8 + host[p]["C"].numel() * 8
+        d2h += (host[p]["A"].numel() + host[p]["b"].numel()) * host[p]["A"].element_size()
+    for p, h in host.items():  # warm-up (staging allocation)
+        lib.fem_integrate_host(tables, p, min(sweep[p], 1000), h["X"], h["C"], sweep[p], prec,
+                               lib.FEM_OUT_FULL, h["A"], h["b"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for p, h in host.items():
+            lib.fem_integrate_host(tables, p, sweep[p], h["X"], h["C"], sweep[p], prec,
+                                   lib.FEM_OUT_FULL, h["A"], h["b"])
+    el = time.perf_counter() - t0
+    return {"value": sum(sweep.values()) * steps / el, "unit": "element matrices/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
+            "path": "fem_integrate_host (C ABI, pinned host buffers, 2-slot copy/compute pipeline)"}
+
+
+# ---------------------------------------------------------------- other workloads
+
+def wl_tets(lib, stream, dev, reps):
+    import torch
+    X = inputs.tet_mesh(16)
+    E = X.shape[0]
+    C = inputs.coefficients(E, kind="laplace")
+    t = lib.fem_tables_build(lib.FEM_TET4, 1, 1)
+    Xd, Cd = torch.from_numpy(X).to(dev), torch.from_numpy(C).to(dev)
+    A = torch.empty((E, 16), dtype=torch.float64, device=dev)
+    b = torch.empty((E, 4), dtype=torch.float64, device=dev)
+    ms = _timed(stream, lambda: lib.fem_integrate(t, 1, E, Xd, Cd, E, 0, 0, A, b, None, stream), reps, 3)
+    vol = float(b.sum().item())
+    t.close()
+    return {"workload": "P1 tets, unit cube 16^3 x 6 = 24576 elements, Laplace, FP64",
+            "ms": round(ms, 4), "elem_per_s": E / ms * 1e3, "sum_b": vol}
+
+
+def wl_tensor(lib, tables, stream, dev, reps, bf16_peak):
+    """Tensor-core forms at p = 4..7, 200k prisms each; errors against the GPU
+    FP64 path (itself within 1e-12 of the oracle) on the first 512 elements."""
+    import torch
+    E = 200000
+    X = inputs.prism_mesh(E)
+    C = inputs.coefficients(E)
+    Xd, Cd = torch.from_numpy(X).to(dev), torch.from_numpy(C).to(dev)
+    out = {}
+    S = 512
+    for p in range(4, 8):
+        n = ns_of(p)
+        A64 = torch.empty((S, n * n), dtype=torch.float64, device=dev)
+        lib.fem_integrate(tables, p, S, Xd, Cd, E, 0, 0, A64, None, None, stream)
+        stream.synchronize()
+        ref = A64.view(S, n, n)
+        A = torch.empty((E, n * n), dtype=torch.float32, device=dev)
+        b = torch.empty((E, n), dtype=torch.float32, device=dev)
+        row = {}
+        for name, prec in (("bf16x3", lib.FEM_BF16X3), ("f16x3", lib.FEM_F16X3)):
+            ms = _timed(stream, lambda: lib.fem_integrate(tables, p, E, Xd, Cd, E, prec, 0, A, b, None,
+                                                          stream), reps)
+            err = ((A[:S].double().view(S, n, n) - ref).flatten(1).norm(dim=1) /
+                   ref.flatten(1).norm(dim=1)).cpu().numpy()
+            fl = 8.0 * nq_of(p) * n * n * E
+            row[name] = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3,
+                         "alg_tflops": round(fl / ms / 1e9, 1),
+                         "hw_tflops_x3": round(3 * fl / ms / 1e9, 1),
+                         "frac_of_bf16_peak_x3": round(3 * fl / ms / 1e9 / bf16_peak, 4),
+                         "err_max": float(err.max()), "err_median": float(np.median(err))}
+        ms32 = _timed(stream, lambda: lib.fem_integrate(tables, p, E, Xd, Cd, E, 1, 0, A, b, None,
+                                                        stream), 1)
+        row["f32_fma"] = {"ms": round(ms32, 3), "elem_per_s": E / ms32 * 1e3}
+        out[str(p)] = row
+        del A, b, A64
+        torch.cuda.empty_cache()
+    return {"workload": "prisms p=4..7, 200000 elements per degree, full A_e + b_e (FP32 out)",
+            "per_degree": out, "error_reference": "GPU FP64 path, first 512 elements"}
+
+
+def wl_batched(lib, tables, stream, dev, reps):
+    import torch
+    E = 500000
+    X = inputs.prism_mesh(E)
+    C = inputs.coefficients(E)
+    P = inputs.mixed_degrees(E)
+    Xd, Cd = torch.from_numpy(X).to(dev), torch.from_numpy(C).to(dev)
+    offA, offb, totA, totb = lib.fem_output_offsets(lib.FEM_PRISM6, P, 0)
+    A = torch.empty(totA, dtype=torch.float32, device=dev)
+    b = torch.empty(totb, dtype=torch.float32, device=dev)
+    res = {}
+    for name, flags in (("graph_autotuned", lib.FEM_PLAN_AUTOTUNE), ("per_degree_loop", lib.FEM_PLAN_LOOP)):
+        plan = lib.fem_plan_create(tables, P, lib.FEM_F32, 0, flags, None)
+        ms = _timed(stream, lambda: lib.fem_plan_execute(plan, Xd, Cd, E, A, b, None, stream), reps, 2)
+        res[name] = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3,
+                     "variants": [plan.variant(p)[0] for p in range(1, 8)]}
+        plan.close()
+    return {"workload": "500000 prisms, seeded degrees p=1..7 (weights .25 .2 .15 .15 .1 .1 .05), FP32",
+            "bins": np.bincount(P, minlength=8)[1:].tolist(), **res}
+
+
+def wl_surrogate(lib, tables, stream, dev, reps):
+    import torch
+    E, p, NS, NQ = 1000000, 3, 40, 64
+    X = inputs.prism_mesh(E)
+    C = inputs.coefficients(E)
+    U = inputs.field_coefficients(E, NS).astype(np.float32)
+    Xd, Cd, Ud = (torch.from_numpy(a).to(dev) for a in (X, C, U))
+    pil = torch.empty((20000, NQ, 2), dtype=torch.float32, device=dev)
+    lib.fem_field_samples(tables, p, 20000, Xd, Ud, pil, stream)
+    stream.synchronize()
+    box = lib.fem_box_from_samples(pil.cpu().numpy())
+    N = 10_000_000
+    us = torch.empty((N, 2), dtype=torch.float32, device=dev)
+    k = torch.empty(N, dtype=torch.float32, device=dev)
+    lib.fem_law_samples(N, box, inputs.SEED_SURROGATE, us, k, stream)
+    m = lib.fem_mlp_create(box, inputs.SEED_SURROGATE)
+    t0 = time.perf_counter()
+    L1 = lib.fem_mlp_train(m, N, us, k, 5000, 8192, 1e-3, 1, stream=stream)
+    L2 = lib.fem_mlp_train(m, N, us, k, 2000, 8192, 3e-4, 2, stream=stream)
+    train_s = time.perf_counter() - t0
+    A = torch.empty((E, NS * NS), dtype=torch.float32, device=dev)
+    b = torch.empty((E, NS), dtype=torch.float32, device=dev)
+    st = torch.empty(E, dtype=torch.int32, device=dev)
+    S = 256
+    A64 = torch.empty((S, NS * NS), dtype=torch.float64, device=dev)
+    lib.fem_integrate_law(tables, p, S, Xd, Cd, E, Ud, lib.FEM_LAW_EXACT, None, 0, 0, A64, None, None, stream)
+    stream.synchronize()
+    ref = A64.view(S, NS, NS)
+    res = {}
+    for name, fn in (
+            ("constant_D", lambda: lib.fem_integrate(tables, p, E, Xd, Cd, E, 1, 0, A, b, st, stream)),
+            ("exact_law", lambda: lib.fem_integrate_law(tables, p, E, Xd, Cd, E, Ud, lib.FEM_LAW_EXACT, None,
+                                                        1, 0, A, b, st, stream)),
+            ("network", lambda: lib.fem_integrate_law(tables, p, E, Xd, Cd, E, Ud, lib.FEM_LAW_MLP, m, 1, 0,
+                                                      A, b, st, stream))):
+        ms = _timed(stream, fn, reps)
+        row = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3}
+        if name != "constant_D":
+            err = ((A[:S].double().view(S, NS, NS) - ref).flatten(1).norm(dim=1) /
+                   ref.flatten(1).norm(dim=1)).cpu().numpy()
+            row.update(err_max=float(err.max()), err_median=float(np.median(err)))
+        if name == "network":
+            row["fallback_elements"] = int(((st & 8) != 0).sum().item())
+        res[name] = row
+    m.close()
+    return {"workload": "1000000 prisms p=3, FP32, D = k(u, |grad u|) I per point, 40 field "
+                        "coefficients per element", "box": [float(x) for x in box],
+            "training": {"samples": N, "steps": 7000, "batch": 8192, "seconds": round(train_s, 3),
+                         "loss_first": float(L1[:20].mean()), "loss_last": float(L2[-100:].mean())},
+            "error_reference": "GPU FP64 path with the exact law, first 256 elements",
+            "network_over_exact_time": round(res["network"]["ms"] / res["exact_law"]["ms"], 3), **res}
 
 
 def run_ours(args):
@@ -180,89 +444,56 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     _build.build()
     lib.load()
+    hbm, bf16_peak, peak_src = measured_peaks()
     prec = lib.FEM_F64 if args.precision == "f64" else lib.FEM_F32
     dt = torch.float64 if prec == lib.FEM_F64 else torch.float32
     osz = 8 if prec == lib.FEM_F64 else 4
     sweep = {p: (max(1, SWEEP_E[p] // args.scale_down)) for p in range(1, 8)}
     tables = lib.fem_tables_build(lib.FEM_PRISM6, 1, 7)
     stream = torch.cuda.Stream(device=dev)
-    data = {}
-    for p, E in sweep.items():
-        X = inputs.prism_mesh(E)
-        C = inputs.coefficients(E)
-        n = ns_of(p)
-        data[p] = dict(
-            X=torch.from_numpy(X).to(dev), C=torch.from_numpy(C).to(dev),
-            A=torch.empty((E, n * n), dtype=dt, device=dev),
-            b=torch.empty((E, n), dtype=dt, device=dev),
-            st=torch.empty((E,), dtype=torch.int32, device=dev), Xh=X, Ch=C)
+    host_inputs = {}
+    data = make_sweep_data(sweep, dev, dt, host_inputs)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def step(events=None):
-        with torch.cuda.stream(stream):
-            for p, d in data.items():
-                if events is not None:
-                    events[p][0].record(stream)
-                lib.fem_integrate(tables, p, sweep[p], d["X"], d["C"], sweep[p], prec,
-                                  lib.FEM_OUT_FULL, d["A"], d["b"], d["st"], stream)
-                if events is not None:
-                    events[p][1].record(stream)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    bad = sum(int((d["st"] != 0).sum().item()) for d in data.values())
-    per_p = {p: [] for p in sweep}
-    step_ms = []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(torch.cuda.current_device()) as clk:
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            ev = {p: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for p in sweep}
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s0.record(stream)
-            step(ev)
-            s1.record(stream)
-            s1.synchronize()
-            step_ms.append(s0.elapsed_time(s1))
-            for p in sweep:
-                per_p[p].append(ev[p][0].elapsed_time(ev[p][1]))
+        step_ms, mean_p = measure_sweep(lib, tables, sweep, data, prec, stream, args.steps,
+                                        args.warmup, flush)
     torch.cuda.synchronize()
+    bad = sum(int((d["st"] != 0).sum().item()) for d in data.values())
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         dist.barrier()
-        total_ms = t.item()
+        total_ms = tt.item()
     units = sum(sweep.values()) * args.steps * world
     value = units / (total_ms / 1e3)
 
-    # dominant kernel and its roofline
-    mean_p = {p: statistics.mean(v) for p, v in per_p.items()}
-    pdom = max(mean_p, key=mean_p.get)
-    fl = flops_per_elem(pdom) * sweep[pdom]
-    achieved = fl / (mean_p[pdom] / 1e3) / 1e12
     peak = PEAK_F64 if prec == lib.FEM_F64 else PEAK_F32
-    per_degree = {}
-    for p in sweep:
-        t_s = mean_p[p] / 1e3
-        tf = flops_per_elem(p) * sweep[p] / t_s / 1e12
-        gbs = bytes_per_elem(p, osz) * sweep[p] / t_s / 1e9
-        t_roof = max(flops_per_elem(p) / (peak * 1e12), bytes_per_elem(p, osz) / 6790.3e9)
-        per_degree[str(p)] = {"elements": sweep[p], "ms": round(mean_p[p], 4),
-                              "elem_per_s": sweep[p] / t_s, "tflops": round(tf, 3),
-                              "gbs": round(gbs, 1),
-                              "roofline_frac": round(t_roof * sweep[p] / t_s, 4)}
-
-    # end to end: host buffers in pinned memory, copies inside the timed region
+    pdom = max(mean_p, key=mean_p.get)
+    achieved = flops_per_elem(pdom) * sweep[pdom] / (mean_p[pdom] / 1e3) / 1e12
+    per_degree = per_degree_table(sweep, mean_p, osz, peak, hbm)
     e2e = None
     if not args.no_e2e:
-        e2e = measure_e2e(lib, tables, sweep, data, prec, dt, stream, args.e2e_steps)
-
+        e2e = measure_e2e(lib, tables, sweep, data, prec, args.e2e_steps)
+    workloads = {}
+    if rank == 0 and not args.no_extras:
+        del data
+        torch.cuda.empty_cache()
+        reps = 3
+        workloads["tets_f64"] = wl_tets(lib, stream, dev, reps)
+        if prec == lib.FEM_F64:
+            d32 = make_sweep_data(sweep, dev, torch.float32, host_inputs)
+            sm32, mp32 = measure_sweep(lib, tables, sweep, d32, lib.FEM_F32, stream, reps, 2, flush)
+            workloads["sweep_f32"] = {"elem_per_s": sum(sweep.values()) * reps / (sum(sm32) / 1e3),
+                                      "per_degree": per_degree_table(sweep, mp32, 4, PEAK_F32, hbm)}
+            del d32
+            torch.cuda.empty_cache()
+        workloads["tensor_core"] = wl_tensor(lib, tables, stream, dev, reps, bf16_peak)
+        workloads["mixed_degree"] = wl_batched(lib, tables, stream, dev, reps)
+        workloads["nonlinear_law"] = wl_surrogate(lib, tables, stream, dev, reps)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_baseline(sweep)
@@ -281,48 +512,19 @@ def run_ours(args):
             "gpu_launches": 7 * args.steps,
             "per_degree": per_degree,
             "roofline": {"bound": "alu", "kernel": "fma_kernel p=%d" % pdom,
-                         "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
-                         "frac": round(achieved / peak, 4), "traffic": None,
-                         "peak_source": "nominal %s ALU peak (unit counts x clock)" % args.precision},
+                         "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                         "frac": round(achieved / peak, 4),
+                         "traffic": None,
+                         "peak_source": "%s ALU peak derived from unit counts x 2.07 GHz; HBM %s %.0f GB/s"
+                                        % (args.precision, peak_src, hbm)},
             "flagged_elements": bad,
             "clocks": clocks,
-            "e2e": e2e, "cpu_baseline": cb,
+            "e2e": e2e, "cpu_baseline": cb, "workloads": workloads,
         }
         print(json.dumps(line), flush=True)
     tables.close()
     if world > 1:
         dist.destroy_process_group()
-
-
-def measure_e2e(lib, tables, sweep, data, prec, dt, stream, steps):
-    """Same sweep with host (pinned) inputs and outputs; H2D of the inputs and
-    D2H of A and b are inside the timed region."""
-    import torch
-    host = {}
-    h2d = d2h = 0
-    for p, d in data.items():
-        host[p] = dict(X=torch.from_numpy(d["Xh"]).pin_memory(), C=torch.from_numpy(d["Ch"]).pin_memory(),
-                       A=torch.empty(d["A"].shape, dtype=dt).pin_memory(),
-                       b=torch.empty(d["b"].shape, dtype=dt).pin_memory())
-        h2d += host[p]["X"].numel() * 8 + host[p]["C"].numel() * 8
-        d2h += host[p]["A"].numel() * host[p]["A"].element_size() + host[p]["b"].numel() * host[p]["b"].element_size()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        with torch.cuda.stream(stream):
-            for p, d in data.items():
-                h = host[p]
-                d["X"].copy_(h["X"], non_blocking=True)
-                d["C"].copy_(h["C"], non_blocking=True)
-                lib.fem_integrate(tables, p, sweep[p], d["X"], d["C"], sweep[p], prec,
-                                  lib.FEM_OUT_FULL, d["A"], d["b"], d["st"], stream)
-                h["A"].copy_(d["A"], non_blocking=True)
-                h["b"].copy_(d["b"], non_blocking=True)
-        stream.synchronize()
-    el = time.perf_counter() - t0
-    return {"value": sum(sweep.values()) * steps / el, "unit": "element matrices/s",
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
-            "path": "torch pinned copies around fem_integrate"}
 
 
 def main():
@@ -336,6 +538,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -113,6 +113,19 @@ int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, con
                   int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out,
                   int32_t *status, void *stream);
 
+/* The same integration for HOST buffers (the paper's host code stages element
+ * data to the device, runs the kernel and copies the matrices back, Section
+ * 4.2): the elements are processed in chunks of `chunk` elements (<= 0: about
+ * 256 MB of staging per chunk) through two pipeline slots on two library
+ * streams, so that the copies of one chunk overlap the kernel of the other.
+ * Host buffers should be page-locked for the copies to overlap.  Layouts as in
+ * fem_integrate but in host memory; b_out and status nullable.  Synchronous:
+ * returns when every result is in host memory.  The staging buffers are owned
+ * by the tables handle (allocated on first use, grown when needed). */
+int fem_integrate_host(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
+                       int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out, int32_t *status,
+                       int64_t chunk);
+
 /* Device error word of the tables' kernels: FEM_ETIMEOUT if a bounded wait
  * inside a tensor-core launch expired since the last clear (the affected
  * elements also carry FEM_ST_TIMEOUT), else FEM_OK.  Synchronises the device.

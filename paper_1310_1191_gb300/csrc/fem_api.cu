@@ -9,6 +9,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -44,6 +45,12 @@ static void free_tables(fem_tables t) {
   for (int p = 0; p <= kMaxP; p++) free_table(t->tab[p]);
   if (t->d_err) cudaFree(t->d_err);
   t->d_err = nullptr;
+  for (int i = 0; i < 2; i++) {
+    if (t->stage[i]) cudaFree(t->stage[i]);
+    if (t->hs[i]) cudaStreamDestroy(t->hs[i]);
+    t->stage[i] = nullptr;
+    t->hs[i] = nullptr;
+  }
 }
 
 template <class T>
@@ -235,6 +242,80 @@ int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, con
       return launch_tc(p, prec == FEM_F16X3, d, l, stream);
     }
   }
+}
+
+int fem_integrate_host(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
+                       int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out, int32_t *status,
+                       int64_t chunk) {
+  if (!t) return invalid("fem_integrate_host: tables handle is NULL");
+  if (p < t->p_min || p > t->p_max || n_elem < 0) return invalid("fem_integrate_host: bad degree or n_elem");
+  if (n_elem == 0) return FEM_OK;
+  if (!coords || !coeffs || !A_out || coeff_stride < n_elem)
+    return invalid("fem_integrate_host: NULL buffer or coeff_stride < n_elem");
+  const int64_t m = fem_matrix_size(t->elem, p, layout);
+  if (m < 0) return invalid("fem_integrate_host: unknown layout");
+  const int nv = nv_of(t->elem), ns = ns_of(t->elem, p);
+  const size_t osz = prec == FEM_F64 ? 8 : 4;
+  // per element: coords, 11 coefficients, A, b, status; staging rounded to 256 B per array
+  const size_t per = (size_t)nv * 3 * 8 + 11 * 8 + (size_t)m * osz + (size_t)ns * osz + 4;
+  if (chunk <= 0) chunk = std::max<int64_t>(1, (int64_t)((size_t)256 << 20) / (int64_t)per);
+  if (chunk > n_elem) chunk = n_elem;
+  const size_t need = (size_t)chunk * per + 5 * 256;
+  if (t->stage_bytes < need) {
+    for (int i = 0; i < 2; i++) {
+      if (t->stage[i]) cudaFree(t->stage[i]);
+      t->stage[i] = nullptr;
+      cudaError_t e = cudaMalloc((void **)&t->stage[i], need);
+      if (e != cudaSuccess) {
+        t->stage_bytes = 0;
+        return cuda_fail("fem_integrate_host: staging allocation", e);
+      }
+    }
+    t->stage_bytes = need;
+  }
+  for (int i = 0; i < 2; i++)
+    if (!t->hs[i]) {
+      cudaError_t e = cudaStreamCreateWithFlags(&t->hs[i], cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail("fem_integrate_host: stream", e);
+    }
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t oX = 0, oC = al(oX + (size_t)chunk * nv * 3 * 8), oA = al(oC + (size_t)chunk * 11 * 8),
+               oB = al(oA + (size_t)chunk * m * osz), oS = al(oB + (size_t)chunk * ns * osz);
+  int rc = FEM_OK;
+  int64_t k = 0;
+  for (int64_t e0 = 0; e0 < n_elem && rc == FEM_OK; e0 += chunk, k++) {
+    const int64_t c = std::min<int64_t>(chunk, n_elem - e0);
+    const int slot = (int)(k & 1);
+    cudaStream_t s = t->hs[slot];
+    unsigned char *st = t->stage[slot];
+    double *dX = reinterpret_cast<double *>(st + oX);
+    double *dC = reinterpret_cast<double *>(st + oC);
+    // the slot's previous chunk finished its copies before these are queued (same stream)
+    cudaError_t e = cudaMemcpyAsync(dX, coords + e0 * nv * 3, (size_t)c * nv * 3 * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(dC, (size_t)c * 8, coeffs + e0, (size_t)coeff_stride * 8, (size_t)c * 8, 11,
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      rc = cuda_fail("fem_integrate_host: copy in", e);
+      break;
+    }
+    rc = fem_integrate(t, p, c, dX, dC, c, prec, layout, st + oA, b_out ? st + oB : nullptr,
+                       status ? reinterpret_cast<int32_t *>(st + oS) : nullptr, s);
+    if (rc != FEM_OK) break;
+    e = cudaMemcpyAsync(static_cast<unsigned char *>(A_out) + (size_t)e0 * m * osz, st + oA, (size_t)c * m * osz,
+                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && b_out)
+      e = cudaMemcpyAsync(static_cast<unsigned char *>(b_out) + (size_t)e0 * ns * osz, st + oB, (size_t)c * ns * osz,
+                          cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && status)
+      e = cudaMemcpyAsync(status + e0, st + oS, (size_t)c * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) rc = cuda_fail("fem_integrate_host: copy out", e);
+  }
+  for (int i = 0; i < 2; i++) {
+    cudaError_t e = cudaStreamSynchronize(t->hs[i]);
+    if (e != cudaSuccess && rc == FEM_OK) rc = cuda_fail("fem_integrate_host: synchronize", e);
+  }
+  return rc;
 }
 
 }  // extern "C"

@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "fem.h"
 
 namespace fem {
@@ -50,6 +52,10 @@ struct fem_tables_s {
   int elem = 0, p_min = 0, p_max = 0, device = 0;
   int *d_err = nullptr;  // device error word (bounded waits that expired)
   fem::DevTable tab[fem::kMaxP + 1];
+  // staging for host-buffer integration (two pipeline slots)
+  unsigned char *stage[2] = {nullptr, nullptr};
+  size_t stage_bytes = 0;
+  cudaStream_t hs[2] = {nullptr, nullptr};
 };
 
 namespace fem {

@@ -172,3 +172,25 @@ def test_prism_parity_full_size_sampled(orc, prism_tables, p, prec):
     RA, Rb, _ = orc.integrate(PRISM, p, X[idx], C[:, idx])
     assert rel_frob(Ai, RA).max() <= TOL[prec]
     assert rel_frob(bi, Rb).max() <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_integrate_host_buffers(orc, lib, prism_tables, prec):
+    """fem_integrate_host (host buffers, chunked copy/compute pipeline with a
+    ragged last chunk) gives the device path's results."""
+    import torch
+    p, E = 3, 301
+    X, C = workload(PRISM, p, E)
+    n = ns(PRISM, p)
+    dt = torch.float64 if prec == 0 else torch.float32
+    Ah = torch.empty((E, n * n), dtype=dt).pin_memory()
+    bh = torch.empty((E, n), dtype=dt).pin_memory()
+    sh = torch.empty((E,), dtype=torch.int32).pin_memory()
+    Xh = torch.from_numpy(X).pin_memory()
+    Ch = torch.from_numpy(C).pin_memory()
+    lib.fem_integrate_host(prism_tables, p, E, Xh, Ch, E, prec, 0, Ah, bh, sh, chunk=37)
+    A, b, st = gpu_integrate(prism_tables, PRISM, p, X, C, prec)
+    assert np.array_equal(Ah.numpy(), A) and np.array_equal(bh.numpy(), b)
+    assert np.array_equal(sh.numpy(), st)
+    RA, Rb, _ = orc.integrate(PRISM, p, X, C)
+    assert rel_frob(Ah.numpy().reshape(E, n, n), RA).max() <= TOL[prec]
