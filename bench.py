@@ -40,7 +40,7 @@ from paper_1310_1191_gb300 import inputs  # noqa: E402
 
 SWEEP_E = {1: 5952381, 2: 730994, 3: 152439, 4: 43860, 5: 15623, 6: 6475, 7: 3004}
 # oracle sample per degree for the CPU baseline (~1-3 s of host work each)
-CPU_SAMPLE = {1: 400000, 2: 40000, 3: 4000, 4: 600, 5: 96, 6: 32, 7: 16}
+CPU_SAMPLE = {1: 200000, 2: 20000, 3: 2000, 4: 300, 5: 48, 6: 16, 7: 16}
 # ALU peaks derived from unit counts and clocks (152 SMs x 2.07 GHz):
 PEAK_F32 = 152 * 2.07e9 * 128 * 2 / 1e12   # 128 FP32 lanes per SM: 80.5 TFLOP/s
 PEAK_F64 = 152 * 2.07e9 * 2 * 2 / 1e12     # 2 FP64 FMA per SM per clock: 1.26 TFLOP/s
