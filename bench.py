@@ -45,6 +45,9 @@ CPU_SAMPLE = {1: 200000, 2: 20000, 3: 2000, 4: 300, 5: 48, 6: 16, 7: 16}
 PEAK_F32 = 152 * 2.07e9 * 128 * 2 / 1e12   # 128 FP32 lanes per SM: 80.5 TFLOP/s
 PEAK_F64 = 152 * 2.07e9 * 2 * 2 / 1e12     # 2 FP64 FMA per SM per clock: 1.26 TFLOP/s
 HBM_FALLBACK, BF16_FALLBACK = 6800.0, 1900.0
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture of the full-size launch (profiles/fma_kernel_f64_p7_traffic.md)
+TRAFFIC = {("f64", 7): 51.51e6 + 1.96e9}
 
 
 def measured_peaks():
@@ -514,7 +517,7 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": "fma_kernel p=%d" % pdom,
                          "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
                          "frac": round(achieved / peak, 4),
-                         "traffic": None,
+                         "traffic": TRAFFIC.get((args.precision, pdom)),
                          "peak_source": "%s ALU peak derived from unit counts x 2.07 GHz; HBM %s %.0f GB/s"
                                         % (args.precision, peak_src, hbm)},
             "flagged_elements": bad,
