@@ -317,17 +317,16 @@ def wl_tets(lib, stream, dev, reps):
             "ms": round(ms, 4), "elem_per_s": E / ms * 1e3, "sum_b": vol}
 
 
-def wl_tensor(lib, tables, stream, dev, reps, bf16_peak):
+def wl_tensor(lib, tables, stream, dev, reps, bf16_peak, E=200000, degrees=(4, 5, 6, 7)):
     """Tensor-core forms at p = 4..7, 200k prisms each; errors against the GPU
     FP64 path (itself within 1e-12 of the oracle) on the first 512 elements."""
     import torch
-    E = 200000
     X = inputs.prism_mesh(E)
     C = inputs.coefficients(E)
     Xd, Cd = torch.from_numpy(X).to(dev), torch.from_numpy(C).to(dev)
     out = {}
-    S = 512
-    for p in range(4, 8):
+    S = min(512, E)
+    for p in degrees:
         n = ns_of(p)
         A64 = torch.empty((S, n * n), dtype=torch.float64, device=dev)
         lib.fem_integrate(tables, p, S, Xd, Cd, E, 0, 0, A64, None, None, stream)
@@ -357,9 +356,8 @@ def wl_tensor(lib, tables, stream, dev, reps, bf16_peak):
             "per_degree": out, "error_reference": "GPU FP64 path, first 512 elements"}
 
 
-def wl_batched(lib, tables, stream, dev, reps):
+def wl_batched(lib, tables, stream, dev, reps, E=500000):
     import torch
-    E = 500000
     X = inputs.prism_mesh(E)
     C = inputs.coefficients(E)
     P = inputs.mixed_degrees(E)
@@ -378,9 +376,9 @@ def wl_batched(lib, tables, stream, dev, reps):
             "bins": np.bincount(P, minlength=8)[1:].tolist(), **res}
 
 
-def wl_surrogate(lib, tables, stream, dev, reps):
+def wl_surrogate(lib, tables, stream, dev, reps, E=1000000):
     import torch
-    E, p, NS, NQ = 1000000, 3, 40, 64
+    p, NS, NQ = 3, 40, 64
     X = inputs.prism_mesh(E)
     C = inputs.coefficients(E)
     U = inputs.field_coefficients(E, NS).astype(np.float32)
@@ -429,6 +427,44 @@ def wl_surrogate(lib, tables, stream, dev, reps):
                          "loss_first": float(L1[:20].mean()), "loss_last": float(L2[-100:].mean())},
             "error_reference": "GPU FP64 path with the exact law, first 256 elements",
             "network_over_exact_time": round(res["network"]["ms"] / res["exact_law"]["ms"], 3), **res}
+
+
+def run_only(args):
+    """One workload alone (for profiling and quick checks); prints its JSON."""
+    import torch
+
+    from paper_1310_1191_gb300 import _lib as lib
+    from paper_1310_1191_gb300 import build as _build
+    _build.build()
+    lib.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    hbm, bf16_peak, _ = measured_peaks()
+    tables = lib.fem_tables_build(lib.FEM_PRISM6, 1, 7)
+    reps = args.steps
+    if args.only == "tets":
+        out = wl_tets(lib, stream, dev, reps)
+    elif args.only == "tc":
+        degs = tuple(int(x) for x in args.degrees.split(",")) if args.degrees else (4, 5, 6, 7)
+        out = wl_tensor(lib, tables, stream, dev, reps, bf16_peak, E=args.elements or 200000, degrees=degs)
+    elif args.only == "mixed":
+        out = wl_batched(lib, tables, stream, dev, reps, E=args.elements or 500000)
+    elif args.only == "law":
+        out = wl_surrogate(lib, tables, stream, dev, reps, E=args.elements or 1000000)
+    else:  # sweep at one precision
+        prec = lib.FEM_F64 if args.precision == "f64" else lib.FEM_F32
+        dt = torch.float64 if prec == lib.FEM_F64 else torch.float32
+        sweep = {p: (max(1, SWEEP_E[p] // args.scale_down)) for p in range(1, 8)}
+        if args.degrees:
+            sweep = {p: sweep[p] for p in (int(x) for x in args.degrees.split(","))}
+        data = make_sweep_data(sweep, dev, dt)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        step_ms, mean_p = measure_sweep(lib, tables, sweep, data, prec, stream, reps, args.warmup, flush)
+        peak = PEAK_F64 if prec == lib.FEM_F64 else PEAK_F32
+        out = {"elem_per_s": sum(sweep.values()) * reps / (sum(step_ms) / 1e3),
+               "per_degree": per_degree_table(sweep, mean_p, 8 if prec == lib.FEM_F64 else 4, peak, hbm)}
+    print(json.dumps({"only": args.only, "result": out}), flush=True)
+    tables.close()
 
 
 def run_ours(args):
@@ -542,8 +578,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--only", choices=["sweep", "tets", "tc", "mixed", "law"],
+                    help="run one workload alone (profiling); prints its own JSON")
+    ap.add_argument("--elements", type=int, default=0, help="elements for --only tc/mixed/law")
+    ap.add_argument("--degrees", default="", help="comma-separated degrees for --only sweep/tc")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.only:
+        run_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -38,13 +38,14 @@ struct FmaCfg {
   static constexpr int TILES = (NS + BM - 1) / BM;
   static constexpr int QC = QC_, KC = 4 * QC, NCH = (NQ + QC - 1) / QC;
   static constexpr int NREC = NV * 3 + 11;  // coords + coefficients per element
+  static constexpr int NEDGE = kEdgeRec;    // FP64 edge record per element
   static_assert(BM % TM == 0 && BN % TN == 0, "tile must split into micro-tiles");
   static_assert(NT <= 1024, "too many threads");
 
   template <class T>
   static constexpr size_t smem_bytes() {
     return sizeof(T) * ((size_t)KC * BM + (size_t)EPB * KC * BN + (size_t)EPB * NQ * kGStride) +
-           sizeof(double) * (size_t)EPB * NREC + sizeof(int) * (size_t)(EPB + 1) +
+           sizeof(double) * (size_t)EPB * (NREC + NEDGE) + sizeof(int) * (size_t)(EPB + 1) +
            sizeof(int64_t) * (size_t)EPB + 64;
   }
 };
@@ -54,6 +55,42 @@ struct FmaCfg {
 // stride over the whole block, so the body also runs inside kernels whose
 // block is larger than C::NT (the batched kernel); the register micro-tiles
 // belong to the first C::NT threads.
+constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
+
+// N consecutive values from shared memory; ALIGN = a number of elements that
+// divides the offset of p from a 16-byte aligned base.  Uses 16- or 8-byte
+// loads when the alignment allows.
+template <class T, int N, int ALIGN>
+__device__ __forceinline__ void lds_vec(const T *p, T (&v)[N]) {
+  if constexpr (sizeof(T) == 4 && N % 4 == 0 && ALIGN % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 4; i++) {
+      const float4 x = reinterpret_cast<const float4 *>(p)[i];
+      v[4 * i] = x.x;
+      v[4 * i + 1] = x.y;
+      v[4 * i + 2] = x.z;
+      v[4 * i + 3] = x.w;
+    }
+  } else if constexpr (sizeof(T) == 4 && N % 2 == 0 && ALIGN % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 2; i++) {
+      const float2 x = reinterpret_cast<const float2 *>(p)[i];
+      v[2 * i] = x.x;
+      v[2 * i + 1] = x.y;
+    }
+  } else if constexpr (sizeof(T) == 8 && N % 2 == 0 && ALIGN % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 2; i++) {
+      const double2 x = reinterpret_cast<const double2 *>(p)[i];
+      v[2 * i] = x.x;
+      v[2 * i + 1] = x.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i++) v[i] = p[i];
+  }
+}
+
 // Extra shared memory of the law variants: field coefficients per element
 // and, for the network, its parameters.
 template <class C>
@@ -68,7 +105,8 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   T *sT = sPA + C::KC * C::BM;                          // [EPB][KC][BN]
   T *sG = sT + C::EPB * C::KC * C::BN;                  // [EPB][NQ][kGStride]
   double *sX = reinterpret_cast<double *>(sG + C::EPB * C::NQ * kGStride);  // [EPB][NREC]
-  int *sSt = reinterpret_cast<int *>(sX + C::EPB * C::NREC);               // [EPB]
+  double *sEd = sX + C::EPB * C::NREC;                                     // [EPB][NEDGE]
+  int *sSt = reinterpret_cast<int *>(sEd + C::EPB * C::NEDGE);             // [EPB]
   int64_t *sE = reinterpret_cast<int64_t *>(sSt + C::EPB + (C::EPB & 1));   // [EPB] element ids
   float *sU = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(sE + C::EPB) + 15) & ~(uintptr_t)15);      // [EPB][NS] (LAW)
@@ -103,6 +141,8 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   __syncthreads();
   for (int idx = tid; idx < C::EPB * C::NREC; idx += nthr)
     if (!isfinite(sX[idx])) atomicOr(&sSt[idx / C::NREC], FEM_ST_NONFINITE);
+  for (int le = tid; le < C::EPB; le += nthr) edge_record<C::ELEM>(sX + le * C::NREC, sEd + le * C::NEDGE);
+  __syncthreads();
   if (a.layout == FEM_OUT_SYMPACKED) {
     for (int le = tid; le < C::EPB; le += nthr) {
       const double *cf = sX + le * C::NREC + C::NV * 3;
@@ -117,12 +157,22 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     const double *rec = sX + le * C::NREC;
     int st;
     if (LAW == 0) {
-      st = point_matrix<C::ELEM>(rec, rec + C::NV * 3, qp + 4 * q, g);
+      double adj[3][3];
+      const double det = jac_adj_edges<C::ELEM>(sEd + le * C::NEDGE, qp + 4 * q, adj);
+      st = det > 0.0 ? 0 : FEM_ST_DET;
+      if (sizeof(T) == 4) {  // FP32 contraction: G products in FP32
+        float gf[11];
+        point_from_adj_f32(adj, det, qp[4 * q + 3], rec + C::NV * 3, gf);
+#pragma unroll
+        for (int k = 0; k < 11; k++) g[k] = gf[k];
+      } else {
+        point_from_adj(adj, det, qp[4 * q + 3], rec + C::NV * 3, g);
+      }
     } else {
       // coefficient stage (Algorithm 1 line 10): u and grad u at the point from
       // the element's old degrees of freedom, then k(u, |grad u|), D = k I
       double adj[3][3];
-      const double det = jac_adj<C::ELEM>(rec, qp + 4 * q, adj);
+      const double det = jac_adj_edges<C::ELEM>(sEd + le * C::NEDGE, qp + 4 * q, adj);
       st = det > 0.0 ? 0 : FEM_ST_DET;
       const T *ph = phi + (size_t)(4 * q) * C::NS;
       const float *U = sU + le * C::NS;
@@ -206,13 +256,14 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     if (owner) {
       const T *pa = sPA + ty * C::TM;
       const T *pb = sT + (size_t)le * C::KC * C::BN + tx * C::TN;
+      // element offsets of the operands from the 16-byte aligned shared base
+      constexpr int ALA = cgcd(C::BM, C::TM);
+      constexpr int ALB = cgcd(cgcd(C::KC * C::BM, C::KC * C::BN), cgcd(C::BN, C::TN));
 #pragma unroll 4
       for (int k = 0; k < C::KC; k++) {
         T av[C::TM], bv[C::TN];
-#pragma unroll
-        for (int i = 0; i < C::TM; i++) av[i] = pa[k * C::BM + i];
-#pragma unroll
-        for (int j = 0; j < C::TN; j++) bv[j] = pb[k * C::BN + j];
+        lds_vec<T, C::TM, ALA>(pa + k * C::BM, av);
+        lds_vec<T, C::TN, ALB>(pb + k * C::BN, bv);
 #pragma unroll
         for (int i = 0; i < C::TM; i++)
 #pragma unroll
@@ -309,28 +360,39 @@ int launch_fma_cfg(const FmaArgs &a, void *stream) {
   return FEM_OK;
 }
 
-// Tile shapes per degree (ELEM, P, BM, TM, TN, EPB, QC).
-template <int ELEM, int P> struct FmaShape;
-template <> struct FmaShape<FEM_TET4, 1> { using type = FmaCfg<FEM_TET4, 1, 4, 1, 4, 64, 4>; };
-template <> struct FmaShape<FEM_PRISM6, 1> { using type = FmaCfg<FEM_PRISM6, 1, 6, 1, 6, 42, 4>; };
-template <> struct FmaShape<FEM_PRISM6, 2> { using type = FmaCfg<FEM_PRISM6, 2, 18, 3, 6, 14, 3>; };
-template <> struct FmaShape<FEM_PRISM6, 3> { using type = FmaCfg<FEM_PRISM6, 3, 40, 4, 4, 2, 8>; };
-template <> struct FmaShape<FEM_PRISM6, 4> { using type = FmaCfg<FEM_PRISM6, 4, 75, 5, 5, 1, 5>; };
-template <> struct FmaShape<FEM_PRISM6, 5> { using type = FmaCfg<FEM_PRISM6, 5, 126, 6, 6, 1, 6>; };
-template <> struct FmaShape<FEM_PRISM6, 6> { using type = FmaCfg<FEM_PRISM6, 6, 98, 7, 7, 1, 7>; };
-template <> struct FmaShape<FEM_PRISM6, 7> { using type = FmaCfg<FEM_PRISM6, 7, 96, 6, 6, 1, 8>; };
+// Tile shapes per precision and degree (ELEM, P, BM, TM, TN, EPB, QC).  FP64
+// is bound by the FP64 pipe, so its shapes only need enough independent FMAs;
+// FP32 is bound by instruction issue, so its micro-tiles are larger and their
+// rows 16-byte aligned for vector shared loads.
+template <class T, int ELEM, int P> struct FmaShape;
+template <> struct FmaShape<double, FEM_TET4, 1> { using type = FmaCfg<FEM_TET4, 1, 4, 1, 4, 64, 4>; };
+template <> struct FmaShape<double, FEM_PRISM6, 1> { using type = FmaCfg<FEM_PRISM6, 1, 6, 1, 6, 42, 4>; };
+template <> struct FmaShape<double, FEM_PRISM6, 2> { using type = FmaCfg<FEM_PRISM6, 2, 18, 3, 6, 14, 3>; };
+template <> struct FmaShape<double, FEM_PRISM6, 3> { using type = FmaCfg<FEM_PRISM6, 3, 40, 4, 4, 2, 8>; };
+template <> struct FmaShape<double, FEM_PRISM6, 4> { using type = FmaCfg<FEM_PRISM6, 4, 75, 5, 5, 1, 5>; };
+template <> struct FmaShape<double, FEM_PRISM6, 5> { using type = FmaCfg<FEM_PRISM6, 5, 126, 6, 6, 1, 6>; };
+template <> struct FmaShape<double, FEM_PRISM6, 6> { using type = FmaCfg<FEM_PRISM6, 6, 98, 7, 7, 1, 7>; };
+template <> struct FmaShape<double, FEM_PRISM6, 7> { using type = FmaCfg<FEM_PRISM6, 7, 96, 6, 6, 1, 8>; };
+template <> struct FmaShape<float, FEM_TET4, 1> { using type = FmaCfg<FEM_TET4, 1, 4, 1, 4, 64, 4>; };
+template <> struct FmaShape<float, FEM_PRISM6, 1> { using type = FmaCfg<FEM_PRISM6, 1, 6, 1, 6, 42, 4>; };
+template <> struct FmaShape<float, FEM_PRISM6, 2> { using type = FmaCfg<FEM_PRISM6, 2, 18, 6, 6, 28, 3>; };
+template <> struct FmaShape<float, FEM_PRISM6, 3> { using type = FmaCfg<FEM_PRISM6, 3, 40, 8, 8, 8, 4>; };
+template <> struct FmaShape<float, FEM_PRISM6, 4> { using type = FmaCfg<FEM_PRISM6, 4, 80, 8, 8, 2, 4>; };
+template <> struct FmaShape<float, FEM_PRISM6, 5> { using type = FmaCfg<FEM_PRISM6, 5, 128, 8, 8, 1, 8>; };
+template <> struct FmaShape<float, FEM_PRISM6, 6> { using type = FmaCfg<FEM_PRISM6, 6, 104, 8, 8, 1, 8>; };
+template <> struct FmaShape<float, FEM_PRISM6, 7> { using type = FmaCfg<FEM_PRISM6, 7, 96, 6, 6, 1, 8>; };
 
 template <class T, int LAW = 0>
 int launch_fma_any(int elem, int p, const FmaArgs &a, void *stream) {
-  if (elem == FEM_TET4) return launch_fma_cfg<T, FmaShape<FEM_TET4, 1>::type, LAW>(a, stream);
+  if (elem == FEM_TET4) return launch_fma_cfg<T, typename FmaShape<T, FEM_TET4, 1>::type, LAW>(a, stream);
   switch (p) {
-    case 1: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 1>::type, LAW>(a, stream);
-    case 2: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 2>::type, LAW>(a, stream);
-    case 3: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 3>::type, LAW>(a, stream);
-    case 4: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 4>::type, LAW>(a, stream);
-    case 5: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 5>::type, LAW>(a, stream);
-    case 6: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 6>::type, LAW>(a, stream);
-    case 7: return launch_fma_cfg<T, FmaShape<FEM_PRISM6, 7>::type, LAW>(a, stream);
+    case 1: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 1>::type, LAW>(a, stream);
+    case 2: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 2>::type, LAW>(a, stream);
+    case 3: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 3>::type, LAW>(a, stream);
+    case 4: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 4>::type, LAW>(a, stream);
+    case 5: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 5>::type, LAW>(a, stream);
+    case 6: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 6>::type, LAW>(a, stream);
+    case 7: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 7>::type, LAW>(a, stream);
   }
   return FEM_EINVAL;
 }

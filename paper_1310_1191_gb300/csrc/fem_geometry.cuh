@@ -58,6 +58,104 @@ __device__ __forceinline__ double jac_adj(const double *X, const double *q4, dou
   return J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
 }
 
+// Element edge record (FP64, computed once per element): for a prism the
+// vectors x1-x0, x4-x3, x2-x0, x5-x3, x3-x0, x4-x1, x5-x2 (21 values), for a
+// tetrahedron x1-x0, x2-x0, x3-x0 (9 values).  J at a point is then
+//   prism: J[:,0] = lo (x1-x0) + hi (x4-x3),  J[:,1] = lo (x2-x0) + hi (x5-x3),
+//          J[:,2] = ((1-xi-eta) (x3-x0) + xi (x4-x1) + eta (x5-x2)) / 2,
+//   lo = (1-zeta)/2, hi = (1+zeta)/2 (the map is bilinear in zeta).
+constexpr int kEdgeRec = 21;
+
+template <int ELEM>
+__device__ __forceinline__ void edge_record(const double *X, double *ed) {
+  if (ELEM == FEM_PRISM6) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      ed[0 + i] = X[3 + i] - X[0 + i];
+      ed[3 + i] = X[12 + i] - X[9 + i];
+      ed[6 + i] = X[6 + i] - X[0 + i];
+      ed[9 + i] = X[15 + i] - X[9 + i];
+      ed[12 + i] = X[9 + i] - X[0 + i];
+      ed[15 + i] = X[12 + i] - X[3 + i];
+      ed[18 + i] = X[15 + i] - X[6 + i];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      ed[0 + i] = X[3 + i] - X[i];
+      ed[3 + i] = X[6 + i] - X[i];
+      ed[6 + i] = X[9 + i] - X[i];
+    }
+  }
+}
+
+// adj J and det J at a point from the element's edge record (FP64).
+template <int ELEM>
+__device__ __forceinline__ double jac_adj_edges(const double *ed, const double *q4, double (&adj)[3][3]) {
+  double J[3][3];
+  if (ELEM == FEM_PRISM6) {
+    const double xi = q4[0], eta = q4[1], ze = q4[2];
+    const double lo = 0.5 * (1.0 - ze), hi = 0.5 * (1.0 + ze);
+    const double h0 = 0.5 * (1.0 - xi - eta), h1 = 0.5 * xi, h2 = 0.5 * eta;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      J[i][0] = fma(lo, ed[0 + i], hi * ed[3 + i]);
+      J[i][1] = fma(lo, ed[6 + i], hi * ed[9 + i]);
+      J[i][2] = fma(h0, ed[12 + i], fma(h1, ed[15 + i], h2 * ed[18 + i]));
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      J[i][0] = ed[0 + i];
+      J[i][1] = ed[3 + i];
+      J[i][2] = ed[6 + i];
+    }
+  }
+  adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  adj[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  adj[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  adj[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  return J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+}
+
+// Point record from FP64 adj J and det J with the 3x3 products in FP32 (for
+// the FP32 and tensor-core contractions, whose point records are FP32).
+__device__ __forceinline__ void point_from_adj_f32(const double (&adj)[3][3], double det, double w,
+                                                   const double *cf, float *g) {
+  float a[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int m = 0; m < 3; m++) a[k][m] = (float)adj[k][m];
+  const float D[3][3] = {{(float)cf[0], (float)cf[3], (float)cf[4]},
+                         {(float)cf[3], (float)cf[1], (float)cf[5]},
+                         {(float)cf[4], (float)cf[5], (float)cf[2]}};
+  float M[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int n = 0; n < 3; n++) M[k][n] = a[k][0] * D[0][n] + a[k][1] * D[1][n] + a[k][2] * D[2][n];
+  const float s = (float)w / (float)det;
+  auto Gd = [&](int k, int l) { return s * (M[k][0] * a[l][0] + M[k][1] * a[l][1] + M[k][2] * a[l][2]); };
+  g[G11] = Gd(0, 0);
+  g[G12] = Gd(0, 1);
+  g[G13] = Gd(0, 2);
+  g[G22] = Gd(1, 1);
+  g[G23] = Gd(1, 2);
+  g[G33] = Gd(2, 2);
+  const float wf = (float)w, b0 = (float)cf[6], b1 = (float)cf[7], b2 = (float)cf[8];
+#pragma unroll
+  for (int l = 0; l < 3; l++) g[G01 + l] = wf * (a[l][0] * b0 + a[l][1] * b1 + a[l][2] * b2);
+  const float wd = (float)(w * det);
+  g[G00] = wd * (float)cf[9];
+  g[GS] = wd * (float)cf[10];
+}
+
 // Point record from adj J, det J and the weight (FP64); cf: 11 coefficients.
 __device__ __forceinline__ void point_from_adj(const double (&adj)[3][3], double det, double w,
                                                const double *cf, double *g) {

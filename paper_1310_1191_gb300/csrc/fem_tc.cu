@@ -65,7 +65,8 @@ struct TcCfg {
   // shared layout (bytes from a 1024-aligned base)
   static constexpr size_t OFF_G = (size_t)STAGES * STAGE_BYTES;
   static constexpr size_t OFF_X = OFF_G + (size_t)MAXEL * NQP * 12 * 4;
-  static constexpr size_t OFF_BAR = (OFF_X + (size_t)MAXEL * NREC * 8 + 15) / 16 * 16;
+  static constexpr size_t OFF_ED = OFF_X + (size_t)MAXEL * NREC * 8;
+  static constexpr size_t OFF_BAR = (OFF_ED + (size_t)MAXEL * kEdgeRec * 8 + 15) / 16 * 16;
   static constexpr size_t OFF_MISC = OFF_BAR + 8 * (2 * STAGES + 3);
   static constexpr size_t SMEM = OFF_MISC + 16 + 28 * MAXEL + 1024;
   static_assert(NH % 16 == 0 && NH >= 16 && NH <= 256, "MMA N out of range");
@@ -92,27 +93,23 @@ struct TcArgs {
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
 
+// x = hi + lo for two values at once: hi = rn16(x), lo = rn16(x - hi), packed
+// as two 16-bit halves (first value in the low half).
 template <bool F16>
 __device__ __forceinline__ uint32_t split_pack(float x0, float x1, uint32_t &lo_word) {
-  uint16_t h0, h1, l0, l1;
   if (F16) {
-    __half a = __float2half_rn(x0), b = __float2half_rn(x1);
-    __half c = __float2half_rn(x0 - __half2float(a)), d = __float2half_rn(x1 - __half2float(b));
-    h0 = __half_as_ushort(a);
-    h1 = __half_as_ushort(b);
-    l0 = __half_as_ushort(c);
-    l1 = __half_as_ushort(d);
+    const __half2 h = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+    lo_word = *reinterpret_cast<const uint32_t *>(&l);
+    return *reinterpret_cast<const uint32_t *>(&h);
   } else {
-    __nv_bfloat16 a = __float2bfloat16_rn(x0), b = __float2bfloat16_rn(x1);
-    __nv_bfloat16 c = __float2bfloat16_rn(x0 - __bfloat162float(a));
-    __nv_bfloat16 d = __float2bfloat16_rn(x1 - __bfloat162float(b));
-    h0 = __bfloat16_as_ushort(a);
-    h1 = __bfloat16_as_ushort(b);
-    l0 = __bfloat16_as_ushort(c);
-    l1 = __bfloat16_as_ushort(d);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+    lo_word = *reinterpret_cast<const uint32_t *>(&l);
+    return *reinterpret_cast<const uint32_t *>(&h);
   }
-  lo_word = (uint32_t)l0 | ((uint32_t)l1 << 16);
-  return (uint32_t)h0 | ((uint32_t)h1 << 16);
 }
 
 template <int P, bool F16>
@@ -122,6 +119,7 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
   unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float *sG = reinterpret_cast<float *>(sm + C::OFF_G);
   double *sX = reinterpret_cast<double *>(sm + C::OFF_X);
+  double *sEd = reinterpret_cast<double *>(sm + C::OFF_ED);
   uint64_t *bar_full = reinterpret_cast<uint64_t *>(sm + C::OFF_BAR);
   uint64_t *bar_empty = bar_full + C::STAGES;
   uint64_t *bar_accf = bar_empty + C::STAGES;
@@ -271,6 +269,10 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
           const double *cf = sX + pt * C::NREC + 18;
           if (cf[6] != 0.0 || cf[7] != 0.0 || cf[8] != 0.0) atomicOr(&sSt[pt], FEM_ST_NONSYM);
         }
+        if (pt < nel) edge_record<FEM_PRISM6>(sX + pt * C::NREC, sEd + pt * kEdgeRec);
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (!*sAbort) {
         // geometry -> G records (FP64 J, adj, det; FP32 products)
         for (int idx = pt; idx < nel * C::NQP; idx += 128) {
           const int el = idx / C::NQP, q = idx % C::NQP;
@@ -278,7 +280,10 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
           if (q < C::NQ) {
             float gv[11];
             const double *rec = sX + el * C::NREC;
-            const int st = point_matrix_f32<FEM_PRISM6>(rec, rec + 18, a.qp + 4 * q, gv);
+            double adj[3][3];
+            const double det = jac_adj_edges<FEM_PRISM6>(sEd + el * kEdgeRec, a.qp + 4 * q, adj);
+            point_from_adj_f32(adj, det, a.qp[4 * q + 3], rec + 18, gv);
+            const int st = det > 0.0 ? 0 : FEM_ST_DET;
 #pragma unroll
             for (int k = 0; k < 11; k++) gr[k] = gv[k];
             if (st) atomicOr(&sSt[el], st);
@@ -321,6 +326,17 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
         if (a.status && e * C::L >= R0) a.status[e] = sSt[pt];  // the tile holding row 0 reports
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (F16 && !*sAbort) {  // fold the power-of-two scales into the point records
+        for (int idx = pt; idx < nel * C::NQP; idx += 128) {
+          const int el = idx / C::NQP;
+          float *gr = sG + (size_t)idx * 12;
+          const float sc = sScale[el];
+#pragma unroll
+          for (int k = 0; k < 10; k++) gr[k] *= sc;
+          gr[GS] *= sScaleB[el];
+        }
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
       if (__any_sync(0xffffffffu, *sAbort != 0)) continue;  // warp-uniform
 
       // K loop: build the A tiles (T^T, hi and lo) of this thread's row
@@ -329,13 +345,36 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
       const int64_t e = valid ? r / C::L : e_first;
       const int j = valid ? (int)(r % C::L) : 0;
       const int el = (int)(e - e_first);
-      const float sc = valid ? (j < C::NS ? sScale[el] : sScaleB[el]) : 0.f;
       const float *gbase = sG + (size_t)el * C::NQP * 12;
+      const bool arow = valid && j < C::NS;  // matrix row (else load-vector or padding row)
+      // Phi values of this row for one chunk: 8 points x 4 (value, 3 derivatives)
+      float fcur[C::QC][4], fnext[C::QC][4];
+      auto load_phi = [&](int c, float (&f)[C::QC][4]) {
+#pragma unroll
+        for (int qq = 0; qq < C::QC; qq++) {
+          const int q = c * C::QC + qq;
+          if (arow && q < C::NQ) {
+            const float *ph = a.phi32 + (size_t)(4 * q) * C::NS + j;
+            f[qq][0] = __ldg(ph);
+            f[qq][1] = __ldg(ph + C::NS);
+            f[qq][2] = __ldg(ph + 2 * C::NS);
+            f[qq][3] = __ldg(ph + 3 * C::NS);
+          } else {
+            f[qq][0] = f[qq][1] = f[qq][2] = f[qq][3] = 0.f;
+          }
+        }
+      };
+      load_phi(0, fnext);
       bool ok = true;
       for (int c = 0; c < C::NCH; c++) {
         const uint32_t g = g0 + c;
         const int s = g % C::STAGES;
         const uint32_t round = g / C::STAGES;
+#pragma unroll
+        for (int qq = 0; qq < C::QC; qq++)
+#pragma unroll
+          for (int d = 0; d < 4; d++) fcur[qq][d] = fnext[qq][d];
+        if (c + 1 < C::NCH) load_phi(c + 1, fnext);  // in flight while this chunk is built
         if (!wait(&bar_empty[s], (round & 1) ^ 1)) {
           ok = false;
           break;
@@ -346,21 +385,20 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
           const int q = c * C::QC + qq;
           float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
           if (valid && q < C::NQ) {
-            const float *gr = gbase + q * 12;
-            if (j < C::NS) {
-              const float *ph = a.phi32 + (size_t)(4 * q) * C::NS + j;
-              const float f0 = __ldg(ph), f1 = __ldg(ph + C::NS), f2 = __ldg(ph + 2 * C::NS),
-                          f3 = __ldg(ph + 3 * C::NS);
-              t0 = gr[G00] * f0 + gr[G01] * f1 + gr[G02] * f2 + gr[G03] * f3;
-              t1 = gr[G11] * f1 + gr[G12] * f2 + gr[G13] * f3;
-              t2 = gr[G12] * f1 + gr[G22] * f2 + gr[G23] * f3;
-              t3 = gr[G13] * f1 + gr[G23] * f2 + gr[G33] * f3;
+            const float4 *g4 = reinterpret_cast<const float4 *>(gbase + q * 12);
+            const float4 ga = g4[0], gb = g4[1], gc = g4[2];  // G00 G01 G02 G03 | G11 G12 G13 G22 | G23 G33 GS -
+            if (arow) {
+              const float f0 = fcur[qq][0], f1 = fcur[qq][1], f2 = fcur[qq][2], f3 = fcur[qq][3];
+              t0 = ga.x * f0 + ga.y * f1 + ga.z * f2 + ga.w * f3;
+              t1 = gb.x * f1 + gb.y * f2 + gb.z * f3;
+              t2 = gb.y * f1 + gb.w * f2 + gc.x * f3;
+              t3 = gb.z * f1 + gc.x * f2 + gc.y * f3;
             } else {
-              t0 = gr[GS];
+              t0 = gc.z;
             }
           }
-          hw[2 * qq] = split_pack<F16>(t0 * sc, t1 * sc, lw[2 * qq]);
-          hw[2 * qq + 1] = split_pack<F16>(t2 * sc, t3 * sc, lw[2 * qq + 1]);
+          hw[2 * qq] = split_pack<F16>(t0, t1, lw[2 * qq]);
+          hw[2 * qq + 1] = split_pack<F16>(t2, t3, lw[2 * qq + 1]);
         }
         unsigned char *aH = sm + (size_t)s * C::STAGE_BYTES;
         unsigned char *aL = aH + C::A_BYTES;
