@@ -55,24 +55,38 @@ struct TcCfg {
   static constexpr int NSPLIT = NP > 256 ? 2 : 1;
   static constexpr int NH = NP / NSPLIT;
   static constexpr int MAXEL = (BM - 1 + L - 1) / L + 1;
-  static constexpr int TMEM_COLS = NP <= 32 ? 32 : NP <= 64 ? 64 : NP <= 128 ? 128 : NP <= 256 ? 256 : 512;
-  static constexpr int STAGES = 3;
+  static constexpr int NACC = 2 * NP <= 512 ? 2 : 1;  // TMEM accumulator buffers
+  static constexpr int TCOLS_NEED = NACC * NP;
+  static constexpr int TMEM_COLS = TCOLS_NEED <= 32 ? 32 : TCOLS_NEED <= 64 ? 64 : TCOLS_NEED <= 128 ? 128
+                                   : TCOLS_NEED <= 256 ? 256 : 512;
+  static constexpr int STAGES = P == 7 ? 2 : 3;
   static constexpr int A_BYTES = BM * KC * 2;  // one half (hi or lo)
   static constexpr int B_BYTES = NP * KC * 2;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int SBO = (KC / 8) * 128;   // 8-row group stride in a stage tile
   static constexpr int NREC = 18 + 11;
-  // shared layout (bytes from a 1024-aligned base)
+  static constexpr int GBUF = MAXEL * NQP * 12;  // floats per point-record buffer
+  // shared layout (bytes from a 1024-aligned base); two buffers of per-tile element data
   static constexpr size_t OFF_G = (size_t)STAGES * STAGE_BYTES;
-  static constexpr size_t OFF_X = OFF_G + (size_t)MAXEL * NQP * 12 * 4;
-  static constexpr size_t OFF_ED = OFF_X + (size_t)MAXEL * NREC * 8;
-  static constexpr size_t OFF_BAR = (OFF_ED + (size_t)MAXEL * kEdgeRec * 8 + 15) / 16 * 16;
-  static constexpr size_t OFF_MISC = OFF_BAR + 8 * (2 * STAGES + 3);
-  static constexpr size_t SMEM = OFF_MISC + 16 + 28 * MAXEL + 1024;
+  static constexpr size_t OFF_X = OFF_G + 2 * (size_t)GBUF * 4;
+  static constexpr size_t OFF_ED = OFF_X + 2 * (size_t)MAXEL * NREC * 8;
+  static constexpr size_t OFF_INV = OFF_ED + 2 * (size_t)MAXEL * kEdgeRec * 8;  // float [2][2][MAXEL]
+  static constexpr size_t OFF_GS = OFF_INV + 16 * (size_t)MAXEL;                // geometry scratch
+  static constexpr size_t OFF_BAR = (OFF_GS + 16 * (size_t)MAXEL + 15) / 16 * 16;
+  static constexpr int NBAR = 2 * STAGES + 9;
+  static constexpr size_t OFF_MISC = OFF_BAR + 8 * NBAR;
+  static constexpr size_t SMEM = OFF_MISC + 16 + 1024;
   static_assert(NH % 16 == 0 && NH >= 16 && NH <= 256, "MMA N out of range");
   static_assert(NQP >= NQ, "padding");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
+
+// warp roles of the 512-thread CTA
+constexpr int kTcThreads = 512;
+constexpr int kEpiWarp0 = 2;    // 4 warps: TMEM lanes 32 (w % 4) .. + 31
+constexpr int kProdWarp0 = 6;   // 8 warps: 256 producer threads
+constexpr int kGeoWarp0 = 14;   // 2 warps: 64 geometry threads
+constexpr int kNProd = 256, kNEpi = 128, kNGeo = 64;
 
 struct TcArgs {
   int64_t n;
@@ -113,27 +127,28 @@ __device__ __forceinline__ uint32_t split_pack(float x0, float x1, uint32_t &lo_
 }
 
 template <int P, bool F16>
-__global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
   using C = TcCfg<P>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float *sG = reinterpret_cast<float *>(sm + C::OFF_G);
-  double *sX = reinterpret_cast<double *>(sm + C::OFF_X);
-  double *sEd = reinterpret_cast<double *>(sm + C::OFF_ED);
+  float *sG = reinterpret_cast<float *>(sm + C::OFF_G);          // [2][MAXEL][NQP][12]
+  double *sX = reinterpret_cast<double *>(sm + C::OFF_X);        // [2][MAXEL][NREC]
+  double *sEd = reinterpret_cast<double *>(sm + C::OFF_ED);      // [2][MAXEL][21]
+  float *sInv = reinterpret_cast<float *>(sm + C::OFF_INV);      // [2][MAXEL] matrix rows
+  float *sInvB = sInv + 2 * C::MAXEL;                            // [2][MAXEL] load-vector row
+  int *sSt = reinterpret_cast<int *>(sm + C::OFF_GS);            // [MAXEL] geometry scratch
+  unsigned *sBnd = reinterpret_cast<unsigned *>(sSt + C::MAXEL);  // [MAXEL]
+  unsigned *sBndB = sBnd + C::MAXEL;                              // [MAXEL]
+  float *sScB = reinterpret_cast<float *>(sBndB + C::MAXEL);      // [MAXEL] load-vector scale
   uint64_t *bar_full = reinterpret_cast<uint64_t *>(sm + C::OFF_BAR);
   uint64_t *bar_empty = bar_full + C::STAGES;
-  uint64_t *bar_accf = bar_empty + C::STAGES;
-  uint64_t *bar_acce = bar_accf + 1;
-  uint64_t *bar_fin = bar_acce + 1;
+  uint64_t *bar_accf = bar_empty + C::STAGES;  // [2]
+  uint64_t *bar_acce = bar_accf + 2;           // [2]
+  uint64_t *bar_gfull = bar_acce + 2;          // [2]
+  uint64_t *bar_gempty = bar_gfull + 2;        // [2]
+  uint64_t *bar_fin = bar_gempty + 2;
   uint32_t *sTmem = reinterpret_cast<uint32_t *>(sm + C::OFF_MISC);
   volatile int *sAbort = reinterpret_cast<volatile int *>(sm + C::OFF_MISC + 4);
-  float *sScale = reinterpret_cast<float *>(sm + C::OFF_MISC + 16);          // [MAXEL]
-  float *sInv = sScale + C::MAXEL;                                            // [MAXEL]
-  int *sSt = reinterpret_cast<int *>(sInv + C::MAXEL);                        // [MAXEL]
-  unsigned *sBnd = reinterpret_cast<unsigned *>(sSt + C::MAXEL);              // [MAXEL]
-  unsigned *sBndB = sBnd + C::MAXEL;                                          // [MAXEL]
-  float *sScaleB = reinterpret_cast<float *>(sBndB + C::MAXEL);               // [MAXEL]
-  float *sInvB = sScaleB + C::MAXEL;                                          // [MAXEL]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nrows = a.n * C::L;
@@ -141,11 +156,15 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
 
   if (tid == 0) {
     for (int s = 0; s < C::STAGES; s++) {
-      ptx::mbar_init(&bar_full[s], 129);
+      ptx::mbar_init(&bar_full[s], kNProd + 1);
       ptx::mbar_init(&bar_empty[s], 1);
     }
-    ptx::mbar_init(bar_accf, 1);
-    ptx::mbar_init(bar_acce, 128);
+    for (int i = 0; i < 2; i++) {
+      ptx::mbar_init(&bar_accf[i], 1);
+      ptx::mbar_init(&bar_acce[i], kNEpi);
+      ptx::mbar_init(&bar_gfull[i], kNGeo);
+      ptx::mbar_init(&bar_gempty[i], kNProd + kNEpi);
+    }
     ptx::mbar_init(bar_fin, 1);
     *sAbort = 0;
     ptx::fence_mbar_init();
@@ -167,9 +186,17 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
     *sAbort = 1;
     return false;
   };
+  // element range of tile t
+  auto tile_elems = [&](int64_t t, int64_t &e_first, int &nel) {
+    const int64_t R0 = t * C::BM;
+    e_first = R0 / C::L;
+    int64_t e_last = (R0 + C::BM - 1) / C::L;
+    if (e_last > a.n - 1) e_last = a.n - 1;
+    nel = (int)(e_last - e_first + 1);
+  };
 
   if (warp == 0) {
-    // ---------------- Phi^T image loader ----------------
+    // ---------------- Phi^T image loader (TMA bulk copies) ----------------
     if (lane == 0) {
       uint32_t g = 0;
       for (int64_t t = blockIdx.x; t < ntiles && !*sAbort; t += gridDim.x) {
@@ -195,8 +222,10 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
       constexpr uint32_t idesc = ptx::idesc_f16(!F16, C::BM, C::NH);
       uint32_t g = 0, tt = 0;
       for (int64_t t = blockIdx.x; t < ntiles && !*sAbort; t += gridDim.x, tt++) {
-        if (!wait(bar_acce, (tt & 1) ^ 1)) break;
+        const uint32_t ab = C::NACC == 2 ? (tt & 1) : 0, use = tt / C::NACC;
+        if (!wait(&bar_acce[ab], (use & 1) ^ 1)) break;
         ptx::tc_fence_after();
+        const uint32_t dacc = tmem + ab * C::NP;
         bool ok = true;
         for (int c = 0; c < C::NCH; c++, g++) {
           const int s = g % C::STAGES;
@@ -217,7 +246,7 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
               const uint32_t boff = h * (C::NH / 8) * C::SBO + ks * 256;
               const uint64_t bdH = ptx::smem_desc(bH + boff, 128, C::SBO);
               const uint64_t bdL = ptx::smem_desc(bL + boff, 128, C::SBO);
-              const uint32_t d = tmem + h * C::NH;
+              const uint32_t d = dacc + h * C::NH;
               ptx::mma_f16(d, adH, bdH, idesc, (c > 0 || ks > 0) ? 1u : 0u);
               ptx::mma_f16(d, adH, bdL, idesc, 1u);
               ptx::mma_f16(d, adL, bdH, idesc, 1u);
@@ -226,73 +255,72 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
           ptx::mma_commit(&bar_empty[s]);
         }
         if (!ok) break;
-        ptx::mma_commit(bar_accf);
+        ptx::mma_commit(&bar_accf[ab]);
       }
       // make sure no MMA is still running before TMEM is released
       ptx::mma_commit(bar_fin);
       ptx::mbar_wait(bar_fin, 0, kWaitLimitNs);
     }
-  } else {
-    // ---------------- producers + epilogue (128 threads) ----------------
-    // Every producer runs every tile iteration and every named barrier; after
-    // an abort the work is skipped but the barrier sequence stays the same, so
-    // no thread can be left waiting on a named barrier.
-    const int pt = tid - 64;
-    const int lq = warp & 3;
-    const int rl = 32 * lq + lane;  // row of the tile this thread builds and drains
+  } else if (warp >= kGeoWarp0) {
+    // ---------------- geometry: point records of the next tile ----------------
+    // All 64 threads run every iteration and every named barrier (work is
+    // skipped after an abort), so none can be left waiting on barrier 2.
+    const int gt = tid - kGeoWarp0 * 32;
     uint32_t tt = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tt++) {
-      const uint32_t g0 = tt * C::NCH;  // first K chunk of this tile in the CTA's sequence
+      const int b = tt & 1;
+      const uint32_t use = tt >> 1;
+      int64_t e_first;
+      int nel;
+      tile_elems(t, e_first, nel);
       const int64_t R0 = t * C::BM;
-      const int64_t e_first = R0 / C::L;
-      int64_t e_last = (R0 + C::BM - 1) / C::L;
-      if (e_last > a.n - 1) e_last = a.n - 1;
-      const int nel = (int)(e_last - e_first + 1);
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (gt == 0) wait(&bar_gempty[b], (use & 1) ^ 1);  // buffer b free again
+      asm volatile("bar.sync 2, 64;" ::: "memory");
+      double *X = sX + (size_t)b * C::MAXEL * C::NREC;
+      double *Ed = sEd + (size_t)b * C::MAXEL * kEdgeRec;
+      float *G = sG + (size_t)b * C::GBUF;
       if (!*sAbort) {
-        for (int idx = pt; idx < nel * C::NREC; idx += 128) {  // element records
+        for (int idx = gt; idx < nel * C::NREC; idx += kNGeo) {
           const int el = idx / C::NREC, k = idx % C::NREC;
           const int64_t e = e_first + el;
-          sX[idx] = k < 18 ? a.coords[e * 18 + k] : a.coeffs[(k - 18) * a.cstride + e];
+          X[idx] = k < 18 ? a.coords[e * 18 + k] : a.coeffs[(k - 18) * a.cstride + e];
         }
-        if (pt < C::MAXEL) {
-          sSt[pt] = 0;
-          sBnd[pt] = 0u;
-          sBndB[pt] = 0u;
+        if (gt < C::MAXEL) {
+          sSt[gt] = 0;
+          sBnd[gt] = 0u;
+          sBndB[gt] = 0u;
         }
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 2, 64;" ::: "memory");
       if (!*sAbort) {
-        for (int idx = pt; idx < nel * C::NREC; idx += 128)
-          if (!isfinite(sX[idx])) atomicOr(&sSt[idx / C::NREC], FEM_ST_NONFINITE);
-        if (a.layout == FEM_OUT_SYMPACKED && pt < nel) {
-          const double *cf = sX + pt * C::NREC + 18;
-          if (cf[6] != 0.0 || cf[7] != 0.0 || cf[8] != 0.0) atomicOr(&sSt[pt], FEM_ST_NONSYM);
+        for (int idx = gt; idx < nel * C::NREC; idx += kNGeo)
+          if (!isfinite(X[idx])) atomicOr(&sSt[idx / C::NREC], FEM_ST_NONFINITE);
+        if (gt < nel) {
+          const double *cf = X + gt * C::NREC + 18;
+          if (a.layout == FEM_OUT_SYMPACKED && (cf[6] != 0.0 || cf[7] != 0.0 || cf[8] != 0.0))
+            atomicOr(&sSt[gt], FEM_ST_NONSYM);
+          edge_record<FEM_PRISM6>(X + gt * C::NREC, Ed + gt * kEdgeRec);
         }
-        if (pt < nel) edge_record<FEM_PRISM6>(sX + pt * C::NREC, sEd + pt * kEdgeRec);
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 2, 64;" ::: "memory");
       if (!*sAbort) {
-        // geometry -> G records (FP64 J, adj, det; FP32 products)
-        for (int idx = pt; idx < nel * C::NQP; idx += 128) {
+        for (int idx = gt; idx < nel * C::NQP; idx += kNGeo) {
           const int el = idx / C::NQP, q = idx % C::NQP;
-          float *gr = sG + (size_t)idx * 12;
+          float *gr = G + (size_t)idx * 12;
           if (q < C::NQ) {
             float gv[11];
-            const double *rec = sX + el * C::NREC;
             double adj[3][3];
-            const double det = jac_adj_edges<FEM_PRISM6>(sEd + el * kEdgeRec, a.qp + 4 * q, adj);
-            point_from_adj_f32(adj, det, a.qp[4 * q + 3], rec + 18, gv);
-            const int st = det > 0.0 ? 0 : FEM_ST_DET;
+            const double det = jac_adj_edges<FEM_PRISM6>(Ed + el * kEdgeRec, a.qp + 4 * q, adj);
+            point_from_adj_f32(adj, det, a.qp[4 * q + 3], X + el * C::NREC + 18, gv);
 #pragma unroll
             for (int k = 0; k < 11; k++) gr[k] = gv[k];
-            if (st) atomicOr(&sSt[el], st);
+            if (!(det > 0.0)) atomicOr(&sSt[el], FEM_ST_DET);
             if (F16) {
-              float b = fabsf(gv[G00]) + fabsf(gv[G01]) + fabsf(gv[G02]) + fabsf(gv[G03]);
-              b = fmaxf(b, fabsf(gv[G11]) + fabsf(gv[G12]) + fabsf(gv[G13]));
-              b = fmaxf(b, fabsf(gv[G12]) + fabsf(gv[G22]) + fabsf(gv[G23]));
-              b = fmaxf(b, fabsf(gv[G13]) + fabsf(gv[G23]) + fabsf(gv[G33]));
-              if (isfinite(b)) atomicMax(&sBnd[el], __float_as_uint(b));
+              float bb = fabsf(gv[G00]) + fabsf(gv[G01]) + fabsf(gv[G02]) + fabsf(gv[G03]);
+              bb = fmaxf(bb, fabsf(gv[G11]) + fabsf(gv[G12]) + fabsf(gv[G13]));
+              bb = fmaxf(bb, fabsf(gv[G12]) + fabsf(gv[G22]) + fabsf(gv[G23]));
+              bb = fmaxf(bb, fabsf(gv[G13]) + fabsf(gv[G23]) + fabsf(gv[G33]));
+              if (isfinite(bb)) atomicMax(&sBnd[el], __float_as_uint(bb));
               // the load-vector row (S_Q, 0, 0, 0) gets its own scale: a small
               // source f must not fall into FP16 subnormals
               const float bs = fabsf(gv[GS]);
@@ -304,55 +332,66 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
           }
         }
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (!*sAbort && pt < nel) {
+      asm volatile("bar.sync 2, 64;" ::: "memory");
+      if (!*sAbort && gt < nel) {
         float sc = 1.f, inv = 1.f, scb = 1.f, invb = 1.f;
         if (F16) {
-          auto pow2_scale = [&](float bnd, float &s, float &is) {
+          auto pow2_scale = [&](float bnd, float &sv, float &is) {
             int ex = 0;
             if (bnd > 0.f) frexpf(bnd, &ex);  // bnd < 2^ex
             const int at = bnd > 0.f ? 14 - ex : 0;
-            s = ldexpf(1.f, at);
+            sv = ldexpf(1.f, at);
             is = ldexpf(1.f, -(at + a.aphi));
           };
-          pow2_scale(__uint_as_float(sBnd[pt]) * a.phimax, sc, inv);
-          pow2_scale(__uint_as_float(sBndB[pt]) * a.phimax, scb, invb);
+          pow2_scale(__uint_as_float(sBnd[gt]) * a.phimax, sc, inv);
+          pow2_scale(__uint_as_float(sBndB[gt]) * a.phimax, scb, invb);
         }
-        sScale[pt] = sc;
-        sInv[pt] = inv;
-        sScaleB[pt] = scb;
-        sInvB[pt] = invb;
-        const int64_t e = e_first + pt;
-        if (a.status && e * C::L >= R0) a.status[e] = sSt[pt];  // the tile holding row 0 reports
+        sInv[b * C::MAXEL + gt] = inv;
+        sInvB[b * C::MAXEL + gt] = invb;
+        sScB[gt] = scb;
+        reinterpret_cast<float *>(sBnd)[gt] = sc;  // reuse as the matrix-row scale
+        const int64_t e = e_first + gt;
+        if (a.status && e * C::L >= R0) a.status[e] = sSt[gt];  // the tile holding row 0 reports
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 2, 64;" ::: "memory");
       if (F16 && !*sAbort) {  // fold the power-of-two scales into the point records
-        for (int idx = pt; idx < nel * C::NQP; idx += 128) {
+        for (int idx = gt; idx < nel * C::NQP; idx += kNGeo) {
           const int el = idx / C::NQP;
-          float *gr = sG + (size_t)idx * 12;
-          const float sc = sScale[el];
+          float *gr = G + (size_t)idx * 12;
+          const float sc = __uint_as_float(sBnd[el]);
 #pragma unroll
           for (int k = 0; k < 10; k++) gr[k] *= sc;
-          gr[GS] *= sScaleB[el];
+          gr[GS] *= sScB[el];
         }
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (__any_sync(0xffffffffu, *sAbort != 0)) continue;  // warp-uniform
-
-      // K loop: build the A tiles (T^T, hi and lo) of this thread's row
-      const int64_t r = R0 + rl;
+      ptx::mbar_arrive(&bar_gfull[b]);  // arrives even after an abort
+    }
+  } else if (warp >= kProdWarp0) {
+    // ---------------- producers: A tiles (T^T hi/lo) of each K chunk ----------------
+    const int pt = tid - kProdWarp0 * 32;
+    const int rl = pt & 127;       // tile row
+    const int half = pt >> 7;      // points 4 half .. 4 half + 3 of each chunk
+    constexpr int QH = C::QC / 2;
+    uint32_t tt = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tt++) {
+      const int b = tt & 1;
+      const uint32_t use = tt >> 1;
+      if (!wait(&bar_gfull[b], use & 1)) break;
+      int64_t e_first;
+      int nel;
+      tile_elems(t, e_first, nel);
+      const int64_t r = t * C::BM + rl;
       const bool valid = r < nrows;
       const int64_t e = valid ? r / C::L : e_first;
       const int j = valid ? (int)(r % C::L) : 0;
       const int el = (int)(e - e_first);
-      const float *gbase = sG + (size_t)el * C::NQP * 12;
-      const bool arow = valid && j < C::NS;  // matrix row (else load-vector or padding row)
-      // Phi values of this row for one chunk: 8 points x 4 (value, 3 derivatives)
-      float fcur[C::QC][4], fnext[C::QC][4];
-      auto load_phi = [&](int c, float (&f)[C::QC][4]) {
+      const float *gbase = sG + (size_t)b * C::GBUF + (size_t)el * C::NQP * 12;
+      const bool arow = valid && j < C::NS;
+      float fcur[QH][4], fnext[QH][4];
+      auto load_phi = [&](int c, float (&f)[QH][4]) {
 #pragma unroll
-        for (int qq = 0; qq < C::QC; qq++) {
-          const int q = c * C::QC + qq;
+        for (int qq = 0; qq < QH; qq++) {
+          const int q = c * C::QC + half * QH + qq;
           if (arow && q < C::NQ) {
             const float *ph = a.phi32 + (size_t)(4 * q) * C::NS + j;
             f[qq][0] = __ldg(ph);
@@ -366,12 +405,13 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
       };
       load_phi(0, fnext);
       bool ok = true;
+      const uint32_t g0 = tt * C::NCH;
       for (int c = 0; c < C::NCH; c++) {
         const uint32_t g = g0 + c;
         const int s = g % C::STAGES;
         const uint32_t round = g / C::STAGES;
 #pragma unroll
-        for (int qq = 0; qq < C::QC; qq++)
+        for (int qq = 0; qq < QH; qq++)
 #pragma unroll
           for (int d = 0; d < 4; d++) fcur[qq][d] = fnext[qq][d];
         if (c + 1 < C::NCH) load_phi(c + 1, fnext);  // in flight while this chunk is built
@@ -379,10 +419,10 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
           ok = false;
           break;
         }
-        uint32_t hw[C::KC / 2], lw[C::KC / 2];
+        uint32_t hw[QH * 2], lw[QH * 2];
 #pragma unroll
-        for (int qq = 0; qq < C::QC; qq++) {
-          const int q = c * C::QC + qq;
+        for (int qq = 0; qq < QH; qq++) {
+          const int q = c * C::QC + half * QH + qq;
           float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
           if (valid && q < C::NQ) {
             const float4 *g4 = reinterpret_cast<const float4 *>(gbase + q * 12);
@@ -403,23 +443,42 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
         unsigned char *aH = sm + (size_t)s * C::STAGE_BYTES;
         unsigned char *aL = aH + C::A_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < C::KC / 8; kk++) {
+        for (int k2 = 0; k2 < QH / 2; k2++) {  // 16-byte core-matrix rows: 2 points each
+          const int kk = half * (QH / 2) + k2;
           const size_t off = (size_t)((rl >> 3) * (C::KC / 8) + kk) * 128 + (rl & 7) * 16;
-          *reinterpret_cast<uint4 *>(aH + off) = make_uint4(hw[4 * kk], hw[4 * kk + 1], hw[4 * kk + 2], hw[4 * kk + 3]);
-          *reinterpret_cast<uint4 *>(aL + off) = make_uint4(lw[4 * kk], lw[4 * kk + 1], lw[4 * kk + 2], lw[4 * kk + 3]);
+          *reinterpret_cast<uint4 *>(aH + off) = make_uint4(hw[4 * k2], hw[4 * k2 + 1], hw[4 * k2 + 2], hw[4 * k2 + 3]);
+          *reinterpret_cast<uint4 *>(aL + off) = make_uint4(lw[4 * k2], lw[4 * k2 + 1], lw[4 * k2 + 2], lw[4 * k2 + 3]);
         }
         ptx::fence_proxy_async();
         ptx::mbar_arrive(&bar_full[s]);
       }
-
-      // epilogue: TMEM -> registers -> columns of A_e / b_e (warp-uniform decision,
-      // tcgen05.ld is collective over the warp)
-      if (ok) ok = wait(bar_accf, tt & 1);
+      ptx::mbar_arrive(&bar_gempty[b]);  // done with point-record buffer b
+      if (!ok) break;
+    }
+  } else {
+    // ---------------- epilogue: TMEM -> columns of A_e / b_e ----------------
+    const int lq = warp & 3;
+    const int rl = 32 * lq + lane;
+    uint32_t tt = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tt++) {
+      const int b = tt & 1;
+      const uint32_t ab = C::NACC == 2 ? (tt & 1) : 0, use = tt / C::NACC;
+      // the tile's element data (written by the geometry warps) and its accumulator
+      bool ok = wait(&bar_gfull[b], (tt >> 1) & 1);
+      ok = ok && wait(&bar_accf[ab], use & 1);
       __syncwarp();
-      if (!__all_sync(0xffffffffu, ok)) continue;
+      if (!__all_sync(0xffffffffu, ok)) break;  // tcgen05.ld is collective over the warp
       ptx::tc_fence_after();
-      const float inv = valid ? (j < C::NS ? sInv[el] : sInvB[el]) : 0.f;
-      const uint32_t tbase = tmem + ((uint32_t)(32 * lq) << 16);
+      int64_t e_first;
+      int nel;
+      tile_elems(t, e_first, nel);
+      const int64_t r = t * C::BM + rl;
+      const bool valid = r < nrows;
+      const int64_t e = valid ? r / C::L : e_first;
+      const int j = valid ? (int)(r % C::L) : 0;
+      const int el = (int)(e - e_first);
+      const float inv = valid ? (j < C::NS ? sInv[b * C::MAXEL + el] : sInvB[b * C::MAXEL + el]) : 0.f;
+      const uint32_t tbase = tmem + ab * C::NP + ((uint32_t)(32 * lq) << 16);
 #pragma unroll 1
       for (int c0 = 0; c0 < C::NP; c0 += 16) {
         uint32_t v[16];
@@ -454,7 +513,8 @@ __global__ void __launch_bounds__(192, 1) tc_kernel(const TcArgs a) {
         }
       }
       ptx::tc_fence_before();
-      ptx::mbar_arrive(bar_acce);
+      ptx::mbar_arrive(&bar_acce[ab]);
+      ptx::mbar_arrive(&bar_gempty[b]);
     }
   }
 
@@ -488,18 +548,14 @@ static int launch_tc_p(const TcArgs &a, void *stream) {
     set_error(std::string("cudaFuncSetAttribute(tc_kernel): ") + cudaGetErrorString(err));
     return FEM_ECUDA;
   }
-  int dev = 0, nsm = 0, per_sm = 0;
+  int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_kernel<P, F16>, 192, C::SMEM);
-  // TMEM: every resident CTA holds TMEM_COLS of the SM's 512 columns
-  const int tmem_cap = 512 / C::TMEM_COLS;
-  if (per_sm > tmem_cap) per_sm = tmem_cap;
-  if (per_sm < 1) per_sm = 1;
+  // one 512-thread CTA per SM (it overlaps its own phases); TMEM_COLS <= 512
   const int64_t ntiles = (a.n * C::L + C::BM - 1) / C::BM;
-  int64_t grid = (int64_t)nsm * per_sm;
+  int64_t grid = nsm;
   if (grid > ntiles) grid = ntiles;
-  tc_kernel<P, F16><<<(unsigned)grid, 192, C::SMEM, (cudaStream_t)stream>>>(a);
+  tc_kernel<P, F16><<<(unsigned)grid, kTcThreads, C::SMEM, (cudaStream_t)stream>>>(a);
   err = cudaGetLastError();
   if (err != cudaSuccess) {
     set_error(std::string("tc_kernel launch: ") + cudaGetErrorString(err));
