@@ -66,10 +66,10 @@ __device__ __forceinline__ void run_item(const BatchArgs &a, const int4 &it, uns
                  it.y % C::TILES, smem);
 }
 
-// FP32 bodies fit 128 registers (two CTAs per SM); the FP64 ones are bound by
-// the FP64 pipe, so one CTA per SM with more registers costs nothing.
+// One CTA per SM: the largest bodies need more than 128 registers, and
+// capping them (two CTAs per SM) made them spill.
 template <class T>
-__global__ void __launch_bounds__(kBatchThreads, sizeof(T) == 4 ? 2 : 1) batch_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(const BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   for (;;) {

@@ -376,10 +376,10 @@ template <> struct FmaShape<double, FEM_PRISM6, 7> { using type = FmaCfg<FEM_PRI
 template <> struct FmaShape<float, FEM_TET4, 1> { using type = FmaCfg<FEM_TET4, 1, 4, 1, 4, 64, 4>; };
 template <> struct FmaShape<float, FEM_PRISM6, 1> { using type = FmaCfg<FEM_PRISM6, 1, 6, 1, 6, 42, 4>; };
 template <> struct FmaShape<float, FEM_PRISM6, 2> { using type = FmaCfg<FEM_PRISM6, 2, 18, 6, 6, 28, 3>; };
-template <> struct FmaShape<float, FEM_PRISM6, 3> { using type = FmaCfg<FEM_PRISM6, 3, 40, 8, 8, 8, 4>; };
-template <> struct FmaShape<float, FEM_PRISM6, 4> { using type = FmaCfg<FEM_PRISM6, 4, 80, 8, 8, 2, 4>; };
+template <> struct FmaShape<float, FEM_PRISM6, 3> { using type = FmaCfg<FEM_PRISM6, 3, 40, 4, 4, 2, 8>; };
+template <> struct FmaShape<float, FEM_PRISM6, 4> { using type = FmaCfg<FEM_PRISM6, 4, 75, 5, 5, 1, 5>; };
 template <> struct FmaShape<float, FEM_PRISM6, 5> { using type = FmaCfg<FEM_PRISM6, 5, 128, 8, 8, 1, 8>; };
-template <> struct FmaShape<float, FEM_PRISM6, 6> { using type = FmaCfg<FEM_PRISM6, 6, 104, 8, 8, 1, 8>; };
+template <> struct FmaShape<float, FEM_PRISM6, 6> { using type = FmaCfg<FEM_PRISM6, 6, 98, 7, 7, 1, 7>; };
 template <> struct FmaShape<float, FEM_PRISM6, 7> { using type = FmaCfg<FEM_PRISM6, 7, 96, 6, 6, 1, 8>; };
 
 template <class T, int LAW = 0>
