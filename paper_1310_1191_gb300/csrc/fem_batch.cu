@@ -66,10 +66,12 @@ __device__ __forceinline__ void run_item(const BatchArgs &a, const int4 &it, uns
                  it.y % C::TILES, smem);
 }
 
-// One CTA per SM: the largest bodies need more than 128 registers, and
-// capping them (two CTAs per SM) made them spill.
+// FP32 bodies are capped at 128 registers (two CTAs per SM: the FMA bodies
+// need the extra warps to hide latency; measured 575 ms vs 720 ms uncapped on
+// the 500k mixed mesh although the largest bodies spill a little); the FP64
+// ones are bound by the FP64 pipe, so one CTA per SM costs nothing.
 template <class T>
-__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, sizeof(T) == 4 ? 2 : 1) batch_kernel(const BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   for (;;) {
