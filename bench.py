@@ -366,7 +366,8 @@ def wl_batched(lib, tables, stream, dev, reps, E=500000):
     A = torch.empty(totA, dtype=torch.float32, device=dev)
     b = torch.empty(totb, dtype=torch.float32, device=dev)
     res = {}
-    for name, flags in (("graph_autotuned", lib.FEM_PLAN_AUTOTUNE), ("per_degree_loop", lib.FEM_PLAN_LOOP)):
+    for name, flags in (("graph_autotuned", lib.FEM_PLAN_AUTOTUNE), ("per_degree_loop", lib.FEM_PLAN_LOOP),
+                        ("graph_concurrent_branches", lib.FEM_PLAN_CONCURRENT)):
         plan = lib.fem_plan_create(tables, P, lib.FEM_F32, 0, flags, None)
         ms = _timed(stream, lambda: lib.fem_plan_execute(plan, Xd, Cd, E, A, b, None, stream), reps, 2)
         res[name] = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3,

@@ -200,6 +200,7 @@ typedef struct fem_plan_s *fem_plan;
 #define FEM_PLAN_AUTOTUNE 1  /* time the candidate tile shapes on the first execution */
 #define FEM_PLAN_LOOP 2      /* run one specialised launch per degree instead of one launch */
 #define FEM_PLAN_NOGRAPH 4   /* launch directly instead of replaying a captured CUDA graph */
+#define FEM_PLAN_CONCURRENT 8 /* one graph branch per degree (specialised kernels, overlapping) */
 
 /* Per-element output offsets of a mixed-degree mesh, elements kept in their
  * original order with unpadded variable-size blocks:
@@ -219,6 +220,8 @@ int fem_output_offsets(int elem, const int8_t *p_host, int64_t n, int layout, in
  * the first execution and replayed afterwards (re-captured when the buffers
  * change).  With FEM_PLAN_AUTOTUNE the first execution times two candidate
  * tile shapes per degree on the plan's own elements and keeps the faster;
+ * with FEM_PLAN_CONCURRENT the graph instead holds one branch per degree, each
+ * running that degree's specialised kernel on its own stream, overlapping;
  * tune_cache (nullable) is a text file that stores and reuses the choices.
  *   t      : prism tables covering every degree in p_host;
  *   p_host : host int8 [n_elem] degrees (copied; not kept);

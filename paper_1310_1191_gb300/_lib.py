@@ -34,7 +34,7 @@ EXPORTS = (
     "fem_integrate_host",
 )
 FEM_LAW_EXACT, FEM_LAW_MLP = 1, 2
-FEM_PLAN_AUTOTUNE, FEM_PLAN_LOOP, FEM_PLAN_NOGRAPH = 1, 2, 4
+FEM_PLAN_AUTOTUNE, FEM_PLAN_LOOP, FEM_PLAN_NOGRAPH, FEM_PLAN_CONCURRENT = 1, 2, 4, 8
 
 _lib = None
 

@@ -165,6 +165,8 @@ struct fem_plan_s {
   std::vector<int4> h_items;
   // graph
   cudaStream_t cap = nullptr;
+  cudaStream_t branch[fem::kMaxP + 1] = {nullptr};  // concurrent mode: one stream per degree
+  cudaEvent_t fork = nullptr, join[fem::kMaxP + 1] = {nullptr};
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   const void *key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -294,6 +296,32 @@ static int launch_per_p_loop(const fem_plan_s *pl, const FmaArgs &base, cudaStre
     const int rc = pl->prec == FEM_F64 ? launch_loop<double>(p, pl->variant[p], a, s)
                                        : launch_loop<float>(p, pl->variant[p], a, s);
     if (rc != FEM_OK) return rc;
+  }
+  return FEM_OK;
+}
+
+// One graph with a branch per degree: each branch runs the specialised kernel
+// of its bin on its own stream, the branches overlap (enqueued inside a
+// capture on pl->cap, forked and joined with events).
+static int launch_concurrent(fem_plan_s *pl, const FmaArgs &base, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(pl->fork, s);
+  if (e != cudaSuccess) return plan_fail("cudaEventRecord(fork)", e);
+  for (int p = 1; p <= kMaxP; p++) {
+    const int64_t k0 = pl->bin_off[p], k1 = pl->bin_off[p + 1];
+    if (k1 <= k0) continue;
+    e = cudaStreamWaitEvent(pl->branch[p], pl->fork, 0);
+    if (e != cudaSuccess) return plan_fail("cudaStreamWaitEvent(fork)", e);
+    FmaArgs a = base;
+    a.n = k1 - k0;
+    a.perm = pl->perm + k0;
+    a.qp = pl->t->tab[p].qp;
+    a.phi = pl->prec == FEM_F64 ? (const void *)pl->t->tab[p].phi64 : (const void *)pl->t->tab[p].phi32;
+    const int rc = pl->prec == FEM_F64 ? launch_loop<double>(p, pl->variant[p], a, pl->branch[p])
+                                       : launch_loop<float>(p, pl->variant[p], a, pl->branch[p]);
+    if (rc != FEM_OK) return rc;
+    e = cudaEventRecord(pl->join[p], pl->branch[p]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, pl->join[p], 0);
+    if (e != cudaSuccess) return plan_fail("join", e);
   }
   return FEM_OK;
 }
@@ -618,6 +646,13 @@ int fem_plan_create(fem_tables t, int64_t n_elem, const int8_t *p_host, int prec
   if (rc == FEM_OK) {
     cudaError_t e = cudaMalloc((void **)&pl->counter, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess && (flags & FEM_PLAN_CONCURRENT)) {
+      e = cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming);
+      for (int p = 1; p <= kMaxP && e == cudaSuccess; p++) {
+        e = cudaStreamCreateWithFlags(&pl->branch[p], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->join[p], cudaEventDisableTiming);
+      }
+    }
     if (e != cudaSuccess) rc = plan_fail("plan setup", e);
   }
   if (rc == FEM_OK) {
@@ -671,7 +706,8 @@ int fem_plan_execute(fem_plan pl, const double *coords, const double *coeffs, in
   }
   if (pl->flags & FEM_PLAN_LOOP) return launch_per_p_loop(pl, base, s);
   BatchArgs b = batch_args(pl, base);
-  if (pl->flags & FEM_PLAN_NOGRAPH) return launch_batch(pl, b, s);
+  const bool conc = (pl->flags & FEM_PLAN_CONCURRENT) != 0;
+  if (pl->flags & FEM_PLAN_NOGRAPH) return conc ? launch_concurrent(pl, base, s) : launch_batch(pl, b, s);
   const void *key[6] = {coords, coeffs, A_out, b_out, status, nullptr};
   bool same = pl->exec && pl->key_stride == coeff_stride;
   for (int i = 0; i < 6 && same; i++) same = key[i] == pl->key[i];
@@ -679,7 +715,7 @@ int fem_plan_execute(fem_plan pl, const double *coords, const double *coeffs, in
     drop_graph(pl);
     cudaError_t e = cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return plan_fail("cudaStreamBeginCapture", e);
-    rc = launch_batch(pl, b, pl->cap);
+    rc = conc ? launch_concurrent(pl, base, pl->cap) : launch_batch(pl, b, pl->cap);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(pl->cap, &g);
     if (rc != FEM_OK) {
@@ -719,6 +755,11 @@ int fem_plan_destroy(fem_plan pl) {
   if (pl->items) cudaFree(pl->items);
   if (pl->counter) cudaFree(pl->counter);
   if (pl->cap) cudaStreamDestroy(pl->cap);
+  for (int p = 0; p <= kMaxP; p++) {
+    if (pl->branch[p]) cudaStreamDestroy(pl->branch[p]);
+    if (pl->join[p]) cudaEventDestroy(pl->join[p]);
+  }
+  if (pl->fork) cudaEventDestroy(pl->fork);
   delete pl;
   return FEM_OK;
 }

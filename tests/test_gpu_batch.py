@@ -94,13 +94,15 @@ def _check(ref, P, res, prec, layout=0, idx=None):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("mode", ["graph", "nograph", "loop"])
+@pytest.mark.parametrize("mode", ["graph", "nograph", "loop", "concurrent", "concurrent_nograph"])
 def test_plan_modes_match_oracle(orc, lib, tables, prec, mode):
     E = 700
     X, C, P = _mesh(E)
     assert set(np.unique(P)) == set(range(1, 8))
     ref = _oracle_by_degree(orc, X, C, P)
-    flags = {"graph": 0, "nograph": lib.FEM_PLAN_NOGRAPH, "loop": lib.FEM_PLAN_LOOP}[mode]
+    flags = {"graph": 0, "nograph": lib.FEM_PLAN_NOGRAPH, "loop": lib.FEM_PLAN_LOOP,
+             "concurrent": lib.FEM_PLAN_CONCURRENT,
+             "concurrent_nograph": lib.FEM_PLAN_CONCURRENT | lib.FEM_PLAN_NOGRAPH}[mode]
     _check(ref, P, _run(lib, tables, X, C, P, prec, flags=flags, reps=2), prec)
 
 
