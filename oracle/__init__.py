@@ -69,6 +69,7 @@ def _load():
             lib.orc_mlp_loss_grad.argtypes = [i, P, P, i64, P, P, P, P]
             lib.orc_mlp_loss_grad.restype = d
             lib.orc_integrate_ex.argtypes = [i, i, i64, P, P, i64, i, P, i, P, P, P, P, P, i]
+            lib.orc_integrate_elastic.argtypes = [i, i64, P, P, i64, P, P, P, i]
             lib.orc_max_threads.argtypes = []
             _lib = lib
     return _lib
@@ -186,4 +187,22 @@ def integrate(elem: int, p: int, coords, coeffs, law: int = 0, ucoef=None, mlp=N
                                   nthreads)
     if rc != 0:
         raise RuntimeError("oracle integrate failed")
+    return A, b, st
+
+
+def integrate_elastic(p: int, coords, coeffs, nthreads: int = 0):
+    """Linear elastostatics on prisms: A [E][3][3][NS][NS], b [E][3][NS], status.
+
+    coeffs SoA [5][E]: Young modulus, Poisson ratio, body force fx, fy, fz."""
+    coords = _f64(coords)
+    coeffs = _f64(coeffs)
+    E = coords.shape[0]
+    n = ns(PRISM, p)
+    A = np.zeros((E, 3, 3, n, n))
+    b = np.zeros((E, 3, n))
+    st = np.zeros(E, dtype=np.int32)
+    rc = _load().orc_integrate_elastic(p, E, _ptr(coords), _ptr(coeffs), coeffs.shape[1], _ptr(A),
+                                       _ptr(b), _ptr(st), nthreads)
+    if rc != 0:
+        raise RuntimeError("oracle integrate_elastic failed")
     return A, b, st

@@ -472,6 +472,103 @@ int orc_integrate_ex(int elem, int p, int64_t E, const double *coords, const dou
     return 0;
 }
 
+/* ------------------------------------------ linear elastostatics (Section 5.1) */
+/* Isotropic elasticity, N_E = 3 (eq. strong_form, fes, sum_int): block (iE, jE)
+ * of A^e, test component iE, trial component jE:
+ *   A[iE][jE][s][r] = sum_Q det w sum_{iD,jD>=1} c[iE][jE][iD][jD] psi[iD][s] psi[jD][r],
+ *   c[i][k][j][l] = c_ijkl = lam d_ij d_kl + mu (d_ik d_jl + d_il d_jk),
+ * lam = E nu / ((1 + nu)(1 - 2 nu)), mu = E / (2 (1 + nu)), constant per
+ * element (the paper's material data: Young modulus and Poisson ratio); body
+ * force load b[iE][s] = sum_Q det w f_iE psi[0][s].
+ * coeffs SoA [5][cstride]: E, nu, fx, fy, fz.  A [E][3][3][NS][NS], b [E][3][NS]. */
+int orc_integrate_elastic(int p, int64_t E, const double *coords, const double *coeffs,
+                          int64_t cstride, double *A, double *bvec, int32_t *status, int nthreads) {
+    const int elem = ORC_PRISM;
+    int NS = orc_ns(elem, p), NQ = orc_nq(elem, p);
+    if (NS < 0 || NQ < 0) return -1;
+    double *xq = (double *)malloc(sizeof(double) * 3 * NQ);
+    double *wq = (double *)malloc(sizeof(double) * NQ);
+    double *phiQ = (double *)malloc(sizeof(double) * (size_t)NQ * 4 * NS);
+    orc_rule(elem, p, xq, wq);
+    orc_basis(elem, p, NQ, xq, phiQ);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel
+    {
+        double *psi = (double *)malloc(sizeof(double) * 4 * NS);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t e = 0; e < E; e++) {
+            const double *X = coords + (size_t)e * 18;
+            double Ey = coeffs[e], nu = coeffs[cstride + e];
+            double f[3] = {coeffs[2 * cstride + e], coeffs[3 * cstride + e], coeffs[4 * cstride + e]};
+            double lam = Ey * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = Ey / (2.0 * (1.0 + nu));
+            int32_t st = 0;
+            for (int k = 0; k < 18; k++)
+                if (!isfinite(X[k])) st |= ORC_ST_NONFINITE;
+            if (!isfinite(Ey) || !isfinite(nu) || !isfinite(f[0]) || !isfinite(f[1]) || !isfinite(f[2]))
+                st |= ORC_ST_NONFINITE;
+            /* c[iE][jE][iD][jD] for the derivative pairs (iD, jD >= 1) */
+            double c[3][3][4][4];
+            memset(c, 0, sizeof(c));
+            for (int i = 0; i < 3; i++)
+                for (int k = 0; k < 3; k++)
+                    for (int j = 0; j < 3; j++)
+                        for (int l = 0; l < 3; l++)
+                            c[i][k][1 + j][1 + l] = lam * (i == j) * (k == l) +
+                                                     mu * ((i == k) * (j == l) + (i == l) * (j == k));
+            double *Ae = A + (size_t)e * 9 * NS * NS, *be = bvec + (size_t)e * 3 * NS;
+            memset(Ae, 0, sizeof(double) * 9 * NS * NS);
+            memset(be, 0, sizeof(double) * 3 * NS);
+            for (int q = 0; q < NQ; q++) {
+                const double *phi = phiQ + (size_t)q * 4 * NS;
+                double dN[3][6], J[3][3], Ji[3][3];
+                map_derivs(elem, xq + 3 * q, dN);
+                for (int i = 0; i < 3; i++)
+                    for (int k = 0; k < 3; k++) {
+                        double sacc = 0.0;
+                        for (int v = 0; v < 6; v++) sacc += X[3 * v + i] * dN[k][v];
+                        J[i][k] = sacc;
+                    }
+                double det = det3(J);
+                if (!(det > 0.0)) st |= ORC_ST_DET;
+                inv3(J, det, Ji);
+                for (int i = 0; i < NS; i++) {
+                    psi[i] = phi[i];
+                    for (int m = 0; m < 3; m++) {
+                        double sacc = 0.0;
+                        for (int k = 0; k < 3; k++) sacc += Ji[k][m] * phi[(1 + k) * NS + i];
+                        psi[(1 + m) * NS + i] = sacc;
+                    }
+                }
+                double dw = det * wq[q];
+                /* Algorithm 1 with the N_E x N_E blocks, non-zero c only */
+                for (int iE = 0; iE < 3; iE++)
+                    for (int jE = 0; jE < 3; jE++) {
+                        double *blk = Ae + ((size_t)iE * 3 + jE) * NS * NS;
+                        for (int s2 = 0; s2 < NS; s2++)
+                            for (int r = 0; r < NS; r++) {
+                                double sacc = 0.0;
+                                for (int iD = 1; iD < 4; iD++)
+                                    for (int jD = 1; jD < 4; jD++)
+                                        if (c[iE][jE][iD][jD] != 0.0)
+                                            sacc += dw * c[iE][jE][iD][jD] * psi[iD * NS + s2] * psi[jD * NS + r];
+                                blk[s2 * NS + r] += sacc;
+                            }
+                    }
+                for (int iE = 0; iE < 3; iE++)
+                    for (int s2 = 0; s2 < NS; s2++) be[iE * NS + s2] += dw * f[iE] * psi[s2];
+            }
+            if (status) status[e] = st;
+        }
+        free(psi);
+    }
+    free(xq);
+    free(wq);
+    free(phiQ);
+    return 0;
+}
+
 int orc_integrate(int elem, int p, int64_t E, const double *coords, const double *coeffs,
                   int64_t cstride, double *A, double *bvec, int32_t *status, int nthreads) {
     return orc_integrate_ex(elem, p, E, coords, coeffs, cstride, 0, NULL, 0, NULL, NULL, A, bvec,

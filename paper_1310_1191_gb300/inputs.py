@@ -253,3 +253,17 @@ def box_samples(n: int, box, seed: int = SEED_SURROGATE, first: int = 0) -> np.n
     a = draw_uniform(seed, idx, 0)
     b = draw_uniform(seed, idx, 1)
     return np.stack([u0 + (u1 - u0) * a, g0 + (g1 - g0) * b], axis=1)
+
+
+def elastic_coefficients(E: int, seed: int = SEED_COEF + 2, first: int = 0) -> np.ndarray:
+    """Per-element isotropic material and body force, SoA float64 [5][E]:
+    Young modulus U[1, 10], Poisson ratio U[0.05, 0.45], body force U[-1,1]^3."""
+    idx = np.arange(first, first + E, dtype=np.uint64)
+    u = [draw_uniform(seed, idx, n) for n in range(5)]
+    out = np.empty((5, E))
+    out[0] = 1.0 + 9.0 * u[0]
+    out[1] = 0.05 + 0.4 * u[1]
+    out[2] = 2 * u[2] - 1
+    out[3] = 2 * u[3] - 1
+    out[4] = 2 * u[4] - 1
+    return out
