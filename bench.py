@@ -356,6 +356,36 @@ def wl_tensor(lib, tables, stream, dev, reps, bf16_peak, E=200000, degrees=(4, 5
             "per_degree": out, "error_reference": "GPU FP64 path, first 512 elements"}
 
 
+def wl_elastic(lib, tables, stream, dev, reps, scale_down=1, degrees=range(1, 8)):
+    """Linear elastostatics (the paper's model problem), about 2 GB of FP64
+    output per degree; FP64 and FP32.  GFLOP/s also in the paper's count of
+    63 flops per 3x3 block and point (63 NQ NS^2 per element)."""
+    import torch
+    out = {}
+    for p in degrees:
+        n = ns_of(p)
+        E = max(1, round(2e9 / (8 * (9 * n * n + 3 * n))) // scale_down)
+        X = inputs.prism_mesh(E)
+        C = inputs.elastic_coefficients(E)
+        Xd, Cd = torch.from_numpy(X).to(dev), torch.from_numpy(C).to(dev)
+        row = {"elements": E}
+        for name, prec, dt in (("f64", lib.FEM_F64, torch.float64), ("f32", lib.FEM_F32, torch.float32)):
+            A = torch.empty((E, 9 * n * n), dtype=dt, device=dev)
+            b = torch.empty((E, 3 * n), dtype=dt, device=dev)
+            ms = _timed(stream, lambda: lib.fem_integrate_elastic(tables, p, E, Xd, Cd, E, prec, A, b, None,
+                                                                  stream), reps)
+            alg = 9 * 6.0 * nq_of(p) * n * n  # 9 blocks, K = 3 NQ
+            row[name] = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3,
+                         "tflops": round(alg * E / ms / 1e9, 3),
+                         "paper_count_gflops": round(63.0 * nq_of(p) * n * n * E / ms / 1e6, 1)}
+            del A, b
+        out[str(p)] = row
+        torch.cuda.empty_cache()
+    return {"workload": "linear elastostatics, isotropic E U[1,10], nu U[0.05,0.45], body force; "
+                        "prisms, about 2 GB FP64 output per degree; A^e[3][3][NS][NS] + b^e[3][NS]",
+            "per_degree": out}
+
+
 def wl_batched(lib, tables, stream, dev, reps, E=500000):
     import torch
     X = inputs.prism_mesh(E)
@@ -452,6 +482,9 @@ def run_only(args):
         out = wl_batched(lib, tables, stream, dev, reps, E=args.elements or 500000)
     elif args.only == "law":
         out = wl_surrogate(lib, tables, stream, dev, reps, E=args.elements or 1000000)
+    elif args.only == "elastic":
+        degs = tuple(int(x) for x in args.degrees.split(",")) if args.degrees else range(1, 8)
+        out = wl_elastic(lib, tables, stream, dev, reps, args.scale_down, degs)
     else:  # sweep at one precision
         prec = lib.FEM_F64 if args.precision == "f64" else lib.FEM_F32
         dt = torch.float64 if prec == lib.FEM_F64 else torch.float32
@@ -534,6 +567,7 @@ def run_ours(args):
         workloads["tensor_core"] = wl_tensor(lib, tables, stream, dev, reps, bf16_peak)
         workloads["mixed_degree"] = wl_batched(lib, tables, stream, dev, reps)
         workloads["nonlinear_law"] = wl_surrogate(lib, tables, stream, dev, reps)
+        workloads["elasticity"] = wl_elastic(lib, tables, stream, dev, reps)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_baseline(sweep)
@@ -579,7 +613,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--only", choices=["sweep", "tets", "tc", "mixed", "law"],
+    ap.add_argument("--only", choices=["sweep", "tets", "tc", "mixed", "law", "elastic"],
                     help="run one workload alone (profiling); prints its own JSON")
     ap.add_argument("--elements", type=int, default=0, help="elements for --only tc/mixed/law")
     ap.add_argument("--degrees", default="", help="comma-separated degrees for --only sweep/tc")

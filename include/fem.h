@@ -113,6 +113,22 @@ int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, con
                   int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out,
                   int32_t *status, void *stream);
 
+/* Linear elastostatics, the paper's model problem (Section 5.1, eqs.
+ * strong_form / fes / sum_int): N_E = 3 components, isotropic
+ * c_ijkl = lam d_ij d_kl + mu (d_ik d_jl + d_il d_jk) from Young's modulus E and
+ * Poisson's ratio nu (lam = E nu / ((1+nu)(1-2nu)), mu = E / (2(1+nu))),
+ * constant per element, and a constant body force f:
+ *   A^e[iE][jE][s][r] = sum_Q det J w sum_{j,l} c_{iE j jE l} psi_j^s psi_l^r,
+ *   b^e[iE][s]        = sum_Q det J w f_iE psi_0^s.
+ *   coeffs : device double SoA [5][coeff_stride]: E, nu, fx, fy, fz;
+ *   A_out  : device [n_elem][3][3][NS][NS] (the paper's A^e[iE][jE][iDOF][jDOF]),
+ *            double (FEM_F64) or float (FEM_F32), 16-byte aligned;
+ *   b_out  : device [n_elem][3][NS] or NULL; status : device int32 [n_elem] or NULL.
+ * Prisms; FEM_F64 / FEM_F32 (others FEM_EUNSUPPORTED). */
+int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
+                          int64_t coeff_stride, int prec, void *A_out, void *b_out, int32_t *status,
+                          void *stream);
+
 /* The same integration for HOST buffers (the paper's host code stages element
  * data to the device, runs the kernel and copies the matrices back, Section
  * 4.2): the elements are processed in chunks of `chunk` elements (<= 0: about

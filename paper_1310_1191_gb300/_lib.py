@@ -31,7 +31,7 @@ EXPORTS = (
     "fem_integrate_law", "fem_field_samples", "fem_box_from_samples", "fem_law_samples",
     "fem_mlp_create", "fem_mlp_destroy", "fem_mlp_nparams", "fem_mlp_forward", "fem_mlp_loss_grad",
     "fem_mlp_train", "fem_mlp_get", "fem_mlp_set", "fem_mlp_save", "fem_mlp_load",
-    "fem_integrate_host",
+    "fem_integrate_host", "fem_integrate_elastic",
 )
 FEM_LAW_EXACT, FEM_LAW_MLP = 1, 2
 FEM_PLAN_AUTOTUNE, FEM_PLAN_LOOP, FEM_PLAN_NOGRAPH, FEM_PLAN_CONCURRENT = 1, 2, 4, 8
@@ -88,6 +88,7 @@ def load():
     lib.fem_mlp_save.argtypes = [P, ctypes.c_char_p]
     lib.fem_mlp_load.argtypes = [ctypes.c_char_p, P]
     lib.fem_integrate_host.argtypes = [P, i, i64, P, P, i64, i, i, P, P, P, i64]
+    lib.fem_integrate_elastic.argtypes = [P, i, i64, P, P, i64, i, P, P, P, P]
     _lib = lib
     return lib
 
@@ -395,3 +396,11 @@ def fem_integrate_host(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_str
     return _check("fem_integrate_host", load().fem_integrate_host(
         t.handle, p, n_elem, _addr(coords), _addr(coeffs), coeff_stride, prec, layout, _addr(A_out),
         _addr(b_out), _addr(status), chunk))
+
+
+def fem_integrate_elastic(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_stride: int, prec: int,
+                          A_out, b_out=None, status=None, stream=None) -> int:
+    """Linear elastostatics: A_out [n][3][3][NS][NS], b_out [n][3][NS] (see fem.h)."""
+    return _check("fem_integrate_elastic", load().fem_integrate_elastic(
+        t.handle, p, n_elem, _addr(coords), _addr(coeffs), coeff_stride, prec, _addr(A_out),
+        _addr(b_out), _addr(status), _stream(stream)))

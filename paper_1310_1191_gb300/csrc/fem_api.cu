@@ -244,6 +244,39 @@ int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, con
   }
 }
 
+int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
+                          int64_t coeff_stride, int prec, void *A_out, void *b_out, int32_t *status,
+                          void *stream) {
+  if (!t || t->elem != FEM_PRISM6) return invalid("fem_integrate_elastic: needs prism tables");
+  if (p < t->p_min || p > t->p_max || n_elem < 0) return invalid("fem_integrate_elastic: bad degree or n_elem");
+  if (prec != FEM_F64 && prec != FEM_F32) {
+    set_error("fem_integrate_elastic: FP64 or FP32 only");
+    return FEM_EUNSUPPORTED;
+  }
+  if (n_elem == 0) return FEM_OK;
+  if (!coords || !coeffs || !A_out || coeff_stride < n_elem)
+    return invalid("fem_integrate_elastic: NULL buffer or coeff_stride < n_elem");
+  if ((((uintptr_t)coords | (uintptr_t)coeffs) & 7) || ((uintptr_t)A_out & 15))
+    return invalid("fem_integrate_elastic: misaligned buffer");
+  if (9 * n_elem > 0x7fffffffLL * 4) return invalid("fem_integrate_elastic: too many elements");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return invalid("fem_integrate_elastic: tables live on another device");
+  const DevTable &d = t->tab[p];
+  FmaArgs a;
+  a.n = n_elem;
+  a.coords = coords;
+  a.coeffs = coeffs;
+  a.cstride = coeff_stride;
+  a.qp = d.qp;
+  a.phi = prec == FEM_F64 ? (const void *)d.phi64 : (const void *)d.phi32;
+  a.A = A_out;
+  a.b = b_out;
+  a.status = status;
+  a.layout = FEM_OUT_FULL;
+  return prec == FEM_F64 ? launch_fma_elastic_f64(p, a, stream) : launch_fma_elastic_f32(p, a, stream);
+}
+
 int fem_integrate_host(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
                        int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out, int32_t *status,
                        int64_t chunk) {

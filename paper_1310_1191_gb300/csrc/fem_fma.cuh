@@ -28,15 +28,17 @@
 
 namespace fem {
 
-template <int ELEM_, int P_, int BM_, int TM_, int TN_, int EPB_, int QC_>
+// ND_ = rows of K per point: 4 (value + 3 derivatives, scalar form) or 3
+// (derivatives only, one 3x3 block of linear elastostatics per virtual element).
+template <int ELEM_, int P_, int BM_, int TM_, int TN_, int EPB_, int QC_, int ND_ = 4>
 struct FmaCfg {
-  static constexpr int ELEM = ELEM_, P = P_;
+  static constexpr int ELEM = ELEM_, P = P_, ND = ND_;
   static constexpr int NS = ns_of(ELEM_, P_), NQ = nq_of(ELEM_, P_), NV = nv_of(ELEM_);
   static constexpr int BM = BM_, BN = BM_, TM = TM_, TN = TN_;
   static constexpr int TY = BM / TM, TX = BN / TN, TPE = TX * TY;
   static constexpr int EPB = EPB_, NT = EPB * TPE;
   static constexpr int TILES = (NS + BM - 1) / BM;
-  static constexpr int QC = QC_, KC = 4 * QC, NCH = (NQ + QC - 1) / QC;
+  static constexpr int QC = QC_, KC = ND * QC, NCH = (NQ + QC - 1) / QC;
   static constexpr int NREC = NV * 3 + 11;  // coords + coefficients per element
   static constexpr int NEDGE = kEdgeRec;    // FP64 edge record per element
   static_assert(BM % TM == 0 && BN % TN == 0, "tile must split into micro-tiles");
@@ -122,12 +124,16 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     sSt[le] = 0;
   }
   __syncthreads();
-  // 0. element records
+  // 0. element records (elasticity: the real element e = v / 9 of virtual element v,
+  //    coefficients E, nu, fx, fy, fz)
+  constexpr bool ELAST = C::ND == 3;
+  constexpr int NCF = ELAST ? 5 : 11;
   for (int idx = tid; idx < C::EPB * C::NREC; idx += nthr) {
     const int le = idx / C::NREC, k = idx % C::NREC;
-    const int64_t e = sE[le];
+    const int64_t e = ELAST ? (sE[le] >= 0 ? sE[le] / 9 : -1) : sE[le];
     double v = 0.0;
-    if (e >= 0) v = k < C::NV * 3 ? a.coords[e * (C::NV * 3) + k] : a.coeffs[(k - C::NV * 3) * a.cstride + e];
+    if (e >= 0 && k < C::NV * 3 + NCF)
+      v = k < C::NV * 3 ? a.coords[e * (C::NV * 3) + k] : a.coeffs[(k - C::NV * 3) * a.cstride + e];
     sX[idx] = v;
   }
   if (LAW != 0) {
@@ -143,7 +149,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     if (!isfinite(sX[idx])) atomicOr(&sSt[idx / C::NREC], FEM_ST_NONFINITE);
   for (int le = tid; le < C::EPB; le += nthr) edge_record<C::ELEM>(sX + le * C::NREC, sEd + le * C::NEDGE);
   __syncthreads();
-  if (a.layout == FEM_OUT_SYMPACKED) {
+  if (!ELAST && a.layout == FEM_OUT_SYMPACKED) {
     for (int le = tid; le < C::EPB; le += nthr) {
       const double *cf = sX + le * C::NREC + C::NV * 3;
       if (cf[6] != 0.0 || cf[7] != 0.0 || cf[8] != 0.0) atomicOr(&sSt[le], FEM_ST_NONSYM);
@@ -156,7 +162,28 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     double g[11];
     const double *rec = sX + le * C::NREC;
     int st;
-    if (LAW == 0) {
+    if (ELAST) {
+      // block (i, k) of isotropic elasticity: G[a][b] = (w / det) (lam adj_ai adj_bk
+      //   + mu d_ik (adj adj^T)_ab + mu adj_ak adj_bi),  G[3][3] slot 9 = w det f_i (k = 0)
+      double adj[3][3];
+      const double det = jac_adj_edges<C::ELEM>(sEd + le * C::NEDGE, qp + 4 * q, adj);
+      st = det > 0.0 ? 0 : FEM_ST_DET;
+      const double *cf = rec + C::NV * 3;
+      const double Ey = cf[0], nu = cf[1];
+      const double lam = Ey * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = Ey / (2.0 * (1.0 + nu));
+      const int blk = sE[le] >= 0 ? (int)(sE[le] % 9) : 0, bi = blk / 3, bk = blk % 3;
+      const double w = qp[4 * q + 3], sw = w / det;
+#pragma unroll
+      for (int aa = 0; aa < 3; aa++)
+#pragma unroll
+        for (int bb = 0; bb < 3; bb++) {
+          double v = lam * adj[aa][bi] * adj[bb][bk] + mu * adj[aa][bk] * adj[bb][bi];
+          if (bi == bk) v += mu * (adj[aa][0] * adj[bb][0] + adj[aa][1] * adj[bb][1] + adj[aa][2] * adj[bb][2]);
+          g[3 * aa + bb] = sw * v;
+        }
+      g[9] = bk == 0 ? w * det * cf[2 + bi] : 0.0;
+      g[10] = 0.0;
+    } else if (LAW == 0) {
       double adj[3][3];
       const double det = jac_adj_edges<C::ELEM>(sEd + le * C::NEDGE, qp + 4 * q, adj);
       st = det > 0.0 ? 0 : FEM_ST_DET;
@@ -229,8 +256,10 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     const int q0 = ch * C::QC;
     for (int idx = tid; idx < C::KC * C::BM; idx += nthr) {
       const int k = idx / C::BM, i = idx % C::BM;
-      const int row = ti * C::BM + i, kg = 4 * q0 + k;
-      sPA[idx] = (row < C::NS && kg < 4 * C::NQ) ? phi[(size_t)kg * C::NS + row] : (T)0;
+      const int row = ti * C::BM + i;
+      const int qk = q0 + k / C::ND;
+      const int kg = ELAST ? 4 * qk + 1 + k % 3 : 4 * q0 + k;  // elasticity: derivative rows only
+      sPA[idx] = (row < C::NS && qk < C::NQ) ? phi[(size_t)kg * C::NS + row] : (T)0;
     }
     for (int idx = tid; idx < C::EPB * C::QC * C::BN; idx += nthr) {
       const int l2 = idx / (C::QC * C::BN), rem = idx % (C::QC * C::BN);
@@ -241,16 +270,22 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
         const T *ph = phi + (size_t)(4 * q) * C::NS + col;
         const T f0 = ph[0], f1 = ph[C::NS], f2 = ph[2 * C::NS], f3 = ph[3 * C::NS];
         const T *g = sG + ((size_t)l2 * C::NQ + q) * kGStride;
-        t0 = g[G00] * f0 + g[G01] * f1 + g[G02] * f2 + g[G03] * f3;
-        t1 = g[G11] * f1 + g[G12] * f2 + g[G13] * f3;
-        t2 = g[G12] * f1 + g[G22] * f2 + g[G23] * f3;
-        t3 = g[G13] * f1 + g[G23] * f2 + g[G33] * f3;
+        if (ELAST) {  // general 3x3 block on the derivative rows
+          t0 = g[0] * f1 + g[1] * f2 + g[2] * f3;
+          t1 = g[3] * f1 + g[4] * f2 + g[5] * f3;
+          t2 = g[6] * f1 + g[7] * f2 + g[8] * f3;
+        } else {
+          t0 = g[G00] * f0 + g[G01] * f1 + g[G02] * f2 + g[G03] * f3;
+          t1 = g[G11] * f1 + g[G12] * f2 + g[G13] * f3;
+          t2 = g[G12] * f1 + g[G22] * f2 + g[G23] * f3;
+          t3 = g[G13] * f1 + g[G23] * f2 + g[G33] * f3;
+        }
       }
-      T *tt = sT + ((size_t)l2 * C::KC + 4 * qq) * C::BN + j;
+      T *tt = sT + ((size_t)l2 * C::KC + C::ND * qq) * C::BN + j;
       tt[0] = t0;
       tt[C::BN] = t1;
       tt[2 * C::BN] = t2;
-      tt[3 * C::BN] = t3;
+      if (!ELAST) tt[3 * C::BN] = t3;
     }
     __syncthreads();
     if (owner) {
@@ -276,14 +311,17 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   // 3. load vector rows of this tile
   if (tj == 0 && a.b != nullptr) {
     T *bo = static_cast<T *>(a.b);
+    constexpr int SLOT = ELAST ? 9 : GS;
     for (int idx = tid; idx < C::EPB * C::BM; idx += nthr) {
       const int l2 = idx / C::BM, i = idx % C::BM, row = ti * C::BM + i;
       const int64_t e = sE[l2];
-      if (row < C::NS && e >= 0) {
+      // elasticity: the (i, 0) block of element e writes component i of b_e
+      if (row < C::NS && e >= 0 && (!ELAST || e % 3 == 0)) {
         T s = 0;
-        const T *g = sG + (size_t)l2 * C::NQ * kGStride + GS;
+        const T *g = sG + (size_t)l2 * C::NQ * kGStride + SLOT;
         for (int q = 0; q < C::NQ; q++) s = fma(g[q * kGStride], phi[(size_t)(4 * q) * C::NS + row], s);
-        bo[(a.offb ? a.offb[e] : e * (int64_t)C::NS) + row] = s;
+        const int64_t boff = ELAST ? (e / 3) * (int64_t)C::NS : (a.offb ? a.offb[e] : e * (int64_t)C::NS);
+        bo[boff + row] = s;
       }
     }
   }
@@ -320,8 +358,10 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     }
   }
   if (a.status != nullptr && ti == 0 && tj == 0)
-    for (int l2 = tid; l2 < C::EPB; l2 += nthr)
-      if (sE[l2] >= 0) a.status[sE[l2]] = sSt[l2];
+    for (int l2 = tid; l2 < C::EPB; l2 += nthr) {
+      const int64_t v = sE[l2];
+      if (v >= 0 && (!ELAST || v % 9 == 0)) a.status[ELAST ? v / 9 : v] = sSt[l2];
+    }
   __syncthreads();  // shared memory is reused by the next work item
 }
 
@@ -381,6 +421,30 @@ template <> struct FmaShape<float, FEM_PRISM6, 4> { using type = FmaCfg<FEM_PRIS
 template <> struct FmaShape<float, FEM_PRISM6, 5> { using type = FmaCfg<FEM_PRISM6, 5, 128, 8, 8, 1, 8>; };
 template <> struct FmaShape<float, FEM_PRISM6, 6> { using type = FmaCfg<FEM_PRISM6, 6, 98, 7, 7, 1, 7>; };
 template <> struct FmaShape<float, FEM_PRISM6, 7> { using type = FmaCfg<FEM_PRISM6, 7, 96, 6, 6, 1, 8>; };
+
+// Elasticity: the scalar shapes with K rows of derivatives only (ND = 3); EPB
+// counts virtual elements (one 3x3 block of one element each).
+template <class T, int P>
+struct FmaShapeE {
+  using S = typename FmaShape<T, FEM_PRISM6, P>::type;
+  using type = FmaCfg<FEM_PRISM6, P, S::BM, S::TM, S::TN, S::EPB, S::QC, 3>;
+};
+
+template <class T>
+int launch_fma_elastic(int p, const FmaArgs &a, void *stream) {
+  FmaArgs v = a;
+  v.n = 9 * a.n;  // virtual elements
+  switch (p) {
+    case 1: return launch_fma_cfg<T, typename FmaShapeE<T, 1>::type>(v, stream);
+    case 2: return launch_fma_cfg<T, typename FmaShapeE<T, 2>::type>(v, stream);
+    case 3: return launch_fma_cfg<T, typename FmaShapeE<T, 3>::type>(v, stream);
+    case 4: return launch_fma_cfg<T, typename FmaShapeE<T, 4>::type>(v, stream);
+    case 5: return launch_fma_cfg<T, typename FmaShapeE<T, 5>::type>(v, stream);
+    case 6: return launch_fma_cfg<T, typename FmaShapeE<T, 6>::type>(v, stream);
+    case 7: return launch_fma_cfg<T, typename FmaShapeE<T, 7>::type>(v, stream);
+  }
+  return FEM_EINVAL;
+}
 
 template <class T, int LAW = 0>
 int launch_fma_any(int elem, int p, const FmaArgs &a, void *stream) {

@@ -6,4 +6,7 @@ namespace fem {
 int launch_fma_f32(int elem, int p, const FmaArgs &a, void *stream) {
   return launch_fma_any<float>(elem, p, a, stream);
 }
+int launch_fma_elastic_f32(int p, const FmaArgs &a, void *stream) {
+  return launch_fma_elastic<float>(p, a, stream);
+}
 }  // namespace fem

@@ -88,6 +88,9 @@ struct FmaArgs {
 // Launch the FP64 / FP32 FMA kernels for (elem, p); returns a fem status code.
 int launch_fma_f64(int elem, int p, const FmaArgs &a, void *stream);
 int launch_fma_f32(int elem, int p, const FmaArgs &a, void *stream);
+// linear elastostatics: a.n real elements, 9 blocks each
+int launch_fma_elastic_f64(int p, const FmaArgs &a, void *stream);
+int launch_fma_elastic_f32(int p, const FmaArgs &a, void *stream);
 // law = 1 exact Newton law, 2 network with exact-law fallback
 int launch_fma_law_f64(int elem, int p, int law, const FmaArgs &a, void *stream);
 int launch_fma_law_f32(int elem, int p, int law, const FmaArgs &a, void *stream);
