@@ -173,15 +173,23 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
       const double lam = Ey * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = Ey / (2.0 * (1.0 + nu));
       const int blk = sE[le] >= 0 ? (int)(sE[le] % 9) : 0, bi = blk / 3, bk = blk % 3;
       const double w = qp[4 * q + 3], sw = w / det;
+      double ci[3], ck[3];  // columns bi and bk of adj J (selected without dynamic indexing)
+#pragma unroll
+      for (int m = 0; m < 3; m++) {
+        ci[m] = bi == 0 ? adj[m][0] : (bi == 1 ? adj[m][1] : adj[m][2]);
+        ck[m] = bk == 0 ? adj[m][0] : (bk == 1 ? adj[m][1] : adj[m][2]);
+      }
+      const double dik = bi == bk ? mu : 0.0;
 #pragma unroll
       for (int aa = 0; aa < 3; aa++)
 #pragma unroll
         for (int bb = 0; bb < 3; bb++) {
-          double v = lam * adj[aa][bi] * adj[bb][bk] + mu * adj[aa][bk] * adj[bb][bi];
-          if (bi == bk) v += mu * (adj[aa][0] * adj[bb][0] + adj[aa][1] * adj[bb][1] + adj[aa][2] * adj[bb][2]);
+          const double v = lam * ci[aa] * ck[bb] + mu * ck[aa] * ci[bb] +
+                           dik * (adj[aa][0] * adj[bb][0] + adj[aa][1] * adj[bb][1] + adj[aa][2] * adj[bb][2]);
           g[3 * aa + bb] = sw * v;
         }
-      g[9] = bk == 0 ? w * det * cf[2 + bi] : 0.0;
+      const double fi = bi == 0 ? cf[2] : (bi == 1 ? cf[3] : cf[4]);
+      g[9] = bk == 0 ? w * det * fi : 0.0;
       g[10] = 0.0;
     } else if (LAW == 0) {
       double adj[3][3];
