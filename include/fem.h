@@ -287,6 +287,14 @@ int fem_integrate_mixed_noalloc(fem_tables t, int64_t n_elem, const int8_t *p_ho
                                 const double *coeffs, int64_t coeff_stride, int prec, int layout,
                                 void *A_out, void *b_out, int32_t *status, void *stream);
 
+/* Failure-detection test hook: the next tensor-core launch on these tables
+ * withholds its operand copies, so its pipeline waits run out after their
+ * bounded limit (about one second).  The kernel then records FEM_ETIMEOUT in
+ * the device error word (fem_error_flag), marks its elements FEM_ST_TIMEOUT,
+ * releases its tensor memory and returns; the context stays usable.  Faults,
+ * traps and unbounded waits are never used. */
+int fem_debug_stall_next(fem_tables t);
+
 /* Number of output values per element for (elem, p, layout): NS*NS or NS(NS+1)/2;
  * -1 if invalid.  */
 int64_t fem_matrix_size(int elem, int p, int layout);

@@ -31,7 +31,7 @@ EXPORTS = (
     "fem_integrate_law", "fem_field_samples", "fem_box_from_samples", "fem_law_samples",
     "fem_mlp_create", "fem_mlp_destroy", "fem_mlp_nparams", "fem_mlp_forward", "fem_mlp_loss_grad",
     "fem_mlp_train", "fem_mlp_get", "fem_mlp_set", "fem_mlp_save", "fem_mlp_load",
-    "fem_integrate_host", "fem_integrate_elastic",
+    "fem_integrate_host", "fem_integrate_elastic", "fem_debug_stall_next",
 )
 FEM_LAW_EXACT, FEM_LAW_MLP = 1, 2
 FEM_PLAN_AUTOTUNE, FEM_PLAN_LOOP, FEM_PLAN_NOGRAPH, FEM_PLAN_CONCURRENT = 1, 2, 4, 8
@@ -89,6 +89,7 @@ def load():
     lib.fem_mlp_load.argtypes = [ctypes.c_char_p, P]
     lib.fem_integrate_host.argtypes = [P, i, i64, P, P, i64, i, i, P, P, P, i64]
     lib.fem_integrate_elastic.argtypes = [P, i, i64, P, P, i64, i, P, P, P, P]
+    lib.fem_debug_stall_next.argtypes = [P]
     _lib = lib
     return lib
 
@@ -404,3 +405,8 @@ def fem_integrate_elastic(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_
     return _check("fem_integrate_elastic", load().fem_integrate_elastic(
         t.handle, p, n_elem, _addr(coords), _addr(coeffs), coeff_stride, prec, _addr(A_out),
         _addr(b_out), _addr(status), _stream(stream)))
+
+
+def fem_debug_stall_next(t: Tables) -> int:
+    """Test hook: the next tensor-core launch withholds its operand copies (bounded waits expire)."""
+    return _check("fem_debug_stall_next", load().fem_debug_stall_next(t.handle))

@@ -177,6 +177,12 @@ int fem_tables_destroy(fem_tables t) {
   return FEM_OK;
 }
 
+int fem_debug_stall_next(fem_tables t) {
+  if (!t) return invalid("fem_debug_stall_next: tables handle is NULL");
+  t->stall_next = 1;
+  return FEM_OK;
+}
+
 int fem_error_flag(fem_tables t, int clear) {
   if (!t || !t->d_err) return invalid("fem_error_flag: tables handle is NULL");
   int h = 0;
@@ -239,6 +245,8 @@ int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, con
       l.status = status;
       l.layout = layout;
       l.err = t->d_err;
+      l.stall = t->stall_next;
+      t->stall_next = 0;
       return launch_tc(p, prec == FEM_F16X3, d, l, stream);
     }
   }

@@ -51,6 +51,7 @@ struct DevTable {
 struct fem_tables_s {
   int elem = 0, p_min = 0, p_max = 0, device = 0;
   int *d_err = nullptr;  // device error word (bounded waits that expired)
+  int stall_next = 0;    // test hook: the next tensor-core launch withholds its operand copies
   fem::DevTable tab[fem::kMaxP + 1];
   // staging for host-buffer integration (two pipeline slots)
   unsigned char *stage[2] = {nullptr, nullptr};
@@ -106,6 +107,7 @@ struct TcLaunch {
   int32_t *status;
   int layout;
   int *err;
+  int stall;  // withhold the operand copies (failure-detection test)
 };
 int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *stream);
 void build_tc_image(int p, const std::vector<double> &phi, bool f16, int aphi, std::vector<uint16_t> &out);

@@ -103,6 +103,7 @@ struct TcArgs {
   int32_t *status;
   int layout;
   int *err;
+  int stall;  // test hook: the loader issues no copies, so the pipeline's waits expire
 };
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
           const int s = g % C::STAGES;
           const uint32_t round = g / C::STAGES;
           if (!wait(&bar_empty[s], (round & 1) ^ 1)) break;
+          if (a.stall) continue;  // nothing arrives on full[s]: the consumers' waits run out
           unsigned char *dst = sm + (size_t)s * C::STAGE_BYTES + 2 * C::A_BYTES;
           ptx::mbar_arrive_expect_tx(&bar_full[s], 2 * C::B_BYTES);
           ptx::bulk_g2s(dst, reinterpret_cast<const unsigned char *>(a.img) + (size_t)c * 2 * C::B_BYTES,
@@ -594,6 +596,7 @@ int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *strea
   a.status = l.status;
   a.layout = l.layout;
   a.err = l.err;
+  a.stall = l.stall;
   if (!a.img) {
     set_error("tensor-core tables missing for this degree");
     return FEM_EUNSUPPORTED;

@@ -70,6 +70,26 @@ def test_tc_sympacked_and_flags(orc, lib, tables, p, prec):
     assert rel_frob(b, Rb).max() <= TOL_TC[prec]
 
 
+def test_tc_bounded_wait_expires_and_recovers(orc, lib, tables):
+    """Failure detection without a fault: the next launch withholds its
+    operand copies, its waits run out (about 1 s), the device error word and
+    the elements' status say so, and the next launch is correct again."""
+    import torch
+    p, E = 4, 20
+    X, C = workload(PRISM, p, E)
+    lib.fem_error_flag(tables)  # clear
+    lib.fem_debug_stall_next(tables)
+    A, b, st = gpu_integrate(tables, PRISM, p, X, C, lib.FEM_BF16X3)
+    assert lib.fem_error_flag(tables) == lib.FEM_ETIMEOUT
+    assert np.all(st & lib.FEM_ST_TIMEOUT)
+    assert lib.fem_error_flag(tables) == lib.FEM_OK  # cleared by the previous call
+    A, b, st = gpu_integrate(tables, PRISM, p, X, C, lib.FEM_BF16X3)
+    assert lib.fem_error_flag(tables) == lib.FEM_OK and np.all(st == 0)
+    RA, _, _ = orc.integrate(PRISM, p, X, C)
+    n = ns(PRISM, p)
+    assert rel_frob(A.reshape(E, n, n), RA).max() <= TOL_TC[2]
+
+
 def test_tc_tet_unsupported(lib):
     import torch
     t = lib.fem_tables_build(lib.FEM_TET4, 1, 1)
