@@ -41,13 +41,15 @@ struct FmaCfg {
   static constexpr int QC = QC_, KC = ND * QC, NCH = (NQ + QC - 1) / QC;
   static constexpr int NREC = NV * 3 + 11;  // coords + coefficients per element
   static constexpr int NEDGE = kEdgeRec;    // FP64 edge record per element
+  static constexpr int NZ = ELEM_ == FEM_PRISM6 ? P_ + 1 : 0;  // zeta levels of the rule
+  static constexpr int NAB = NZ * NZ;                           // (xi, eta) points per level
   static_assert(BM % TM == 0 && BN % TN == 0, "tile must split into micro-tiles");
   static_assert(NT <= 1024, "too many threads");
 
   template <class T>
   static constexpr size_t smem_bytes() {
     return sizeof(T) * ((size_t)KC * BM + (size_t)EPB * KC * BN + (size_t)EPB * NQ * kGStride) +
-           sizeof(double) * (size_t)EPB * (NREC + NEDGE) + sizeof(int) * (size_t)(EPB + 1) +
+           sizeof(double) * (size_t)EPB * (NREC + NEDGE + NZ * kZf + NAB * kXf) + sizeof(int) * (size_t)(EPB + 1) +
            sizeof(int64_t) * (size_t)EPB + 64;
   }
 };
@@ -108,7 +110,9 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   T *sG = sT + C::EPB * C::KC * C::BN;                  // [EPB][NQ][kGStride]
   double *sX = reinterpret_cast<double *>(sG + C::EPB * C::NQ * kGStride);  // [EPB][NREC]
   double *sEd = sX + C::EPB * C::NREC;                                     // [EPB][NEDGE]
-  int *sSt = reinterpret_cast<int *>(sEd + C::EPB * C::NEDGE);             // [EPB]
+  double *sZF = sEd + C::EPB * C::NEDGE;                                   // [EPB][NZ][9]  (prisms)
+  double *sXF = sZF + C::EPB * C::NZ * kZf;                                // [EPB][NAB][3] (prisms)
+  int *sSt = reinterpret_cast<int *>(sXF + C::EPB * C::NAB * kXf);         // [EPB]
   int64_t *sE = reinterpret_cast<int64_t *>(sSt + C::EPB + (C::EPB & 1));   // [EPB] element ids
   float *sU = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(sE + C::EPB) + 15) & ~(uintptr_t)15);      // [EPB][NS] (LAW)
@@ -149,6 +153,25 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     if (!isfinite(sX[idx])) atomicOr(&sSt[idx / C::NREC], FEM_ST_NONFINITE);
   for (int le = tid; le < C::EPB; le += nthr) edge_record<C::ELEM>(sX + le * C::NREC, sEd + le * C::NEDGE);
   __syncthreads();
+  if (C::ELEM == FEM_PRISM6) {  // tensor-product factors of J (per zeta level and per (xi, eta))
+    for (int idx = tid; idx < C::EPB * (C::NZ + C::NAB); idx += nthr) {
+      const int le = idx / (C::NZ + C::NAB), r = idx % (C::NZ + C::NAB);
+      const double *ed = sEd + le * C::NEDGE;
+      if (r < C::NZ)
+        prism_zf(ed, qp[4 * (r * C::NAB) + 2], sZF + (le * C::NZ + r) * kZf);
+      else
+        prism_xf(ed, qp[4 * (r - C::NZ)], qp[4 * (r - C::NZ) + 1], sXF + (le * C::NAB + r - C::NZ) * kXf);
+    }
+    __syncthreads();
+  }
+  // adj J and det J at point q of local element le
+  auto geo = [&](int le, int q, double (&adj)[3][3]) -> double {
+    if (C::ELEM == FEM_PRISM6) {
+      const int iz = q / C::NAB, iab = q % C::NAB;
+      return jac_adj_tp(sZF + (le * C::NZ + iz) * kZf, sXF + (le * C::NAB + iab) * kXf, adj);
+    }
+    return jac_adj_edges<C::ELEM>(sEd + le * C::NEDGE, qp + 4 * q, adj);
+  };
   if (!ELAST && a.layout == FEM_OUT_SYMPACKED) {
     for (int le = tid; le < C::EPB; le += nthr) {
       const double *cf = sX + le * C::NREC + C::NV * 3;
@@ -166,7 +189,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
       // block (i, k) of isotropic elasticity: G[a][b] = (w / det) (lam adj_ai adj_bk
       //   + mu d_ik (adj adj^T)_ab + mu adj_ak adj_bi),  G[3][3] slot 9 = w det f_i (k = 0)
       double adj[3][3];
-      const double det = jac_adj_edges<C::ELEM>(sEd + le * C::NEDGE, qp + 4 * q, adj);
+      const double det = geo(le, q, adj);
       st = det > 0.0 ? 0 : FEM_ST_DET;
       const double *cf = rec + C::NV * 3;
       const double Ey = cf[0], nu = cf[1];
@@ -193,7 +216,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
       g[10] = 0.0;
     } else if (LAW == 0) {
       double adj[3][3];
-      const double det = jac_adj_edges<C::ELEM>(sEd + le * C::NEDGE, qp + 4 * q, adj);
+      const double det = geo(le, q, adj);
       st = det > 0.0 ? 0 : FEM_ST_DET;
       if (sizeof(T) == 4) {  // FP32 contraction: G products in FP32
         float gf[11];
@@ -207,7 +230,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
       // coefficient stage (Algorithm 1 line 10): u and grad u at the point from
       // the element's old degrees of freedom, then k(u, |grad u|), D = k I
       double adj[3][3];
-      const double det = jac_adj_edges<C::ELEM>(sEd + le * C::NEDGE, qp + 4 * q, adj);
+      const double det = geo(le, q, adj);
       st = det > 0.0 ? 0 : FEM_ST_DET;
       const T *ph = phi + (size_t)(4 * q) * C::NS;
       const float *U = sU + le * C::NS;

@@ -123,6 +123,52 @@ __device__ __forceinline__ double jac_adj_edges(const double *ed, const double *
   return J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
 }
 
+// Tensor-product geometry factors of a prism (FP64).  The rule's points are
+// q = iz n^2 + iab (iab = ia n + ib), with zeta depending on iz only and
+// (xi, eta) on iab only, so
+//   J[:,0], J[:,1] and adj row 2 = J[:,0] x J[:,1] depend on iz only  (zf[iz][9]),
+//   J[:,2]                                       depends on iab only (xf[iab][3]),
+// and per point only adj rows 0, 1 (J[:,1] x J[:,2], J[:,2] x J[:,0]) and
+// det = J[:,2] . adj row 2 remain: 15 FP64 operations instead of about 45.
+constexpr int kZf = 9, kXf = 3;
+
+__device__ __forceinline__ void prism_zf(const double *ed, double zeta, double *zf) {
+  const double lo = 0.5 * (1.0 - zeta), hi = 0.5 * (1.0 + zeta);
+  double c0[3], c1[3];
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    c0[i] = fma(lo, ed[0 + i], hi * ed[3 + i]);
+    c1[i] = fma(lo, ed[6 + i], hi * ed[9 + i]);
+  }
+  zf[0] = c0[0], zf[1] = c0[1], zf[2] = c0[2];
+  zf[3] = c1[0], zf[4] = c1[1], zf[5] = c1[2];
+  zf[6] = c0[1] * c1[2] - c0[2] * c1[1];
+  zf[7] = c0[2] * c1[0] - c0[0] * c1[2];
+  zf[8] = c0[0] * c1[1] - c0[1] * c1[0];
+}
+
+__device__ __forceinline__ void prism_xf(const double *ed, double xi, double eta, double *xf) {
+  const double h0 = 0.5 * (1.0 - xi - eta), h1 = 0.5 * xi, h2 = 0.5 * eta;
+#pragma unroll
+  for (int i = 0; i < 3; i++) xf[i] = fma(h0, ed[12 + i], fma(h1, ed[15 + i], h2 * ed[18 + i]));
+}
+
+// adj J and det J at point (iz, iab) from the element's factors.
+__device__ __forceinline__ double jac_adj_tp(const double *zf, const double *xf, double (&adj)[3][3]) {
+  const double c0x = zf[0], c0y = zf[1], c0z = zf[2], c1x = zf[3], c1y = zf[4], c1z = zf[5];
+  const double c2x = xf[0], c2y = xf[1], c2z = xf[2];
+  adj[0][0] = c1y * c2z - c1z * c2y;
+  adj[0][1] = c1z * c2x - c1x * c2z;
+  adj[0][2] = c1x * c2y - c1y * c2x;
+  adj[1][0] = c2y * c0z - c2z * c0y;
+  adj[1][1] = c2z * c0x - c2x * c0z;
+  adj[1][2] = c2x * c0y - c2y * c0x;
+  adj[2][0] = zf[6];
+  adj[2][1] = zf[7];
+  adj[2][2] = zf[8];
+  return c2x * zf[6] + c2y * zf[7] + c2z * zf[8];
+}
+
 // Point record from FP64 adj J and det J with the 3x3 products in FP32 (for
 // the FP32 and tensor-core contractions, whose point records are FP32).
 __device__ __forceinline__ void point_from_adj_f32(const double (&adj)[3][3], double det, double w,

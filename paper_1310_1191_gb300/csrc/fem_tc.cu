@@ -70,7 +70,10 @@ struct TcCfg {
   static constexpr size_t OFF_G = (size_t)STAGES * STAGE_BYTES;
   static constexpr size_t OFF_X = OFF_G + 2 * (size_t)GBUF * 4;
   static constexpr size_t OFF_ED = OFF_X + 2 * (size_t)MAXEL * NREC * 8;
-  static constexpr size_t OFF_INV = OFF_ED + 2 * (size_t)MAXEL * kEdgeRec * 8;  // float [2][2][MAXEL]
+  static constexpr int NZ = P + 1, NAB = NZ * NZ;  // tensor-product factors of J per element
+  static constexpr size_t OFF_ZF = OFF_ED + 2 * (size_t)MAXEL * kEdgeRec * 8;
+  static constexpr size_t OFF_XF = OFF_ZF + (size_t)MAXEL * NZ * kZf * 8;  // one buffer (geometry warps only)
+  static constexpr size_t OFF_INV = OFF_XF + (size_t)MAXEL * NAB * kXf * 8;  // float [2][2][MAXEL]
   static constexpr size_t OFF_GS = OFF_INV + 16 * (size_t)MAXEL;                // geometry scratch
   static constexpr size_t OFF_BAR = (OFF_GS + 16 * (size_t)MAXEL + 15) / 16 * 16;
   static constexpr int NBAR = 2 * STAGES + 9;
@@ -135,6 +138,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
   float *sG = reinterpret_cast<float *>(sm + C::OFF_G);          // [2][MAXEL][NQP][12]
   double *sX = reinterpret_cast<double *>(sm + C::OFF_X);        // [2][MAXEL][NREC]
   double *sEd = reinterpret_cast<double *>(sm + C::OFF_ED);      // [2][MAXEL][21]
+  double *sZF = reinterpret_cast<double *>(sm + C::OFF_ZF);      // [MAXEL][NZ][9]
+  double *sXF = reinterpret_cast<double *>(sm + C::OFF_XF);      // [MAXEL][NAB][3]
   float *sInv = reinterpret_cast<float *>(sm + C::OFF_INV);      // [2][MAXEL] matrix rows
   float *sInvB = sInv + 2 * C::MAXEL;                            // [2][MAXEL] load-vector row
   int *sSt = reinterpret_cast<int *>(sm + C::OFF_GS);            // [MAXEL] geometry scratch
@@ -305,6 +310,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
         }
       }
       asm volatile("bar.sync 2, 64;" ::: "memory");
+      if (!*sAbort) {  // tensor-product factors of J
+        for (int idx = gt; idx < nel * (C::NZ + C::NAB); idx += kNGeo) {
+          const int el = idx / (C::NZ + C::NAB), r = idx % (C::NZ + C::NAB);
+          const double *ed = Ed + el * kEdgeRec;
+          if (r < C::NZ)
+            prism_zf(ed, a.qp[4 * (r * C::NAB) + 2], sZF + (el * C::NZ + r) * kZf);
+          else
+            prism_xf(ed, a.qp[4 * (r - C::NZ)], a.qp[4 * (r - C::NZ) + 1], sXF + (el * C::NAB + r - C::NZ) * kXf);
+        }
+      }
+      asm volatile("bar.sync 2, 64;" ::: "memory");
       if (!*sAbort) {
         for (int idx = gt; idx < nel * C::NQP; idx += kNGeo) {
           const int el = idx / C::NQP, q = idx % C::NQP;
@@ -312,7 +328,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
           if (q < C::NQ) {
             float gv[11];
             double adj[3][3];
-            const double det = jac_adj_edges<FEM_PRISM6>(Ed + el * kEdgeRec, a.qp + 4 * q, adj);
+            const int iz = q / C::NAB, iab = q % C::NAB;
+            const double det = jac_adj_tp(sZF + (el * C::NZ + iz) * kZf, sXF + (el * C::NAB + iab) * kXf, adj);
             point_from_adj_f32(adj, det, a.qp[4 * q + 3], X + el * C::NREC + 18, gv);
 #pragma unroll
             for (int k = 0; k < 11; k++) gr[k] = gv[k];
