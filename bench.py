@@ -47,7 +47,7 @@ PEAK_F64 = 152 * 2.07e9 * 2 * 2 / 1e12     # 2 FP64 FMA per SM per clock: 1.26 T
 HBM_FALLBACK, BF16_FALLBACK = 6800.0, 1900.0
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture of the full-size launch (profiles/fma_kernel_f64_p7_traffic.md)
-TRAFFIC = {}
+TRAFFIC = {("f64", 7): 45.63e6 + 1.96e9}
 
 
 def measured_peaks():
@@ -386,6 +386,63 @@ def wl_elastic(lib, tables, stream, dev, reps, scale_down=1, degrees=range(1, 8)
             "per_degree": out}
 
 
+def _copy_ms(stream, pairs, reps=2):
+    """Device time (ms) of the host<->device copies dst.copy_(src) in pairs."""
+    return _timed(stream, lambda: [d.copy_(s, non_blocking=True) for d, s in pairs], reps)
+
+
+def wl_split(lib, tables, stream, dev, reps, scale_down=1, degrees=range(1, 8)):
+    """Split geometry (the paper's NOJAC variants: det J and J^{-1} per point
+    stored, then read) against the fused kernels (JAC), FP64, at the sweep's
+    element counts; and the per-stage host<->device times of the paper's
+    Tables 6/7 (pinned host buffers, over NVLink-C2C)."""
+    import torch
+    out = {}
+    for p in degrees:
+        E = max(1, SWEEP_E[p] // scale_down)
+        n, q = ns_of(p), nq_of(p)
+        X, C = inputs.prism_mesh(E), inputs.coefficients(E)
+        Xd, Cd = torch.from_numpy(X).to(dev), torch.from_numpy(C).to(dev)
+        A = torch.empty((E, n * n), dtype=torch.float64, device=dev)
+        b = torch.empty((E, n), dtype=torch.float64, device=dev)
+        T = torch.empty((E, q, 10), dtype=torch.float64, device=dev)
+        st = torch.empty((E,), dtype=torch.int32, device=dev)
+        F, L = lib.FEM_F64, lib.FEM_OUT_FULL
+        fused = _timed(stream, lambda: lib.fem_integrate(tables, p, E, Xd, Cd, E, F, L, A, b, st, stream), reps)
+        A_ref = A[:: max(1, E // 64)].clone()
+        terms = _timed(stream, lambda: lib.fem_jacobian_terms(tables, p, E, Xd, T, st, stream), reps)
+        nojac = _timed(stream, lambda: lib.fem_integrate_terms(tables, p, E, T, Cd, E, F, L, A, b, st, stream),
+                       reps)
+        stream.synchronize()
+        dev_rel = float(((A[:: max(1, E // 64)] - A_ref).norm() / A_ref.norm()).item())
+        Xh, Ch = torch.from_numpy(X).pin_memory(), torch.from_numpy(C).pin_memory()
+        Th = torch.empty(T.shape, dtype=T.dtype).pin_memory()
+        Ah = torch.empty(A.shape, dtype=A.dtype).pin_memory()
+        bh = torch.empty(b.shape, dtype=b.dtype).pin_memory()
+        h2d_jac = _copy_ms(stream, [(Xd, Xh), (Cd, Ch)])
+        h2d_nojac = _copy_ms(stream, [(T, Th), (Cd, Ch)])
+        d2h = _copy_ms(stream, [(Ah, A), (bh, b)])
+        init = _timed(stream, lambda: (A.zero_(), b.zero_()), 2)
+        tb = E * q * 80
+        out[str(p)] = {
+            "elements": E,
+            "fused_jac_ms": round(fused, 3), "terms_pass_ms": round(terms, 3),
+            "nojac_integrate_ms": round(nojac, 3), "nojac_total_ms": round(terms + nojac, 3),
+            "nojac_over_jac": round((terms + nojac) / fused, 3),
+            "nojac_integrate_over_jac": round(nojac / fused, 3),
+            "terms_bytes": tb, "terms_pass_gbs": round((tb + E * 144) / terms / 1e6, 1),
+            "max_rel_diff_nojac_vs_jac": dev_rel,
+            "stages_ms": {"input_transfer_jac": round(h2d_jac, 3), "input_transfer_nojac": round(h2d_nojac, 3),
+                          "output_memory_init": round(init, 3), "output_transfer": round(d2h, 3)},
+        }
+        del Xd, Cd, A, b, T, st, Xh, Ch, Th, Ah, bh, A_ref
+        torch.cuda.empty_cache()
+    return {"workload": "prism degree sweep element counts, FP64, full A_e + b_e; JAC = fused geometry, "
+                        "NOJAC = device terms pass (det J, J^-1 per point, 80 B) + integration reading them; "
+                        "stages: pinned host buffers <-> HBM",
+            "per_degree": out}
+
+
 def wl_batched(lib, tables, stream, dev, reps, E=500000):
     import torch
     X = inputs.prism_mesh(E)
@@ -485,6 +542,9 @@ def run_only(args):
     elif args.only == "elastic":
         degs = tuple(int(x) for x in args.degrees.split(",")) if args.degrees else range(1, 8)
         out = wl_elastic(lib, tables, stream, dev, reps, args.scale_down, degs)
+    elif args.only == "split":
+        degs = tuple(int(x) for x in args.degrees.split(",")) if args.degrees else range(1, 8)
+        out = wl_split(lib, tables, stream, dev, reps, args.scale_down, degs)
     else:  # sweep at one precision
         prec = lib.FEM_F64 if args.precision == "f64" else lib.FEM_F32
         dt = torch.float64 if prec == lib.FEM_F64 else torch.float32
@@ -568,6 +628,7 @@ def run_ours(args):
         workloads["mixed_degree"] = wl_batched(lib, tables, stream, dev, reps)
         workloads["nonlinear_law"] = wl_surrogate(lib, tables, stream, dev, reps)
         workloads["elasticity"] = wl_elastic(lib, tables, stream, dev, reps)
+        workloads["split_geometry"] = wl_split(lib, tables, stream, dev, 2)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_baseline(sweep)
@@ -613,7 +674,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--only", choices=["sweep", "tets", "tc", "mixed", "law", "elastic"],
+    ap.add_argument("--only", choices=["sweep", "tets", "tc", "mixed", "law", "elastic", "split"],
                     help="run one workload alone (profiling); prints its own JSON")
     ap.add_argument("--elements", type=int, default=0, help="elements for --only tc/mixed/law")
     ap.add_argument("--degrees", default="", help="comma-separated degrees for --only sweep/tc")

@@ -129,6 +129,38 @@ int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coo
                           int64_t coeff_stride, int prec, void *A_out, void *b_out, int32_t *status,
                           void *stream);
 
+/* Split geometry (the paper's NOJAC kernel variants, Section 4 "Jacobian
+ * terms"; Algorithm 1 line 8 moved out of the integration kernel): for every
+ * element and quadrature point, det J and the 9 entries of J^{-1}.
+ *   coords : device, double [n_elem][NV][3] (as fem_integrate), 8-byte aligned;
+ *   terms  : device, double [n_elem][NQ][10], 16-byte aligned, caller-owned:
+ *            terms[e][q][0] = det J, terms[e][q][1 + 3k + m] = (J^{-1})[k][m]
+ *            = d xi_k / d x_m, q in the rule's point order (fem_reference_rule);
+ *   status : device int32 [n_elem] or NULL: FEM_ST_NONFINITE for a non-finite
+ *            coordinate, FEM_ST_DET if det J <= 0 at some point.
+ * The paper prepares these terms on the host; this pass computes them on the
+ * device.  Errors as fem_integrate (FEM_EINVAL for NULL/misaligned pointers,
+ * n_elem < 0, p outside the tables; FEM_ECUDA for a failed launch). */
+int fem_jacobian_terms(fem_tables t, int p, int64_t n_elem, const double *coords, double *terms,
+                       int32_t *status, void *stream);
+
+/* Integration from stored Jacobian terms (NOJAC): the result of fem_integrate
+ * for the elements whose terms fem_jacobian_terms (or any producer of the same
+ * layout) wrote.  terms: device double [n_elem][NQ][10], 8-byte aligned; the
+ * other arguments as fem_integrate.  adj J = det J * J^{-1} replaces the
+ * geometry stage; non-finite terms set FEM_ST_NONFINITE, det J <= 0 sets
+ * FEM_ST_DET.  prec FEM_F64 / FEM_F32 (tensor-core precisions
+ * FEM_EUNSUPPORTED). */
+int fem_integrate_terms(fem_tables t, int p, int64_t n_elem, const double *terms, const double *coeffs,
+                        int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out,
+                        int32_t *status, void *stream);
+
+/* Linear elastostatics (as fem_integrate_elastic) from stored Jacobian terms
+ * (NOJAC, the variant the paper measures on its model problem, Section 5). */
+int fem_integrate_elastic_terms(fem_tables t, int p, int64_t n_elem, const double *terms,
+                                const double *coeffs, int64_t coeff_stride, int prec, void *A_out,
+                                void *b_out, int32_t *status, void *stream);
+
 /* The same integration for HOST buffers (the paper's host code stages element
  * data to the device, runs the kernel and copies the matrices back, Section
  * 4.2): the elements are processed in chunks of `chunk` elements (<= 0: about

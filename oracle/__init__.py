@@ -70,6 +70,7 @@ def _load():
             lib.orc_mlp_loss_grad.restype = d
             lib.orc_integrate_ex.argtypes = [i, i, i64, P, P, i64, i, P, i, P, P, P, P, P, i]
             lib.orc_integrate_elastic.argtypes = [i, i64, P, P, i64, P, P, P, i]
+            lib.orc_jacobian_terms.argtypes = [i, i, i64, P, P, P]
             lib.orc_max_threads.argtypes = []
             _lib = lib
     return _lib
@@ -188,6 +189,22 @@ def integrate(elem: int, p: int, coords, coeffs, law: int = 0, ucoef=None, mlp=N
     if rc != 0:
         raise RuntimeError("oracle integrate failed")
     return A, b, st
+
+
+def jacobian_terms(elem: int, p: int, coords):
+    """Per element and quadrature point: det J and J^{-1} (the NOJAC kernels'
+    input, Section 4).  Returns terms [E][NQ][10] (det, then (J^{-1})[k][m] at
+    1 + 3k + m) and status [E]."""
+    coords = _f64(coords)
+    E = coords.shape[0]
+    n = nq(elem, p)
+    if n < 0:
+        raise ValueError("unsupported element/degree")
+    terms = np.zeros((E, n, 10))
+    st = np.zeros(E, dtype=np.int32)
+    if _load().orc_jacobian_terms(elem, p, E, _ptr(coords), _ptr(terms), _ptr(st)) != 0:
+        raise RuntimeError("oracle jacobian_terms failed")
+    return terms, st
 
 
 def integrate_elastic(p: int, coords, coeffs, nthreads: int = 0):

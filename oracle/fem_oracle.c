@@ -261,6 +261,48 @@ static void inv3(const double J[3][3], double det, double Ji[3][3]) {
         }
 }
 
+/* Jacobian terms (Section 4: the NOJAC kernel variants read them instead of
+ * computing them): for every element and quadrature point, det J and the 9
+ * entries of J^{-1}.  terms[e][q][0] = det J, terms[e][q][1 + 3k + m] =
+ * (J^{-1})[k][m] = d xi_k / d x_m.  status[e]: ORC_ST_NONFINITE for a
+ * non-finite coordinate, ORC_ST_DET if det J <= 0 (or NaN) at some point. */
+int orc_jacobian_terms(int elem, int p, int64_t E, const double *coords, double *terms,
+                       int32_t *status) {
+    int NQ = orc_nq(elem, p);
+    if (NQ < 0) return -1;
+    int nv = elem == ORC_TET ? 4 : 6;
+    double *xq = (double *)malloc(sizeof(double) * 3 * NQ);
+    double *wq = (double *)malloc(sizeof(double) * NQ);
+    orc_rule(elem, p, xq, wq);
+    for (int64_t e = 0; e < E; e++) {
+        const double *X = coords + (size_t)e * nv * 3;
+        int32_t st = 0;
+        for (int k = 0; k < nv * 3; k++)
+            if (!isfinite(X[k])) st |= ORC_ST_NONFINITE;
+        for (int q = 0; q < NQ; q++) {
+            double dN[3][6], J[3][3], Ji[3][3];
+            map_derivs(elem, xq + 3 * q, dN);
+            for (int i = 0; i < 3; i++)
+                for (int k = 0; k < 3; k++) {
+                    double s = 0.0;
+                    for (int v = 0; v < nv; v++) s += X[3 * v + i] * dN[k][v];
+                    J[i][k] = s;
+                }
+            double det = det3(J);
+            if (!(det > 0.0)) st |= ORC_ST_DET;
+            inv3(J, det, Ji);
+            double *t = terms + ((size_t)e * NQ + q) * 10;
+            t[0] = det;
+            for (int k = 0; k < 3; k++)
+                for (int m = 0; m < 3; m++) t[1 + 3 * k + m] = Ji[k][m];
+        }
+        if (status) status[e] = st;
+    }
+    free(xq);
+    free(wq);
+    return 0;
+}
+
 /* ------------------------------------------------ nonlinear coefficient law */
 /* k solves F(k) = k - 1 - 0.5 exp(-u^2) - 0.2 log(1 + k g) = 0; exactly 8
  * Newton steps from k0 = 1 + 0.5 exp(-u^2), no early exit. */

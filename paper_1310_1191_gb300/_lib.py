@@ -32,6 +32,7 @@ EXPORTS = (
     "fem_mlp_create", "fem_mlp_destroy", "fem_mlp_nparams", "fem_mlp_forward", "fem_mlp_loss_grad",
     "fem_mlp_train", "fem_mlp_get", "fem_mlp_set", "fem_mlp_save", "fem_mlp_load",
     "fem_integrate_host", "fem_integrate_elastic", "fem_debug_stall_next",
+    "fem_jacobian_terms", "fem_integrate_terms", "fem_integrate_elastic_terms",
 )
 FEM_LAW_EXACT, FEM_LAW_MLP = 1, 2
 FEM_PLAN_AUTOTUNE, FEM_PLAN_LOOP, FEM_PLAN_NOGRAPH, FEM_PLAN_CONCURRENT = 1, 2, 4, 8
@@ -89,6 +90,9 @@ def load():
     lib.fem_mlp_load.argtypes = [ctypes.c_char_p, P]
     lib.fem_integrate_host.argtypes = [P, i, i64, P, P, i64, i, i, P, P, P, i64]
     lib.fem_integrate_elastic.argtypes = [P, i, i64, P, P, i64, i, P, P, P, P]
+    lib.fem_jacobian_terms.argtypes = [P, i, i64, P, P, P, P]
+    lib.fem_integrate_terms.argtypes = [P, i, i64, P, P, i64, i, i, P, P, P, P]
+    lib.fem_integrate_elastic_terms.argtypes = [P, i, i64, P, P, i64, i, P, P, P, P]
     lib.fem_debug_stall_next.argtypes = [P]
     _lib = lib
     return lib
@@ -404,6 +408,28 @@ def fem_integrate_elastic(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_
     """Linear elastostatics: A_out [n][3][3][NS][NS], b_out [n][3][NS] (see fem.h)."""
     return _check("fem_integrate_elastic", load().fem_integrate_elastic(
         t.handle, p, n_elem, _addr(coords), _addr(coeffs), coeff_stride, prec, _addr(A_out),
+        _addr(b_out), _addr(status), _stream(stream)))
+
+
+def fem_jacobian_terms(t: Tables, p: int, n_elem: int, coords, terms, status=None, stream=None) -> int:
+    """Split geometry pass: terms [n][NQ][10] = det J, J^{-1} per point (see fem.h)."""
+    return _check("fem_jacobian_terms", load().fem_jacobian_terms(
+        t.handle, p, n_elem, _addr(coords), _addr(terms), _addr(status), _stream(stream)))
+
+
+def fem_integrate_terms(t: Tables, p: int, n_elem: int, terms, coeffs, coeff_stride: int, prec: int,
+                        layout: int, A_out, b_out=None, status=None, stream=None) -> int:
+    """Integration from stored Jacobian terms (NOJAC); outputs as fem_integrate."""
+    return _check("fem_integrate_terms", load().fem_integrate_terms(
+        t.handle, p, n_elem, _addr(terms), _addr(coeffs), coeff_stride, prec, layout,
+        _addr(A_out), _addr(b_out), _addr(status), _stream(stream)))
+
+
+def fem_integrate_elastic_terms(t: Tables, p: int, n_elem: int, terms, coeffs, coeff_stride: int,
+                                prec: int, A_out, b_out=None, status=None, stream=None) -> int:
+    """Linear elastostatics from stored Jacobian terms; outputs as fem_integrate_elastic."""
+    return _check("fem_integrate_elastic_terms", load().fem_integrate_elastic_terms(
+        t.handle, p, n_elem, _addr(terms), _addr(coeffs), coeff_stride, prec, _addr(A_out),
         _addr(b_out), _addr(status), _stream(stream)))
 
 

@@ -285,6 +285,77 @@ int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coo
   return prec == FEM_F64 ? launch_fma_elastic_f64(p, a, stream) : launch_fma_elastic_f32(p, a, stream);
 }
 
+int fem_integrate_terms(fem_tables t, int p, int64_t n_elem, const double *terms, const double *coeffs,
+                        int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out,
+                        int32_t *status, void *stream) {
+  if (!t) return invalid("fem_integrate_terms: tables handle is NULL");
+  if (p < t->p_min || p > t->p_max || n_elem < 0) return invalid("fem_integrate_terms: bad degree or n_elem");
+  if (prec != FEM_F64 && prec != FEM_F32) {
+    set_error("fem_integrate_terms: FEM_F64 or FEM_F32 only");
+    return FEM_EUNSUPPORTED;
+  }
+  if (layout != FEM_OUT_FULL && layout != FEM_OUT_SYMPACKED) return invalid("fem_integrate_terms: unknown layout");
+  if (n_elem == 0) return FEM_OK;
+  if (!terms || !coeffs || !A_out) return invalid("fem_integrate_terms: NULL terms, coeffs or A_out");
+  if (coeff_stride < n_elem) return invalid("fem_integrate_terms: coeff_stride < n_elem");
+  if (((uintptr_t)terms | (uintptr_t)coeffs) & 7) return invalid("fem_integrate_terms: terms/coeffs not 8-byte aligned");
+  if ((uintptr_t)A_out & 15) return invalid("fem_integrate_terms: A_out not 16-byte aligned");
+  const size_t osz = prec == FEM_F64 ? 8 : 4;
+  if (b_out && ((uintptr_t)b_out & (osz - 1))) return invalid("fem_integrate_terms: b_out misaligned");
+  if (status && ((uintptr_t)status & 3)) return invalid("fem_integrate_terms: status misaligned");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return invalid("fem_integrate_terms: tables live on another device");
+  const DevTable &d = t->tab[p];
+  FmaArgs a;
+  a.n = n_elem;
+  a.coords = nullptr;
+  a.terms = terms;
+  a.coeffs = coeffs;
+  a.cstride = coeff_stride;
+  a.qp = d.qp;
+  a.A = A_out;
+  a.b = b_out;
+  a.status = status;
+  a.layout = layout;
+  a.phi = prec == FEM_F64 ? (const void *)d.phi64 : (const void *)d.phi32;
+  return launch_fma_terms(t->elem, p, prec, a, stream);
+}
+
+int fem_integrate_elastic_terms(fem_tables t, int p, int64_t n_elem, const double *terms, const double *coeffs,
+                                int64_t coeff_stride, int prec, void *A_out, void *b_out, int32_t *status,
+                                void *stream) {
+  if (!t || t->elem != FEM_PRISM6) return invalid("fem_integrate_elastic_terms: needs prism tables");
+  if (p < t->p_min || p > t->p_max || n_elem < 0) return invalid("fem_integrate_elastic_terms: bad degree or n_elem");
+  if (prec != FEM_F64 && prec != FEM_F32) {
+    set_error("fem_integrate_elastic_terms: FP64 or FP32 only");
+    return FEM_EUNSUPPORTED;
+  }
+  if (n_elem == 0) return FEM_OK;
+  if (!terms || !coeffs || !A_out || coeff_stride < n_elem)
+    return invalid("fem_integrate_elastic_terms: NULL buffer or coeff_stride < n_elem");
+  if ((((uintptr_t)terms | (uintptr_t)coeffs) & 7) || ((uintptr_t)A_out & 15))
+    return invalid("fem_integrate_elastic_terms: misaligned buffer");
+  if (9 * n_elem > 0x7fffffffLL * 4) return invalid("fem_integrate_elastic_terms: too many elements");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return invalid("fem_integrate_elastic_terms: tables live on another device");
+  const DevTable &d = t->tab[p];
+  FmaArgs a;
+  a.n = n_elem;
+  a.coords = nullptr;
+  a.terms = terms;
+  a.coeffs = coeffs;
+  a.cstride = coeff_stride;
+  a.qp = d.qp;
+  a.phi = prec == FEM_F64 ? (const void *)d.phi64 : (const void *)d.phi32;
+  a.A = A_out;
+  a.b = b_out;
+  a.status = status;
+  a.layout = FEM_OUT_FULL;
+  return launch_fma_elastic_terms(p, prec, a, stream);
+}
+
 int fem_integrate_host(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
                        int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out, int32_t *status,
                        int64_t chunk) {

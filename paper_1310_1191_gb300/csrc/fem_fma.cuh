@@ -102,7 +102,9 @@ constexpr size_t law_smem_bytes(int law) {
   return law == 0 ? 0 : (size_t)C::EPB * C::NS * 4 + 16 + (law == 2 ? (size_t)kMlpP * 4 + 16 : 0);
 }
 
-template <class T, class C, int LAW = 0>
+// SPLIT: the Jacobian terms (det J, J^{-1} per point) are read from a.terms
+// instead of computed from a.coords (the paper's NOJAC variants).
+template <class T, class C, int LAW = 0, bool SPLIT = false>
 __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, const T *phi, int64_t k0,
                                          int64_t k_end, int ti, int tj, unsigned char *smem) {
   T *sPA = reinterpret_cast<T *>(smem);                 // [KC][BM]
@@ -121,6 +123,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
 
   const int tid = threadIdx.x, nthr = blockDim.x;
   constexpr int NSZ = C::NS * C::NS, NPK = C::NS * (C::NS + 1) / 2;
+  constexpr bool split = SPLIT;  // Jacobian terms read, not computed
 
   for (int le = tid; le < C::EPB; le += nthr) {
     const int64_t k = k0 + le;
@@ -136,8 +139,12 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     const int le = idx / C::NREC, k = idx % C::NREC;
     const int64_t e = ELAST ? (sE[le] >= 0 ? sE[le] / 9 : -1) : sE[le];
     double v = 0.0;
-    if (e >= 0 && k < C::NV * 3 + NCF)
-      v = k < C::NV * 3 ? a.coords[e * (C::NV * 3) + k] : a.coeffs[(k - C::NV * 3) * a.cstride + e];
+    if (e >= 0 && k < C::NV * 3 + NCF) {
+      if (k >= C::NV * 3)
+        v = a.coeffs[(k - C::NV * 3) * a.cstride + e];
+      else if (!split)
+        v = a.coords[e * (C::NV * 3) + k];
+    }
     sX[idx] = v;
   }
   if (LAW != 0) {
@@ -151,26 +158,54 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   __syncthreads();
   for (int idx = tid; idx < C::EPB * C::NREC; idx += nthr)
     if (!isfinite(sX[idx])) atomicOr(&sSt[idx / C::NREC], FEM_ST_NONFINITE);
-  for (int le = tid; le < C::EPB; le += nthr) edge_record<C::ELEM>(sX + le * C::NREC, sEd + le * C::NEDGE);
+  if (!split)
+    for (int le = tid; le < C::EPB; le += nthr) edge_record<C::ELEM>(sX + le * C::NREC, sEd + le * C::NEDGE);
   __syncthreads();
-  if (C::ELEM == FEM_PRISM6) {  // tensor-product factors of J (per zeta level and per (xi, eta))
-    for (int idx = tid; idx < C::EPB * (C::NZ + C::NAB); idx += nthr) {
-      const int le = idx / (C::NZ + C::NAB), r = idx % (C::NZ + C::NAB);
-      const double *ed = sEd + le * C::NEDGE;
-      if (r < C::NZ)
-        prism_zf(ed, qp[4 * (r * C::NAB) + 2], sZF + (le * C::NZ + r) * kZf);
-      else
-        prism_xf(ed, qp[4 * (r - C::NZ)], qp[4 * (r - C::NZ) + 1], sXF + (le * C::NAB + r - C::NZ) * kXf);
+  if constexpr (C::ELEM == FEM_PRISM6) {
+    if (!split) {  // tensor-product factors of J (per zeta level and per (xi, eta))
+      for (int idx = tid; idx < C::EPB * (C::NZ + C::NAB); idx += nthr) {
+        const int le = idx / (C::NZ + C::NAB), r = idx % (C::NZ + C::NAB);
+        const double *ed = sEd + le * C::NEDGE;
+        if (r < C::NZ)
+          prism_zf(ed, qp[4 * (r * C::NAB) + 2], sZF + (le * C::NZ + r) * kZf);
+        else
+          prism_xf(ed, qp[4 * (r - C::NZ)], qp[4 * (r - C::NZ) + 1], sXF + (le * C::NAB + r - C::NZ) * kXf);
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
-  // adj J and det J at point q of local element le
+  // adj J and det J at point q of local element le; split geometry: adj J =
+  // det J * J^{-1} from the stored terms (non-finite terms flag the element)
   auto geo = [&](int le, int q, double (&adj)[3][3]) -> double {
-    if (C::ELEM == FEM_PRISM6) {
+    if constexpr (split) {
+      const int64_t e = ELAST ? (sE[le] >= 0 ? sE[le] / 9 : -1) : sE[le];
+      if (e < 0) {
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+#pragma unroll
+          for (int m = 0; m < 3; m++) adj[k][m] = k == m ? 1.0 : 0.0;
+        return 1.0;
+      }
+      const double *tr = a.terms + ((size_t)e * C::NQ + q) * 10;
+      const double det = tr[0];
+      bool fin = isfinite(det);
+#pragma unroll
+      for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int m = 0; m < 3; m++) {
+          const double v = tr[1 + 3 * k + m];
+          fin = fin && isfinite(v);
+          adj[k][m] = det * v;
+        }
+      if (!fin) atomicOr(&sSt[le], FEM_ST_NONFINITE);
+      return det;
+    }
+    if constexpr (C::ELEM == FEM_PRISM6) {
       const int iz = q / C::NAB, iab = q % C::NAB;
       return jac_adj_tp(sZF + (le * C::NZ + iz) * kZf, sXF + (le * C::NAB + iab) * kXf, adj);
+    } else {
+      return jac_adj_edges<C::ELEM>(sEd + le * C::NEDGE, qp + 4 * q, adj);
     }
-    return jac_adj_edges<C::ELEM>(sEd + le * C::NEDGE, qp + 4 * q, adj);
   };
   if (!ELAST && a.layout == FEM_OUT_SYMPACKED) {
     for (int le = tid; le < C::EPB; le += nthr) {
@@ -396,7 +431,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   __syncthreads();  // shared memory is reused by the next work item
 }
 
-template <class T, class C, int LAW = 0>
+template <class T, class C, int LAW = 0, bool SPLIT = false>
 __global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   long long blk = blockIdx.x;
@@ -404,14 +439,14 @@ __global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
   blk /= C::TILES;
   const int ti = (int)(blk % C::TILES);
   blk /= C::TILES;
-  fma_body<T, C, LAW>(a, a.qp, static_cast<const T *>(a.phi), blk * (int64_t)C::EPB, a.n, ti, tj, smem);
+  fma_body<T, C, LAW, SPLIT>(a, a.qp, static_cast<const T *>(a.phi), blk * (int64_t)C::EPB, a.n, ti, tj, smem);
 }
 
-template <class T, class C, int LAW = 0>
+template <class T, class C, int LAW = 0, bool SPLIT = false>
 int launch_fma_cfg(const FmaArgs &a, void *stream) {
   if (a.n == 0) return FEM_OK;
   const size_t smem = C::template smem_bytes<T>() + law_smem_bytes<C>(LAW);
-  cudaError_t err = cudaFuncSetAttribute(fma_kernel<T, C, LAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = cudaFuncSetAttribute(fma_kernel<T, C, LAW, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) {
     set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(err));
     return FEM_ECUDA;
@@ -422,7 +457,7 @@ int launch_fma_cfg(const FmaArgs &a, void *stream) {
     set_error("too many elements for one launch");
     return FEM_EINVAL;
   }
-  fma_kernel<T, C, LAW><<<(unsigned)grid, C::NT, smem, (cudaStream_t)stream>>>(a);
+  fma_kernel<T, C, LAW, SPLIT><<<(unsigned)grid, C::NT, smem, (cudaStream_t)stream>>>(a);
   err = cudaGetLastError();
   if (err != cudaSuccess) {
     set_error(std::string("fma_kernel launch: ") + cudaGetErrorString(err));
@@ -432,17 +467,20 @@ int launch_fma_cfg(const FmaArgs &a, void *stream) {
 }
 
 // Tile shapes per precision and degree (ELEM, P, BM, TM, TN, EPB, QC).  FP64
-// is bound by the FP64 pipe, so its shapes only need enough independent FMAs;
+// is bound by the FP64 pipe, which spends the same cycles on a warp
+// instruction whatever its active lanes, so its shapes fill whole warps
+// (threads per CTA at or just below a multiple of 32) and need only enough
+// independent FMAs;
 // FP32 is bound by instruction issue, so its micro-tiles are larger and their
 // rows 16-byte aligned for vector shared loads.
 template <class T, int ELEM, int P> struct FmaShape;
 template <> struct FmaShape<double, FEM_TET4, 1> { using type = FmaCfg<FEM_TET4, 1, 4, 1, 4, 64, 4>; };
 template <> struct FmaShape<double, FEM_PRISM6, 1> { using type = FmaCfg<FEM_PRISM6, 1, 6, 1, 6, 42, 4>; };
 template <> struct FmaShape<double, FEM_PRISM6, 2> { using type = FmaCfg<FEM_PRISM6, 2, 18, 3, 6, 14, 3>; };
-template <> struct FmaShape<double, FEM_PRISM6, 3> { using type = FmaCfg<FEM_PRISM6, 3, 40, 4, 4, 2, 8>; };
-template <> struct FmaShape<double, FEM_PRISM6, 4> { using type = FmaCfg<FEM_PRISM6, 4, 75, 5, 5, 1, 5>; };
+template <> struct FmaShape<double, FEM_PRISM6, 3> { using type = FmaCfg<FEM_PRISM6, 3, 40, 5, 8, 4, 8>; };
+template <> struct FmaShape<double, FEM_PRISM6, 4> { using type = FmaCfg<FEM_PRISM6, 4, 75, 3, 5, 1, 5>; };
 template <> struct FmaShape<double, FEM_PRISM6, 5> { using type = FmaCfg<FEM_PRISM6, 5, 126, 6, 6, 1, 6>; };
-template <> struct FmaShape<double, FEM_PRISM6, 6> { using type = FmaCfg<FEM_PRISM6, 6, 98, 7, 7, 1, 7>; };
+template <> struct FmaShape<double, FEM_PRISM6, 6> { using type = FmaCfg<FEM_PRISM6, 6, 98, 2, 7, 1, 7>; };
 template <> struct FmaShape<double, FEM_PRISM6, 7> { using type = FmaCfg<FEM_PRISM6, 7, 96, 6, 6, 1, 8>; };
 template <> struct FmaShape<float, FEM_TET4, 1> { using type = FmaCfg<FEM_TET4, 1, 4, 1, 4, 64, 4>; };
 template <> struct FmaShape<float, FEM_PRISM6, 1> { using type = FmaCfg<FEM_PRISM6, 1, 6, 1, 6, 42, 4>; };
@@ -461,33 +499,33 @@ struct FmaShapeE {
   using type = FmaCfg<FEM_PRISM6, P, S::BM, S::TM, S::TN, S::EPB, S::QC, 3>;
 };
 
-template <class T>
+template <class T, bool SPLIT = false>
 int launch_fma_elastic(int p, const FmaArgs &a, void *stream) {
   FmaArgs v = a;
   v.n = 9 * a.n;  // virtual elements
   switch (p) {
-    case 1: return launch_fma_cfg<T, typename FmaShapeE<T, 1>::type>(v, stream);
-    case 2: return launch_fma_cfg<T, typename FmaShapeE<T, 2>::type>(v, stream);
-    case 3: return launch_fma_cfg<T, typename FmaShapeE<T, 3>::type>(v, stream);
-    case 4: return launch_fma_cfg<T, typename FmaShapeE<T, 4>::type>(v, stream);
-    case 5: return launch_fma_cfg<T, typename FmaShapeE<T, 5>::type>(v, stream);
-    case 6: return launch_fma_cfg<T, typename FmaShapeE<T, 6>::type>(v, stream);
-    case 7: return launch_fma_cfg<T, typename FmaShapeE<T, 7>::type>(v, stream);
+    case 1: return launch_fma_cfg<T, typename FmaShapeE<T, 1>::type, 0, SPLIT>(v, stream);
+    case 2: return launch_fma_cfg<T, typename FmaShapeE<T, 2>::type, 0, SPLIT>(v, stream);
+    case 3: return launch_fma_cfg<T, typename FmaShapeE<T, 3>::type, 0, SPLIT>(v, stream);
+    case 4: return launch_fma_cfg<T, typename FmaShapeE<T, 4>::type, 0, SPLIT>(v, stream);
+    case 5: return launch_fma_cfg<T, typename FmaShapeE<T, 5>::type, 0, SPLIT>(v, stream);
+    case 6: return launch_fma_cfg<T, typename FmaShapeE<T, 6>::type, 0, SPLIT>(v, stream);
+    case 7: return launch_fma_cfg<T, typename FmaShapeE<T, 7>::type, 0, SPLIT>(v, stream);
   }
   return FEM_EINVAL;
 }
 
-template <class T, int LAW = 0>
+template <class T, int LAW = 0, bool SPLIT = false>
 int launch_fma_any(int elem, int p, const FmaArgs &a, void *stream) {
-  if (elem == FEM_TET4) return launch_fma_cfg<T, typename FmaShape<T, FEM_TET4, 1>::type, LAW>(a, stream);
+  if (elem == FEM_TET4) return launch_fma_cfg<T, typename FmaShape<T, FEM_TET4, 1>::type, LAW, SPLIT>(a, stream);
   switch (p) {
-    case 1: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 1>::type, LAW>(a, stream);
-    case 2: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 2>::type, LAW>(a, stream);
-    case 3: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 3>::type, LAW>(a, stream);
-    case 4: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 4>::type, LAW>(a, stream);
-    case 5: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 5>::type, LAW>(a, stream);
-    case 6: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 6>::type, LAW>(a, stream);
-    case 7: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 7>::type, LAW>(a, stream);
+    case 1: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 1>::type, LAW, SPLIT>(a, stream);
+    case 2: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 2>::type, LAW, SPLIT>(a, stream);
+    case 3: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 3>::type, LAW, SPLIT>(a, stream);
+    case 4: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 4>::type, LAW, SPLIT>(a, stream);
+    case 5: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 5>::type, LAW, SPLIT>(a, stream);
+    case 6: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 6>::type, LAW, SPLIT>(a, stream);
+    case 7: return launch_fma_cfg<T, typename FmaShape<T, FEM_PRISM6, 7>::type, LAW, SPLIT>(a, stream);
   }
   return FEM_EINVAL;
 }

@@ -79,6 +79,9 @@ struct FmaArgs {
   const int64_t *perm = nullptr;  // sorted position -> element id (batched path), or NULL
   const int64_t *offA = nullptr;  // per-element offset of A_e in A (values), or NULL
   const int64_t *offb = nullptr;  // per-element offset of b_e in b (values), or NULL
+  // split geometry: [n][NQ][10] det J and J^{-1} per point, read instead of
+  // computing J from coords (coords unused then), or NULL
+  const double *terms = nullptr;
   // nonlinear coefficient law (law kernels only)
   const float *ucoef = nullptr;  // [n][NS] field coefficients of u per element
   const float *mlpw = nullptr;   // network parameters (FP32 values of BF16 weights)
@@ -91,6 +94,9 @@ int launch_fma_f64(int elem, int p, const FmaArgs &a, void *stream);
 int launch_fma_f32(int elem, int p, const FmaArgs &a, void *stream);
 // linear elastostatics: a.n real elements, 9 blocks each
 int launch_fma_elastic_f64(int p, const FmaArgs &a, void *stream);
+// split geometry (a.terms set, a.coords unused): scalar form and elastostatics
+int launch_fma_terms(int elem, int p, int prec, const FmaArgs &a, void *stream);
+int launch_fma_elastic_terms(int p, int prec, const FmaArgs &a, void *stream);
 int launch_fma_elastic_f32(int p, const FmaArgs &a, void *stream);
 // law = 1 exact Newton law, 2 network with exact-law fallback
 int launch_fma_law_f64(int elem, int p, int law, const FmaArgs &a, void *stream);
