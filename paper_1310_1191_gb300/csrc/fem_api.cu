@@ -36,6 +36,8 @@ static void free_table(DevTable &d) {
   if (d.qp) cudaFree(d.qp);
   if (d.phi64) cudaFree(d.phi64);
   if (d.phi32) cudaFree(d.phi32);
+  if (d.phiT64) cudaFree(d.phiT64);
+  if (d.phiT32) cudaFree(d.phiT32);
   if (d.img_bf16) cudaFree(d.img_bf16);
   if (d.img_f16) cudaFree(d.img_f16);
   d = DevTable();
@@ -137,9 +139,20 @@ int fem_tables_build(int elem, int p_min, int p_max, fem_tables *out) {
     }
     std::vector<float> phi32(r.phi.size());
     for (size_t i = 0; i < r.phi.size(); i++) phi32[i] = (float)r.phi[i];
+    std::vector<double> phiT64(r.phi.size());
+    std::vector<float> phiT32(r.phi.size());
+    for (int q = 0; q < r.nq; q++)
+      for (int dd = 0; dd < 4; dd++)
+        for (int i = 0; i < r.ns; i++) {
+          const size_t src = ((size_t)(4 * q + dd)) * r.ns + i, dst = ((size_t)i * r.nq + q) * 4 + dd;
+          phiT64[dst] = r.phi[src];
+          phiT32[dst] = phi32[src];
+        }
     rc = upload(&d.qp, qp.data(), qp.size());
     if (rc == FEM_OK) rc = upload(&d.phi64, r.phi.data(), r.phi.size());
     if (rc == FEM_OK) rc = upload(&d.phi32, phi32.data(), phi32.size());
+    if (rc == FEM_OK) rc = upload(&d.phiT64, phiT64.data(), phiT64.size());
+    if (rc == FEM_OK) rc = upload(&d.phiT32, phiT32.data(), phiT32.size());
     if (rc == FEM_OK && elem == FEM_PRISM6) {
       double mx = 0.0;
       for (double v : r.phi) mx = std::fmax(mx, std::fabs(v));

@@ -61,7 +61,7 @@ struct FmaCfg {
 // belong to the first C::NT threads.
 constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
 
-// N consecutive values from shared memory; ALIGN = a number of elements that
+// N consecutive values (shared or global memory); ALIGN = a number of elements that
 // divides the offset of p from a 16-byte aligned base.  Uses 16- or 8-byte
 // loads when the alignment allows.
 template <class T, int N, int ALIGN>
@@ -267,15 +267,20 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
       double adj[3][3];
       const double det = geo(le, q, adj);
       st = det > 0.0 ? 0 : FEM_ST_DET;
-      const T *ph = phi + (size_t)(4 * q) * C::NS;
+      // point-major table: the 4 values of shape function k at point q are
+      // contiguous, so the threads of a warp (consecutive q) read one
+      // contiguous run per k
+      const T *ph = static_cast<const T *>(a.phiT) + (size_t)q * 4;
       const float *U = sU + le * C::NS;
       T u = 0, r0 = 0, r1 = 0, r2 = 0;
       for (int k = 0; k < C::NS; k++) {
         const T uk = (T)U[k];
-        u = fma(uk, ph[k], u);
-        r0 = fma(uk, ph[C::NS + k], r0);
-        r1 = fma(uk, ph[2 * C::NS + k], r1);
-        r2 = fma(uk, ph[3 * C::NS + k], r2);
+        T f[4];
+        lds_vec<T, 4, 4>(ph + (size_t)k * C::NQ * 4, f);
+        u = fma(uk, f[0], u);
+        r0 = fma(uk, f[1], r0);
+        r1 = fma(uk, f[2], r1);
+        r2 = fma(uk, f[3], r2);
       }
       const double gx = (adj[0][0] * r0 + adj[1][0] * r1 + adj[2][0] * r2) / det;
       const double gy = (adj[0][1] * r0 + adj[1][1] * r1 + adj[2][1] * r2) / det;

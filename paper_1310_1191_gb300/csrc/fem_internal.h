@@ -39,6 +39,11 @@ struct DevTable {
   double *qp = nullptr;     // [nq][4]: xi, eta, zeta, w (FP64)
   double *phi64 = nullptr;  // [4 nq][ns] row k = 4 q + d (FP64)
   float *phi32 = nullptr;   // same, FP32
+  // point-major copies [ns][nq][4] (value + 3 derivatives of shape function i
+  // at point q contiguous): threads that own consecutive points read
+  // consecutive 4-vectors when they evaluate a field at their points
+  double *phiT64 = nullptr;
+  float *phiT32 = nullptr;
   // tensor-core operand images of Phi^T (hi | lo per K chunk), prisms only
   uint16_t *img_bf16 = nullptr;
   uint16_t *img_f16 = nullptr;
@@ -84,6 +89,7 @@ struct FmaArgs {
   const double *terms = nullptr;
   // nonlinear coefficient law (law kernels only)
   const float *ucoef = nullptr;  // [n][NS] field coefficients of u per element
+  const void *phiT = nullptr;    // point-major table [NS][NQ][4] in the kernel's precision
   const float *mlpw = nullptr;   // network parameters (FP32 values of BF16 weights)
   float nrm[4] = {0, 0, 0, 0};   // input normalisation of the network
   float box[4] = {0, 0, 0, 0};   // u0, u1, s0, s1 (network used inside)

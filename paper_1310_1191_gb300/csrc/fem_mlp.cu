@@ -615,6 +615,7 @@ int fem_integrate_law(fem_tables t, int p, int64_t n_elem, const double *coords,
   a.cstride = coeff_stride;
   a.qp = d.qp;
   a.phi = prec == FEM_F64 ? (const void *)d.phi64 : (const void *)d.phi32;
+  a.phiT = prec == FEM_F64 ? (const void *)d.phiT64 : (const void *)d.phiT32;
   a.A = A_out;
   a.b = b_out;
   a.status = status;

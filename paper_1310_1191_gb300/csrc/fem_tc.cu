@@ -19,13 +19,17 @@
 // T per element from a bound on |G| |Phi|) so the largest magnitude sits near
 // 2^14; the epilogue removes the scale exactly.
 //
-// CTA roles (192 threads, persistent over M tiles):
-//   warp 0, lane 0 : bulk-copies the Phi^T hi/lo image of each K chunk (TMA);
-//   warp 1, lane 0 : issues tcgen05.mma and commits (warp 1 owns TMEM);
-//   warps 2..5     : FP64 geometry -> G records (shared), then build the A
-//                    tiles (T^T hi/lo) of each K chunk, then drain TMEM and
-//                    write A_e / b_e (epilogue); warp w drains TMEM lanes
-//                    32 (w % 4) .. + 31, so it builds those rows too.
+// CTA roles (512 threads, one CTA per SM, each CTA owns a contiguous range of
+// M tiles):
+//   warp 0, lane 0   : bulk-copies the Phi^T hi/lo image of each K chunk (TMA);
+//   warp 1, lane 0   : issues tcgen05.mma and commits (warp 1 owns TMEM);
+//   warps 6..13      : build the A tiles (T^T hi/lo) of each K chunk from the
+//                      point records, two threads per row;
+//   warps 2..5, 14, 15 : FP64 geometry of the elements each tile brings in ->
+//                      point records in a ring of element slots (consecutive
+//                      tiles share elements, so each element is computed once);
+//                      warps 2..5 then drain TMEM and write A_e / b_e of the
+//                      previous tile (warp w reads TMEM lanes 32 (w % 4) ..).
 // Every mbarrier wait is bounded (about a second); a CTA whose wait expires
 // sets the library's device error word, marks its elements FEM_ST_TIMEOUT,
 // waits for its own copies and MMAs, frees TMEM and returns.
@@ -59,23 +63,35 @@ struct TcCfg {
   static constexpr int TCOLS_NEED = NACC * NP;
   static constexpr int TMEM_COLS = TCOLS_NEED <= 32 ? 32 : TCOLS_NEED <= 64 ? 64 : TCOLS_NEED <= 128 ? 128
                                    : TCOLS_NEED <= 256 ? 256 : 512;
-  static constexpr int STAGES = P == 7 ? 2 : 3;
+  // operand stages: as many as shared memory holds (the Phi^T copies come
+  // from L2, partly across the die boundary, so deep rings hide their latency)
+  static constexpr int STAGES = P == 7 ? 3 : P == 6 ? 4 : P == 5 ? 5 : P == 4 ? 7 : 8;
+  // chunks of Phi values the producers keep in flight (registers)
+  static constexpr int PD = 3;
   static constexpr int A_BYTES = BM * KC * 2;  // one half (hi or lo)
   static constexpr int B_BYTES = NP * KC * 2;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int SBO = (KC / 8) * 128;   // 8-row group stride in a stage tile
   static constexpr int NREC = 18 + 11;
-  static constexpr int GBUF = MAXEL * NQP * 12;  // floats per point-record buffer
-  // shared layout (bytes from a 1024-aligned base); two buffers of per-tile element data
-  static constexpr size_t OFF_G = (size_t)STAGES * STAGE_BYTES;
-  static constexpr size_t OFF_X = OFF_G + 2 * (size_t)GBUF * 4;
-  static constexpr size_t OFF_ED = OFF_X + 2 * (size_t)MAXEL * NREC * 8;
   static constexpr int NZ = P + 1, NAB = NZ * NZ;  // tensor-product factors of J per element
-  static constexpr size_t OFF_ZF = OFF_ED + 2 * (size_t)MAXEL * kEdgeRec * 8;
-  static constexpr size_t OFF_XF = OFF_ZF + (size_t)MAXEL * NZ * kZf * 8;  // one buffer (geometry warps only)
-  static constexpr size_t OFF_INV = OFF_XF + (size_t)MAXEL * NAB * kXf * 8;  // float [2][2][MAXEL]
-  static constexpr size_t OFF_GS = OFF_INV + 16 * (size_t)MAXEL;                // geometry scratch
-  static constexpr size_t OFF_BAR = (OFF_GS + 16 * (size_t)MAXEL + 15) / 16 * 16;
+  // Each CTA owns a contiguous range of tiles, so consecutive tiles share
+  // elements; point records live in a ring of RING element slots (slot =
+  // element mod RING) and every element's geometry is computed once per CTA.
+  // RING covers the elements of two consecutive tiles (the tile being built
+  // and the next one), MAXEL those of one tile (new elements per pass).
+  static constexpr int RING = (2 * BM - 1 + L - 1) / L + 1;
+  static constexpr int GSLOT = NQP * 12;  // floats of point records per element
+  // shared layout (bytes from a 1024-aligned base)
+  static constexpr size_t OFF_G = (size_t)STAGES * STAGE_BYTES;                // float [RING][NQP][12]
+  static constexpr size_t OFF_X = OFF_G + (size_t)RING * GSLOT * 4;            // double [MAXEL][NREC]
+  static constexpr size_t OFF_ED = OFF_X + (size_t)MAXEL * NREC * 8;           // double [MAXEL][21]
+  static constexpr size_t OFF_ZF = OFF_ED + (size_t)MAXEL * kEdgeRec * 8;      // double [MAXEL][NZ][9]
+  static constexpr size_t OFF_XF = OFF_ZF + (size_t)MAXEL * NZ * kZf * 8;      // double [MAXEL][NAB][3]
+  static constexpr size_t OFF_ZR = OFF_XF + (size_t)MAXEL * NAB * kXf * 8;     // float [MAXEL][NZ][4]
+  static constexpr size_t OFF_CF = OFF_ZR + (size_t)MAXEL * NZ * 16;           // float [MAXEL][12]
+  static constexpr size_t OFF_W = OFF_CF + (size_t)MAXEL * 48;                 // float [NQP] weights
+  static constexpr size_t OFF_RS = OFF_W + (size_t)NQP * 4;                    // per slot: 7 x [RING] words
+  static constexpr size_t OFF_BAR = (OFF_RS + 28 * (size_t)RING + 15) / 16 * 16;
   static constexpr int NBAR = 2 * STAGES + 9;
   static constexpr size_t OFF_MISC = OFF_BAR + 8 * NBAR;
   static constexpr size_t SMEM = OFF_MISC + 16 + 1024;
@@ -86,10 +102,10 @@ struct TcCfg {
 
 // warp roles of the 512-thread CTA
 constexpr int kTcThreads = 512;
-constexpr int kEpiWarp0 = 2;    // 4 warps: TMEM lanes 32 (w % 4) .. + 31
+constexpr int kEpiWarp0 = 2;    // 4 warps: TMEM lanes 32 (w % 4) .. + 31; also geometry
 constexpr int kProdWarp0 = 6;   // 8 warps: 256 producer threads
-constexpr int kGeoWarp0 = 14;   // 2 warps: 64 geometry threads
-constexpr int kNProd = 256, kNEpi = 128, kNGeo = 64;
+constexpr int kGeoWarp0 = 14;   // 2 warps: geometry only
+constexpr int kNProd = 256, kNEpi = 128, kNGeo = 192;  // geometry: warps 2..5 and 14..15
 
 struct TcArgs {
   int64_t n;
@@ -135,17 +151,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
   using C = TcCfg<P>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float *sG = reinterpret_cast<float *>(sm + C::OFF_G);          // [2][MAXEL][NQP][12]
-  double *sX = reinterpret_cast<double *>(sm + C::OFF_X);        // [2][MAXEL][NREC]
-  double *sEd = reinterpret_cast<double *>(sm + C::OFF_ED);      // [2][MAXEL][21]
+  float *sG = reinterpret_cast<float *>(sm + C::OFF_G);          // [RING][NQP][12] point records
+  double *sX = reinterpret_cast<double *>(sm + C::OFF_X);        // [MAXEL][NREC] new elements of a pass
+  double *sEd = reinterpret_cast<double *>(sm + C::OFF_ED);      // [MAXEL][21]
   double *sZF = reinterpret_cast<double *>(sm + C::OFF_ZF);      // [MAXEL][NZ][9]
   double *sXF = reinterpret_cast<double *>(sm + C::OFF_XF);      // [MAXEL][NAB][3]
-  float *sInv = reinterpret_cast<float *>(sm + C::OFF_INV);      // [2][MAXEL] matrix rows
-  float *sInvB = sInv + 2 * C::MAXEL;                            // [2][MAXEL] load-vector row
-  int *sSt = reinterpret_cast<int *>(sm + C::OFF_GS);            // [MAXEL] geometry scratch
-  unsigned *sBnd = reinterpret_cast<unsigned *>(sSt + C::MAXEL);  // [MAXEL]
-  unsigned *sBndB = sBnd + C::MAXEL;                              // [MAXEL]
-  float *sScB = reinterpret_cast<float *>(sBndB + C::MAXEL);      // [MAXEL] load-vector scale
+  float *sZR = reinterpret_cast<float *>(sm + C::OFF_ZR);        // [MAXEL][NZ][4] adj row 2, FP32
+  float *sCF = reinterpret_cast<float *>(sm + C::OFF_CF);        // [MAXEL][12] coefficients, FP32
+  float *sW = reinterpret_cast<float *>(sm + C::OFF_W);          // [NQP] quadrature weights, FP32
+  float *sInv = reinterpret_cast<float *>(sm + C::OFF_RS);       // [RING] matrix-row unscale
+  float *sInvB = sInv + C::RING;                                 // [RING] load-vector-row unscale
+  float *sScl = sInvB + C::RING;                                 // [RING] matrix-row scale (FP16)
+  float *sScB = sScl + C::RING;                                  // [RING] load-vector-row scale (FP16)
+  int *sSt = reinterpret_cast<int *>(sScB + C::RING);            // [RING] status bits
+  unsigned *sBnd = reinterpret_cast<unsigned *>(sSt + C::RING);  // [RING] bound of |G| (FP16)
+  unsigned *sBndB = sBnd + C::RING;                              // [RING] bound of |S| (FP16)
   uint64_t *bar_full = reinterpret_cast<uint64_t *>(sm + C::OFF_BAR);
   uint64_t *bar_empty = bar_full + C::STAGES;
   uint64_t *bar_accf = bar_empty + C::STAGES;  // [2]
@@ -159,17 +179,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nrows = a.n * C::L;
   const int64_t ntiles = (nrows + C::BM - 1) / C::BM;
+  // this CTA's contiguous range of M tiles
+  const int64_t t_begin = (int64_t)blockIdx.x * ntiles / gridDim.x;
+  const int64_t t_end = ((int64_t)blockIdx.x + 1) * ntiles / gridDim.x;
+  for (int q = tid; q < C::NQP; q += blockDim.x) sW[q] = q < C::NQ ? (float)a.qp[4 * q + 3] : 0.f;
 
   if (tid == 0) {
     for (int s = 0; s < C::STAGES; s++) {
-      ptx::mbar_init(&bar_full[s], kNProd + 1);
+      ptx::mbar_init(&bar_full[s], kNProd / 32 + 1);  // one arrival per producer warp + the loader
       ptx::mbar_init(&bar_empty[s], 1);
     }
     for (int i = 0; i < 2; i++) {
       ptx::mbar_init(&bar_accf[i], 1);
-      ptx::mbar_init(&bar_acce[i], kNEpi);
-      ptx::mbar_init(&bar_gfull[i], kNGeo);
-      ptx::mbar_init(&bar_gempty[i], kNProd + kNEpi);
+      ptx::mbar_init(&bar_acce[i], kNEpi / 32);
+      ptx::mbar_init(&bar_gfull[i], 1);
+      ptx::mbar_init(&bar_gempty[i], (kNProd + kNEpi) / 32);
     }
     ptx::mbar_init(bar_fin, 1);
     *sAbort = 0;
@@ -205,7 +229,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
     // ---------------- Phi^T image loader (TMA bulk copies) ----------------
     if (lane == 0) {
       uint32_t g = 0;
-      for (int64_t t = blockIdx.x; t < ntiles && !*sAbort; t += gridDim.x) {
+      for (int64_t t = t_begin; t < t_end && !*sAbort; t++) {
         for (int c = 0; c < C::NCH; c++, g++) {
           const int s = g % C::STAGES;
           const uint32_t round = g / C::STAGES;
@@ -228,7 +252,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
     if (lane == 0) {
       constexpr uint32_t idesc = ptx::idesc_f16(!F16, C::BM, C::NH);
       uint32_t g = 0, tt = 0;
-      for (int64_t t = blockIdx.x; t < ntiles && !*sAbort; t += gridDim.x, tt++) {
+      for (int64_t t = t_begin; t < t_end && !*sAbort; t++, tt++) {
         const uint32_t ab = C::NACC == 2 ? (tt & 1) : 0, use = tt / C::NACC;
         if (!wait(&bar_acce[ab], (use & 1) ^ 1)) break;
         ptx::tc_fence_after();
@@ -268,134 +292,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
       ptx::mma_commit(bar_fin);
       ptx::mbar_wait(bar_fin, 0, kWaitLimitNs);
     }
-  } else if (warp >= kGeoWarp0) {
-    // ---------------- geometry: point records of the next tile ----------------
-    // All 64 threads run every iteration and every named barrier (work is
-    // skipped after an abort), so none can be left waiting on barrier 2.
-    const int gt = tid - kGeoWarp0 * 32;
-    uint32_t tt = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tt++) {
-      const int b = tt & 1;
-      const uint32_t use = tt >> 1;
-      int64_t e_first;
-      int nel;
-      tile_elems(t, e_first, nel);
-      const int64_t R0 = t * C::BM;
-      if (gt == 0) wait(&bar_gempty[b], (use & 1) ^ 1);  // buffer b free again
-      asm volatile("bar.sync 2, 64;" ::: "memory");
-      double *X = sX + (size_t)b * C::MAXEL * C::NREC;
-      double *Ed = sEd + (size_t)b * C::MAXEL * kEdgeRec;
-      float *G = sG + (size_t)b * C::GBUF;
-      if (!*sAbort) {
-        for (int idx = gt; idx < nel * C::NREC; idx += kNGeo) {
-          const int el = idx / C::NREC, k = idx % C::NREC;
-          const int64_t e = e_first + el;
-          X[idx] = k < 18 ? a.coords[e * 18 + k] : a.coeffs[(k - 18) * a.cstride + e];
-        }
-        if (gt < C::MAXEL) {
-          sSt[gt] = 0;
-          sBnd[gt] = 0u;
-          sBndB[gt] = 0u;
-        }
-      }
-      asm volatile("bar.sync 2, 64;" ::: "memory");
-      if (!*sAbort) {
-        for (int idx = gt; idx < nel * C::NREC; idx += kNGeo)
-          if (!isfinite(X[idx])) atomicOr(&sSt[idx / C::NREC], FEM_ST_NONFINITE);
-        if (gt < nel) {
-          const double *cf = X + gt * C::NREC + 18;
-          if (a.layout == FEM_OUT_SYMPACKED && (cf[6] != 0.0 || cf[7] != 0.0 || cf[8] != 0.0))
-            atomicOr(&sSt[gt], FEM_ST_NONSYM);
-          edge_record<FEM_PRISM6>(X + gt * C::NREC, Ed + gt * kEdgeRec);
-        }
-      }
-      asm volatile("bar.sync 2, 64;" ::: "memory");
-      if (!*sAbort) {  // tensor-product factors of J
-        for (int idx = gt; idx < nel * (C::NZ + C::NAB); idx += kNGeo) {
-          const int el = idx / (C::NZ + C::NAB), r = idx % (C::NZ + C::NAB);
-          const double *ed = Ed + el * kEdgeRec;
-          if (r < C::NZ)
-            prism_zf(ed, a.qp[4 * (r * C::NAB) + 2], sZF + (el * C::NZ + r) * kZf);
-          else
-            prism_xf(ed, a.qp[4 * (r - C::NZ)], a.qp[4 * (r - C::NZ) + 1], sXF + (el * C::NAB + r - C::NZ) * kXf);
-        }
-      }
-      asm volatile("bar.sync 2, 64;" ::: "memory");
-      if (!*sAbort) {
-        for (int idx = gt; idx < nel * C::NQP; idx += kNGeo) {
-          const int el = idx / C::NQP, q = idx % C::NQP;
-          float *gr = G + (size_t)idx * 12;
-          if (q < C::NQ) {
-            float gv[11];
-            double adj[3][3];
-            const int iz = q / C::NAB, iab = q % C::NAB;
-            const double det = jac_adj_tp(sZF + (el * C::NZ + iz) * kZf, sXF + (el * C::NAB + iab) * kXf, adj);
-            point_from_adj_f32(adj, det, a.qp[4 * q + 3], X + el * C::NREC + 18, gv);
-#pragma unroll
-            for (int k = 0; k < 11; k++) gr[k] = gv[k];
-            if (!(det > 0.0)) atomicOr(&sSt[el], FEM_ST_DET);
-            if (F16) {
-              float bb = fabsf(gv[G00]) + fabsf(gv[G01]) + fabsf(gv[G02]) + fabsf(gv[G03]);
-              bb = fmaxf(bb, fabsf(gv[G11]) + fabsf(gv[G12]) + fabsf(gv[G13]));
-              bb = fmaxf(bb, fabsf(gv[G12]) + fabsf(gv[G22]) + fabsf(gv[G23]));
-              bb = fmaxf(bb, fabsf(gv[G13]) + fabsf(gv[G23]) + fabsf(gv[G33]));
-              if (isfinite(bb)) atomicMax(&sBnd[el], __float_as_uint(bb));
-              // the load-vector row (S_Q, 0, 0, 0) gets its own scale: a small
-              // source f must not fall into FP16 subnormals
-              const float bs = fabsf(gv[GS]);
-              if (isfinite(bs)) atomicMax(&sBndB[el], __float_as_uint(bs));
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < 11; k++) gr[k] = 0.f;
-          }
-        }
-      }
-      asm volatile("bar.sync 2, 64;" ::: "memory");
-      if (!*sAbort && gt < nel) {
-        float sc = 1.f, inv = 1.f, scb = 1.f, invb = 1.f;
-        if (F16) {
-          auto pow2_scale = [&](float bnd, float &sv, float &is) {
-            int ex = 0;
-            if (bnd > 0.f) frexpf(bnd, &ex);  // bnd < 2^ex
-            const int at = bnd > 0.f ? 14 - ex : 0;
-            sv = ldexpf(1.f, at);
-            is = ldexpf(1.f, -(at + a.aphi));
-          };
-          pow2_scale(__uint_as_float(sBnd[gt]) * a.phimax, sc, inv);
-          pow2_scale(__uint_as_float(sBndB[gt]) * a.phimax, scb, invb);
-        }
-        sInv[b * C::MAXEL + gt] = inv;
-        sInvB[b * C::MAXEL + gt] = invb;
-        sScB[gt] = scb;
-        reinterpret_cast<float *>(sBnd)[gt] = sc;  // reuse as the matrix-row scale
-        const int64_t e = e_first + gt;
-        if (a.status && e * C::L >= R0) a.status[e] = sSt[gt];  // the tile holding row 0 reports
-      }
-      asm volatile("bar.sync 2, 64;" ::: "memory");
-      if (F16 && !*sAbort) {  // fold the power-of-two scales into the point records
-        for (int idx = gt; idx < nel * C::NQP; idx += kNGeo) {
-          const int el = idx / C::NQP;
-          float *gr = G + (size_t)idx * 12;
-          const float sc = __uint_as_float(sBnd[el]);
-#pragma unroll
-          for (int k = 0; k < 10; k++) gr[k] *= sc;
-          gr[GS] *= sScB[el];
-        }
-      }
-      ptx::mbar_arrive(&bar_gfull[b]);  // arrives even after an abort
-    }
-  } else if (warp >= kProdWarp0) {
+  } else if (warp >= kProdWarp0 && warp < kGeoWarp0) {
     // ---------------- producers: A tiles (T^T hi/lo) of each K chunk ----------------
     const int pt = tid - kProdWarp0 * 32;
     const int rl = pt & 127;       // tile row
     const int half = pt >> 7;      // points 4 half .. 4 half + 3 of each chunk
     constexpr int QH = C::QC / 2;
     uint32_t tt = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tt++) {
+    for (int64_t t = t_begin; t < t_end; t++, tt++) {
       const int b = tt & 1;
       const uint32_t use = tt >> 1;
-      if (!wait(&bar_gfull[b], use & 1)) break;
+      if (!__all_sync(0xffffffffu, wait(&bar_gfull[b], use & 1))) break;
       int64_t e_first;
       int nel;
       tile_elems(t, e_first, nel);
@@ -403,10 +310,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
       const bool valid = r < nrows;
       const int64_t e = valid ? r / C::L : e_first;
       const int j = valid ? (int)(r % C::L) : 0;
-      const int el = (int)(e - e_first);
-      const float *gbase = sG + (size_t)b * C::GBUF + (size_t)el * C::NQP * 12;
+      const float *gbase = sG + (size_t)(e % C::RING) * C::GSLOT;
       const bool arow = valid && j < C::NS;
-      float fcur[QH][4], fnext[QH][4];
+      // Phi values of the next PD - 1 chunks are in flight while a chunk is
+      // built (ring of PD register sets, indexed statically by unrolling)
+      float fr[C::PD][QH][4];
       auto load_phi = [&](int c, float (&f)[QH][4]) {
 #pragma unroll
         for (int qq = 0; qq < QH; qq++) {
@@ -422,22 +330,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
           }
         }
       };
-      load_phi(0, fnext);
+#pragma unroll
+      for (int u = 0; u < C::PD - 1; u++)
+        if (u < C::NCH) load_phi(u, fr[u]);
       bool ok = true;
       const uint32_t g0 = tt * C::NCH;
-      for (int c = 0; c < C::NCH; c++) {
+      // builds chunk c from the Phi values in f; false if a wait expired
+      auto build = [&](int c, const float (&f)[QH][4]) -> bool {
         const uint32_t g = g0 + c;
         const int s = g % C::STAGES;
         const uint32_t round = g / C::STAGES;
-#pragma unroll
-        for (int qq = 0; qq < QH; qq++)
-#pragma unroll
-          for (int d = 0; d < 4; d++) fcur[qq][d] = fnext[qq][d];
-        if (c + 1 < C::NCH) load_phi(c + 1, fnext);  // in flight while this chunk is built
-        if (!wait(&bar_empty[s], (round & 1) ^ 1)) {
-          ok = false;
-          break;
-        }
+        // warp-uniform: the stage is handed over by one arrival per warp
+        if (!__all_sync(0xffffffffu, wait(&bar_empty[s], (round & 1) ^ 1))) return false;
         uint32_t hw[QH * 2], lw[QH * 2];
 #pragma unroll
         for (int qq = 0; qq < QH; qq++) {
@@ -447,7 +351,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
             const float4 *g4 = reinterpret_cast<const float4 *>(gbase + q * 12);
             const float4 ga = g4[0], gb = g4[1], gc = g4[2];  // G00 G01 G02 G03 | G11 G12 G13 G22 | G23 G33 GS -
             if (arow) {
-              const float f0 = fcur[qq][0], f1 = fcur[qq][1], f2 = fcur[qq][2], f3 = fcur[qq][3];
+              const float f0 = f[qq][0], f1 = f[qq][1], f2 = f[qq][2], f3 = f[qq][3];
               t0 = ga.x * f0 + ga.y * f1 + ga.z * f2 + ga.w * f3;
               t1 = gb.x * f1 + gb.y * f2 + gb.z * f3;
               t2 = gb.y * f1 + gb.w * f2 + gc.x * f3;
@@ -469,71 +373,224 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
           *reinterpret_cast<uint4 *>(aL + off) = make_uint4(lw[4 * k2], lw[4 * k2 + 1], lw[4 * k2 + 2], lw[4 * k2 + 3]);
         }
         ptx::fence_proxy_async();
-        ptx::mbar_arrive(&bar_full[s]);
-      }
-      ptx::mbar_arrive(&bar_gempty[b]);  // done with point-record buffer b
-      if (!ok) break;
-    }
-  } else {
-    // ---------------- epilogue: TMEM -> columns of A_e / b_e ----------------
-    const int lq = warp & 3;
-    const int rl = 32 * lq + lane;
-    uint32_t tt = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, tt++) {
-      const int b = tt & 1;
-      const uint32_t ab = C::NACC == 2 ? (tt & 1) : 0, use = tt / C::NACC;
-      // the tile's element data (written by the geometry warps) and its accumulator
-      bool ok = wait(&bar_gfull[b], (tt >> 1) & 1);
-      ok = ok && wait(&bar_accf[ab], use & 1);
-      __syncwarp();
-      if (!__all_sync(0xffffffffu, ok)) break;  // tcgen05.ld is collective over the warp
-      ptx::tc_fence_after();
-      int64_t e_first;
-      int nel;
-      tile_elems(t, e_first, nel);
-      const int64_t r = t * C::BM + rl;
-      const bool valid = r < nrows;
-      const int64_t e = valid ? r / C::L : e_first;
-      const int j = valid ? (int)(r % C::L) : 0;
-      const int el = (int)(e - e_first);
-      const float inv = valid ? (j < C::NS ? sInv[b * C::MAXEL + el] : sInvB[b * C::MAXEL + el]) : 0.f;
-      const uint32_t tbase = tmem + ab * C::NP + ((uint32_t)(32 * lq) << 16);
-#pragma unroll 1
-      for (int c0 = 0; c0 < C::NP; c0 += 16) {
-        uint32_t v[16];
-        ptx::tmem_ld16(tbase + c0, v);
-        ptx::tmem_ld_wait();
-        if (valid) {
-          if (j < C::NS) {
-            if (a.layout == FEM_OUT_FULL) {
-              float *Ae = static_cast<float *>(a.A) + e * (int64_t)(C::NS * C::NS) + j;
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&bar_full[s]);
+        return true;
+      };
+      for (int c0 = 0; c0 < C::NCH && ok; c0 += C::PD) {
 #pragma unroll
-              for (int u = 0; u < 16; u++) {
-                const int i = c0 + u;
-                if (i < C::NS) Ae[(size_t)i * C::NS] = __uint_as_float(v[u]) * inv;
-              }
-            } else {
-              constexpr int NPK = C::NS * (C::NS + 1) / 2;
-              float *Ae = static_cast<float *>(a.A) + e * (int64_t)NPK;
-#pragma unroll
-              for (int u = 0; u < 16; u++) {
-                const int i = c0 + u;
-                if (i < C::NS && i <= j) Ae[i * C::NS - i * (i - 1) / 2 + j - i] = __uint_as_float(v[u]) * inv;
-              }
-            }
-          } else if (a.b != nullptr) {
-            float *be = static_cast<float *>(a.b) + e * (int64_t)C::NS;
-#pragma unroll
-            for (int u = 0; u < 16; u++) {
-              const int i = c0 + u;
-              if (i < C::NS) be[i] = __uint_as_float(v[u]) * inv;
-            }
+        for (int u = 0; u < C::PD; u++) {
+          const int c = c0 + u;
+          if (ok && c < C::NCH) {
+            if (c + C::PD - 1 < C::NCH) load_phi(c + C::PD - 1, fr[(u + C::PD - 1) % C::PD]);
+            ok = build(c, fr[u]);
           }
         }
       }
-      ptx::tc_fence_before();
-      ptx::mbar_arrive(&bar_acce[ab]);
-      ptx::mbar_arrive(&bar_gempty[b]);
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&bar_gempty[b]);  // done with the tile's point records
+      if (!ok) break;
+    }
+  } else {
+    // ---------------- geometry (warps 2..5 and 14..15) and epilogue (warps 2..5) ----------------
+    // Iteration tt computes the point records of the elements that tile tt
+    // brings in (ring slots), then warps 2..5 drain the accumulator of tile
+    // tt - 1.  All 192 threads run every iteration and every named barrier
+    // (work is skipped after an abort), so none can be left waiting on barrier 2.
+    const bool epi = warp < kProdWarp0;
+    const int gt = epi ? tid - kEpiWarp0 * 32 : 128 + tid - kGeoWarp0 * 32;
+    int64_t e_done = -1;  // last element whose records are in the ring
+    uint32_t tt = 0;
+    auto gbar = [] { asm volatile("bar.sync 2, 192;" ::: "memory"); };
+    for (int64_t t = t_begin; t <= t_end; t++, tt++) {
+      if (t < t_end) {
+        const int b = tt & 1;
+        const uint32_t use = tt >> 1;
+        int64_t e_first;
+        int nel;
+        tile_elems(t, e_first, nel);
+        const int64_t R0 = t * C::BM;
+        const int64_t e_last = e_first + nel - 1;
+        const int64_t e_new = e_first > e_done + 1 ? e_first : e_done + 1;
+        const int nnew = (int)(e_last - e_new + 1);  // 0 .. MAXEL
+        e_done = e_last;
+        // tile tt - 2 is finished by the producers and the epilogue: its
+        // elements that tiles tt - 1 and tt do not share may be overwritten
+        if (gt == 0) wait(&bar_gempty[b], (use & 1) ^ 1);
+        gbar();
+        const bool go = !*sAbort;
+        if (go) {
+          for (int idx = gt; idx < nnew * C::NREC; idx += kNGeo) {
+            const int el = idx / C::NREC, k = idx % C::NREC;
+            const int64_t e = e_new + el;
+            sX[idx] = k < 18 ? a.coords[e * 18 + k] : a.coeffs[(k - 18) * a.cstride + e];
+          }
+          if (gt < nnew) {
+            const int sl = (int)((e_new + gt) % C::RING);
+            sSt[sl] = 0;
+            sBnd[sl] = 0u;
+            sBndB[sl] = 0u;
+          }
+        }
+        gbar();
+        if (go) {
+          for (int idx = gt; idx < nnew * C::NREC; idx += kNGeo)
+            if (!isfinite(sX[idx])) atomicOr(&sSt[(e_new + idx / C::NREC) % C::RING], FEM_ST_NONFINITE);
+          if (gt < nnew) {
+            const double *cf = sX + gt * C::NREC + 18;
+            if (a.layout == FEM_OUT_SYMPACKED && (cf[6] != 0.0 || cf[7] != 0.0 || cf[8] != 0.0))
+              atomicOr(&sSt[(e_new + gt) % C::RING], FEM_ST_NONSYM);
+            edge_record<FEM_PRISM6>(sX + gt * C::NREC, sEd + gt * kEdgeRec);
+            float *cfl = sCF + gt * 12;  // D00 D11 D22 D01 D02 D12 b0 b1 b2 c f
+#pragma unroll
+            for (int k = 0; k < 11; k++) cfl[k] = (float)cf[k];
+          }
+        }
+        gbar();
+        if (go) {  // tensor-product factors of J
+          for (int idx = gt; idx < nnew * (C::NZ + C::NAB); idx += kNGeo) {
+            const int el = idx / (C::NZ + C::NAB), r = idx % (C::NZ + C::NAB);
+            const double *ed = sEd + el * kEdgeRec;
+            if (r < C::NZ) {
+              double *zf = sZF + (el * C::NZ + r) * kZf;
+              prism_zf(ed, a.qp[4 * (r * C::NAB) + 2], zf);
+              float *zr = sZR + (el * C::NZ + r) * 4;
+              zr[0] = (float)zf[6];
+              zr[1] = (float)zf[7];
+              zr[2] = (float)zf[8];
+            } else {
+              prism_xf(ed, a.qp[4 * (r - C::NZ)], a.qp[4 * (r - C::NZ) + 1], sXF + (el * C::NAB + r - C::NZ) * kXf);
+            }
+          }
+        }
+        gbar();
+        if (go) {
+          for (int idx = gt; idx < nnew * C::NQP; idx += kNGeo) {
+            const int el = idx / C::NQP, q = idx % C::NQP;
+            const int sl = (int)((e_new + el) % C::RING);
+            float *gr = sG + (size_t)sl * C::GSLOT + q * 12;
+            if (q < C::NQ) {
+              float gv[11];
+              const int iz = q / C::NAB, iab = q % C::NAB;
+              const double det = point_tc(sZF + (el * C::NZ + iz) * kZf, sZR + (el * C::NZ + iz) * 4,
+                                          sXF + (el * C::NAB + iab) * kXf, sW[q], sCF + el * 12, gv);
+#pragma unroll
+              for (int k = 0; k < 11; k++) gr[k] = gv[k];
+              if (!(det > 0.0)) atomicOr(&sSt[sl], FEM_ST_DET);
+              if (F16) {
+                float bb = fabsf(gv[G00]) + fabsf(gv[G01]) + fabsf(gv[G02]) + fabsf(gv[G03]);
+                bb = fmaxf(bb, fabsf(gv[G11]) + fabsf(gv[G12]) + fabsf(gv[G13]));
+                bb = fmaxf(bb, fabsf(gv[G12]) + fabsf(gv[G22]) + fabsf(gv[G23]));
+                bb = fmaxf(bb, fabsf(gv[G13]) + fabsf(gv[G23]) + fabsf(gv[G33]));
+                if (isfinite(bb)) atomicMax(&sBnd[sl], __float_as_uint(bb));
+                // the load-vector row (S_Q, 0, 0, 0) gets its own scale: a small
+                // source f must not fall into FP16 subnormals
+                const float bs = fabsf(gv[GS]);
+                if (isfinite(bs)) atomicMax(&sBndB[sl], __float_as_uint(bs));
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < 11; k++) gr[k] = 0.f;
+            }
+          }
+        }
+        gbar();
+        if (go && gt < nnew) {
+          const int64_t e = e_new + gt;
+          const int sl = (int)(e % C::RING);
+          float sc = 1.f, inv = 1.f, scb = 1.f, invb = 1.f;
+          if (F16) {
+            auto pow2_scale = [&](float bnd, float &sv, float &is) {
+              int ex = 0;
+              if (bnd > 0.f) frexpf(bnd, &ex);  // bnd < 2^ex
+              const int at = bnd > 0.f ? 14 - ex : 0;
+              sv = ldexpf(1.f, at);
+              is = ldexpf(1.f, -(at + a.aphi));
+            };
+            pow2_scale(__uint_as_float(sBnd[sl]) * a.phimax, sc, inv);
+            pow2_scale(__uint_as_float(sBndB[sl]) * a.phimax, scb, invb);
+          }
+          sInv[sl] = inv;
+          sInvB[sl] = invb;
+          sScl[sl] = sc;
+          sScB[sl] = scb;
+          if (a.status && e * C::L >= R0) a.status[e] = sSt[sl];  // the tile holding row 0 reports
+        }
+        if (F16) {
+          gbar();
+          if (go) {  // fold the power-of-two scales into the point records
+            for (int idx = gt; idx < nnew * C::NQP; idx += kNGeo) {
+              const int sl = (int)((e_new + idx / C::NQP) % C::RING);
+              float *gr = sG + (size_t)sl * C::GSLOT + (idx % C::NQP) * 12;
+              const float sc = sScl[sl];
+#pragma unroll
+              for (int k = 0; k < 10; k++) gr[k] *= sc;
+              gr[GS] *= sScB[sl];
+            }
+          }
+        }
+        gbar();  // the pass is complete for the whole group before the drain reads it
+        if (gt == 0) ptx::mbar_arrive(&bar_gfull[b]);  // arrives even after an abort
+      }
+      if (epi && t > t_begin) {
+        // ---------------- epilogue of tile t - 1: TMEM -> columns of A_e / b_e ----------------
+        const uint32_t tp = tt - 1;
+        const int64_t tq = t - 1;
+        const uint32_t ab = C::NACC == 2 ? (tp & 1) : 0, use = tp / C::NACC;
+        const bool ok = wait(&bar_accf[ab], use & 1);
+        __syncwarp();
+        if (__all_sync(0xffffffffu, ok)) {  // tcgen05.ld is collective over the warp
+          ptx::tc_fence_after();
+          const int lq = warp & 3;
+          const int rl = 32 * lq + lane;
+          const int64_t r = tq * C::BM + rl;
+          const bool valid = r < nrows;
+          const int64_t e = valid ? r / C::L : 0;
+          const int j = valid ? (int)(r % C::L) : 0;
+          const int sl = (int)(e % C::RING);
+          const float inv = valid ? (j < C::NS ? sInv[sl] : sInvB[sl]) : 0.f;
+          const uint32_t tbase = tmem + ab * C::NP + ((uint32_t)(32 * lq) << 16);
+#pragma unroll 1
+          for (int c0 = 0; c0 < C::NP; c0 += 16) {
+            uint32_t v[16];
+            ptx::tmem_ld16(tbase + c0, v);
+            ptx::tmem_ld_wait();
+            if (valid) {
+              if (j < C::NS) {
+                if (a.layout == FEM_OUT_FULL) {
+                  float *Ae = static_cast<float *>(a.A) + e * (int64_t)(C::NS * C::NS) + j;
+#pragma unroll
+                  for (int u = 0; u < 16; u++) {
+                    const int i = c0 + u;
+                    if (i < C::NS) Ae[(size_t)i * C::NS] = __uint_as_float(v[u]) * inv;
+                  }
+                } else {
+                  constexpr int NPK = C::NS * (C::NS + 1) / 2;
+                  float *Ae = static_cast<float *>(a.A) + e * (int64_t)NPK;
+#pragma unroll
+                  for (int u = 0; u < 16; u++) {
+                    const int i = c0 + u;
+                    if (i < C::NS && i <= j) Ae[i * C::NS - i * (i - 1) / 2 + j - i] = __uint_as_float(v[u]) * inv;
+                  }
+                }
+              } else if (a.b != nullptr) {
+                float *be = static_cast<float *>(a.b) + e * (int64_t)C::NS;
+#pragma unroll
+                for (int u = 0; u < 16; u++) {
+                  const int i = c0 + u;
+                  if (i < C::NS) be[i] = __uint_as_float(v[u]) * inv;
+                }
+              }
+            }
+          }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            ptx::mbar_arrive(&bar_acce[ab]);
+            ptx::mbar_arrive(&bar_gempty[tp & 1]);
+          }
+        }
+      }
     }
   }
 
@@ -542,7 +599,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
     if (tid == 0 && a.err) atomicExch(a.err, 1);
     // flag the elements of this CTA's tiles that may be incomplete
     if (a.status) {
-      for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      for (int64_t t = t_begin; t < t_end; t++) {
         const int64_t e0 = (t * C::BM) / C::L;
         int64_t e1 = (t * C::BM + C::BM - 1) / C::L;
         if (e1 > a.n - 1) e1 = a.n - 1;
