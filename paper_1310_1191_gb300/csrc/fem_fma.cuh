@@ -99,7 +99,7 @@ __device__ __forceinline__ void lds_vec(const T *p, T (&v)[N]) {
 // and, for the network, its parameters.
 template <class C>
 constexpr size_t law_smem_bytes(int law) {
-  return law == 0 ? 0 : (size_t)C::EPB * C::NS * 4 + 16 + (law == 2 ? (size_t)kMlpP * 4 + 16 : 0);
+  return law == 0 ? 0 : (size_t)C::EPB * C::NS * 4 + 16 + (law == 2 ? (size_t)kMlpSmemBytes + 16 : 0);
 }
 
 // SPLIT: the Jacobian terms (det J, J^{-1} per point) are read from a.terms
@@ -119,7 +119,14 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   float *sU = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(sE + C::EPB) + 15) & ~(uintptr_t)15);      // [EPB][NS] (LAW)
   float *sW = reinterpret_cast<float *>(
-      (reinterpret_cast<uintptr_t>(sU + C::EPB * C::NS) + 15) & ~(uintptr_t)15);  // [kMlpP] (LAW 2)
+      (reinterpret_cast<uintptr_t>(sU + C::EPB * C::NS) + 15) & ~(uintptr_t)15);  // network (LAW 2)
+  uint32_t *sW2 = reinterpret_cast<uint32_t *>(sW + kMlpSmall);                   // W2, BF16 pairs
+  // network inputs of the points (LAW 2), in the contraction's staging area,
+  // which is idle during the geometry stage
+  float *sNet = reinterpret_cast<float *>(sPA);
+  static_assert(LAW != 2 || (size_t)(C::KC * C::BM + C::EPB * C::KC * C::BN) * sizeof(T) >=
+                                (size_t)2 * C::EPB * C::NQ * sizeof(float),
+                "staging area too small for the network inputs");
 
   const int tid = threadIdx.x, nthr = blockDim.x;
   constexpr int NSZ = C::NS * C::NS, NPK = C::NS * (C::NS + 1) / 2;
@@ -152,8 +159,18 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
       const int64_t e = sE[idx / C::NS];
       sU[idx] = e >= 0 ? a.ucoef[e * C::NS + idx % C::NS] : 0.f;
     }
-    if (LAW == 2)
-      for (int idx = tid; idx < kMlpP; idx += nthr) sW[idx] = a.mlpw[idx];
+    if (LAW == 2) {
+      // FP32 W1, b1, b2, W3, b3 and the BF16 image of W2 (rows padded to kW2Stride)
+      constexpr int H = kMlpH;
+      for (int idx = tid; idx < kMlpSmall; idx += nthr) {
+        float v = 0.f;
+        if (idx < 3 * H) v = a.mlpw[idx];                          // W1, b1
+        else if (idx < 5 * H + 1) v = a.mlpw[3 * H + H * H + (idx - 3 * H)];  // b2, W3, b3
+        sW[idx] = v;
+      }
+      for (int idx = tid; idx < H * (H / 2); idx += nthr)
+        sW2[(idx / (H / 2)) * (kW2Stride / 2) + idx % (H / 2)] = a.mlpw2[idx];
+    }
   }
   __syncthreads();
   for (int idx = tid; idx < C::EPB * C::NREC; idx += nthr)
@@ -218,6 +235,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   for (int idx = tid; idx < C::EPB * C::NQ; idx += nthr) {
     const int le = idx / C::NQ, q = idx % C::NQ;
     double g[11];
+    bool pend = false;  // LAW 2: k from the network, applied after this loop
     const double *rec = sX + le * C::NREC;
     int st;
     if (ELAST) {
@@ -286,13 +304,18 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
       const double gy = (adj[0][1] * r0 + adj[1][1] * r1 + adj[2][1] * r2) / det;
       const double gz = (adj[0][2] * r0 + adj[1][2] * r1 + adj[2][2] * r2) / det;
       const T gg = (T)(gx * gx + gy * gy + gz * gz);
-      T kq;
+      T kq = (T)1;
       if (LAW == 1) {
         kq = law_exact<T>(u, gg);
       } else {
+        // inside the box the network gives k after this stage (the record is
+        // built with k = 1 and its diffusion block scaled then); outside, the
+        // exact law
         const float uf = (float)u, sf = sqrtf((float)gg);
         if (uf >= a.box[0] && uf <= a.box[1] && sf >= a.box[2] && sf <= a.box[3]) {
-          kq = (T)mlp_eval(sW, a.nrm, uf, sf);
+          pend = true;
+          sNet[2 * idx] = fmaf(uf, a.nrm[0], a.nrm[1]);
+          sNet[2 * idx + 1] = fmaf(logf(sf), a.nrm[2], a.nrm[3]);
         } else {
           kq = law_exact<T>(u, gg);
           st |= FEM_ST_FALLBACK;
@@ -310,9 +333,23 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     } else {
 #pragma unroll
       for (int k = 0; k < 11; k++) dst[k] = (T)0;
+      pend = false;
     }
+    if (LAW == 2) dst[GPAD] = pend ? (T)1 : (T)0;  // the network still owes this point its k
   }
   __syncthreads();
+  if constexpr (LAW == 2) {
+    // network coefficient of the pending points (tensor cores), then D = k I:
+    // the diffusion block G11..G33 of the record is linear in k
+    mlp_points_mma(
+        sW, sW2, sNet, C::EPB * C::NQ, [&](int pt) { return sG[(size_t)pt * kGStride + GPAD] != (T)0; },
+        [&](int pt, float k) {
+          T *r = sG + (size_t)pt * kGStride;
+#pragma unroll
+          for (int m = G11; m <= G33; m++) r[m] *= (T)k;
+        });
+    __syncthreads();
+  }
 
   // 2. contraction over chunks of points
   const bool owner = tid < C::NT;

@@ -91,6 +91,7 @@ struct FmaArgs {
   const float *ucoef = nullptr;  // [n][NS] field coefficients of u per element
   const void *phiT = nullptr;    // point-major table [NS][NQ][4] in the kernel's precision
   const float *mlpw = nullptr;   // network parameters (FP32 values of BF16 weights)
+  const uint32_t *mlpw2 = nullptr;  // the network's W2 as BF16 pairs, [H][H/2] words
   float nrm[4] = {0, 0, 0, 0};   // input normalisation of the network
   float box[4] = {0, 0, 0, 0};   // u0, u1, s0, s1 (network used inside)
 };

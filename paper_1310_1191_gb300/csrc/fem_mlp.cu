@@ -26,6 +26,7 @@ struct fem_mlp_s {
   float nrm[4] = {0, 0, 0, 0};
   float *master = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *wc = nullptr;
   float *losses = nullptr;  // per-step losses of the last training call
+  uint32_t *w2img = nullptr;  // W2 of the compute weights as BF16 pairs (integration kernels)
   int64_t nlosses = 0;
   int64_t step = 0;
   bool bias_init = false;
@@ -77,6 +78,17 @@ __global__ void mean_kernel(int64_t n, const float *t, float *out) {
     s += t[i];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(out, s / (float)n);
+}
+
+// W2 of the compute weights (BF16 values held as FP32) packed as BF16 pairs,
+// row n = output neuron: the B operand of the integration kernels' network stage.
+__global__ void pack_w2_kernel(const float *wc, uint32_t *img) {
+  constexpr int H = kMlpH;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= H * H / 2) return;
+  const float *W2 = wc + 3 * H;
+  const __nv_bfloat162 v = __floats2bfloat162_rn(W2[2 * i], W2[2 * i + 1]);
+  img[i] = *reinterpret_cast<const uint32_t *>(&v);
 }
 
 __global__ void set_bias_kernel(float *master, float *wc, const float *mean, int idx) {
@@ -376,6 +388,11 @@ int fem_mlp_create(const double *box, uint64_t seed, fem_mlp *out) {
   alloc(&m->v);
   alloc(&m->grad);
   alloc(&m->wc);
+  if (rc == FEM_OK && cudaMalloc((void **)&m->w2img, sizeof(uint32_t) * H * H / 2) != cudaSuccess) {
+    m->w2img = nullptr;
+    set_error("fem_mlp_create: cudaMalloc");
+    rc = FEM_ENOMEM;
+  }
   if (rc == FEM_OK) rc = cuda_check("fem_mlp_create", cudaMemcpy(m->master, w.data(), sizeof(float) * kMlpP,
                                                                  cudaMemcpyHostToDevice));
   if (rc == FEM_OK) {
@@ -394,6 +411,7 @@ int fem_mlp_destroy(fem_mlp m) {
   if (!m) return FEM_OK;
   for (float *p : {m->master, m->m, m->v, m->grad, m->wc, m->losses})
     if (p) cudaFree(p);
+  if (m->w2img) cudaFree(m->w2img);
   delete m;
   return FEM_OK;
 }
@@ -622,6 +640,9 @@ int fem_integrate_law(fem_tables t, int p, int64_t n_elem, const double *coords,
   a.layout = layout;
   a.ucoef = ucoef;
   if (law == FEM_LAW_MLP) {
+    // the compute weights may have changed since the last call (training)
+    pack_w2_kernel<<<(kMlpH * kMlpH / 2 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(mlp->wc, mlp->w2img);
+    a.mlpw2 = mlp->w2img;
     a.mlpw = mlp->wc;
     for (int i = 0; i < 4; i++) {
       a.nrm[i] = mlp->nrm[i];
