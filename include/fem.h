@@ -130,7 +130,7 @@ int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coo
                           void *stream);
 
 /* Split geometry (the paper's NOJAC kernel variants, Section 4 "Jacobian
- * terms"; Algorithm 1 line 8 moved out of the integration kernel): for every
+ * terms"; Algorithm 1's Jacobian step moved out of the integration kernel): for every
  * element and quadrature point, det J and the 9 entries of J^{-1}.
  *   coords : device, double [n_elem][NV][3] (as fem_integrate), 8-byte aligned;
  *   terms  : device, double [n_elem][NQ][10], 16-byte aligned, caller-owned:
@@ -182,7 +182,7 @@ int fem_error_flag(fem_tables t, int clear);
 
 /* ---- nonlinear coefficient law and its learned surrogate ---- */
 /* The law (coefficients at quadrature points computed from "old" degrees of
- * freedom, Algorithm 1 line 10):
+ * freedom, Algorithm 1's coefficient step):
  *     k = 1 + 0.5 exp(-u^2) + 0.2 log(1 + k |grad u|^2),  D = k I,
  * solved per point by exactly 8 Newton steps from k0 = 1 + 0.5 exp(-u^2).
  * The surrogate is a 2 -> 64 -> 64 -> 1 tanh network of (u, |grad u|) with

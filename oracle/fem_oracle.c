@@ -424,7 +424,7 @@ int orc_integrate_ex(int elem, int p, int64_t E, const double *coords, const dou
         double h1[256], h2[256];
 #pragma omp for schedule(dynamic, 1)
         for (int64_t e = 0; e < E; e++) {
-            /* Algorithm 1, lines 1-5: coefficients, geometry, old DOFs, init */
+            /* Algorithm 1, element set-up: coefficients, geometry, old DOFs, init */
             const double *X = coords + (size_t)e * nv * 3;
             double cf[11];
             for (int k = 0; k < 11; k++) cf[k] = coeffs[(size_t)k * cstride + e];
@@ -438,7 +438,7 @@ int orc_integrate_ex(int elem, int p, int64_t E, const double *coords, const dou
             memset(Ae, 0, sizeof(double) * NS * NS);
             memset(be, 0, sizeof(double) * NS);
             for (int q = 0; q < NQ; q++) {
-                /* lines 7-8: shape functions at iQ; Jacobian, det, inverse */
+                /* Algorithm 1, per point: shape functions at iQ; Jacobian, det, inverse */
                 const double *phi = phiQ + (size_t)q * 4 * NS;
                 double dN[3][6], J[3][3], Ji[3][3];
                 map_derivs(elem, xq + 3 * q, dN);
@@ -451,7 +451,7 @@ int orc_integrate_ex(int elem, int p, int64_t E, const double *coords, const dou
                 double det = det3(J);
                 if (!(det > 0.0)) st |= ORC_ST_DET;
                 inv3(J, det, Ji);
-                /* line 9: physical derivatives psi = J^{-T} grad_ref phi */
+                /* physical derivatives psi = J^{-T} grad_ref phi */
                 for (int i = 0; i < NS; i++) {
                     psi[i] = phi[i];
                     for (int m = 0; m < 3; m++) {
@@ -460,7 +460,7 @@ int orc_integrate_ex(int elem, int p, int64_t E, const double *coords, const dou
                         psi[(1 + m) * NS + i] = s;
                     }
                 }
-                /* line 10: coefficients at the point */
+                /* coefficients at the point */
                 double c[4][4] = {{0}};
                 c[0][0] = cf[9];
                 c[0][1] = cf[6];
@@ -492,7 +492,7 @@ int orc_integrate_ex(int elem, int p, int64_t E, const double *coords, const dou
                     c[1][1] = c[2][2] = c[3][3] = k;
                 }
                 double dw = det * wq[q];
-                /* lines 11-15: update A^e for every DOF pair, non-zero c only */
+                /* Algorithm 1 innermost loops: update A^e for every DOF pair, non-zero c only */
                 for (int i = 0; i < NS; i++)
                     for (int j = 0; j < NS; j++) {
                         double s = 0.0;

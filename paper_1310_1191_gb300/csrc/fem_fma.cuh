@@ -280,7 +280,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
         point_from_adj(adj, det, qp[4 * q + 3], rec + C::NV * 3, g);
       }
     } else {
-      // coefficient stage (Algorithm 1 line 10): u and grad u at the point from
+      // coefficient stage (Algorithm 1, coefficients at the point): u and grad u from
       // the element's old degrees of freedom, then k(u, |grad u|), D = k I
       double adj[3][3];
       const double det = geo(le, q, adj);
