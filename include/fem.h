@@ -266,8 +266,8 @@ int fem_output_offsets(int elem, const int8_t *p_host, int64_t n, int layout, in
  * executed by one persistent launch whose CTAs pull items from an atomic
  * counter; the counter reset and the launch are captured in a CUDA graph on
  * the first execution and replayed afterwards (re-captured when the buffers
- * change).  With FEM_PLAN_AUTOTUNE the first execution times two candidate
- * tile shapes per degree on the plan's own elements and keeps the faster;
+ * change).  With FEM_PLAN_AUTOTUNE the first execution times the candidate
+ * tile shapes of each degree on the plan's own elements and keeps the fastest;
  * with FEM_PLAN_CONCURRENT the graph instead holds one branch per degree, each
  * running that degree's specialised kernel on its own stream, overlapping;
  * tune_cache (nullable) is a text file that stores and reuses the choices.
@@ -289,8 +289,13 @@ int fem_plan_create(fem_tables t, int64_t n_elem, const int8_t *p_host, int prec
 int fem_plan_execute(fem_plan plan, const double *coords, const double *coeffs, int64_t coeff_stride,
                      void *A_out, void *b_out, int32_t *status, void *stream);
 
-/* Tile-shape variant chosen for degree p (0 or 1), and the autotuner's times
- * of both candidates in ms (ms[2], nullable; 0 if not timed); -1 if invalid. */
+/* Tile-shape variant chosen for degree p, and the autotuner's times of the
+ * candidates in ms (ms[3], nullable; 0 if not timed); -1 if invalid.
+ * Variants 0 and 1 are the persistent kernel's candidate shapes; plans with
+ * FEM_PLAN_LOOP or FEM_PLAN_CONCURRENT also have variant 2, the degree's
+ * uniform-degree kernel (as fem_integrate runs it), their default without
+ * FEM_PLAN_AUTOTUNE.  Per-degree plans are tuned by timing each candidate
+ * as one launch over the degree's bin. */
 int fem_plan_variant(fem_plan plan, int p, double *ms);
 int fem_plan_destroy(fem_plan plan);
 

@@ -9,10 +9,12 @@
 // which every CTA pulls the next item from an atomic counter, balances the
 // expensive high-degree elements against the cheap ones.  The counter reset
 // and the launch are captured once in a CUDA graph and replayed.  Each degree
-// has two candidate tile shapes; the autotuner times both on the plan's own
-// elements (the first execution) and keeps the faster, optionally caching the
-// choice in a text file.  The per-degree launch loop (one specialised launch
-// per bin) is kept as an execution mode to compare against.
+// has two candidate tile shapes for the persistent kernel; the autotuner times
+// both on the plan's own elements (the first execution) and keeps the faster,
+// optionally caching the choice in a text file.  The per-degree modes (a
+// launch loop, or one graph branch per degree) run one specialised launch per
+// bin and add a third candidate, the degree's uniform-degree kernel, timed the
+// same way.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,7 +33,11 @@
 namespace fem {
 
 constexpr int kBatchThreads = 256;
-constexpr int kVariants = 2;
+constexpr int kVariants = 2;   // candidate shapes of the persistent kernel
+// Per-degree launches (loop and concurrent-branch plans) have a third
+// candidate: the degree's uniform-degree kernel (no 256-thread limit).
+constexpr int kStandalone = 2;
+constexpr int kLoopVariants = 3;
 
 // Candidate shapes (ELEM, P, BM, TM, TN, EPB, QC), all with at most 256 threads.
 template <int P, int V> struct BShape;
@@ -135,6 +141,8 @@ static int launch_loop_pv(FmaArgs a, void *stream) {
 
 template <class T>
 static int launch_loop(int p, int v, const FmaArgs &a, void *stream) {
+  if (v == kStandalone)
+    return sizeof(T) == 8 ? launch_fma_f64(FEM_PRISM6, p, a, stream) : launch_fma_f32(FEM_PRISM6, p, a, stream);
   switch ((p << 4) | v) {
 #define FEM_LL(P, V) \
   case (P << 4) | V: return launch_loop_pv<T, P, V>(a, stream);
@@ -156,7 +164,7 @@ struct fem_plan_s {
   int64_t bin_off[fem::kMaxP + 2] = {0};  // sorted positions of each degree's bin
   int variant[fem::kMaxP + 1] = {0};
   bool tuned = false;
-  double tuned_ms[fem::kMaxP + 1][fem::kVariants] = {{0}};
+  double tuned_ms[fem::kMaxP + 1][fem::kLoopVariants] = {{0}};
   // device data (plan-owned)
   int64_t *perm = nullptr, *offA = nullptr, *offb = nullptr;
   int4 *items = nullptr;
@@ -180,6 +188,8 @@ static int plan_fail(const char *what, cudaError_t e) {
   return FEM_ECUDA;
 }
 
+static bool per_degree(const fem_plan_s *pl) { return (pl->flags & (FEM_PLAN_LOOP | FEM_PLAN_CONCURRENT)) != 0; }
+
 static double item_cost(int p) {  // relative cost of one element of degree p (contraction flops)
   const double ns = ns_of(FEM_PRISM6, p), nq = nq_of(FEM_PRISM6, p);
   return 8.0 * nq * ns * ns + 150.0 * nq;
@@ -195,12 +205,15 @@ static void build_items_raw(const int64_t *bin_off, const int *variant, int only
     if (only_p > 0 && p != only_p) continue;
     const int64_t k0 = bin_off[p], k1 = bin_off[p + 1];
     if (k1 <= k0) continue;
-    const ShapeInfo si = shape_info(p, variant[p]);
+    // the persistent kernel's shapes only (a per-degree plan's uniform-degree
+    // variant has no work-list form; such plans do not use the list)
+    const int vp = variant[p] < kVariants ? variant[p] : 0;
+    const ShapeInfo si = shape_info(p, vp);
     for (int64_t k = k0; k < k1; k += si.epb) {
       const int64_t ke = std::min<int64_t>(k + si.epb, k1);
       for (int t = 0; t < si.tiles * si.tiles; t++) {
         int4 it;
-        it.x = (p << 4) | variant[p];
+        it.x = (p << 4) | vp;
         it.y = t;
         it.z = (int)k;
         it.w = (int)ke;
@@ -332,7 +345,8 @@ static std::string cache_key(const fem_plan_s *pl, int p) {
   cudaGetDevice(&dev);
   cudaGetDeviceProperties(&prop, dev);
   std::ostringstream o;
-  o << prop.name << "|sm" << prop.major << prop.minor << "|prec" << pl->prec << "|layout" << pl->layout << "|p" << p;
+  o << prop.name << "|sm" << prop.major << prop.minor << "|prec" << pl->prec << "|layout" << pl->layout << "|p" << p
+    << (per_degree(pl) ? "|per-degree" : "|persistent");
   std::string k = o.str();
   for (char &c : k)
     if (c == ' ') c = '_';
@@ -346,7 +360,7 @@ static bool cache_lookup(const fem_plan_s *pl, int p, int *v) {
   int val;
   double ms;
   while (f >> k >> val >> ms)
-    if (k == key && val >= 0 && val < kVariants) {
+    if (k == key && val >= 0 && val < (per_degree(pl) ? kLoopVariants : kVariants)) {
       *v = val;
       return true;
     }
@@ -375,6 +389,34 @@ static int autotune(fem_plan_s *pl, const FmaArgs &base, cudaStream_t s) {
     }
     double best = 1e30;
     int bestv = 0;
+    if (per_degree(pl)) {  // time the candidates as they are launched: one kernel over the bin
+      FmaArgs a = base;
+      a.n = pl->bin_off[p + 1] - pl->bin_off[p];
+      a.perm = pl->perm + pl->bin_off[p];
+      a.qp = pl->t->tab[p].qp;
+      a.phi = pl->prec == FEM_F64 ? (const void *)pl->t->tab[p].phi64 : (const void *)pl->t->tab[p].phi32;
+      for (int cand = 0; cand < kLoopVariants && rc == FEM_OK; cand++) {
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 3 && rc == FEM_OK; rep++) {
+          cudaEventRecord(e0, s);
+          rc = pl->prec == FEM_F64 ? launch_loop<double>(p, cand, a, s) : launch_loop<float>(p, cand, a, s);
+          cudaEventRecord(e1, s);
+          cudaError_t err = cudaEventSynchronize(e1);
+          if (err != cudaSuccess) rc = plan_fail("autotune", err);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) tmin = std::min(tmin, ms);  // first run warms up
+        }
+        pl->tuned_ms[p][cand] = tmin;
+        if (tmin < best) {
+          best = tmin;
+          bestv = cand;
+        }
+      }
+      pl->variant[p] = bestv;
+      cache_store(pl, p);
+      continue;
+    }
     for (int cand = 0; cand < kVariants && rc == FEM_OK; cand++) {
       pl->variant[p] = cand;
       std::vector<int4> items;
@@ -628,6 +670,8 @@ int fem_plan_create(fem_tables t, int64_t n_elem, const int8_t *p_host, int prec
   if (tune_cache) pl->cache = tune_cache;
   pl->bin_off[1] = 0;
   for (int p = 1; p <= kMaxP; p++) pl->bin_off[p + 1] = pl->bin_off[p] + cnt[p];
+  if (per_degree(pl))  // untuned per-degree launches use the uniform-degree kernels
+    for (int p = 1; p <= kMaxP; p++) pl->variant[p] = kStandalone;
   // counting sort by degree (stable)
   std::vector<int64_t> perm(std::max<int64_t>(n_elem, 1)), offA(std::max<int64_t>(n_elem, 1)),
       offb(std::max<int64_t>(n_elem, 1));
@@ -739,10 +783,8 @@ int fem_plan_execute(fem_plan pl, const double *coords, const double *coeffs, in
 
 int fem_plan_variant(fem_plan pl, int p, double *ms) {
   if (!pl || p < 1 || p > kMaxP) return -1;
-  if (ms) {
-    ms[0] = pl->tuned_ms[p][0];
-    ms[1] = pl->tuned_ms[p][1];
-  }
+  if (ms)
+    for (int v = 0; v < kLoopVariants; v++) ms[v] = pl->tuned_ms[p][v];
   return pl->variant[p];
 }
 

@@ -106,6 +106,39 @@ def test_plan_modes_match_oracle(orc, lib, tables, prec, mode):
     _check(ref, P, _run(lib, tables, X, C, P, prec, flags=flags, reps=2), prec)
 
 
+@pytest.mark.parametrize("mode", ["loop", "concurrent"])
+def test_per_degree_plans_tune_three_candidates(orc, lib, tables, tmp_path, mode):
+    """Per-degree plans default to the uniform-degree kernels (variant 2) and,
+    with autotuning, keep the fastest of the three candidates per degree,
+    each timed as one launch over the bin; results stay exact."""
+    E = 1500
+    X, C, P = _mesh(E)
+    idx = np.arange(0, E, 11)
+    ref = _oracle_by_degree(orc, X, C, P, idx)
+    base = {"loop": lib.FEM_PLAN_LOOP, "concurrent": lib.FEM_PLAN_CONCURRENT}[mode]
+    plan = lib.fem_plan_create(tables, P, 1, 0, base, None)
+    assert all(plan.variant(p)[0] == 2 for p in range(1, 8))
+    _check(ref, P, _run(lib, tables, X, C, P, 1, plan=plan), 1, idx=list(idx))
+    plan.close()
+    cache = str(tmp_path / "tune.txt")
+    plan = lib.fem_plan_create(tables, P, 1, 0, base | lib.FEM_PLAN_AUTOTUNE, cache)
+    _check(ref, P, _run(lib, tables, X, C, P, 1, plan=plan, reps=2), 1, idx=list(idx))
+    for p in range(1, 8):
+        v, ms = plan.variant(p)
+        assert v in (0, 1, 2) and ms.min() > 0 and ms[v] == ms.min()
+    chosen = [plan.variant(p)[0] for p in range(1, 8)]
+    plan.close()
+    # the cache is keyed by execution mode: a persistent plan ignores these entries
+    plan = lib.fem_plan_create(tables, P, 1, 0, lib.FEM_PLAN_AUTOTUNE, cache)
+    _check(ref, P, _run(lib, tables, X, C, P, 1, plan=plan), 1, idx=list(idx))
+    assert all(plan.variant(p)[0] in (0, 1) for p in range(1, 8))
+    plan.close()
+    plan = lib.fem_plan_create(tables, P, 1, 0, base | lib.FEM_PLAN_AUTOTUNE, cache)
+    _run(lib, tables, X, C, P, 1, plan=plan)
+    assert [plan.variant(p)[0] for p in range(1, 8)] == chosen
+    plan.close()
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_plan_sympacked(orc, lib, tables, prec):
     E = 300
