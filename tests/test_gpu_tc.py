@@ -56,6 +56,48 @@ def test_tc_parity_small(orc, lib, tables, p, prec):
     assert eA.max() <= TOL_TC[prec] and eb.max() <= TOL_TC[prec]
 
 
+# about 10 or more M tiles per persistent CTA (152 CTAs), so consecutive tiles
+# of one CTA share elements (the ring of element slots) and the ranges of
+# neighbouring CTAs split elements between them
+MANY_E_ORACLE = {1: 40000, 2: 12000, 3: 5000, 4: 2000}
+MANY_E_FP64 = {5: 1600, 6: 1100, 7: 800}
+
+
+@pytest.mark.parametrize("p", sorted(MANY_E_ORACLE))
+def test_tc_many_tiles_per_cta_vs_oracle(orc, lib, tables, p):
+    """Every element of a mesh with about ten tiles per CTA vs the oracle (BF16x3)."""
+    E = MANY_E_ORACLE[p]
+    X, C = workload(PRISM, p, E)
+    A, b, st = gpu_integrate(tables, PRISM, p, X, C, 2)
+    assert lib.fem_error_flag(tables) == lib.FEM_OK
+    RA, Rb, Rst = orc.integrate(PRISM, p, X, C)
+    n = ns(PRISM, p)
+    eA = rel_frob(A.reshape(E, n, n), RA)
+    print("many tiles p=%d: A max %.3e" % (p, eA.max()))
+    assert np.all(st == Rst)
+    assert eA.max() <= TOL_TC[2] and rel_frob(b, Rb).max() <= TOL_TC[2]
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("p", sorted(MANY_E_FP64))
+def test_tc_many_tiles_per_cta_vs_fp64_kernel(orc, lib, tables, p, prec):
+    """Every element of a mesh with ten or more tiles per CTA vs the FP64 kernel
+    (itself within 1e-12 of the oracle, checked here on a sample)."""
+    E = MANY_E_FP64[p]
+    X, C = workload(PRISM, p, E)
+    A, b, st = gpu_integrate(tables, PRISM, p, X, C, prec)
+    A64, b64, st64 = gpu_integrate(tables, PRISM, p, X, C, 0)
+    assert lib.fem_error_flag(tables) == lib.FEM_OK
+    idx = np.array([0, E // 2, E - 1])
+    RA, _, _ = orc.integrate(PRISM, p, X[idx], C[:, idx])
+    n = ns(PRISM, p)
+    assert rel_frob(A64[idx].reshape(-1, n, n), RA).max() <= 1e-12
+    eA = rel_frob(A.reshape(E, n, n), A64.reshape(E, n, n))
+    print("many tiles p=%d prec=%d: A max %.3e" % (p, prec, eA.max()))
+    assert np.all(st == st64) and np.all(st == 0)
+    assert eA.max() <= TOL_TC[prec] and rel_frob(b, b64).max() <= TOL_TC[prec]
+
+
 @pytest.mark.parametrize("prec", [2, 3])
 @pytest.mark.parametrize("p", [3, 7])
 def test_tc_sympacked_and_flags(orc, lib, tables, p, prec):
