@@ -50,7 +50,7 @@ struct FmaCfg {
   static constexpr size_t smem_bytes() {
     return sizeof(T) * ((size_t)KC * BM + (size_t)EPB * KC * BN + (size_t)EPB * NQ * kGStride) +
            sizeof(double) * (size_t)EPB * (NREC + NEDGE + NZ * kZf + NAB * kXf) + sizeof(int) * (size_t)(EPB + 1) +
-           sizeof(int64_t) * (size_t)EPB + 64;
+           sizeof(int64_t) * (size_t)EPB + 64 + sizeof(float) * ((size_t)EPB * (12 + 4 * NZ) + NQ) + 16;
   }
 };
 
@@ -116,8 +116,14 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   double *sXF = sZF + C::EPB * C::NZ * kZf;                                // [EPB][NAB][3] (prisms)
   int *sSt = reinterpret_cast<int *>(sXF + C::EPB * C::NAB * kXf);         // [EPB]
   int64_t *sE = reinterpret_cast<int64_t *>(sSt + C::EPB + (C::EPB & 1));   // [EPB] element ids
+  // FP32 copies for the FP32 point records of prisms: coefficients, adj row 2
+  // per zeta level, quadrature weights
+  float *sCF = reinterpret_cast<float *>(
+      (reinterpret_cast<uintptr_t>(sE + C::EPB) + 15) & ~(uintptr_t)15);      // [EPB][12]
+  float *sZR = sCF + C::EPB * 12;                                               // [EPB][NZ][4]
+  float *sWq = sZR + C::EPB * C::NZ * 4;                                        // [NQ]
   float *sU = reinterpret_cast<float *>(
-      (reinterpret_cast<uintptr_t>(sE + C::EPB) + 15) & ~(uintptr_t)15);      // [EPB][NS] (LAW)
+      (reinterpret_cast<uintptr_t>(sWq + C::NQ) + 15) & ~(uintptr_t)15);      // [EPB][NS] (LAW)
   float *sW = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(sU + C::EPB * C::NS) + 15) & ~(uintptr_t)15);  // network (LAW 2)
   uint32_t *sW2 = reinterpret_cast<uint32_t *>(sW + kMlpSmall);                   // W2, BF16 pairs
@@ -131,6 +137,8 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   const int tid = threadIdx.x, nthr = blockDim.x;
   constexpr int NSZ = C::NS * C::NS, NPK = C::NS * (C::NS + 1) / 2;
   constexpr bool split = SPLIT;  // Jacobian terms read, not computed
+  // FP32 records of prisms from the tensor-product factors with FP32 coefficients
+  constexpr bool fastf32 = sizeof(T) == 4 && C::ELEM == FEM_PRISM6 && !SPLIT && C::ND == 4 && LAW == 0;
 
   for (int le = tid; le < C::EPB; le += nthr) {
     const int64_t k = k0 + le;
@@ -177,15 +185,27 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     if (!isfinite(sX[idx])) atomicOr(&sSt[idx / C::NREC], FEM_ST_NONFINITE);
   if (!split)
     for (int le = tid; le < C::EPB; le += nthr) edge_record<C::ELEM>(sX + le * C::NREC, sEd + le * C::NEDGE);
+  if constexpr (fastf32) {
+    for (int idx = tid; idx < C::EPB * 11; idx += nthr)
+      sCF[(idx / 11) * 12 + idx % 11] = (float)sX[(idx / 11) * C::NREC + C::NV * 3 + idx % 11];
+    for (int q = tid; q < C::NQ; q += nthr) sWq[q] = (float)qp[4 * q + 3];
+  }
   __syncthreads();
   if constexpr (C::ELEM == FEM_PRISM6) {
     if (!split) {  // tensor-product factors of J (per zeta level and per (xi, eta))
       for (int idx = tid; idx < C::EPB * (C::NZ + C::NAB); idx += nthr) {
         const int le = idx / (C::NZ + C::NAB), r = idx % (C::NZ + C::NAB);
         const double *ed = sEd + le * C::NEDGE;
-        if (r < C::NZ)
-          prism_zf(ed, qp[4 * (r * C::NAB) + 2], sZF + (le * C::NZ + r) * kZf);
-        else
+        if (r < C::NZ) {
+          double *zf = sZF + (le * C::NZ + r) * kZf;
+          prism_zf(ed, qp[4 * (r * C::NAB) + 2], zf);
+          if (fastf32) {
+            float *zr = sZR + (le * C::NZ + r) * 4;
+            zr[0] = (float)zf[6];
+            zr[1] = (float)zf[7];
+            zr[2] = (float)zf[8];
+          }
+        } else
           prism_xf(ed, qp[4 * (r - C::NZ)], qp[4 * (r - C::NZ) + 1], sXF + (le * C::NAB + r - C::NZ) * kXf);
       }
       __syncthreads();
@@ -267,6 +287,15 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
       const double fi = bi == 0 ? cf[2] : (bi == 1 ? cf[3] : cf[4]);
       g[9] = bk == 0 ? w * det * fi : 0.0;
       g[10] = 0.0;
+    } else if constexpr (fastf32) {
+      // FP64 adj rows 0, 1 and det J, the rest in FP32 (7 FP64 -> FP32 conversions per point)
+      float gf[11];
+      const int iz = q / C::NAB, iab = q % C::NAB;
+      const double det = point_tc(sZF + (le * C::NZ + iz) * kZf, sZR + (le * C::NZ + iz) * 4,
+                                  sXF + (le * C::NAB + iab) * kXf, sWq[q], sCF + le * 12, gf);
+      st = det > 0.0 ? 0 : FEM_ST_DET;
+#pragma unroll
+      for (int k = 0; k < 11; k++) g[k] = gf[k];
     } else if (LAW == 0) {
       double adj[3][3];
       const double det = geo(le, q, adj);
@@ -484,11 +513,39 @@ __global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
   fma_body<T, C, LAW, SPLIT>(a, a.qp, static_cast<const T *>(a.phi), blk * (int64_t)C::EPB, a.n, ti, tj, smem);
 }
 
+// FP32 kernels with the network stage: the MMA fragments and activations keep
+// many registers live, and with small CTAs the compiler then takes so many
+// that only one to three CTAs fit per SM; capping them at about 72 registers
+// (four CTAs of up to 227 threads) keeps the contraction's latency hidden
+// (measured 1.3x on the p = 3 workload).  Shapes too large for two CTAs at
+// that cap keep the plain kernel.
+template <class C>
+constexpr int net_min_blocks() {
+  return 65536 / (C::NT * 72) > 4 ? 4 : 65536 / (C::NT * 72);
+}
+template <class T, class C, bool SPLIT = false>
+__global__ void __launch_bounds__(C::NT, (net_min_blocks<C>() >= 2 ? net_min_blocks<C>() : 2))
+    fma_kernel_net(const FmaArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  long long blk = blockIdx.x;
+  const int tj = (int)(blk % C::TILES);
+  blk /= C::TILES;
+  const int ti = (int)(blk % C::TILES);
+  blk /= C::TILES;
+  fma_body<T, C, 2, SPLIT>(a, a.qp, static_cast<const T *>(a.phi), blk * (int64_t)C::EPB, a.n, ti, tj, smem);
+}
+
 template <class T, class C, int LAW = 0, bool SPLIT = false>
 int launch_fma_cfg(const FmaArgs &a, void *stream) {
   if (a.n == 0) return FEM_OK;
   const size_t smem = C::template smem_bytes<T>() + law_smem_bytes<C>(LAW);
-  cudaError_t err = cudaFuncSetAttribute(fma_kernel<T, C, LAW, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr bool net = LAW == 2 && sizeof(T) == 4 && net_min_blocks<C>() >= 2;
+  void (*kern)(const FmaArgs);
+  if constexpr (net)
+    kern = fma_kernel_net<T, C, SPLIT>;
+  else
+    kern = fma_kernel<T, C, LAW, SPLIT>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) {
     set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(err));
     return FEM_ECUDA;
@@ -499,7 +556,7 @@ int launch_fma_cfg(const FmaArgs &a, void *stream) {
     set_error("too many elements for one launch");
     return FEM_EINVAL;
   }
-  fma_kernel<T, C, LAW, SPLIT><<<(unsigned)grid, C::NT, smem, (cudaStream_t)stream>>>(a);
+  kern<<<(unsigned)grid, C::NT, smem, (cudaStream_t)stream>>>(a);
   err = cudaGetLastError();
   if (err != cudaSuccess) {
     set_error(std::string("fma_kernel launch: ") + cudaGetErrorString(err));
