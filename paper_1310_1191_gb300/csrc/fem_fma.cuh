@@ -138,7 +138,8 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   constexpr int NSZ = C::NS * C::NS, NPK = C::NS * (C::NS + 1) / 2;
   constexpr bool split = SPLIT;  // Jacobian terms read, not computed
   // FP32 records of prisms from the tensor-product factors with FP32 coefficients
-  constexpr bool fastf32 = sizeof(T) == 4 && C::ELEM == FEM_PRISM6 && !SPLIT && C::ND == 4 && LAW == 0;
+  constexpr bool fp32rec = sizeof(T) == 4 && C::ELEM == FEM_PRISM6 && !SPLIT && C::ND == 4;
+  constexpr bool fastf32 = fp32rec && LAW == 0;
 
   for (int le = tid; le < C::EPB; le += nthr) {
     const int64_t k = k0 + le;
@@ -185,7 +186,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     if (!isfinite(sX[idx])) atomicOr(&sSt[idx / C::NREC], FEM_ST_NONFINITE);
   if (!split)
     for (int le = tid; le < C::EPB; le += nthr) edge_record<C::ELEM>(sX + le * C::NREC, sEd + le * C::NEDGE);
-  if constexpr (fastf32) {
+  if constexpr (fp32rec) {
     for (int idx = tid; idx < C::EPB * 11; idx += nthr)
       sCF[(idx / 11) * 12 + idx % 11] = (float)sX[(idx / 11) * C::NREC + C::NV * 3 + idx % 11];
     for (int q = tid; q < C::NQ; q += nthr) sWq[q] = (float)qp[4 * q + 3];
@@ -199,7 +200,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
         if (r < C::NZ) {
           double *zf = sZF + (le * C::NZ + r) * kZf;
           prism_zf(ed, qp[4 * (r * C::NAB) + 2], zf);
-          if (fastf32) {
+          if (fp32rec) {
             float *zr = sZR + (le * C::NZ + r) * 4;
             zr[0] = (float)zf[6];
             zr[1] = (float)zf[7];
@@ -308,6 +309,51 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
       } else {
         point_from_adj(adj, det, qp[4 * q + 3], rec + C::NV * 3, g);
       }
+    } else if constexpr (fp32rec) {
+      // coefficient stage (Algorithm 1, coefficients at the point), FP32 kernel:
+      // adj J and det J from FP64 factors, u, grad u, k and the record in FP32
+      float a32[3][3];
+      const int iz = q / C::NAB, iab = q % C::NAB;
+      const double det = adj_tp_f32(sZF + (le * C::NZ + iz) * kZf, sZR + (le * C::NZ + iz) * 4,
+                                    sXF + (le * C::NAB + iab) * kXf, a32);
+      st = det > 0.0 ? 0 : FEM_ST_DET;
+      const float *ph = static_cast<const float *>(a.phiT) + (size_t)q * 4;
+      const float *U = sU + le * C::NS;
+      float u = 0.f, r0 = 0.f, r1 = 0.f, r2 = 0.f;
+      for (int k = 0; k < C::NS; k++) {
+        const float uk = U[k];
+        float f[4];
+        lds_vec<float, 4, 4>(ph + (size_t)k * C::NQ * 4, f);
+        u = fmaf(uk, f[0], u);
+        r0 = fmaf(uk, f[1], r0);
+        r1 = fmaf(uk, f[2], r1);
+        r2 = fmaf(uk, f[3], r2);
+      }
+      const float detf = (float)det, idet = 1.f / detf;
+      const float gx = (a32[0][0] * r0 + a32[1][0] * r1 + a32[2][0] * r2) * idet;
+      const float gy = (a32[0][1] * r0 + a32[1][1] * r1 + a32[2][1] * r2) * idet;
+      const float gz = (a32[0][2] * r0 + a32[1][2] * r1 + a32[2][2] * r2) * idet;
+      const float gg = gx * gx + gy * gy + gz * gz;
+      float kq = 1.f;
+      if (LAW == 1) {
+        kq = law_exact<float>(u, gg);
+      } else {
+        const float sf = sqrtf(gg);
+        if (u >= a.box[0] && u <= a.box[1] && sf >= a.box[2] && sf <= a.box[3]) {
+          pend = true;
+          sNet[2 * idx] = fmaf(u, a.nrm[0], a.nrm[1]);
+          sNet[2 * idx + 1] = fmaf(logf(sf), a.nrm[2], a.nrm[3]);
+        } else {
+          kq = law_exact<float>(u, gg);
+          st |= FEM_ST_FALLBACK;
+        }
+      }
+      const float *cf = sCF + le * 12;
+      const float cfl[11] = {kq, kq, kq, 0.f, 0.f, 0.f, cf[6], cf[7], cf[8], cf[9], cf[10]};
+      float gf[11];
+      record_f32(a32, detf, sWq[q], cfl, gf);
+#pragma unroll
+      for (int k = 0; k < 11; k++) g[k] = gf[k];
     } else {
       // coefficient stage (Algorithm 1, coefficients at the point): u and grad u from
       // the element's old degrees of freedom, then k(u, |grad u|), D = k I

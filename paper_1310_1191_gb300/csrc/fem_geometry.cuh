@@ -169,26 +169,34 @@ __device__ __forceinline__ double jac_adj_tp(const double *zf, const double *xf,
   return c2x * zf[6] + c2y * zf[7] + c2z * zf[8];
 }
 
-// Point record of the tensor-core path from the element's tensor-product
+// adj J and det J at a prism point from the element's tensor-product
 // factors: adj rows 0, 1 and det J in FP64 (two cross products and a dot
-// product), then FP32 from there on.  zr: adj row 2 of the point's zeta level
-// already rounded to FP32; w: the point's weight in FP32; cf: D00 D11 D22 D01
-// D02 D12 b0 b1 b2 c f in FP32.  Returns det J (FP64).
-__device__ __forceinline__ double point_tc(const double *zf, const float *zr, const double *xf, float w,
-                                           const float *cf, float *g) {
+// product), rounded to FP32 (a); zr: adj row 2 of the point's zeta level
+// already in FP32.  Returns det J (FP64).
+__device__ __forceinline__ double adj_tp_f32(const double *zf, const float *zr, const double *xf, float (&a)[3][3]) {
   const double c0x = zf[0], c0y = zf[1], c0z = zf[2], c1x = zf[3], c1y = zf[4], c1z = zf[5];
   const double c2x = xf[0], c2y = xf[1], c2z = xf[2];
-  const double det = c2x * zf[6] + c2y * zf[7] + c2z * zf[8];
-  const float a[3][3] = {{(float)(c1y * c2z - c1z * c2y), (float)(c1z * c2x - c1x * c2z), (float)(c1x * c2y - c1y * c2x)},
-                         {(float)(c2y * c0z - c2z * c0y), (float)(c2z * c0x - c2x * c0z), (float)(c2x * c0y - c2y * c0x)},
-                         {zr[0], zr[1], zr[2]}};
+  a[0][0] = (float)(c1y * c2z - c1z * c2y);
+  a[0][1] = (float)(c1z * c2x - c1x * c2z);
+  a[0][2] = (float)(c1x * c2y - c1y * c2x);
+  a[1][0] = (float)(c2y * c0z - c2z * c0y);
+  a[1][1] = (float)(c2z * c0x - c2x * c0z);
+  a[1][2] = (float)(c2x * c0y - c2y * c0x);
+  a[2][0] = zr[0];
+  a[2][1] = zr[1];
+  a[2][2] = zr[2];
+  return c2x * zf[6] + c2y * zf[7] + c2z * zf[8];
+}
+
+// FP32 point record from FP32 adj J, det J (FP32), weight and coefficients
+// cf: D00 D11 D22 D01 D02 D12 b0 b1 b2 c f.
+__device__ __forceinline__ void record_f32(const float (&a)[3][3], float detf, float w, const float *cf, float *g) {
   const float D[3][3] = {{cf[0], cf[3], cf[4]}, {cf[3], cf[1], cf[5]}, {cf[4], cf[5], cf[2]}};
   float M[3][3];
 #pragma unroll
   for (int k = 0; k < 3; k++)
 #pragma unroll
     for (int n = 0; n < 3; n++) M[k][n] = a[k][0] * D[0][n] + a[k][1] * D[1][n] + a[k][2] * D[2][n];
-  const float detf = (float)det;
   const float s = w / detf;
   auto Gd = [&](int k, int l) { return s * (M[k][0] * a[l][0] + M[k][1] * a[l][1] + M[k][2] * a[l][2]); };
   g[G11] = Gd(0, 0);
@@ -202,6 +210,15 @@ __device__ __forceinline__ double point_tc(const double *zf, const float *zr, co
   const float wd = w * detf;
   g[G00] = wd * cf[9];
   g[GS] = wd * cf[10];
+}
+
+// Point record of the FP32 prism paths from the element's tensor-product
+// factors (adj_tp_f32, then record_f32).  Returns det J (FP64).
+__device__ __forceinline__ double point_tc(const double *zf, const float *zr, const double *xf, float w,
+                                           const float *cf, float *g) {
+  float a[3][3];
+  const double det = adj_tp_f32(zf, zr, xf, a);
+  record_f32(a, (float)det, w, cf, g);
   return det;
 }
 
