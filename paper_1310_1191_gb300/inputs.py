@@ -134,8 +134,23 @@ def prism_grid_dims(E: int):
     return nx, nx, nz
 
 
+def _vertex_coords(vid: np.ndarray, grid_shape, h, seed, amp) -> np.ndarray:
+    """Coordinates of the given vertex ids of the jittered grid of
+    _jitter_vertices (the same counter-based draws, addressed by vertex id)."""
+    NX, NY, NZ = grid_shape
+    ix, iy, iz = vid % NX, (vid // NX) % NY, vid // (NX * NY)
+    xyz = np.stack([ix * h[0], iy * h[1], iz * h[2]], axis=1).astype(np.float64)
+    interior = (ix > 0) & (ix < NX - 1) & (iy > 0) & (iy < NY - 1) & (iz > 0) & (iz < NZ - 1)
+    if amp > 0:
+        v = vid[interior]
+        for c in range(3):
+            u = draw_uniform(seed, v, c)
+            xyz[interior, c] += (2.0 * u - 1.0) * amp * h[c]
+    return xyz
+
+
 def prism_mesh(E: int, seed: int = SEED_MESH, jitter: float = 0.1,
-               dims=None) -> np.ndarray:
+               dims=None, first: int = 0) -> np.ndarray:
     """Straight-edged 6-node prisms from a jittered hex grid; coords [E][6][3].
 
     Each hex (ix,iy,iz) (hex id ix + nx*(iy + ny*iz)) is cut along its xy
@@ -144,7 +159,31 @@ def prism_mesh(E: int, seed: int = SEED_MESH, jitter: float = 0.1,
     triangle (counter-clockwise seen from +z) and 3..5 the top one.  The first
     E prisms are returned.  With jitter the quadrilateral side faces are not
     planar, so the map is bilinear in the vertical direction.
+
+    ``first`` > 0 returns prisms first .. first+E-1 of the grid ``dims`` (a
+    shard of a larger mesh, identical to slicing the whole mesh), computing
+    only the vertices those prisms use.
     """
+    if first > 0:
+        if dims is None:
+            raise ValueError("a shard (first > 0) needs the grid dims of the whole mesh")
+        nx, ny, nz = dims
+        if 2 * nx * ny * nz < first + E:
+            raise ValueError("grid too small for the shard")
+        h = 1.0 / nx
+        NX, NY = nx + 1, ny + 1
+        k = np.arange(first, first + E, dtype=np.int64)
+        hid, side = k // 2, k % 2
+        ix, iy, iz = hid % nx, (hid // nx) % ny, hid // (nx * ny)
+
+        def vid(dx, dy, dz):
+            return (ix + dx) + NX * ((iy + dy) + NY * (iz + dz))
+
+        pa = np.stack([vid(0, 0, 0), vid(1, 0, 0), vid(1, 1, 0), vid(0, 0, 1), vid(1, 0, 1), vid(1, 1, 1)], axis=1)
+        pb = np.stack([vid(0, 0, 0), vid(1, 1, 0), vid(0, 1, 0), vid(0, 0, 1), vid(1, 1, 1), vid(0, 1, 1)], axis=1)
+        conn = np.where(side[:, None] == 0, pa, pb)
+        xyz = _vertex_coords(conn.ravel(), (NX, NY, nz + 1), (h, h, h), seed, jitter)
+        return np.ascontiguousarray(xyz.reshape(E, 6, 3))
     nx, ny, nz = dims if dims is not None else prism_grid_dims(E)
     if 2 * nx * ny * nz < E:
         raise ValueError("grid too small for E elements")
