@@ -158,6 +158,16 @@ def cpu_baseline(sweep, sample=CPU_SAMPLE):
                       "extrapolated per degree" % ",".join(desc)}
 
 
+def sweep_config(sweep, precision):
+    """The workload description shared by both arms' JSON lines."""
+    return {"workload": "prism degree sweep p=1..7 (jittered prisms, random SPD D, b, c, f), E_p=%s"
+                        % list(sweep.values()),
+            "precision": precision, "layout": "full",
+            "l2": "flushed between timed steps (256 MB write)",
+            "sharding": "per rank E_p prisms: rank r integrates prisms r E_p .. (r+1) E_p - 1 "
+                        "of an (N E_p)-prism mesh; no data-path collective"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -176,8 +186,7 @@ def run_reference(args):
             "unit": "element matrices/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": units / v * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "prism degree sweep p=1..7, E_p=%s" % list(sweep.values()),
-                       "precision": "f64", "layout": "full"},
+            "config": sweep_config(sweep, "f64"),
             "cpu_baseline": dict(cb, value=v),
             "e2e": {"value": v, "unit": "element matrices/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
@@ -661,12 +670,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": "prism degree sweep p=1..7 (jittered prisms, random SPD D, b, "
-                                   "c, f), E_p=%s" % list(sweep.values()),
-                       "precision": args.precision, "layout": "full",
-                       "sharding": "per rank E_p prisms: rank r integrates prisms r E_p .. (r+1) E_p - 1 "
-                                   "of an (N E_p)-prism mesh; no data-path collective",
-                       "l2": "flushed between timed steps (256 MB write)"},
+            "config": sweep_config(sweep, args.precision),
             "gpu_launches": 7 * args.steps,
             "per_degree": per_degree,
             "roofline": {"bound": "alu", "kernel": "fma_kernel p=%d" % pdom,
