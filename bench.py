@@ -390,7 +390,7 @@ def wl_tensor(lib, tables, stream, dev, reps, bf16_peak, E=200000, degrees=(4, 5
 
 def wl_elastic(lib, tables, stream, dev, reps, scale_down=1, degrees=range(1, 8)):
     """Linear elastostatics (the paper's model problem), about 2 GB of FP64
-    output per degree; FP64 and FP32.  GFLOP/s also in the paper's count of
+    output per degree; FP64, FP32 and the BF16x3 tensor-core form.  GFLOP/s also in the paper's count of
     63 flops per 3x3 block and point (63 NQ NS^2 per element)."""
     import torch
     out = {}
@@ -401,7 +401,10 @@ def wl_elastic(lib, tables, stream, dev, reps, scale_down=1, degrees=range(1, 8)
         C = inputs.elastic_coefficients(E)
         Xd, Cd = torch.from_numpy(X).to(dev), torch.from_numpy(C).to(dev)
         row = {"elements": E}
-        for name, prec, dt in (("f64", lib.FEM_F64, torch.float64), ("f32", lib.FEM_F32, torch.float32)):
+        S = min(E, 64)
+        ref = None
+        for name, prec, dt in (("f64", lib.FEM_F64, torch.float64), ("f32", lib.FEM_F32, torch.float32),
+                               ("bf16x3", lib.FEM_BF16X3, torch.float32)):
             A = torch.empty((E, 9 * n * n), dtype=dt, device=dev)
             b = torch.empty((E, 3 * n), dtype=dt, device=dev)
             ms = _timed(stream, lambda: lib.fem_integrate_elastic(tables, p, E, Xd, Cd, E, prec, A, b, None,
@@ -410,6 +413,10 @@ def wl_elastic(lib, tables, stream, dev, reps, scale_down=1, degrees=range(1, 8)
             row[name] = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3,
                          "tflops": round(alg * E / ms / 1e9, 3),
                          "paper_count_gflops": round(63.0 * nq_of(p) * n * n * E / ms / 1e6, 1)}
+            if ref is None:
+                ref = A[:S].clone()
+            else:
+                row[name]["err_max_vs_f64"] = float(((A[:S].double() - ref).norm(dim=1) / ref.norm(dim=1)).max())
             del A, b
         out[str(p)] = row
         torch.cuda.empty_cache()

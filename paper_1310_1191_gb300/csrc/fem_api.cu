@@ -270,8 +270,8 @@ int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coo
                           void *stream) {
   if (!t || t->elem != FEM_PRISM6) return invalid("fem_integrate_elastic: needs prism tables");
   if (p < t->p_min || p > t->p_max || n_elem < 0) return invalid("fem_integrate_elastic: bad degree or n_elem");
-  if (prec != FEM_F64 && prec != FEM_F32) {
-    set_error("fem_integrate_elastic: FP64 or FP32 only");
+  if (prec != FEM_F64 && prec != FEM_F32 && prec != FEM_BF16X3) {
+    set_error("fem_integrate_elastic: FEM_F64, FEM_F32 or FEM_BF16X3 only");
     return FEM_EUNSUPPORTED;
   }
   if (n_elem == 0) return FEM_OK;
@@ -284,6 +284,22 @@ int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coo
   cudaGetDevice(&dev);
   if (dev != t->device) return invalid("fem_integrate_elastic: tables live on another device");
   const DevTable &d = t->tab[p];
+  if (prec == FEM_BF16X3) {
+    TcLaunch l;
+    l.n = n_elem;
+    l.coords = coords;
+    l.coeffs = coeffs;
+    l.cstride = coeff_stride;
+    l.A = A_out;
+    l.b = b_out;
+    l.status = status;
+    l.layout = FEM_OUT_FULL;
+    l.err = t->d_err;
+    l.stall = t->stall_next;
+    l.elastic = 1;
+    t->stall_next = 0;
+    return launch_tc(p, false, d, l, stream);
+  }
   FmaArgs a;
   a.n = n_elem;
   a.coords = coords;

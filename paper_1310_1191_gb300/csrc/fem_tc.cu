@@ -45,7 +45,7 @@
 
 namespace fem {
 
-template <int P>
+template <int P, bool ELAS = false>
 struct TcCfg {
   static constexpr int NS = ns_of(FEM_PRISM6, P), NQ = nq_of(FEM_PRISM6, P);
   static constexpr int L = NS + 1;  // MMA rows per element
@@ -72,7 +72,7 @@ struct TcCfg {
   static constexpr int B_BYTES = NP * KC * 2;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int SBO = (KC / 8) * 128;   // 8-row group stride in a stage tile
-  static constexpr int NREC = 18 + 11;
+  static constexpr int NREC = 18 + (ELAS ? 5 : 11);  // coordinates + coefficients
   static constexpr int NZ = P + 1, NAB = NZ * NZ;  // tensor-product factors of J per element
   // Each CTA owns a contiguous range of tiles, so consecutive tiles share
   // elements; point records live in a ring of RING element slots (slot =
@@ -91,7 +91,8 @@ struct TcCfg {
   static constexpr size_t OFF_CF = OFF_ZR + (size_t)MAXEL * NZ * 16;           // float [MAXEL][12]
   static constexpr size_t OFF_W = OFF_CF + (size_t)MAXEL * 48;                 // float [NQP] weights
   static constexpr size_t OFF_RS = OFF_W + (size_t)NQP * 4;                    // per slot: 7 x [RING] words
-  static constexpr size_t OFF_BAR = (OFF_RS + 28 * (size_t)RING + 15) / 16 * 16;
+  static constexpr size_t OFF_EC = (OFF_RS + 28 * (size_t)RING + 15) / 16 * 16;   // float [RING][8] (elasticity)
+  static constexpr size_t OFF_BAR = OFF_EC + 32 * (size_t)RING;
   static constexpr int NBAR = 2 * STAGES + 9;
   static constexpr size_t OFF_MISC = OFF_BAR + 8 * NBAR;
   static constexpr size_t SMEM = OFF_MISC + 16 + 1024;
@@ -146,9 +147,15 @@ __device__ __forceinline__ uint32_t split_pack(float x0, float x1, uint32_t &lo_
   }
 }
 
-template <int P, bool F16>
+// ELAS: linear elastostatics (the model problem), BF16 only.  The rows are
+// (virtual element v, trial function r) with v = 9 e + 3 i + k the block
+// (i, k) of element e; the point records hold adj J, w / det J and w det J,
+// and the producers form each block's weighted rows from them (see below).
+template <int P, bool F16, bool ELAS = false>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
-  using C = TcCfg<P>;
+  using C = TcCfg<P, ELAS>;
+  static_assert(!(ELAS && F16), "elasticity runs the BF16 form only");
+  constexpr int VPE = ELAS ? 9 : 1;  // row blocks (virtual elements) per element
   extern __shared__ unsigned char smem_raw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float *sG = reinterpret_cast<float *>(sm + C::OFF_G);          // [RING][NQP][12] point records
@@ -159,6 +166,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
   float *sZR = reinterpret_cast<float *>(sm + C::OFF_ZR);        // [MAXEL][NZ][4] adj row 2, FP32
   float *sCF = reinterpret_cast<float *>(sm + C::OFF_CF);        // [MAXEL][12] coefficients, FP32
   float *sW = reinterpret_cast<float *>(sm + C::OFF_W);          // [NQP] quadrature weights, FP32
+  float *sEC = reinterpret_cast<float *>(sm + C::OFF_EC);        // [RING][8] lambda, mu, f (elasticity)
   float *sInv = reinterpret_cast<float *>(sm + C::OFF_RS);       // [RING] matrix-row unscale
   float *sInvB = sInv + C::RING;                                 // [RING] load-vector-row unscale
   float *sScl = sInvB + C::RING;                                 // [RING] matrix-row scale (FP16)
@@ -177,7 +185,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
   volatile int *sAbort = reinterpret_cast<volatile int *>(sm + C::OFF_MISC + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t nrows = a.n * C::L;
+  const int64_t nrows = a.n * VPE * C::L;
   const int64_t ntiles = (nrows + C::BM - 1) / C::BM;
   // this CTA's contiguous range of M tiles
   const int64_t t_begin = (int64_t)blockIdx.x * ntiles / gridDim.x;
@@ -219,8 +227,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
   // element range of tile t
   auto tile_elems = [&](int64_t t, int64_t &e_first, int &nel) {
     const int64_t R0 = t * C::BM;
-    e_first = R0 / C::L;
-    int64_t e_last = (R0 + C::BM - 1) / C::L;
+    e_first = R0 / C::L / VPE;
+    int64_t e_last = (R0 + C::BM - 1) / C::L / VPE;
     if (e_last > a.n - 1) e_last = a.n - 1;
     nel = (int)(e_last - e_first + 1);
   };
@@ -308,10 +316,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
       tile_elems(t, e_first, nel);
       const int64_t r = t * C::BM + rl;
       const bool valid = r < nrows;
-      const int64_t e = valid ? r / C::L : e_first;
+      const int64_t v = valid ? r / C::L : e_first * VPE;  // virtual element
+      const int64_t e = v / VPE;
       const int j = valid ? (int)(r % C::L) : 0;
       const float *gbase = sG + (size_t)(e % C::RING) * C::GSLOT;
       const bool arow = valid && j < C::NS;
+      // elasticity: block (bi, bk) of the row, the element's lambda, mu, f_bi
+      const int blk = (int)(v % VPE), bi = blk / 3, bk = blk % 3;
+      float lam = 0.f, mu = 0.f, fbi = 0.f;
+      if (ELAS) {
+        const float *ec = sEC + (e % C::RING) * 8;
+        lam = ec[0];
+        mu = ec[1];
+        fbi = bi == 0 ? ec[2] : (bi == 1 ? ec[3] : ec[4]);
+      }
       // Phi values of the next PD - 1 chunks are in flight while a chunk is
       // built (ring of PD register sets, indexed statically by unrolling)
       float fr[C::PD][QH][4];
@@ -349,15 +367,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
           float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
           if (valid && q < C::NQ) {
             const float4 *g4 = reinterpret_cast<const float4 *>(gbase + q * 12);
-            const float4 ga = g4[0], gb = g4[1], gc = g4[2];  // G00 G01 G02 G03 | G11 G12 G13 G22 | G23 G33 GS -
-            if (arow) {
-              const float f0 = f[qq][0], f1 = f[qq][1], f2 = f[qq][2], f3 = f[qq][3];
-              t0 = ga.x * f0 + ga.y * f1 + ga.z * f2 + ga.w * f3;
-              t1 = gb.x * f1 + gb.y * f2 + gb.z * f3;
-              t2 = gb.y * f1 + gb.w * f2 + gc.x * f3;
-              t3 = gb.z * f1 + gc.x * f2 + gc.y * f3;
+            const float4 ga = g4[0], gb = g4[1], gc = g4[2];
+            if (ELAS) {
+              // record: adj J row-major (a[k][m], k reference, m physical
+              // direction) | w / det | w det.  Block (bi, bk):
+              //   G[a][b] = (w/det) (lam a[a][bi] a[b][bk] + mu a[a][bk] a[b][bi]
+              //                      + d_ik mu (a[a] . a[b])),
+              // so with u = adj^T (f1, f2, f3) (det J times the physical gradient)
+              //   t_{1+a} = (w/det) (lam a[a][bi] u_bk + mu a[a][bk] u_bi + d_ik mu a[a] . u);
+              // the value row is zero, the load-vector row (w det f_bi, 0, 0, 0).
+              const float a00 = ga.x, a01 = ga.y, a02 = ga.z, a10 = ga.w, a11 = gb.x, a12 = gb.y;
+              const float a20 = gb.z, a21 = gb.w, a22 = gc.x, sw = gc.y;
+              if (arow) {
+                const float f1 = f[qq][1], f2 = f[qq][2], f3 = f[qq][3];
+                const float u0 = a00 * f1 + a10 * f2 + a20 * f3;
+                const float u1 = a01 * f1 + a11 * f2 + a21 * f3;
+                const float u2 = a02 * f1 + a12 * f2 + a22 * f3;
+                const float ubi = bi == 0 ? u0 : (bi == 1 ? u1 : u2);
+                const float ubk = bk == 0 ? u0 : (bk == 1 ? u1 : u2);
+                const float li = sw * lam * ubk, mi = sw * mu * ubi, dm = bi == bk ? sw * mu : 0.f;
+                const float c0i = bi == 0 ? a00 : (bi == 1 ? a01 : a02);
+                const float c1i = bi == 0 ? a10 : (bi == 1 ? a11 : a12);
+                const float c2i = bi == 0 ? a20 : (bi == 1 ? a21 : a22);
+                const float c0k = bk == 0 ? a00 : (bk == 1 ? a01 : a02);
+                const float c1k = bk == 0 ? a10 : (bk == 1 ? a11 : a12);
+                const float c2k = bk == 0 ? a20 : (bk == 1 ? a21 : a22);
+                t1 = c0i * li + c0k * mi + dm * (a00 * u0 + a01 * u1 + a02 * u2);
+                t2 = c1i * li + c1k * mi + dm * (a10 * u0 + a11 * u1 + a12 * u2);
+                t3 = c2i * li + c2k * mi + dm * (a20 * u0 + a21 * u1 + a22 * u2);
+              } else {
+                t0 = bk == 0 ? gc.z * fbi : 0.f;
+              }
             } else {
-              t0 = gc.z;
+              // G00 G01 G02 G03 | G11 G12 G13 G22 | G23 G33 GS -
+              if (arow) {
+                const float f0 = f[qq][0], f1 = f[qq][1], f2 = f[qq][2], f3 = f[qq][3];
+                t0 = ga.x * f0 + ga.y * f1 + ga.z * f2 + ga.w * f3;
+                t1 = gb.x * f1 + gb.y * f2 + gb.z * f3;
+                t2 = gb.y * f1 + gb.w * f2 + gc.x * f3;
+                t3 = gb.z * f1 + gc.x * f2 + gc.y * f3;
+              } else {
+                t0 = gc.z;
+              }
             }
           }
           hw[2 * qq] = split_pack<F16>(t0, t1, lw[2 * qq]);
@@ -438,12 +489,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
             if (!isfinite(sX[idx])) atomicOr(&sSt[(e_new + idx / C::NREC) % C::RING], FEM_ST_NONFINITE);
           if (gt < nnew) {
             const double *cf = sX + gt * C::NREC + 18;
-            if (a.layout == FEM_OUT_SYMPACKED && (cf[6] != 0.0 || cf[7] != 0.0 || cf[8] != 0.0))
-              atomicOr(&sSt[(e_new + gt) % C::RING], FEM_ST_NONSYM);
             edge_record<FEM_PRISM6>(sX + gt * C::NREC, sEd + gt * kEdgeRec);
-            float *cfl = sCF + gt * 12;  // D00 D11 D22 D01 D02 D12 b0 b1 b2 c f
+            if (ELAS) {  // E, nu, f -> lambda, mu, f of the element's slot
+              const double Ey = cf[0], nu = cf[1];
+              float *ec = sEC + ((e_new + gt) % C::RING) * 8;
+              ec[0] = (float)(Ey * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+              ec[1] = (float)(Ey / (2.0 * (1.0 + nu)));
+              ec[2] = (float)cf[2];
+              ec[3] = (float)cf[3];
+              ec[4] = (float)cf[4];
+            } else {
+              if (a.layout == FEM_OUT_SYMPACKED && (cf[6] != 0.0 || cf[7] != 0.0 || cf[8] != 0.0))
+                atomicOr(&sSt[(e_new + gt) % C::RING], FEM_ST_NONSYM);
+              float *cfl = sCF + gt * 12;  // D00 D11 D22 D01 D02 D12 b0 b1 b2 c f
 #pragma unroll
-            for (int k = 0; k < 11; k++) cfl[k] = (float)cf[k];
+              for (int k = 0; k < 11; k++) cfl[k] = (float)cf[k];
+            }
           }
         }
         gbar();
@@ -472,8 +533,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
             if (q < C::NQ) {
               float gv[11];
               const int iz = q / C::NAB, iab = q % C::NAB;
-              const double det = point_tc(sZF + (el * C::NZ + iz) * kZf, sZR + (el * C::NZ + iz) * 4,
-                                          sXF + (el * C::NAB + iab) * kXf, sW[q], sCF + el * 12, gv);
+              double det;
+              if (ELAS) {  // adj J (row-major), w / det J, w det J
+                float a32[3][3];
+                det = adj_tp_f32(sZF + (el * C::NZ + iz) * kZf, sZR + (el * C::NZ + iz) * 4,
+                                 sXF + (el * C::NAB + iab) * kXf, a32);
+#pragma unroll
+                for (int k = 0; k < 9; k++) gv[k] = a32[k / 3][k % 3];
+                const float detf = (float)det;
+                gv[9] = sW[q] / detf;
+                gv[10] = sW[q] * detf;
+              } else {
+                det = point_tc(sZF + (el * C::NZ + iz) * kZf, sZR + (el * C::NZ + iz) * 4,
+                               sXF + (el * C::NAB + iab) * kXf, sW[q], sCF + el * 12, gv);
+              }
 #pragma unroll
               for (int k = 0; k < 11; k++) gr[k] = gv[k];
               if (!(det > 0.0)) atomicOr(&sSt[sl], FEM_ST_DET);
@@ -514,7 +587,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
           sInvB[sl] = invb;
           sScl[sl] = sc;
           sScB[sl] = scb;
-          if (a.status && e * C::L >= R0) a.status[e] = sSt[sl];  // the tile holding row 0 reports
+          if (a.status && e * VPE * C::L >= R0) a.status[e] = sSt[sl];  // the tile holding row 0 reports
         }
         if (F16) {
           gbar();
@@ -545,7 +618,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
           const int rl = 32 * lq + lane;
           const int64_t r = tq * C::BM + rl;
           const bool valid = r < nrows;
-          const int64_t e = valid ? r / C::L : 0;
+          const int64_t ve = valid ? r / C::L : 0;  // virtual element (the element for the scalar form)
+          const int64_t e = ve / VPE;
           const int j = valid ? (int)(r % C::L) : 0;
           const int sl = (int)(e % C::RING);
           const float inv = valid ? (j < C::NS ? sInv[sl] : sInvB[sl]) : 0.f;
@@ -558,7 +632,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
             if (valid) {
               if (j < C::NS) {
                 if (a.layout == FEM_OUT_FULL) {
-                  float *Ae = static_cast<float *>(a.A) + e * (int64_t)(C::NS * C::NS) + j;
+                  // elasticity: block-major A^e[i][k][s][r] = block ve's [s][r]
+                  float *Ae = static_cast<float *>(a.A) + ve * (int64_t)(C::NS * C::NS) + j;
 #pragma unroll
                   for (int u = 0; u < 16; u++) {
                     const int i = c0 + u;
@@ -573,8 +648,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                     if (i < C::NS && i <= j) Ae[i * C::NS - i * (i - 1) / 2 + j - i] = __uint_as_float(v[u]) * inv;
                   }
                 }
-              } else if (a.b != nullptr) {
-                float *be = static_cast<float *>(a.b) + e * (int64_t)C::NS;
+              } else if (a.b != nullptr && (!ELAS || ve % 3 == 0)) {
+                // elasticity: the blocks (i, 0) carry b^e[i] (index 3 e + i = ve / 3)
+                float *be = static_cast<float *>(a.b) + (ELAS ? ve / 3 : e) * (int64_t)C::NS;
 #pragma unroll
                 for (int u = 0; u < 16; u++) {
                   const int i = c0 + u;
@@ -600,8 +676,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
     // flag the elements of this CTA's tiles that may be incomplete
     if (a.status) {
       for (int64_t t = t_begin; t < t_end; t++) {
-        const int64_t e0 = (t * C::BM) / C::L;
-        int64_t e1 = (t * C::BM + C::BM - 1) / C::L;
+        const int64_t e0 = (t * C::BM) / C::L / VPE;
+        int64_t e1 = (t * C::BM + C::BM - 1) / C::L / VPE;
         if (e1 > a.n - 1) e1 = a.n - 1;
         for (int64_t e = e0 + tid; e <= e1; e += blockDim.x) atomicOr(&a.status[e], FEM_ST_TIMEOUT);
       }
@@ -615,11 +691,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
 
 // ---------------------------------------------------------------- host side
 
-template <int P, bool F16>
+template <int P, bool F16, bool ELAS>
 static int launch_tc_p(const TcArgs &a, void *stream) {
-  using C = TcCfg<P>;
+  using C = TcCfg<P, ELAS>;
   if (a.n == 0) return FEM_OK;
-  cudaError_t err = cudaFuncSetAttribute(tc_kernel<P, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  cudaError_t err =
+      cudaFuncSetAttribute(tc_kernel<P, F16, ELAS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   if (err != cudaSuccess) {
     set_error(std::string("cudaFuncSetAttribute(tc_kernel): ") + cudaGetErrorString(err));
     return FEM_ECUDA;
@@ -628,10 +705,10 @@ static int launch_tc_p(const TcArgs &a, void *stream) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   // one 512-thread CTA per SM (it overlaps its own phases); TMEM_COLS <= 512
-  const int64_t ntiles = (a.n * C::L + C::BM - 1) / C::BM;
+  const int64_t ntiles = (a.n * (ELAS ? 9 : 1) * C::L + C::BM - 1) / C::BM;
   int64_t grid = nsm;
   if (grid > ntiles) grid = ntiles;
-  tc_kernel<P, F16><<<(unsigned)grid, kTcThreads, C::SMEM, (cudaStream_t)stream>>>(a);
+  tc_kernel<P, F16, ELAS><<<(unsigned)grid, kTcThreads, C::SMEM, (cudaStream_t)stream>>>(a);
   err = cudaGetLastError();
   if (err != cudaSuccess) {
     set_error(std::string("tc_kernel launch: ") + cudaGetErrorString(err));
@@ -640,16 +717,16 @@ static int launch_tc_p(const TcArgs &a, void *stream) {
   return FEM_OK;
 }
 
-template <bool F16>
+template <bool F16, bool ELAS>
 static int launch_tc_any(int p, const TcArgs &a, void *stream) {
   switch (p) {
-    case 1: return launch_tc_p<1, F16>(a, stream);
-    case 2: return launch_tc_p<2, F16>(a, stream);
-    case 3: return launch_tc_p<3, F16>(a, stream);
-    case 4: return launch_tc_p<4, F16>(a, stream);
-    case 5: return launch_tc_p<5, F16>(a, stream);
-    case 6: return launch_tc_p<6, F16>(a, stream);
-    case 7: return launch_tc_p<7, F16>(a, stream);
+    case 1: return launch_tc_p<1, F16, ELAS>(a, stream);
+    case 2: return launch_tc_p<2, F16, ELAS>(a, stream);
+    case 3: return launch_tc_p<3, F16, ELAS>(a, stream);
+    case 4: return launch_tc_p<4, F16, ELAS>(a, stream);
+    case 5: return launch_tc_p<5, F16, ELAS>(a, stream);
+    case 6: return launch_tc_p<6, F16, ELAS>(a, stream);
+    case 7: return launch_tc_p<7, F16, ELAS>(a, stream);
   }
   return FEM_EINVAL;
 }
@@ -675,7 +752,14 @@ int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *strea
     set_error("tensor-core tables missing for this degree");
     return FEM_EUNSUPPORTED;
   }
-  return f16 ? launch_tc_any<true>(p, a, stream) : launch_tc_any<false>(p, a, stream);
+  if (l.elastic) {
+    if (f16) {
+      set_error("elasticity runs the BF16x3 tensor-core form only");
+      return FEM_EUNSUPPORTED;
+    }
+    return launch_tc_any<false, true>(p, a, stream);
+  }
+  return f16 ? launch_tc_any<true, false>(p, a, stream) : launch_tc_any<false, false>(p, a, stream);
 }
 
 // Image of Phi^T for the B operand: per K chunk of 32, [hi | lo] blocks of
