@@ -19,6 +19,11 @@
 // T per element from a bound on |G| |Phi|) so the largest magnitude sits near
 // 2^14; the epilogue removes the scale exactly.
 //
+// Linear elastostatics (ELAS, BF16 only) reuses the whole pipeline: each
+// element's 3x3 blocks are nine row blocks ("virtual elements", NS+1 rows
+// each), the value row of T is zero, and the blocks (i, 0) carry the load
+// vector b^e[i] in their extra row (see the producers).
+//
 // CTA roles (512 threads, one CTA per SM, each CTA owns a contiguous range of
 // M tiles):
 //   warp 0, lane 0   : bulk-copies the Phi^T hi/lo image of each K chunk (TMA);
