@@ -390,7 +390,7 @@ def wl_tensor(lib, tables, stream, dev, reps, bf16_peak, E=200000, degrees=(4, 5
 
 def wl_elastic(lib, tables, stream, dev, reps, scale_down=1, degrees=range(1, 8)):
     """Linear elastostatics (the paper's model problem), about 2 GB of FP64
-    output per degree; FP64, FP32 and the BF16x3 tensor-core form.  GFLOP/s also in the paper's count of
+    output per degree; FP64, FP32 and the BF16x3 / FP16x3 tensor-core forms.  GFLOP/s also in the paper's count of
     63 flops per 3x3 block and point (63 NQ NS^2 per element)."""
     import torch
     out = {}
@@ -404,7 +404,7 @@ def wl_elastic(lib, tables, stream, dev, reps, scale_down=1, degrees=range(1, 8)
         S = min(E, 64)
         ref = None
         for name, prec, dt in (("f64", lib.FEM_F64, torch.float64), ("f32", lib.FEM_F32, torch.float32),
-                               ("bf16x3", lib.FEM_BF16X3, torch.float32)):
+                               ("bf16x3", lib.FEM_BF16X3, torch.float32), ("f16x3", lib.FEM_F16X3, torch.float32)):
             A = torch.empty((E, 9 * n * n), dtype=dt, device=dev)
             b = torch.empty((E, 3 * n), dtype=dt, device=dev)
             ms = _timed(stream, lambda: lib.fem_integrate_elastic(tables, p, E, Xd, Cd, E, prec, A, b, None,

@@ -122,13 +122,13 @@ int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, con
  *   b^e[iE][s]        = sum_Q det J w f_iE psi_0^s.
  *   coeffs : device double SoA [5][coeff_stride]: E, nu, fx, fy, fz;
  *   A_out  : device [n_elem][3][3][NS][NS] (the paper's A^e[iE][jE][iDOF][jDOF]),
- *            double (FEM_F64) or float (FEM_F32, FEM_BF16X3), 16-byte aligned;
+ *            double (FEM_F64) or float (the others), 16-byte aligned;
  *   b_out  : device [n_elem][3][NS] or NULL; status : device int32 [n_elem] or NULL.
- * Prisms; FEM_F64 / FEM_F32 (CUDA-core FMA kernels) or FEM_BF16X3 (tensor
- * cores: each 3x3 block of an element is a row block of the tensor-core
- * contraction, BF16 hi + lo operands, FP32 accumulation; the per-element
- * error bound is the one of fem_integrate's FEM_BF16X3); others
- * FEM_EUNSUPPORTED. */
+ * Prisms; FEM_F64 / FEM_F32 (CUDA-core FMA kernels) or FEM_BF16X3 /
+ * FEM_F16X3 (tensor cores: each 3x3 block of an element is a row block of
+ * the tensor-core contraction, 16-bit hi + lo operands, FP32 accumulation;
+ * the per-element error bound is the one of fem_integrate's tensor-core
+ * forms). */
 int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
                           int64_t coeff_stride, int prec, void *A_out, void *b_out, int32_t *status,
                           void *stream);

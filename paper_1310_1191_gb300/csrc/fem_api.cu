@@ -270,8 +270,8 @@ int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coo
                           void *stream) {
   if (!t || t->elem != FEM_PRISM6) return invalid("fem_integrate_elastic: needs prism tables");
   if (p < t->p_min || p > t->p_max || n_elem < 0) return invalid("fem_integrate_elastic: bad degree or n_elem");
-  if (prec != FEM_F64 && prec != FEM_F32 && prec != FEM_BF16X3) {
-    set_error("fem_integrate_elastic: FEM_F64, FEM_F32 or FEM_BF16X3 only");
+  if (prec != FEM_F64 && prec != FEM_F32 && prec != FEM_BF16X3 && prec != FEM_F16X3) {
+    set_error("fem_integrate_elastic: unknown precision");
     return FEM_EUNSUPPORTED;
   }
   if (n_elem == 0) return FEM_OK;
@@ -284,7 +284,7 @@ int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coo
   cudaGetDevice(&dev);
   if (dev != t->device) return invalid("fem_integrate_elastic: tables live on another device");
   const DevTable &d = t->tab[p];
-  if (prec == FEM_BF16X3) {
+  if (prec == FEM_BF16X3 || prec == FEM_F16X3) {
     TcLaunch l;
     l.n = n_elem;
     l.coords = coords;
@@ -298,7 +298,7 @@ int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coo
     l.stall = t->stall_next;
     l.elastic = 1;
     t->stall_next = 0;
-    return launch_tc(p, false, d, l, stream);
+    return launch_tc(p, prec == FEM_F16X3, d, l, stream);
   }
   FmaArgs a;
   a.n = n_elem;

@@ -19,7 +19,7 @@
 // T per element from a bound on |G| |Phi|) so the largest magnitude sits near
 // 2^14; the epilogue removes the scale exactly.
 //
-// Linear elastostatics (ELAS, BF16 only) reuses the whole pipeline: each
+// Linear elastostatics (ELAS) reuses the whole pipeline: each
 // element's 3x3 blocks are nine row blocks ("virtual elements", NS+1 rows
 // each), the value row of T is zero, and the blocks (i, 0) carry the load
 // vector b^e[i] in their extra row (see the producers).
@@ -152,14 +152,13 @@ __device__ __forceinline__ uint32_t split_pack(float x0, float x1, uint32_t &lo_
   }
 }
 
-// ELAS: linear elastostatics (the model problem), BF16 only.  The rows are
+// ELAS: linear elastostatics (the model problem).  The rows are
 // (virtual element v, trial function r) with v = 9 e + 3 i + k the block
 // (i, k) of element e; the point records hold adj J, w / det J and w det J,
 // and the producers form each block's weighted rows from them (see below).
 template <int P, bool F16, bool ELAS = false>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
   using C = TcCfg<P, ELAS>;
-  static_assert(!(ELAS && F16), "elasticity runs the BF16 form only");
   constexpr int VPE = ELAS ? 9 : 1;  // row blocks (virtual elements) per element
   extern __shared__ unsigned char smem_raw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -555,7 +554,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
 #pragma unroll
               for (int k = 0; k < 11; k++) gr[k] = gv[k];
               if (!(det > 0.0)) atomicOr(&sSt[sl], FEM_ST_DET);
-              if (F16) {
+              if (F16 && ELAS) {
+                // |t_{1+a}| <= (w/det) (|lam| + 2 mu) |adj_a| sum_b |adj_b| max|Phi| over
+                // every block (Cauchy-Schwarz on the three terms); the
+                // load-vector row w det f_i by its own bound
+                const float *ec = sEC + sl * 8;
+                const float n0 = sqrtf(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
+                const float n1 = sqrtf(gv[3] * gv[3] + gv[4] * gv[4] + gv[5] * gv[5]);
+                const float n2 = sqrtf(gv[6] * gv[6] + gv[7] * gv[7] + gv[8] * gv[8]);
+                const float bb = fabsf(gv[9]) * (fabsf(ec[0]) + 2.f * fabsf(ec[1])) * fmaxf(n0, fmaxf(n1, n2)) *
+                                 (n0 + n1 + n2);
+                if (isfinite(bb)) atomicMax(&sBnd[sl], __float_as_uint(bb));
+                const float bs = fabsf(gv[10]) * fmaxf(fabsf(ec[2]), fmaxf(fabsf(ec[3]), fabsf(ec[4])));
+                if (isfinite(bs)) atomicMax(&sBndB[sl], __float_as_uint(bs));
+              } else if (F16) {
                 float bb = fabsf(gv[G00]) + fabsf(gv[G01]) + fabsf(gv[G02]) + fabsf(gv[G03]);
                 bb = fmaxf(bb, fabsf(gv[G11]) + fabsf(gv[G12]) + fabsf(gv[G13]));
                 bb = fmaxf(bb, fabsf(gv[G12]) + fabsf(gv[G22]) + fabsf(gv[G23]));
@@ -601,9 +613,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
               const int sl = (int)((e_new + idx / C::NQP) % C::RING);
               float *gr = sG + (size_t)sl * C::GSLOT + (idx % C::NQP) * 12;
               const float sc = sScl[sl];
+              if (ELAS) {  // every t scales with w/det, the load-vector row with w det
+                gr[9] *= sc;
+                gr[10] *= sScB[sl];
+              } else {
 #pragma unroll
-              for (int k = 0; k < 10; k++) gr[k] *= sc;
-              gr[GS] *= sScB[sl];
+                for (int k = 0; k < 10; k++) gr[k] *= sc;
+                gr[GS] *= sScB[sl];
+              }
             }
           }
         }
@@ -757,13 +774,7 @@ int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *strea
     set_error("tensor-core tables missing for this degree");
     return FEM_EUNSUPPORTED;
   }
-  if (l.elastic) {
-    if (f16) {
-      set_error("elasticity runs the BF16x3 tensor-core form only");
-      return FEM_EUNSUPPORTED;
-    }
-    return launch_tc_any<false, true>(p, a, stream);
-  }
+  if (l.elastic) return f16 ? launch_tc_any<true, true>(p, a, stream) : launch_tc_any<false, true>(p, a, stream);
   return f16 ? launch_tc_any<true, false>(p, a, stream) : launch_tc_any<false, false>(p, a, stream);
 }
 

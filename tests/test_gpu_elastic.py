@@ -95,23 +95,25 @@ def test_elastic_full_size_sampled(orc, lib, tables, p, prec):
     assert rel_frob(b[ti].double().cpu().numpy().reshape(len(idx), -1), Rb.reshape(len(idx), -1)).max() <= TOL[prec]
 
 
-# ---- tensor-core form (BF16x3): the bound of the scalar tensor-core form,
-# which the FP32 accumulator sets (it grows with K = 4 NQ, not with the form)
+# ---- tensor-core forms (BF16x3, FP16x3): the bound of the scalar
+# tensor-core form, which the FP32 accumulator sets (it grows with K = 4 NQ,
+# not with the form)
 TOL_TC = 3e-5
 
 
+@pytest.mark.parametrize("prec", [2, 3])
 @pytest.mark.parametrize("p", range(1, 8))
-def test_elastic_tc_parity_small(orc, lib, tables, p):
+def test_elastic_tc_parity_small(orc, lib, tables, p, prec):
     E = SMALL_E[p]
     X = inputs.prism_mesh(E)
     C = inputs.elastic_coefficients(E)
-    A, b, st = _run(lib, tables, p, X, C, lib.FEM_BF16X3)
+    A, b, st = _run(lib, tables, p, X, C, prec)
     assert lib.fem_error_flag(tables) == lib.FEM_OK
     RA, Rb, Rst = orc.integrate_elastic(p, X, C)
     n = ns(PRISM, p)
     eA = rel_frob(A.reshape(E, 9 * n * n), RA.reshape(E, 9 * n * n))
     eb = rel_frob(b.reshape(E, 3 * n), Rb.reshape(E, 3 * n))
-    print("elastic tc p=%d: A max %.3e b max %.3e" % (p, eA.max(), eb.max()))
+    print("elastic tc p=%d prec=%d: A max %.3e b max %.3e" % (p, prec, eA.max(), eb.max()))
     assert np.array_equal(st, Rst) and np.all(st == 0)
     assert eA.max() <= TOL_TC and eb.max() <= TOL_TC
 
@@ -129,35 +131,43 @@ def test_elastic_tc_many_tiles_vs_oracle(orc, lib, tables):
     assert rel_frob(b.reshape(E, -1), Rb.reshape(E, -1)).max() <= TOL_TC
 
 
+@pytest.mark.parametrize("prec", [2, 3])
 @pytest.mark.parametrize("p,E", [(5, 150), (7, 80)])
-def test_elastic_tc_many_tiles_vs_fp64_kernel(orc, lib, tables, p, E):
+def test_elastic_tc_many_tiles_vs_fp64_kernel(orc, lib, tables, p, E, prec):
     """Eight or more M tiles per CTA, every element against the FP64 kernel
     (itself within 1e-12 of the oracle, checked on one element)."""
     X = inputs.prism_mesh(E)
     C = inputs.elastic_coefficients(E)
-    A, b, st = _run(lib, tables, p, X, C, lib.FEM_BF16X3)
+    A, b, st = _run(lib, tables, p, X, C, prec)
     A64, b64, st64 = _run(lib, tables, p, X, C, lib.FEM_F64)
     RA, _, _ = orc.integrate_elastic(p, X[:1], C[:, :1])
     assert rel_frob(A64[:1].reshape(1, -1), RA.reshape(1, -1)).max() <= 1e-12
     assert np.array_equal(st, st64) and np.all(st == 0)
     eA = rel_frob(A.reshape(E, -1), A64.reshape(E, -1))
-    print("elastic tc many tiles p=%d: A max %.3e" % (p, eA.max()))
+    print("elastic tc many tiles p=%d prec=%d: A max %.3e" % (p, prec, eA.max()))
     assert eA.max() <= TOL_TC and rel_frob(b.reshape(E, -1), b64.reshape(E, -1)).max() <= TOL_TC
 
 
-def test_elastic_tc_flags_and_fp16_unsupported(orc, lib, tables):
-    import torch
+def test_elastic_tc_flags(orc, lib, tables):
     p = 2
     X = inputs.prism_mesh(4)
     C = inputs.elastic_coefficients(4)
     X[1] = X[1][[1, 0, 2, 4, 3, 5]]  # mirrored: det J < 0
     C[1, 2] = np.nan
-    _, _, st = _run(lib, tables, p, X, C, lib.FEM_BF16X3)
     _, _, Rst = orc.integrate_elastic(p, X, C)
-    assert list(st) == list(Rst)
-    n = ns(PRISM, p)
-    A = torch.empty((4, 9 * n * n), dtype=torch.float32, device="cuda")
-    with pytest.raises(lib.FemError) as ei:
-        lib.fem_integrate_elastic(tables, p, 4, torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda(), 4,
-                                  lib.FEM_F16X3, A, None, None)
-    assert ei.value.code == lib.FEM_EUNSUPPORTED
+    for prec in (lib.FEM_BF16X3, lib.FEM_F16X3):
+        _, _, st = _run(lib, tables, p, X, C, prec)
+        assert list(st) == list(Rst)
+
+
+def test_elastic_f16_small_load(orc, lib, tables):
+    """FP16x3 with a body force 1e-6 of the stiffness scale: the load-vector
+    row has its own power-of-two scale, so b stays accurate."""
+    p, E = 3, 6
+    X = inputs.prism_mesh(E)
+    C = inputs.elastic_coefficients(E)
+    C[2:5] *= 1e-6
+    A, b, st = _run(lib, tables, p, X, C, lib.FEM_F16X3)
+    RA, Rb, _ = orc.integrate_elastic(p, X, C)
+    assert rel_frob(A.reshape(E, -1), RA.reshape(E, -1)).max() <= TOL_TC
+    assert rel_frob(b.reshape(E, -1), Rb.reshape(E, -1)).max() <= TOL_TC
