@@ -491,15 +491,27 @@ def wl_batched(lib, tables, stream, dev, reps, E=500000):
     offA, offb, totA, totb = lib.fem_output_offsets(lib.FEM_PRISM6, P, 0)
     A = torch.empty(totA, dtype=torch.float32, device=dev)
     b = torch.empty(totb, dtype=torch.float32, device=dev)
-    res = {}
-    for name, flags in (("graph_autotuned", lib.FEM_PLAN_AUTOTUNE), ("per_degree_loop", lib.FEM_PLAN_LOOP),
-                        ("graph_concurrent_branches", lib.FEM_PLAN_CONCURRENT)):
-        plan = lib.fem_plan_create(tables, P, lib.FEM_F32, 0, flags, None)
+    # error sample: the first elements of each degree, against the FP32 result
+    sample = [int(np.flatnonzero(P == p)[k]) for p in range(1, 8) for k in range(8)]
+    res, ref = {}, None
+    for name, prec, flags in (("graph_autotuned", lib.FEM_F32, lib.FEM_PLAN_AUTOTUNE),
+                              ("per_degree_loop", lib.FEM_F32, lib.FEM_PLAN_LOOP),
+                              ("graph_concurrent_branches", lib.FEM_F32, lib.FEM_PLAN_CONCURRENT),
+                              ("graph_concurrent_bf16x3", lib.FEM_BF16X3, lib.FEM_PLAN_CONCURRENT),
+                              ("graph_concurrent_f16x3", lib.FEM_F16X3, lib.FEM_PLAN_CONCURRENT)):
+        plan = lib.fem_plan_create(tables, P, prec, 0, flags, None)
         ms = _timed(stream, lambda: lib.fem_plan_execute(plan, Xd, Cd, E, A, b, None, stream), reps, 2)
         res[name] = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3,
                      "variants": [plan.variant(p)[0] for p in range(1, 8)]}
+        stream.synchronize()
+        blocks = [A[int(offA[e]):int(offA[e]) + ns_of(int(P[e])) ** 2].double() for e in sample]
+        if ref is None:
+            ref = blocks
+        else:
+            res[name]["err_max_vs_f32"] = max(float((x - r).norm() / r.norm()) for x, r in zip(blocks, ref))
         plan.close()
-    return {"workload": "500000 prisms, seeded degrees p=1..7 (weights .25 .2 .15 .15 .1 .1 .05), FP32",
+    return {"workload": "500000 prisms, seeded degrees p=1..7 (weights .25 .2 .15 .15 .1 .1 .05), FP32 outputs; "
+                        "variants per degree: 0/1 persistent shapes, 2 uniform-degree FP32 kernel, 3 tensor cores",
             "bins": np.bincount(P, minlength=8)[1:].tolist(), **res}
 
 

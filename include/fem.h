@@ -277,7 +277,10 @@ int fem_output_offsets(int elem, const int8_t *p_host, int64_t n, int layout, in
  * tune_cache (nullable) is a text file that stores and reuses the choices.
  *   t      : prism tables covering every degree in p_host;
  *   p_host : host int8 [n_elem] degrees (copied; not kept);
- *   prec   : FEM_F64 or FEM_F32 (others FEM_EUNSUPPORTED);
+ *   prec   : FEM_F64 or FEM_F32; or FEM_BF16X3 / FEM_F16X3 with
+ *            FEM_PLAN_LOOP or FEM_PLAN_CONCURRENT (each degree then runs the
+ *            tensor-core kernel or an FP32 kernel, see fem_plan_variant;
+ *            float outputs); others FEM_EUNSUPPORTED;
  *   layout : FEM_OUT_FULL / FEM_OUT_SYMPACKED.
  * The plan owns device memory for the permutation, the offsets, the work
  * list and the counter; release it with fem_plan_destroy. */
@@ -293,13 +296,15 @@ int fem_plan_create(fem_tables t, int64_t n_elem, const int8_t *p_host, int prec
 int fem_plan_execute(fem_plan plan, const double *coords, const double *coeffs, int64_t coeff_stride,
                      void *A_out, void *b_out, int32_t *status, void *stream);
 
-/* Tile-shape variant chosen for degree p, and the autotuner's times of the
- * candidates in ms (ms[3], nullable; 0 if not timed); -1 if invalid.
+/* Kernel variant chosen for degree p, and the autotuner's times of the
+ * candidates in ms (ms[4], nullable; 0 if not timed); -1 if invalid.
  * Variants 0 and 1 are the persistent kernel's candidate shapes; plans with
  * FEM_PLAN_LOOP or FEM_PLAN_CONCURRENT also have variant 2, the degree's
  * uniform-degree kernel (as fem_integrate runs it), their default without
- * FEM_PLAN_AUTOTUNE.  Per-degree plans are tuned by timing each candidate
- * as one launch over the degree's bin. */
+ * FEM_PLAN_AUTOTUNE; plans with a tensor-core precision also variant 3, the
+ * tensor-core kernel, their default for p >= 3 (variants 0-2 then run in
+ * FP32).  Per-degree plans are tuned by timing each candidate as one launch
+ * over the degree's bin. */
 int fem_plan_variant(fem_plan plan, int p, double *ms);
 int fem_plan_destroy(fem_plan plan);
 

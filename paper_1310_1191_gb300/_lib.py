@@ -225,7 +225,7 @@ class Plan:
         self.handle = h
 
     def variant(self, p: int):
-        ms = np.zeros(3)
+        ms = np.zeros(4)
         v = load().fem_plan_variant(self.handle, p, ms.ctypes.data)
         return v, ms
 

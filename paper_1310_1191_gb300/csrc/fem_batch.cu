@@ -37,7 +37,10 @@ constexpr int kVariants = 2;   // candidate shapes of the persistent kernel
 // Per-degree launches (loop and concurrent-branch plans) have a third
 // candidate: the degree's uniform-degree kernel (no 256-thread limit).
 constexpr int kStandalone = 2;
-constexpr int kLoopVariants = 3;
+// Plans with a tensor-core precision (per-degree modes only) have a fourth:
+// the tensor-core kernel; their FMA candidates run in FP32.
+constexpr int kTensor = 3;
+constexpr int kMaxVariants = 4;
 
 // Candidate shapes (ELEM, P, BM, TM, TN, EPB, QC), all with at most 256 threads.
 template <int P, int V> struct BShape;
@@ -164,7 +167,7 @@ struct fem_plan_s {
   int64_t bin_off[fem::kMaxP + 2] = {0};  // sorted positions of each degree's bin
   int variant[fem::kMaxP + 1] = {0};
   bool tuned = false;
-  double tuned_ms[fem::kMaxP + 1][fem::kLoopVariants] = {{0}};
+  double tuned_ms[fem::kMaxP + 1][fem::kMaxVariants] = {{0}};
   // device data (plan-owned)
   int64_t *perm = nullptr, *offA = nullptr, *offb = nullptr;
   int4 *items = nullptr;
@@ -189,6 +192,9 @@ static int plan_fail(const char *what, cudaError_t e) {
 }
 
 static bool per_degree(const fem_plan_s *pl) { return (pl->flags & (FEM_PLAN_LOOP | FEM_PLAN_CONCURRENT)) != 0; }
+static bool tensor_plan(const fem_plan_s *pl) { return pl->prec == FEM_BF16X3 || pl->prec == FEM_F16X3; }
+// candidates of a degree's per-degree launch
+static int loop_variants(const fem_plan_s *pl) { return tensor_plan(pl) ? kMaxVariants : kMaxVariants - 1; }
 
 static double item_cost(int p) {  // relative cost of one element of degree p (contraction flops)
   const double ns = ns_of(FEM_PRISM6, p), nq = nq_of(FEM_PRISM6, p);
@@ -297,17 +303,39 @@ static int launch_batch(const fem_plan_s *pl, const BatchArgs &b, cudaStream_t s
   return launch_batch_raw(pl->prec == FEM_F64, b, s);
 }
 
+// One launch over the bin of degree p with variant v (per-degree modes).
+static int launch_bin(const fem_plan_s *pl, int p, int v, const FmaArgs &base, cudaStream_t s) {
+  const int64_t k0 = pl->bin_off[p], k1 = pl->bin_off[p + 1];
+  const DevTable &d = pl->t->tab[p];
+  if (v == kTensor) {
+    TcLaunch l;
+    l.n = k1 - k0;
+    l.coords = base.coords;
+    l.coeffs = base.coeffs;
+    l.cstride = base.cstride;
+    l.A = base.A;
+    l.b = base.b;
+    l.status = base.status;
+    l.layout = base.layout;
+    l.err = pl->t->d_err;
+    l.stall = 0;
+    l.perm = pl->perm + k0;
+    l.offA = base.offA;
+    l.offb = base.offb;
+    return launch_tc(p, pl->prec == FEM_F16X3, d, l, s);
+  }
+  FmaArgs a = base;
+  a.n = k1 - k0;
+  a.perm = pl->perm + k0;
+  a.qp = d.qp;
+  a.phi = pl->prec == FEM_F64 ? (const void *)d.phi64 : (const void *)d.phi32;
+  return pl->prec == FEM_F64 ? launch_loop<double>(p, v, a, s) : launch_loop<float>(p, v, a, s);
+}
+
 static int launch_per_p_loop(const fem_plan_s *pl, const FmaArgs &base, cudaStream_t s) {
   for (int p = 1; p <= kMaxP; p++) {
-    const int64_t k0 = pl->bin_off[p], k1 = pl->bin_off[p + 1];
-    if (k1 <= k0) continue;
-    FmaArgs a = base;
-    a.n = k1 - k0;
-    a.perm = pl->perm + k0;
-    a.qp = pl->t->tab[p].qp;
-    a.phi = pl->prec == FEM_F64 ? (const void *)pl->t->tab[p].phi64 : (const void *)pl->t->tab[p].phi32;
-    const int rc = pl->prec == FEM_F64 ? launch_loop<double>(p, pl->variant[p], a, s)
-                                       : launch_loop<float>(p, pl->variant[p], a, s);
+    if (pl->bin_off[p + 1] <= pl->bin_off[p]) continue;
+    const int rc = launch_bin(pl, p, pl->variant[p], base, s);
     if (rc != FEM_OK) return rc;
   }
   return FEM_OK;
@@ -324,13 +352,7 @@ static int launch_concurrent(fem_plan_s *pl, const FmaArgs &base, cudaStream_t s
     if (k1 <= k0) continue;
     e = cudaStreamWaitEvent(pl->branch[p], pl->fork, 0);
     if (e != cudaSuccess) return plan_fail("cudaStreamWaitEvent(fork)", e);
-    FmaArgs a = base;
-    a.n = k1 - k0;
-    a.perm = pl->perm + k0;
-    a.qp = pl->t->tab[p].qp;
-    a.phi = pl->prec == FEM_F64 ? (const void *)pl->t->tab[p].phi64 : (const void *)pl->t->tab[p].phi32;
-    const int rc = pl->prec == FEM_F64 ? launch_loop<double>(p, pl->variant[p], a, pl->branch[p])
-                                       : launch_loop<float>(p, pl->variant[p], a, pl->branch[p]);
+    const int rc = launch_bin(pl, p, pl->variant[p], base, pl->branch[p]);
     if (rc != FEM_OK) return rc;
     e = cudaEventRecord(pl->join[p], pl->branch[p]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, pl->join[p], 0);
@@ -360,7 +382,7 @@ static bool cache_lookup(const fem_plan_s *pl, int p, int *v) {
   int val;
   double ms;
   while (f >> k >> val >> ms)
-    if (k == key && val >= 0 && val < (per_degree(pl) ? kLoopVariants : kVariants)) {
+    if (k == key && val >= 0 && val < (per_degree(pl) ? loop_variants(pl) : kVariants)) {
       *v = val;
       return true;
     }
@@ -390,16 +412,11 @@ static int autotune(fem_plan_s *pl, const FmaArgs &base, cudaStream_t s) {
     double best = 1e30;
     int bestv = 0;
     if (per_degree(pl)) {  // time the candidates as they are launched: one kernel over the bin
-      FmaArgs a = base;
-      a.n = pl->bin_off[p + 1] - pl->bin_off[p];
-      a.perm = pl->perm + pl->bin_off[p];
-      a.qp = pl->t->tab[p].qp;
-      a.phi = pl->prec == FEM_F64 ? (const void *)pl->t->tab[p].phi64 : (const void *)pl->t->tab[p].phi32;
-      for (int cand = 0; cand < kLoopVariants && rc == FEM_OK; cand++) {
+      for (int cand = 0; cand < loop_variants(pl) && rc == FEM_OK; cand++) {
         float tmin = 1e30f;
         for (int rep = 0; rep < 3 && rc == FEM_OK; rep++) {
           cudaEventRecord(e0, s);
-          rc = pl->prec == FEM_F64 ? launch_loop<double>(p, cand, a, s) : launch_loop<float>(p, cand, a, s);
+          rc = launch_bin(pl, p, cand, base, s);
           cudaEventRecord(e1, s);
           cudaError_t err = cudaEventSynchronize(e1);
           if (err != cudaSuccess) rc = plan_fail("autotune", err);
@@ -643,8 +660,13 @@ int fem_plan_create(fem_tables t, int64_t n_elem, const int8_t *p_host, int prec
     set_error("fem_plan_create: bad n_elem or NULL degrees");
     return FEM_EINVAL;
   }
-  if (prec != FEM_F64 && prec != FEM_F32) {
-    set_error("fem_plan_create: mixed-degree plans run the FP64 / FP32 kernels");
+  const bool tc = prec == FEM_BF16X3 || prec == FEM_F16X3;
+  if (prec != FEM_F64 && prec != FEM_F32 && !tc) {
+    set_error("fem_plan_create: unknown precision");
+    return FEM_EUNSUPPORTED;
+  }
+  if (tc && !(flags & (FEM_PLAN_LOOP | FEM_PLAN_CONCURRENT))) {
+    set_error("fem_plan_create: tensor-core precisions need FEM_PLAN_LOOP or FEM_PLAN_CONCURRENT");
     return FEM_EUNSUPPORTED;
   }
   if (layout != FEM_OUT_FULL && layout != FEM_OUT_SYMPACKED) {
@@ -671,7 +693,7 @@ int fem_plan_create(fem_tables t, int64_t n_elem, const int8_t *p_host, int prec
   pl->bin_off[1] = 0;
   for (int p = 1; p <= kMaxP; p++) pl->bin_off[p + 1] = pl->bin_off[p] + cnt[p];
   if (per_degree(pl))  // untuned per-degree launches use the uniform-degree kernels
-    for (int p = 1; p <= kMaxP; p++) pl->variant[p] = kStandalone;
+    for (int p = 1; p <= kMaxP; p++) pl->variant[p] = tensor_plan(pl) && p >= 3 ? kTensor : kStandalone;
   // counting sort by degree (stable)
   std::vector<int64_t> perm(std::max<int64_t>(n_elem, 1)), offA(std::max<int64_t>(n_elem, 1)),
       offb(std::max<int64_t>(n_elem, 1));
@@ -784,7 +806,7 @@ int fem_plan_execute(fem_plan pl, const double *coords, const double *coeffs, in
 int fem_plan_variant(fem_plan pl, int p, double *ms) {
   if (!pl || p < 1 || p > kMaxP) return -1;
   if (ms)
-    for (int v = 0; v < kLoopVariants; v++) ms[v] = pl->tuned_ms[p][v];
+    for (int v = 0; v < kMaxVariants; v++) ms[v] = pl->tuned_ms[p][v];
   return pl->variant[p];
 }
 

@@ -122,6 +122,10 @@ struct TcLaunch {
   int *err;
   int stall;  // withhold the operand copies (failure-detection test)
   int elastic = 0;  // linear elastostatics (coeffs E, nu, f; A [n][3][3][NS][NS], b [n][3][NS])
+  // element permutation and output offsets of mixed-degree plans (or NULL)
+  const int64_t *perm = nullptr;
+  const int64_t *offA = nullptr;
+  const int64_t *offb = nullptr;
 };
 int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *stream);
 void build_tc_image(int p, const std::vector<double> &phi, bool f16, int aphi, std::vector<uint16_t> &out);

@@ -129,6 +129,12 @@ struct TcArgs {
   int layout;
   int *err;
   int stall;  // test hook: the loader issues no copies, so the pipeline's waits expire
+  // mixed-degree plans (scalar form): element k of this launch is perm[k] of
+  // the mesh, its A_e / b_e start at offA / offb[perm[k]] (all NULL: k itself,
+  // dense outputs)
+  const int64_t *perm;
+  const int64_t *offA;
+  const int64_t *offb;
 };
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
@@ -478,7 +484,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
           for (int idx = gt; idx < nnew * C::NREC; idx += kNGeo) {
             const int el = idx / C::NREC, k = idx % C::NREC;
             const int64_t e = e_new + el;
-            sX[idx] = k < 18 ? a.coords[e * 18 + k] : a.coeffs[(k - 18) * a.cstride + e];
+            const int64_t eg = a.perm ? a.perm[e] : e;  // element of the mesh
+            sX[idx] = k < 18 ? a.coords[eg * 18 + k] : a.coeffs[(k - 18) * a.cstride + eg];
           }
           if (gt < nnew) {
             const int sl = (int)((e_new + gt) % C::RING);
@@ -604,7 +611,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
           sInvB[sl] = invb;
           sScl[sl] = sc;
           sScB[sl] = scb;
-          if (a.status && e * VPE * C::L >= R0) a.status[e] = sSt[sl];  // the tile holding row 0 reports
+          if (a.status && e * VPE * C::L >= R0) a.status[a.perm ? a.perm[e] : e] = sSt[sl];  // the tile holding row 0 reports
         }
         if (F16) {
           gbar();
@@ -642,6 +649,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
           const bool valid = r < nrows;
           const int64_t ve = valid ? r / C::L : 0;  // virtual element (the element for the scalar form)
           const int64_t e = ve / VPE;
+          const int64_t eg = a.perm && valid ? a.perm[e] : e;  // element of the mesh
           const int j = valid ? (int)(r % C::L) : 0;
           const int sl = (int)(e % C::RING);
           const float inv = valid ? (j < C::NS ? sInv[sl] : sInvB[sl]) : 0.f;
@@ -655,7 +663,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
               if (j < C::NS) {
                 if (a.layout == FEM_OUT_FULL) {
                   // elasticity: block-major A^e[i][k][s][r] = block ve's [s][r]
-                  float *Ae = static_cast<float *>(a.A) + ve * (int64_t)(C::NS * C::NS) + j;
+                  float *Ae = static_cast<float *>(a.A) + (a.offA ? a.offA[eg] : ve * (int64_t)(C::NS * C::NS)) + j;
 #pragma unroll
                   for (int u = 0; u < 16; u++) {
                     const int i = c0 + u;
@@ -663,7 +671,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                   }
                 } else {
                   constexpr int NPK = C::NS * (C::NS + 1) / 2;
-                  float *Ae = static_cast<float *>(a.A) + e * (int64_t)NPK;
+                  float *Ae = static_cast<float *>(a.A) + (a.offA ? a.offA[eg] : e * (int64_t)NPK);
 #pragma unroll
                   for (int u = 0; u < 16; u++) {
                     const int i = c0 + u;
@@ -672,7 +680,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                 }
               } else if (a.b != nullptr && (!ELAS || ve % 3 == 0)) {
                 // elasticity: the blocks (i, 0) carry b^e[i] (index 3 e + i = ve / 3)
-                float *be = static_cast<float *>(a.b) + (ELAS ? ve / 3 : e) * (int64_t)C::NS;
+                float *be = static_cast<float *>(a.b) + (a.offb ? a.offb[eg] : (ELAS ? ve / 3 : e) * (int64_t)C::NS);
 #pragma unroll
                 for (int u = 0; u < 16; u++) {
                   const int i = c0 + u;
@@ -701,7 +709,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
         const int64_t e0 = (t * C::BM) / C::L / VPE;
         int64_t e1 = (t * C::BM + C::BM - 1) / C::L / VPE;
         if (e1 > a.n - 1) e1 = a.n - 1;
-        for (int64_t e = e0 + tid; e <= e1; e += blockDim.x) atomicOr(&a.status[e], FEM_ST_TIMEOUT);
+        for (int64_t e = e0 + tid; e <= e1; e += blockDim.x) atomicOr(&a.status[a.perm ? a.perm[e] : e], FEM_ST_TIMEOUT);
       }
     }
   }
@@ -770,6 +778,13 @@ int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *strea
   a.layout = l.layout;
   a.err = l.err;
   a.stall = l.stall;
+  a.perm = l.perm;
+  a.offA = l.offA;
+  a.offb = l.offb;
+  if (l.elastic && (a.perm || a.offA || a.offb)) {
+    set_error("tensor-core elasticity takes dense outputs only");
+    return FEM_EINVAL;
+  }
   if (!a.img) {
     set_error("tensor-core tables missing for this degree");
     return FEM_EUNSUPPORTED;

@@ -125,7 +125,7 @@ def test_per_degree_plans_tune_three_candidates(orc, lib, tables, tmp_path, mode
     _check(ref, P, _run(lib, tables, X, C, P, 1, plan=plan, reps=2), 1, idx=list(idx))
     for p in range(1, 8):
         v, ms = plan.variant(p)
-        assert v in (0, 1, 2) and ms.min() > 0 and ms[v] == ms.min()
+        assert v in (0, 1, 2) and ms[:3].min() > 0 and ms[v] == ms[:3].min() and ms[3] == 0
     chosen = [plan.variant(p)[0] for p in range(1, 8)]
     plan.close()
     # the cache is keyed by execution mode: a persistent plan ignores these entries
@@ -137,6 +137,56 @@ def test_per_degree_plans_tune_three_candidates(orc, lib, tables, tmp_path, mode
     _run(lib, tables, X, C, P, 1, plan=plan)
     assert [plan.variant(p)[0] for p in range(1, 8)] == chosen
     plan.close()
+
+
+TOL_TC = 3e-5  # the tensor-core forms' bound (FP32 accumulation over K = 4 NQ)
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("mode", ["loop", "concurrent"])
+def test_tensor_core_plans_match_oracle(orc, lib, tables, prec, mode):
+    """Per-degree plans with a tensor-core precision: the p >= 3 bins run the
+    tensor-core kernel on the plan's permutation and output offsets, the
+    p <= 2 bins an FP32 kernel; every element vs the oracle."""
+    E = 700
+    X, C, P = _mesh(E)
+    ref = _oracle_by_degree(orc, X, C, P)
+    flags = {"loop": lib.FEM_PLAN_LOOP, "concurrent": lib.FEM_PLAN_CONCURRENT}[mode]
+    plan = lib.fem_plan_create(tables, P, prec, 0, flags, None)
+    assert [plan.variant(p)[0] for p in range(1, 8)] == [2, 2, 3, 3, 3, 3, 3]
+    A, b, st, offA, offb = _run(lib, tables, X, C, P, prec, plan=plan, reps=2)
+    plan.close()
+    assert lib.fem_error_flag(tables) == lib.FEM_OK
+    errs = []
+    for e in range(E):
+        p = int(P[e])
+        n = ns(PRISM, p)
+        RA, Rb, Rst = ref[e]
+        errs.append(rel_frob(A[offA[e]:offA[e] + n * n].reshape(1, n, n), RA[None])[0])
+        assert rel_frob(b[offb[e]:offb[e] + n][None], Rb[None])[0] <= TOL_TC
+        assert st[e] == Rst
+    print("tensor-core plan prec=%d %s: max %.2e" % (prec, mode, max(errs)))
+    assert max(errs) <= TOL_TC
+
+
+def test_tensor_core_plan_autotune_and_persistent_refused(orc, lib, tables):
+    E = 1500
+    X, C, P = _mesh(E)
+    idx = np.arange(0, E, 13)
+    ref = _oracle_by_degree(orc, X, C, P, idx)
+    plan = lib.fem_plan_create(tables, P, lib.FEM_BF16X3, 0, lib.FEM_PLAN_CONCURRENT | lib.FEM_PLAN_AUTOTUNE, None)
+    A, b, st, offA, offb = _run(lib, tables, X, C, P, 2, plan=plan, reps=2)
+    for p in range(1, 8):
+        v, ms = plan.variant(p)
+        assert v in (0, 1, 2, 3) and ms.min() > 0 and ms[v] == ms.min()
+    plan.close()
+    for e in idx:
+        p = int(P[e])
+        n = ns(PRISM, p)
+        assert rel_frob(A[offA[e]:offA[e] + n * n].reshape(1, n, n), ref[int(e)][0][None])[0] <= TOL_TC
+    with pytest.raises(lib.FemError) as ei:
+        lib.fem_plan_create(tables, P, lib.FEM_BF16X3, 0, 0, None)
+    assert ei.value.code == lib.FEM_EUNSUPPORTED
 
 
 @pytest.mark.parametrize("prec", [0, 1])
