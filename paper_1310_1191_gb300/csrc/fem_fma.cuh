@@ -48,7 +48,7 @@ struct FmaCfg {
 
   template <class T>
   static constexpr size_t smem_bytes() {
-    return sizeof(T) * ((size_t)KC * BM + (size_t)EPB * KC * BN + (size_t)EPB * NQ * kGStride) +
+    return sizeof(T) * ((size_t)KC * BM + (size_t)EPB * KC * BN + (size_t)EPB * NQ * kGStride) + 16 +
            sizeof(double) * (size_t)EPB * (NREC + NEDGE + NZ * kZf + NAB * kXf) + sizeof(int) * (size_t)(EPB + 1) +
            sizeof(int64_t) * (size_t)EPB + 64 + sizeof(float) * ((size_t)EPB * (12 + 4 * NZ) + NQ) + 16;
   }
@@ -110,7 +110,9 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   T *sPA = reinterpret_cast<T *>(smem);                 // [KC][BM]
   T *sT = sPA + C::KC * C::BM;                          // [EPB][KC][BN]
   T *sG = sT + C::EPB * C::KC * C::BN;                  // [EPB][NQ][kGStride]
-  double *sX = reinterpret_cast<double *>(sG + C::EPB * C::NQ * kGStride);  // [EPB][NREC]
+  // the FP64 records start on a 16-byte boundary whatever the FP32 arrays' sizes
+  double *sX = reinterpret_cast<double *>(
+      (reinterpret_cast<uintptr_t>(sG + C::EPB * C::NQ * kGStride) + 15) & ~(uintptr_t)15);  // [EPB][NREC]
   double *sEd = sX + C::EPB * C::NREC;                                     // [EPB][NEDGE]
   double *sZF = sEd + C::EPB * C::NEDGE;                                   // [EPB][NZ][9]  (prisms)
   double *sXF = sZF + C::EPB * C::NZ * kZf;                                // [EPB][NAB][3] (prisms)
@@ -631,9 +633,9 @@ template <> struct FmaShape<double, FEM_PRISM6, 6> { using type = FmaCfg<FEM_PRI
 template <> struct FmaShape<double, FEM_PRISM6, 7> { using type = FmaCfg<FEM_PRISM6, 7, 96, 6, 6, 1, 8>; };
 template <> struct FmaShape<float, FEM_TET4, 1> { using type = FmaCfg<FEM_TET4, 1, 4, 1, 4, 64, 4>; };
 template <> struct FmaShape<float, FEM_PRISM6, 1> { using type = FmaCfg<FEM_PRISM6, 1, 6, 1, 6, 42, 4>; };
-template <> struct FmaShape<float, FEM_PRISM6, 2> { using type = FmaCfg<FEM_PRISM6, 2, 18, 6, 6, 28, 3>; };
+template <> struct FmaShape<float, FEM_PRISM6, 2> { using type = FmaCfg<FEM_PRISM6, 2, 18, 3, 6, 28, 3>; };
 template <> struct FmaShape<float, FEM_PRISM6, 3> { using type = FmaCfg<FEM_PRISM6, 3, 40, 8, 4, 4, 8>; };
-template <> struct FmaShape<float, FEM_PRISM6, 4> { using type = FmaCfg<FEM_PRISM6, 4, 75, 5, 5, 1, 5>; };
+template <> struct FmaShape<float, FEM_PRISM6, 4> { using type = FmaCfg<FEM_PRISM6, 4, 75, 5, 5, 2, 5>; };
 template <> struct FmaShape<float, FEM_PRISM6, 5> { using type = FmaCfg<FEM_PRISM6, 5, 128, 8, 8, 1, 8>; };
 template <> struct FmaShape<float, FEM_PRISM6, 6> { using type = FmaCfg<FEM_PRISM6, 6, 200, 8, 8, 1, 16>; };
 template <> struct FmaShape<float, FEM_PRISM6, 7> { using type = FmaCfg<FEM_PRISM6, 7, 96, 6, 6, 1, 8>; };
