@@ -47,7 +47,7 @@ PEAK_F64 = 152 * 2.07e9 * 2 * 2 / 1e12     # 2 FP64 FMA per SM per clock: 1.26 T
 HBM_FALLBACK, BF16_FALLBACK = 6800.0, 1900.0
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture of the full-size launch (profiles/fma_kernel_f64_p7_traffic.md)
-TRAFFIC = {("f64", 7): 45.63e6 + 1.96e9}
+TRAFFIC = {("f64", 7): 51.21e6 + 1.9624e9}
 
 
 def measured_peaks():

@@ -647,6 +647,10 @@ struct FmaShapeE {
   using S = typename FmaShape<T, FEM_PRISM6, P>::type;
   using type = FmaCfg<FEM_PRISM6, P, S::BM, S::TM, S::TN, S::EPB, S::QC, 3>;
 };
+// FP32 at p = 2 and 4: the scalar shapes' larger element groups measured
+// slower for the nine-block elasticity (5.5 -> 8.4 ms and 8.3 -> 9.6 ms)
+template <> struct FmaShapeE<float, 2> { using type = FmaCfg<FEM_PRISM6, 2, 18, 6, 6, 28, 3, 3>; };
+template <> struct FmaShapeE<float, 4> { using type = FmaCfg<FEM_PRISM6, 4, 75, 5, 5, 1, 5, 3>; };
 
 template <class T, bool SPLIT = false>
 int launch_fma_elastic(int p, const FmaArgs &a, void *stream) {
