@@ -549,14 +549,20 @@ def wl_surrogate(lib, tables, stream, dev, reps, E=1000000):
             ("exact_law", lambda: lib.fem_integrate_law(tables, p, E, Xd, Cd, E, Ud, lib.FEM_LAW_EXACT, None,
                                                         1, 0, A, b, st, stream)),
             ("network", lambda: lib.fem_integrate_law(tables, p, E, Xd, Cd, E, Ud, lib.FEM_LAW_MLP, m, 1, 0,
-                                                      A, b, st, stream))):
+                                                      A, b, st, stream)),
+            ("constant_D_bf16x3", lambda: lib.fem_integrate(tables, p, E, Xd, Cd, E, lib.FEM_BF16X3, 0, A, b, st,
+                                                            stream)),
+            ("exact_law_bf16x3", lambda: lib.fem_integrate_law(tables, p, E, Xd, Cd, E, Ud, lib.FEM_LAW_EXACT, None,
+                                                               lib.FEM_BF16X3, 0, A, b, st, stream)),
+            ("network_bf16x3", lambda: lib.fem_integrate_law(tables, p, E, Xd, Cd, E, Ud, lib.FEM_LAW_MLP, m,
+                                                             lib.FEM_BF16X3, 0, A, b, st, stream))):
         ms = _timed(stream, fn, reps)
         row = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3}
-        if name != "constant_D":
+        if not name.startswith("constant_D"):
             err = ((A[:S].double().view(S, NS, NS) - ref).flatten(1).norm(dim=1) /
                    ref.flatten(1).norm(dim=1)).cpu().numpy()
             row.update(err_max=float(err.max()), err_median=float(np.median(err)))
-        if name == "network":
+        if name.startswith("network"):
             row["fallback_elements"] = int(((st & 8) != 0).sum().item())
         res[name] = row
     m.close()
@@ -565,7 +571,9 @@ def wl_surrogate(lib, tables, stream, dev, reps, E=1000000):
             "training": {"samples": N, "steps": 7000, "batch": 8192, "seconds": round(train_s, 3),
                          "loss_first": float(L1[:20].mean()), "loss_last": float(L2[-100:].mean())},
             "error_reference": "GPU FP64 path with the exact law, first 256 elements",
-            "network_over_exact_time": round(res["network"]["ms"] / res["exact_law"]["ms"], 3), **res}
+            "network_over_exact_time": round(res["network"]["ms"] / res["exact_law"]["ms"], 3),
+            "network_over_exact_time_bf16x3": round(res["network_bf16x3"]["ms"] / res["exact_law_bf16x3"]["ms"], 3),
+            **res}
 
 
 def run_only(args):

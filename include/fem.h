@@ -202,7 +202,11 @@ typedef struct fem_mlp_s *fem_mlp;
  *   ucoef : device float [n_elem][NS] coefficients of the scalar field u in
  *           the element's shape functions (the "old" degrees of freedom);
  *   law   : FEM_LAW_EXACT or FEM_LAW_MLP (then mlp must be a network);
- *   prec  : FEM_F64 or FEM_F32 (the law in that precision; the network in FP32).
+ *   prec  : FEM_F64 or FEM_F32 (the law in that precision; the network in FP32),
+ *           or FEM_BF16X3 for prisms (the tensor-core contraction, with the
+ *           coefficient stage -- u, grad u, the law or the network -- in FP32
+ *           on the geometry warps; float outputs, the tensor-core forms'
+ *           error bound).
  * The coefficient rows Dxx..Dyz are ignored (D = k I); b, c, f are used. */
 int fem_integrate_law(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
                       int64_t coeff_stride, const float *ucoef, int law, fem_mlp mlp, int prec, int layout,

@@ -126,6 +126,13 @@ struct TcLaunch {
   const int64_t *perm = nullptr;
   const int64_t *offA = nullptr;
   const int64_t *offb = nullptr;
+  // nonlinear coefficient law: 1 exact, 2 network (BF16x3 scalar form)
+  int law = 0;
+  const float *ucoef = nullptr;
+  const float *mlpw = nullptr;
+  const uint32_t *mlpw2 = nullptr;
+  float nrm[4] = {0, 0, 0, 0};
+  float box[4] = {0, 0, 0, 0};
 };
 int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *stream);
 void build_tc_image(int p, const std::vector<double> &phi, bool f16, int aphi, std::vector<uint16_t> &out);

@@ -125,15 +125,20 @@ constexpr int kMlpSmemBytes = kMlpSmall * 4 + kMlpH * kW2Stride * 2;
 // so hi*W + lo*W keeps about 16 bits of the activations) and FP32
 // accumulation, then tanh and the 64 -> 1 layer.  xin: normalised inputs
 // [npts][2]; pending(p) -> whether point p uses the network; apply(p, k)
-// consumes its output.  Only whole warps of the block take part.
+// consumes its output.  warp / nwarp: this warp's index among the nwarp
+// whole warps that share the points (negative: all whole warps of the block).
 template <class Pending, class Apply>
 __device__ __forceinline__ void mlp_points_mma(const float *sp, const uint32_t *w2, const float *xin, int npts,
-                                               Pending pending, Apply apply) {
+                                               Pending pending, Apply apply, int warp = -1, int nwarp = 0) {
   constexpr int H = kMlpH;
   const float *W1 = sp, *b1 = W1 + 2 * H, *b2 = b1 + H, *W3 = b2 + H;
   const float b3 = W3[H];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  if (warp >= nwarp) return;  // the trailing partial warp of a block
+  const int lane = threadIdx.x & 31;
+  if (warp < 0) {
+    warp = threadIdx.x >> 5;
+    nwarp = blockDim.x >> 5;
+    if (warp >= nwarp) return;  // the trailing partial warp of a block
+  }
   const int g = lane >> 2, t4 = lane & 3;
   const int nmt = (npts + 15) / 16;
   for (int mt = warp; mt < nmt; mt += nwarp) {

@@ -602,8 +602,8 @@ int fem_integrate_law(fem_tables t, int p, int64_t n_elem, const double *coords,
     set_error("fem_integrate_law: FEM_LAW_MLP needs a network");
     return FEM_EINVAL;
   }
-  if (prec != FEM_F64 && prec != FEM_F32) {
-    set_error("fem_integrate_law: the law kernels run in FP64 or FP32");
+  if (prec != FEM_F64 && prec != FEM_F32 && !(prec == FEM_BF16X3 && t->elem == FEM_PRISM6)) {
+    set_error("fem_integrate_law: FP64, FP32, or BF16x3 tensor cores (prisms)");
     return FEM_EUNSUPPORTED;
   }
   if (p < t->p_min || p > t->p_max || n_elem < 0 || (layout != FEM_OUT_FULL && layout != FEM_OUT_SYMPACKED)) {
@@ -626,6 +626,32 @@ int fem_integrate_law(fem_tables t, int p, int64_t n_elem, const double *coords,
     return FEM_EINVAL;
   }
   const DevTable &d = t->tab[p];
+  if (law == FEM_LAW_MLP)  // the compute weights may have changed since the last call (training)
+    pack_w2_kernel<<<(kMlpH * kMlpH / 2 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(mlp->wc, mlp->w2img);
+  if (prec == FEM_BF16X3) {
+    TcLaunch l;
+    l.n = n_elem;
+    l.coords = coords;
+    l.coeffs = coeffs;
+    l.cstride = coeff_stride;
+    l.A = A_out;
+    l.b = b_out;
+    l.status = status;
+    l.layout = layout;
+    l.err = t->d_err;
+    l.stall = 0;
+    l.law = law;
+    l.ucoef = ucoef;
+    if (law == FEM_LAW_MLP) {
+      l.mlpw = mlp->wc;
+      l.mlpw2 = mlp->w2img;
+      for (int i = 0; i < 4; i++) {
+        l.nrm[i] = mlp->nrm[i];
+        l.box[i] = (float)mlp->box[i];
+      }
+    }
+    return launch_tc(p, false, d, l, stream);
+  }
   FmaArgs a;
   a.n = n_elem;
   a.coords = coords;
@@ -640,8 +666,6 @@ int fem_integrate_law(fem_tables t, int p, int64_t n_elem, const double *coords,
   a.layout = layout;
   a.ucoef = ucoef;
   if (law == FEM_LAW_MLP) {
-    // the compute weights may have changed since the last call (training)
-    pack_w2_kernel<<<(kMlpH * kMlpH / 2 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(mlp->wc, mlp->w2img);
     a.mlpw2 = mlp->w2img;
     a.mlpw = mlp->wc;
     for (int i = 0; i < 4; i++) {

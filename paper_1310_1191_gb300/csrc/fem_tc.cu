@@ -46,11 +46,12 @@
 
 #include "fem_geometry.cuh"
 #include "fem_internal.h"
+#include "fem_law.cuh"
 #include "fem_tc_ptx.cuh"
 
 namespace fem {
 
-template <int P, bool ELAS = false>
+template <int P, bool ELAS = false, int LAW = 0>
 struct TcCfg {
   static constexpr int NS = ns_of(FEM_PRISM6, P), NQ = nq_of(FEM_PRISM6, P);
   static constexpr int L = NS + 1;  // MMA rows per element
@@ -70,7 +71,7 @@ struct TcCfg {
                                    : TCOLS_NEED <= 256 ? 256 : 512;
   // operand stages: as many as shared memory holds (the Phi^T copies come
   // from L2, partly across the die boundary, so deep rings hide their latency)
-  static constexpr int STAGES = P == 7 ? 3 : P == 6 ? 4 : P == 5 ? 5 : P == 4 ? 7 : 8;
+  static constexpr int STAGES = (P == 7 ? 3 : P == 6 ? 4 : P == 5 ? 5 : P == 4 ? 7 : 8) - (LAW != 0 && P >= 4 ? 1 : 0);
   // chunks of Phi values the producers keep in flight (registers)
   static constexpr int PD = 3;
   static constexpr int A_BYTES = BM * KC * 2;  // one half (hi or lo)
@@ -97,7 +98,12 @@ struct TcCfg {
   static constexpr size_t OFF_W = OFF_CF + (size_t)MAXEL * 48;                 // float [NQP] weights
   static constexpr size_t OFF_RS = OFF_W + (size_t)NQP * 4;                    // per slot: 7 x [RING] words
   static constexpr size_t OFF_EC = (OFF_RS + 28 * (size_t)RING + 15) / 16 * 16;   // float [RING][8] (elasticity)
-  static constexpr size_t OFF_BAR = OFF_EC + 32 * (size_t)RING;
+  // coefficient law: field coefficients of the pass's new elements; network
+  // weights and the inputs of the pass's points (network only)
+  static constexpr size_t OFF_UC = OFF_EC + 32 * (size_t)RING;                               // float [MAXEL][NS]
+  static constexpr size_t OFF_MLP = (OFF_UC + (LAW ? 4 * (size_t)MAXEL * NS : 0) + 15) / 16 * 16;
+  static constexpr size_t OFF_XIN = OFF_MLP + (LAW == 2 ? (size_t)kMlpSmemBytes : 0);       // float [MAXEL][NQP][2]
+  static constexpr size_t OFF_BAR = (OFF_XIN + (LAW == 2 ? 8 * (size_t)MAXEL * NQP : 0) + 15) / 16 * 16;
   static constexpr int NBAR = 2 * STAGES + 9;
   static constexpr size_t OFF_MISC = OFF_BAR + 8 * NBAR;
   static constexpr size_t SMEM = OFF_MISC + 16 + 1024;
@@ -135,6 +141,12 @@ struct TcArgs {
   const int64_t *perm;
   const int64_t *offA;
   const int64_t *offb;
+  // nonlinear coefficient law (D = k(u, |grad u|) I per point)
+  const float *ucoef;     // [n][NS] field coefficients
+  const float *phiT;      // point-major table [NS][NQ][4] (FP32)
+  const float *mlpw;      // network parameters (FP32 values of BF16 weights)
+  const uint32_t *mlpw2;  // its W2 as BF16 pairs
+  float nrm[4], box[4];
 };
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
@@ -162,9 +174,14 @@ __device__ __forceinline__ uint32_t split_pack(float x0, float x1, uint32_t &lo_
 // (virtual element v, trial function r) with v = 9 e + 3 i + k the block
 // (i, k) of element e; the point records hold adj J, w / det J and w det J,
 // and the producers form each block's weighted rows from them (see below).
-template <int P, bool F16, bool ELAS = false>
+// LAW 1 / 2 (scalar form, BF16): the coefficient stage of the nonlinear law
+// in the geometry warps -- u and grad u from the element's field
+// coefficients, k from the exact law or from the network (its 64x64 layer on
+// warp-level MMAs, the exact law outside its box), D = k I.
+template <int P, bool F16, bool ELAS = false, int LAW = 0>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
-  using C = TcCfg<P, ELAS>;
+  using C = TcCfg<P, ELAS, LAW>;
+  static_assert(LAW == 0 || (!F16 && !ELAS), "the law runs in the BF16 scalar form");
   constexpr int VPE = ELAS ? 9 : 1;  // row blocks (virtual elements) per element
   extern __shared__ unsigned char smem_raw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -177,6 +194,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
   float *sCF = reinterpret_cast<float *>(sm + C::OFF_CF);        // [MAXEL][12] coefficients, FP32
   float *sW = reinterpret_cast<float *>(sm + C::OFF_W);          // [NQP] quadrature weights, FP32
   float *sEC = reinterpret_cast<float *>(sm + C::OFF_EC);        // [RING][8] lambda, mu, f (elasticity)
+  float *sUC = reinterpret_cast<float *>(sm + C::OFF_UC);        // [MAXEL][NS] field coefficients (law)
+  float *sMP = reinterpret_cast<float *>(sm + C::OFF_MLP);       // network: FP32 W1 b1 b2 W3 b3 (law 2)
+  uint32_t *sW2 = reinterpret_cast<uint32_t *>(sMP + kMlpSmall);  // network: W2 BF16 rows (law 2)
+  float *sXin = reinterpret_cast<float *>(sm + C::OFF_XIN);      // [MAXEL][NQP][2] network inputs (law 2)
   float *sInv = reinterpret_cast<float *>(sm + C::OFF_RS);       // [RING] matrix-row unscale
   float *sInvB = sInv + C::RING;                                 // [RING] load-vector-row unscale
   float *sScl = sInvB + C::RING;                                 // [RING] matrix-row scale (FP16)
@@ -201,6 +222,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
   const int64_t t_begin = (int64_t)blockIdx.x * ntiles / gridDim.x;
   const int64_t t_end = ((int64_t)blockIdx.x + 1) * ntiles / gridDim.x;
   for (int q = tid; q < C::NQP; q += blockDim.x) sW[q] = q < C::NQ ? (float)a.qp[4 * q + 3] : 0.f;
+  if (LAW == 2) {  // network parameters (layout of the CUDA-core law kernels)
+    constexpr int H = kMlpH;
+    for (int idx = tid; idx < kMlpSmall; idx += blockDim.x) {
+      float v = 0.f;
+      if (idx < 3 * H) v = a.mlpw[idx];                                      // W1, b1
+      else if (idx < 5 * H + 1) v = a.mlpw[3 * H + H * H + (idx - 3 * H)];  // b2, W3, b3
+      sMP[idx] = v;
+    }
+    for (int idx = tid; idx < H * (H / 2); idx += blockDim.x)
+      sW2[(idx / (H / 2)) * (kW2Stride / 2) + idx % (H / 2)] = a.mlpw2[idx];
+  }
 
   if (tid == 0) {
     for (int s = 0; s < C::STAGES; s++) {
@@ -487,6 +519,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
             const int64_t eg = a.perm ? a.perm[e] : e;  // element of the mesh
             sX[idx] = k < 18 ? a.coords[eg * 18 + k] : a.coeffs[(k - 18) * a.cstride + eg];
           }
+          if (LAW != 0)
+            for (int idx = gt; idx < nnew * C::NS; idx += kNGeo) {
+              const int64_t e = e_new + idx / C::NS;
+              sUC[idx] = a.ucoef[(a.perm ? a.perm[e] : e) * C::NS + idx % C::NS];
+            }
           if (gt < nnew) {
             const int sl = (int)((e_new + gt) % C::RING);
             sSt[sl] = 0;
@@ -554,6 +591,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                 const float detf = (float)det;
                 gv[9] = sW[q] / detf;
                 gv[10] = sW[q] * detf;
+              } else if (LAW != 0) {
+                // coefficient stage: u, grad u in FP32 from the field coefficients
+                float a32[3][3];
+                det = adj_tp_f32(sZF + (el * C::NZ + iz) * kZf, sZR + (el * C::NZ + iz) * 4,
+                                 sXF + (el * C::NAB + iab) * kXf, a32);
+                const float *U = sUC + el * C::NS;
+                float u = 0.f, r0 = 0.f, r1 = 0.f, r2 = 0.f;
+                for (int k = 0; k < C::NS; k++) {
+                  const float4 f = __ldg(reinterpret_cast<const float4 *>(a.phiT) + (size_t)k * C::NQ + q);
+                  u = fmaf(U[k], f.x, u);
+                  r0 = fmaf(U[k], f.y, r0);
+                  r1 = fmaf(U[k], f.z, r1);
+                  r2 = fmaf(U[k], f.w, r2);
+                }
+                const float detf = (float)det, idet = 1.f / detf;
+                const float gx = (a32[0][0] * r0 + a32[1][0] * r1 + a32[2][0] * r2) * idet;
+                const float gy = (a32[0][1] * r0 + a32[1][1] * r1 + a32[2][1] * r2) * idet;
+                const float gz = (a32[0][2] * r0 + a32[1][2] * r1 + a32[2][2] * r2) * idet;
+                const float gg = gx * gx + gy * gy + gz * gz;
+                float kq = 1.f;
+                bool pend = false;
+                if (LAW == 1) {
+                  kq = law_exact<float>(u, gg);
+                } else {
+                  const float sf = sqrtf(gg);
+                  if (u >= a.box[0] && u <= a.box[1] && sf >= a.box[2] && sf <= a.box[3]) {
+                    pend = true;  // k from the network after this phase
+                    sXin[2 * idx] = fmaf(u, a.nrm[0], a.nrm[1]);
+                    sXin[2 * idx + 1] = fmaf(logf(sf), a.nrm[2], a.nrm[3]);
+                  } else {
+                    kq = law_exact<float>(u, gg);
+                    atomicOr(&sSt[sl], FEM_ST_FALLBACK);
+                  }
+                }
+                const float *cf = sCF + el * 12;
+                const float cfl[11] = {kq, kq, kq, 0.f, 0.f, 0.f, cf[6], cf[7], cf[8], cf[9], cf[10]};
+                record_f32(a32, detf, sW[q], cfl, gv);
+                gr[11] = pend ? 1.f : 0.f;
               } else {
                 det = point_tc(sZF + (el * C::NZ + iz) * kZf, sZR + (el * C::NZ + iz) * 4,
                                sXF + (el * C::NAB + iab) * kXf, sW[q], sCF + el * 12, gv);
@@ -592,6 +667,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
           }
         }
         gbar();
+        if (LAW == 2) {
+          // network for the pending points of the pass (whole geometry warps)
+          if (__all_sync(0xffffffffu, go)) {
+            auto rec = [&](int pt) { return sG + (size_t)((e_new + pt / C::NQP) % C::RING) * C::GSLOT + (pt % C::NQP) * 12; };
+            mlp_points_mma(
+                sMP, sW2, sXin, nnew * C::NQP, [&](int pt) { return pt % C::NQP < C::NQ && rec(pt)[11] != 0.f; },
+                [&](int pt, float k) {
+                  float *r = rec(pt);
+#pragma unroll
+                  for (int m = G11; m <= G33; m++) r[m] *= k;
+                },
+                gt >> 5, kNGeo / 32);
+          }
+          gbar();
+        }
         if (go && gt < nnew) {
           const int64_t e = e_new + gt;
           const int sl = (int)(e % C::RING);
@@ -721,12 +811,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
 
 // ---------------------------------------------------------------- host side
 
-template <int P, bool F16, bool ELAS>
+template <int P, bool F16, bool ELAS, int LAW = 0>
 static int launch_tc_p(const TcArgs &a, void *stream) {
-  using C = TcCfg<P, ELAS>;
+  using C = TcCfg<P, ELAS, LAW>;
   if (a.n == 0) return FEM_OK;
   cudaError_t err =
-      cudaFuncSetAttribute(tc_kernel<P, F16, ELAS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      cudaFuncSetAttribute(tc_kernel<P, F16, ELAS, LAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   if (err != cudaSuccess) {
     set_error(std::string("cudaFuncSetAttribute(tc_kernel): ") + cudaGetErrorString(err));
     return FEM_ECUDA;
@@ -738,7 +828,7 @@ static int launch_tc_p(const TcArgs &a, void *stream) {
   const int64_t ntiles = (a.n * (ELAS ? 9 : 1) * C::L + C::BM - 1) / C::BM;
   int64_t grid = nsm;
   if (grid > ntiles) grid = ntiles;
-  tc_kernel<P, F16, ELAS><<<(unsigned)grid, kTcThreads, C::SMEM, (cudaStream_t)stream>>>(a);
+  tc_kernel<P, F16, ELAS, LAW><<<(unsigned)grid, kTcThreads, C::SMEM, (cudaStream_t)stream>>>(a);
   err = cudaGetLastError();
   if (err != cudaSuccess) {
     set_error(std::string("tc_kernel launch: ") + cudaGetErrorString(err));
@@ -747,16 +837,16 @@ static int launch_tc_p(const TcArgs &a, void *stream) {
   return FEM_OK;
 }
 
-template <bool F16, bool ELAS>
+template <bool F16, bool ELAS, int LAW = 0>
 static int launch_tc_any(int p, const TcArgs &a, void *stream) {
   switch (p) {
-    case 1: return launch_tc_p<1, F16, ELAS>(a, stream);
-    case 2: return launch_tc_p<2, F16, ELAS>(a, stream);
-    case 3: return launch_tc_p<3, F16, ELAS>(a, stream);
-    case 4: return launch_tc_p<4, F16, ELAS>(a, stream);
-    case 5: return launch_tc_p<5, F16, ELAS>(a, stream);
-    case 6: return launch_tc_p<6, F16, ELAS>(a, stream);
-    case 7: return launch_tc_p<7, F16, ELAS>(a, stream);
+    case 1: return launch_tc_p<1, F16, ELAS, LAW>(a, stream);
+    case 2: return launch_tc_p<2, F16, ELAS, LAW>(a, stream);
+    case 3: return launch_tc_p<3, F16, ELAS, LAW>(a, stream);
+    case 4: return launch_tc_p<4, F16, ELAS, LAW>(a, stream);
+    case 5: return launch_tc_p<5, F16, ELAS, LAW>(a, stream);
+    case 6: return launch_tc_p<6, F16, ELAS, LAW>(a, stream);
+    case 7: return launch_tc_p<7, F16, ELAS, LAW>(a, stream);
   }
   return FEM_EINVAL;
 }
@@ -781,6 +871,14 @@ int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *strea
   a.perm = l.perm;
   a.offA = l.offA;
   a.offb = l.offb;
+  a.ucoef = l.ucoef;
+  a.phiT = d.phiT32;
+  a.mlpw = l.mlpw;
+  a.mlpw2 = l.mlpw2;
+  for (int i = 0; i < 4; i++) {
+    a.nrm[i] = l.nrm[i];
+    a.box[i] = l.box[i];
+  }
   if (l.elastic && (a.perm || a.offA || a.offb)) {
     set_error("tensor-core elasticity takes dense outputs only");
     return FEM_EINVAL;
@@ -790,6 +888,13 @@ int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *strea
     return FEM_EUNSUPPORTED;
   }
   if (l.elastic) return f16 ? launch_tc_any<true, true>(p, a, stream) : launch_tc_any<false, true>(p, a, stream);
+  if (l.law != 0) {
+    if (f16 || !a.ucoef || (l.law == 2 && (!a.mlpw || !a.mlpw2))) {
+      set_error("tensor-core law integration: BF16x3 with field coefficients (and a network) only");
+      return FEM_EINVAL;
+    }
+    return l.law == 1 ? launch_tc_any<false, false, 1>(p, a, stream) : launch_tc_any<false, false, 2>(p, a, stream);
+  }
   return f16 ? launch_tc_any<true, false>(p, a, stream) : launch_tc_any<false, false>(p, a, stream);
 }
 

@@ -196,6 +196,60 @@ def test_integrate_network_vs_oracle(orc, lib, tables, prec):
         m.close()
 
 
+TOL_TC = 3e-5  # the tensor-core forms' bound (FP32 accumulation over K = 4 NQ)
+
+
+@pytest.mark.parametrize("p,E", [(1, 400), (3, 30), (3, 5000), (5, 12)])
+def test_tensor_core_exact_law_vs_oracle(orc, lib, tables, p, E):
+    """The law on the tensor-core kernel (BF16x3): every element vs the
+    oracle; p = 3 with 5,000 elements puts about ten M tiles on each CTA."""
+    import torch
+    NS = (p + 1) ** 2 * (p + 2) // 2
+    X = inputs.prism_mesh(E)
+    C = inputs.coefficients(E)
+    U = _field(E, NS)
+    A = torch.empty((E, NS * NS), dtype=torch.float32, device="cuda")
+    b = torch.empty((E, NS), dtype=torch.float32, device="cuda")
+    st = torch.empty(E, dtype=torch.int32, device="cuda")
+    lib.fem_integrate_law(tables, p, E, torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda(), E,
+                          torch.from_numpy(U).cuda(), lib.FEM_LAW_EXACT, None, lib.FEM_BF16X3, 0, A, b, st)
+    torch.cuda.synchronize()
+    assert lib.fem_error_flag(tables) == lib.FEM_OK
+    RA, Rb, Rst = orc.integrate(PRISM, p, X, C, law=1, ucoef=U.astype(np.float64))
+    eA = rel_frob(A.cpu().numpy().reshape(E, NS, NS), RA)
+    print("tensor-core exact law p=%d E=%d: max %.2e" % (p, E, eA.max()))
+    assert eA.max() <= TOL_TC and rel_frob(b.cpu().numpy(), Rb).max() <= TOL_TC
+    assert np.array_equal(st.cpu().numpy(), Rst)
+
+
+def test_tensor_core_network_vs_oracle(orc, lib, tables):
+    """Network on the tensor-core kernel: a box that holds every point (no
+    fallback) and one that holds none (exact law everywhere, every element
+    flagged); with the box of the workload, the mixture."""
+    import torch
+    E = 40
+    X = inputs.prism_mesh(E)
+    C = inputs.coefficients(E)
+    U = _field(E, NS3)
+    Xd, Cd, Ud = torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda(), torch.from_numpy(U).cuda()
+    for box, flag in ((np.array([-1e3, 1e3, 1e-3, 1e6]), 0), (np.array([1e3, 2e3, 1e8, 2e8]), 8), (BOX, None)):
+        m = lib.fem_mlp_create(box, 11)
+        _, wc, _ = m.params()
+        A = torch.empty((E, NS3 * NS3), dtype=torch.float32, device="cuda")
+        st = torch.empty(E, dtype=torch.int32, device="cuda")
+        lib.fem_integrate_law(tables, P3, E, Xd, Cd, E, Ud, lib.FEM_LAW_MLP, m, lib.FEM_BF16X3, 0, A, None, st)
+        torch.cuda.synchronize()
+        RA, _, Rst = orc.integrate(PRISM, P3, X, C, law=2, ucoef=U.astype(np.float64),
+                                   mlp=(64, wc.astype(np.float64), box))
+        eA = rel_frob(A.cpu().numpy().reshape(E, NS3, NS3), RA)
+        print("tensor-core network flag=%s: max %.2e" % (flag, eA.max()))
+        assert eA.max() <= TOL_TC
+        assert np.array_equal(st.cpu().numpy(), Rst)
+        if flag is not None:
+            assert np.all(Rst == flag)
+        m.close()
+
+
 @pytest.mark.slow
 def test_surrogate_gain_measured(orc, lib, tables):
     """What the trained network gains over the exact law on the nonlinear
