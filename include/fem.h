@@ -185,7 +185,7 @@ int fem_integrate_host(fem_tables t, int p, int64_t n_elem, const double *coords
 int fem_error_flag(fem_tables t, int clear);
 
 /* ---- nonlinear coefficient law and its learned surrogate ---- */
-/* The law (coefficients at quadrature points computed from "old" degrees of
+/* The law (coefficients at quadrature points computed from previous-solution degrees of
  * freedom, Algorithm 1's coefficient step):
  *     k = 1 + 0.5 exp(-u^2) + 0.2 log(1 + k |grad u|^2),  D = k I,
  * solved per point by exactly 8 Newton steps from k0 = 1 + 0.5 exp(-u^2).
@@ -200,7 +200,7 @@ typedef struct fem_mlp_s *fem_mlp;
 
 /* Integration with the per-point law.  Arguments as fem_integrate, plus
  *   ucoef : device float [n_elem][NS] coefficients of the scalar field u in
- *           the element's shape functions (the "old" degrees of freedom);
+ *           the element's shape functions (the previous solution's degrees of freedom);
  *   law   : FEM_LAW_EXACT or FEM_LAW_MLP (then mlp must be a network);
  *   prec  : FEM_F64 or FEM_F32 (the law in that precision; the network in FP32),
  *           or FEM_BF16X3 for prisms (the tensor-core contraction, with the
