@@ -7,7 +7,8 @@ C with OpenMP over elements, which follows Algorithms 1/2 of the paper; this
 module compiles it with gcc on first use and wraps it with ctypes.
 
 Parity status of each function (what pins it is in tests/test_oracle_*.py):
-  rule, basis, integrate (constant coefficients), law_k, mlp_loss_grad: pinned;
+  rule, basis, integrate (constant coefficients), law_k, mlp_loss_grad,
+  apply (the element operator applied to a coefficient vector): pinned;
   integrate with law=2 (MLP coefficient): pinned through its parts (the MLP
   forward is pinned by the finite-difference and closed-form tests, the
   integration by the law=0 pins).
@@ -189,6 +190,22 @@ def integrate(elem: int, p: int, coords, coeffs, law: int = 0, ucoef=None, mlp=N
     if rc != 0:
         raise RuntimeError("oracle integrate failed")
     return A, b, st
+
+
+def apply(elem: int, p: int, coords, coeffs, x, nthreads: int = 0):
+    """Element operator applied to per-element coefficient vectors (FP64).
+
+    y[e] = A_e x[e] with A_e the element matrix of ``integrate`` (constant
+    coefficients): the element-level matrix-vector product that a Krylov
+    solver of the assembled system performs with the element matrices left
+    in device memory (Section 4), here by its definition, the formed matrix
+    times the vector.  Returns (y [E][NS], status [E]).
+    """
+    A, _, st = integrate(elem, p, coords, coeffs, nthreads=nthreads)
+    x = _f64(x)
+    if x.shape != A.shape[:2]:
+        raise ValueError("x must be [E][NS]")
+    return np.einsum("eij,ej->ei", A, x), st
 
 
 def jacobian_terms(elem: int, p: int, coords):
