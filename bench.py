@@ -425,6 +425,54 @@ def wl_elastic(lib, tables, stream, dev, reps, scale_down=1, degrees=range(1, 8)
             "per_degree": out}
 
 
+def wl_apply(lib, tables, stream, dev, reps, hbm, scale_down=1, degrees=range(1, 8)):
+    """Matrix-free operator apply y_e = A_e x_e (fem_apply), prisms p = 1..7,
+    about 1 GB of algorithmic FP64 traffic per degree (x and y, coordinates,
+    11 coefficients, status), every operand larger than L2.  HBM roofline per
+    degree; the FP64 result is checked against the formed matrices
+    (fem_integrate FP64, then A_e x_e) on the first elements, FP32 against FP64."""
+    import torch
+    out = {}
+    for p in degrees:
+        n = ns_of(p)
+        E = max(1, round(1e9 / (8 * (2 * n + 29))) // scale_down)
+        X = inputs.prism_mesh(E)
+        C = inputs.coefficients(E)
+        x = inputs.dof_vectors(E, n)
+        Xd, Cd = torch.from_numpy(X).to(dev), torch.from_numpy(C).to(dev)
+        st = torch.empty(E, dtype=torch.int32, device=dev)
+        row = {"elements": E}
+        S = min(E, 32)
+        y64 = None
+        for name, prec, dt, osz in (("f64", lib.FEM_F64, torch.float64, 8), ("f32", lib.FEM_F32, torch.float32, 4)):
+            xd = torch.from_numpy(x).to(dev, dt)
+            y = torch.empty_like(xd)
+            ms = _timed(stream, lambda: lib.fem_apply(tables, p, E, Xd, Cd, E, prec, xd, y, st, stream), reps)
+            nbytes = (2 * osz * n + 8 * 29 + 4) * E
+            gbs = nbytes / ms / 1e6
+            row[name] = {"ms": round(ms, 4), "elem_per_s": E / ms * 1e3, "gbs": round(gbs, 1),
+                         "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                                      "frac": round(gbs / hbm, 4)}}
+            if y64 is None:
+                y64 = y[:S].clone()
+                A = torch.empty((S, n * n), dtype=torch.float64, device=dev)
+                lib.fem_integrate(tables, p, S, Xd, Cd, E, lib.FEM_F64, lib.FEM_OUT_FULL, A, None, None, stream)
+                stream.synchronize()
+                yf = torch.bmm(A.view(S, n, n), xd[:S].unsqueeze(2)).squeeze(2)
+                row[name]["err_max_vs_formed"] = float(((y64 - yf).norm(dim=1) / yf.norm(dim=1)).max())
+                del A
+            else:
+                row[name]["err_max_vs_f64"] = float(((y[:S].double() - y64).norm(dim=1) / y64.norm(dim=1)).max())
+            row[name]["flagged"] = int((st != 0).sum().item())
+            del xd, y
+        out[str(p)] = row
+        del Xd, Cd, st
+        torch.cuda.empty_cache()
+    return {"workload": "matrix-free operator apply y_e = A_e x_e (sum factorisation), jittered prisms, "
+                        "random D/b/c, x_e ~ U[-1,1]; about 1 GB of FP64 traffic per degree",
+            "per_degree": out}
+
+
 def _copy_ms(stream, pairs, reps=2):
     """Device time (ms) of the host<->device copies dst.copy_(src) in pairs."""
     return _timed(stream, lambda: [d.copy_(s, non_blocking=True) for d, s in pairs], reps)
@@ -601,6 +649,9 @@ def run_only(args):
     elif args.only == "elastic":
         degs = tuple(int(x) for x in args.degrees.split(",")) if args.degrees else range(1, 8)
         out = wl_elastic(lib, tables, stream, dev, reps, args.scale_down, degs)
+    elif args.only == "apply":
+        degs = tuple(int(x) for x in args.degrees.split(",")) if args.degrees else range(1, 8)
+        out = wl_apply(lib, tables, stream, dev, reps, hbm, args.scale_down, degs)
     elif args.only == "split":
         degs = tuple(int(x) for x in args.degrees.split(",")) if args.degrees else range(1, 8)
         out = wl_split(lib, tables, stream, dev, reps, args.scale_down, degs)
@@ -686,6 +737,7 @@ def run_ours(args):
         workloads["nonlinear_law"] = wl_surrogate(lib, tables, stream, dev, reps)
         workloads["elasticity"] = wl_elastic(lib, tables, stream, dev, reps)
         workloads["split_geometry"] = wl_split(lib, tables, stream, dev, 2)
+        workloads["operator_apply"] = wl_apply(lib, tables, stream, dev, reps, hbm)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_baseline(sweep)
@@ -728,7 +780,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--only", choices=["sweep", "tets", "tc", "mixed", "law", "elastic", "split"],
+    ap.add_argument("--only", choices=["sweep", "tets", "tc", "mixed", "law", "elastic", "split", "apply"],
                     help="run one workload alone (profiling); prints its own JSON")
     ap.add_argument("--elements", type=int, default=0, help="elements for --only tc/mixed/law")
     ap.add_argument("--degrees", default="", help="comma-separated degrees for --only sweep/tc")

@@ -178,6 +178,30 @@ int fem_integrate_host(fem_tables t, int p, int64_t n_elem, const double *coords
                        int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out, int32_t *status,
                        int64_t chunk);
 
+/* Matrix-free operator apply: y_e = A_e x_e for every element, with A_e the
+ * matrix fem_integrate computes (FEM_OUT_FULL: row = test function), without
+ * forming it.  This is the element-level product a Krylov solver of the
+ * assembled system needs when the element operators stay in device memory
+ * (Section 4), and the high-order alternative to forming A_e that Section 3
+ * points to: per element y = sum_Q Phi_Q^T G_Q Phi_Q x, on prisms by sum
+ * factorisation over the triangle x Legendre structure of the basis and the
+ * rule (16 NQ NS flops per element at most instead of 8 NQ NS^2).
+ *   t, p, n_elem, coords, coeffs, coeff_stride : as fem_integrate (f unused);
+ *   prec   : FEM_F64 (x, y double) or FEM_F32 (x, y float; geometry and point
+ *            stage FP64, contractions FP32); tensor-core precisions give
+ *            FEM_EUNSUPPORTED;
+ *   x      : device [n_elem][NS] of the precision's type, DOF order of the
+ *            tables, aligned to its element size; read only;
+ *   y      : device [n_elem][NS], same type and alignment, must not overlap x;
+ *   status : device int32 [n_elem] or NULL: FEM_ST_NONFINITE for a non-finite
+ *            coordinate or coefficient, FEM_ST_DET if det J <= 0 at some point
+ *            (the flags of fem_integrate).
+ * Errors as fem_integrate (FEM_EINVAL for NULL/misaligned pointers, n_elem < 0,
+ * p outside the tables, coeff_stride < n_elem; FEM_ECUDA for a failed launch).
+ * Stream-ordered; allocates nothing. */
+int fem_apply(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
+              int64_t coeff_stride, int prec, const void *x, void *y, int32_t *status, void *stream);
+
 /* Device error word of the tables' kernels: FEM_ETIMEOUT if a bounded wait
  * inside a tensor-core launch expired since the last clear (the affected
  * elements also carry FEM_ST_TIMEOUT), else FEM_OK.  Synchronises the device.

@@ -32,7 +32,7 @@ EXPORTS = (
     "fem_mlp_create", "fem_mlp_destroy", "fem_mlp_nparams", "fem_mlp_forward", "fem_mlp_loss_grad",
     "fem_mlp_train", "fem_mlp_get", "fem_mlp_set", "fem_mlp_save", "fem_mlp_load",
     "fem_integrate_host", "fem_integrate_elastic", "fem_debug_stall_next",
-    "fem_jacobian_terms", "fem_integrate_terms", "fem_integrate_elastic_terms",
+    "fem_jacobian_terms", "fem_integrate_terms", "fem_integrate_elastic_terms", "fem_apply",
 )
 FEM_LAW_EXACT, FEM_LAW_MLP = 1, 2
 FEM_PLAN_AUTOTUNE, FEM_PLAN_LOOP, FEM_PLAN_NOGRAPH, FEM_PLAN_CONCURRENT = 1, 2, 4, 8
@@ -90,6 +90,7 @@ def load():
     lib.fem_mlp_load.argtypes = [ctypes.c_char_p, P]
     lib.fem_integrate_host.argtypes = [P, i, i64, P, P, i64, i, i, P, P, P, i64]
     lib.fem_integrate_elastic.argtypes = [P, i, i64, P, P, i64, i, P, P, P, P]
+    lib.fem_apply.argtypes = [P, i, i64, P, P, i64, i, P, P, P, P]
     lib.fem_jacobian_terms.argtypes = [P, i, i64, P, P, P, P]
     lib.fem_integrate_terms.argtypes = [P, i, i64, P, P, i64, i, i, P, P, P, P]
     lib.fem_integrate_elastic_terms.argtypes = [P, i, i64, P, P, i64, i, P, P, P, P]
@@ -190,6 +191,14 @@ def fem_integrate(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_stride: 
     return _check("fem_integrate", load().fem_integrate(
         t.handle, p, n_elem, _addr(coords), _addr(coeffs), coeff_stride, prec, layout,
         _addr(A_out), _addr(b_out), _addr(status), _stream(stream)))
+
+
+def fem_apply(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_stride: int, prec: int, x, y,
+              status=None, stream=None) -> int:
+    """Enqueue y_e = A_e x_e for n_elem elements without forming A_e (see fem.h)."""
+    return _check("fem_apply", load().fem_apply(
+        t.handle, p, n_elem, _addr(coords), _addr(coeffs), coeff_stride, prec, _addr(x), _addr(y),
+        _addr(status), _stream(stream)))
 
 
 def fem_error_flag(t: Tables, clear: bool = True) -> int:

@@ -38,6 +38,8 @@ static void free_table(DevTable &d) {
   if (d.phi32) cudaFree(d.phi32);
   if (d.phiT64) cudaFree(d.phiT64);
   if (d.phiT32) cudaFree(d.phiT32);
+  if (d.sf64) cudaFree(d.sf64);
+  if (d.sf32) cudaFree(d.sf32);
   if (d.img_bf16) cudaFree(d.img_bf16);
   if (d.img_f16) cudaFree(d.img_f16);
   d = DevTable();
@@ -158,6 +160,11 @@ int fem_tables_build(int elem, int p_min, int p_max, fem_tables *out) {
       for (double v : r.phi) mx = std::fmax(mx, std::fabs(v));
       int ex = 0;
       std::frexp(mx, &ex);  // mx < 2^ex
+      std::vector<double> sf;
+      build_sf_tables(r, p, sf);
+      std::vector<float> sf32(sf.begin(), sf.end());
+      rc = upload(&d.sf64, sf.data(), sf.size());
+      if (rc == FEM_OK) rc = upload(&d.sf32, sf32.data(), sf32.size());
       d.phimax = (float)mx;
       d.aphi_f16 = 14 - ex;  // scaled magnitudes below 2^14
       std::vector<uint16_t> img;
@@ -263,6 +270,46 @@ int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, con
       return launch_tc(p, prec == FEM_F16X3, d, l, stream);
     }
   }
+}
+
+int fem_apply(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
+              int64_t coeff_stride, int prec, const void *x, void *y, int32_t *status, void *stream) {
+  if (!t) return invalid("fem_apply: tables handle is NULL");
+  if (p < t->p_min || p > t->p_max) return invalid("fem_apply: degree not in the tables");
+  if (n_elem < 0) return invalid("fem_apply: n_elem < 0");
+  if (prec < FEM_F64 || prec > FEM_F16X3) return invalid("fem_apply: unknown precision");
+  if (prec != FEM_F64 && prec != FEM_F32) {
+    set_error("fem_apply: FEM_F64 and FEM_F32 only");
+    return FEM_EUNSUPPORTED;
+  }
+  if (n_elem == 0) return FEM_OK;
+  if (!coords || !coeffs || !x || !y) return invalid("fem_apply: NULL coords, coeffs, x or y");
+  if (coeff_stride < n_elem) return invalid("fem_apply: coeff_stride < n_elem");
+  if (((uintptr_t)coords | (uintptr_t)coeffs) & 7) return invalid("fem_apply: coords/coeffs not 8-byte aligned");
+  const uintptr_t osz = prec == FEM_F64 ? 8 : 4;
+  if (((uintptr_t)x | (uintptr_t)y) & (osz - 1)) return invalid("fem_apply: x or y misaligned");
+  if (status && ((uintptr_t)status & 3)) return invalid("fem_apply: status misaligned");
+  const DevTable &d = t->tab[p];
+  const size_t bytes = (size_t)n_elem * d.ns * osz;
+  const uintptr_t xa = (uintptr_t)x, ya = (uintptr_t)y;
+  if (xa < ya + bytes && ya < xa + bytes) return invalid("fem_apply: x and y overlap");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return invalid("fem_apply: tables live on another device");
+  ApplyArgs a;
+  a.n = n_elem;
+  a.coords = coords;
+  a.coeffs = coeffs;
+  a.cstride = coeff_stride;
+  a.qp = d.qp;
+  if (t->elem == FEM_PRISM6)
+    a.tab = prec == FEM_F64 ? (const void *)d.sf64 : (const void *)d.sf32;
+  else
+    a.tab = prec == FEM_F64 ? (const void *)d.phi64 : (const void *)d.phi32;
+  a.x = x;
+  a.y = y;
+  a.status = status;
+  return launch_apply(t->elem, p, prec == FEM_F32, a, stream);
 }
 
 int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,

@@ -1,0 +1,359 @@
+// Matrix-free application of the element operators, y_e = A_e x_e, without
+// forming A_e.
+//
+// The element matrix of the weak form is a sum over quadrature points of
+// Phi^T G_Q Phi (the G-form of the integration kernels: Phi the 4 NQ x NS
+// table of values and reference derivatives, G_Q the 4x4 point matrix that
+// folds geometry, weight and coefficients), so
+//     y = sum_Q Phi_Q^T (G_Q (Phi_Q x)):
+// evaluate the field and its reference gradient at the points, apply G_Q per
+// point, and test against the basis.  This is the element-level product that
+// an iterative solver of the assembled system performs with the element
+// matrices kept in device memory (Section 4), and the high-order alternative
+// to forming them that Section 3 points to: 16 NQ NS flops per element
+// instead of 8 NQ NS^2 for A_e.
+//
+// Prisms use sum factorisation.  The basis is a triangle function T_t(xi, eta)
+// times a Legendre polynomial L_k(zeta) (DOF t + NT k) and the rule a
+// collapsed triangle rule times a Gauss rule in zeta (point iz NAB + iab), so
+// the field at the points comes out of two small contractions,
+//     W[iz][t]  = sum_k L[iz][k] x[k][t],   Wd[iz][t] = sum_k L'[iz][k] x[k][t],
+//     u   = sum_t T[iab][t]   W[iz][t],     u_xi  = sum_t T_xi[iab][t]  W[iz][t],
+//     u_eta = sum_t T_eta[iab][t] W[iz][t], u_zeta = sum_t T[iab][t]    Wd[iz][t],
+// the point stage v = G_Q u, and the transposed contractions in reverse order
+// give y.  That is 4 N NS + 8 NQ NT multiply-adds per element instead of
+// 8 NQ NS (7.5x fewer at p = 7), and the kernel is bound by HBM (x in, y out,
+// the element's coordinates and coefficients) at every degree.
+//
+// Work decomposition: a CTA owns groups of EB elements (grid-stride over the
+// groups, one or two CTAs per SM), keeps the factor tables in shared memory
+// for the whole launch, and pipelines the groups: the next group's x,
+// coordinates and coefficients are fetched with cp.async while the current
+// one is computed.  Per group four phases separated by barriers:
+//   A. element status, tensor-product geometry factors, zeta contraction;
+//   B. triangle contraction + point stage (one thread per point);
+//   C. transposed triangle contraction;
+//   D. transposed zeta contraction, y written to global memory.
+// The geometry (J, adj J, det J and the point stage) is FP64 in both
+// precisions; the contractions run in the precision of x and y.
+//
+// P1 tetrahedra (NS = NQ = 4, J constant) use one thread per element.
+#include "fem_geometry.cuh"
+
+namespace fem {
+namespace {
+
+// Point stage v = G_Q u for the scalar form, without forming G_Q:
+// with t = adj^T grad_ref u (= det J times the physical gradient),
+//   v[1 + k] = (w / det) (adj D t)[k],   v[0] = w (det c u0 + b . t).
+__device__ __forceinline__ void apply_point(const double (&adj)[3][3], double det, double w, const double *cf,
+                                            double u0, double u1, double u2, double u3, double (&v)[4]) {
+  const double t0 = adj[0][0] * u1 + adj[1][0] * u2 + adj[2][0] * u3;
+  const double t1 = adj[0][1] * u1 + adj[1][1] * u2 + adj[2][1] * u3;
+  const double t2 = adj[0][2] * u1 + adj[1][2] * u2 + adj[2][2] * u3;
+  // cf: Dxx Dyy Dzz Dxy Dxz Dyz bx by bz c
+  const double s0 = cf[0] * t0 + cf[3] * t1 + cf[4] * t2;
+  const double s1 = cf[3] * t0 + cf[1] * t1 + cf[5] * t2;
+  const double s2 = cf[4] * t0 + cf[5] * t1 + cf[2] * t2;
+  const double sc = w / det;
+  v[1] = sc * (adj[0][0] * s0 + adj[0][1] * s1 + adj[0][2] * s2);
+  v[2] = sc * (adj[1][0] * s0 + adj[1][1] * s1 + adj[1][2] * s2);
+  v[3] = sc * (adj[2][0] * s0 + adj[2][1] * s1 + adj[2][2] * s2);
+  v[0] = w * (det * cf[9] * u0 + cf[6] * t0 + cf[7] * t1 + cf[8] * t2);
+}
+
+template <int B>
+__device__ __forceinline__ void cp_async(void *sdst, const void *gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gsrc), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <int P, class T>
+struct ApCfg {
+  static constexpr int N = P + 1, NT = N * (N + 1) / 2, NS = NT * N, NAB = N * N, NABP = NAB | 1, NQ = N * NAB;
+  static constexpr int NTH = 256;
+  static constexpr int EB = NTH / NAB > 1 ? NTH / NAB : 1;  // elements per group: about one point per thread
+  static constexpr int NGC = 18 + 11;                       // coordinates + coefficients per element
+  static constexpr int NTAB = 3 * NT * NABP + 2 * N * N;    // triangle factors, L, L'
+  static constexpr int OL = 3 * NT * NABP, OD = OL + N * N;
+  // shared memory (bytes)
+  static constexpr size_t O_TAB = 0;                                         // T [NTAB]
+  static constexpr size_t O_WQ = al16(O_TAB + sizeof(T) * NTAB);             // double [NQ] weights
+  static constexpr size_t O_X = al16(O_WQ + sizeof(double) * NQ);            // T [2][EB][NS]
+  static constexpr size_t O_W = al16(O_X + sizeof(T) * 2 * EB * NS);         // T [EB][2][N][NT]
+  static constexpr size_t O_V = al16(O_W + sizeof(T) * EB * 2 * NS);         // T [EB][4][NQ]
+  static constexpr size_t O_GC = al16(O_V + sizeof(T) * EB * 4 * NQ);        // double [2][EB][NGC]
+  static constexpr size_t O_ZF = al16(O_GC + sizeof(double) * 2 * EB * NGC); // double [EB][N][9]
+  static constexpr size_t O_XF = al16(O_ZF + sizeof(double) * EB * N * kZf); // double [EB][NAB][3]
+  static constexpr size_t O_ST = al16(O_XF + sizeof(double) * EB * NAB * kXf);
+  static constexpr size_t SMEM = al16(O_ST + sizeof(int) * EB);
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+// Start the asynchronous copies of group g (its x, coordinates, coefficients).
+template <class C, class T>
+__device__ __forceinline__ void prefetch_group(const ApplyArgs &a, int64_t g, T *sX, double *sGC) {
+  const int64_t e0 = g * C::EB;
+  const int ne = (int)min((int64_t)C::EB, a.n - e0);
+  const T *xg = static_cast<const T *>(a.x) + e0 * C::NS;
+  for (int i = threadIdx.x; i < ne * C::NS; i += C::NTH) cp_async<sizeof(T)>(sX + i, xg + i);
+  const double *cg = a.coords + e0 * 18;
+  for (int i = threadIdx.x; i < ne * 18; i += C::NTH) cp_async<8>(sGC + (i / 18) * C::NGC + i % 18, cg + i);
+  for (int i = threadIdx.x; i < ne * 11; i += C::NTH) {
+    const int k = i / ne, e = i - k * ne;
+    cp_async<8>(sGC + e * C::NGC + 18 + k, a.coeffs + k * a.cstride + e0 + e);
+  }
+}
+
+template <int P, class T>
+__global__ void __launch_bounds__(256) apply_prism_kernel(const ApplyArgs a) {
+  using C = ApCfg<P, T>;
+  constexpr int N = C::N, NT = C::NT, NS = C::NS, NAB = C::NAB, NABP = C::NABP, NQ = C::NQ, EB = C::EB;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *sTab = reinterpret_cast<T *>(smem + C::O_TAB);
+  double *sWq = reinterpret_cast<double *>(smem + C::O_WQ);
+  T *sX = reinterpret_cast<T *>(smem + C::O_X);
+  T *sW = reinterpret_cast<T *>(smem + C::O_W);
+  T *sV = reinterpret_cast<T *>(smem + C::O_V);
+  double *sGC = reinterpret_cast<double *>(smem + C::O_GC);
+  double *sZF = reinterpret_cast<double *>(smem + C::O_ZF);
+  double *sXF = reinterpret_cast<double *>(smem + C::O_XF);
+  int *sSt = reinterpret_cast<int *>(smem + C::O_ST);
+  const int tid = threadIdx.x;
+  const int64_t ngroups = (a.n + EB - 1) / EB;
+  int64_t g = blockIdx.x;
+  if (g >= ngroups) return;
+
+  const T *tab = static_cast<const T *>(a.tab);
+  for (int i = tid; i < C::NTAB; i += C::NTH) sTab[i] = tab[i];
+  for (int q = tid; q < NQ; q += C::NTH) sWq[q] = a.qp[4 * q + 3];
+  prefetch_group<C>(a, g, sX, sGC);
+  cp_commit();
+  const T *sL = sTab + C::OL, *sD = sTab + C::OD;
+
+  for (int it = 0; g < ngroups; g += gridDim.x, it++) {
+    const int cur = it & 1;
+    cp_wait_all();
+    if (g + gridDim.x < ngroups)
+      prefetch_group<C>(a, g + gridDim.x, sX + (cur ^ 1) * EB * NS, sGC + (cur ^ 1) * EB * C::NGC);
+    cp_commit();
+    __syncthreads();
+    const int64_t e0 = g * EB;
+    const int ne = (int)min((int64_t)EB, a.n - e0);
+    const T *X = sX + cur * EB * NS;
+    const double *GC = sGC + cur * EB * C::NGC;
+
+    // A. status, geometry factors, zeta contraction
+    for (int e = tid; e < ne; e += C::NTH) {
+      int st = 0;
+      for (int k = 0; k < C::NGC; k++)
+        if (!isfinite(GC[e * C::NGC + k])) st = FEM_ST_NONFINITE;
+      sSt[e] = st;
+    }
+    for (int i = tid; i < ne * N; i += C::NTH) {
+      const int e = i / N, iz = i - e * N;
+      double ed[kEdgeRec];
+      edge_record<FEM_PRISM6>(GC + e * C::NGC, ed);
+      prism_zf(ed, a.qp[4 * (iz * NAB) + 2], sZF + i * kZf);
+    }
+    for (int i = tid; i < ne * NAB; i += C::NTH) {
+      const int e = i / NAB, iab = i - e * NAB;
+      double ed[kEdgeRec];
+      edge_record<FEM_PRISM6>(GC + e * C::NGC, ed);
+      prism_xf(ed, a.qp[4 * iab], a.qp[4 * iab + 1], sXF + i * kXf);
+    }
+    for (int i = tid; i < ne * NS; i += C::NTH) {
+      const int e = i / NS, r = i - e * NS, iz = r / NT, t = r - iz * NT;
+      const T *xe = X + e * NS + t;
+      T w = 0, wd = 0;
+#pragma unroll
+      for (int k = 0; k < N; k++) {
+        const T xv = xe[k * NT];
+        w = fma(sL[iz * N + k], xv, w);
+        wd = fma(sD[iz * N + k], xv, wd);
+      }
+      sW[e * 2 * NS + r] = w;
+      sW[e * 2 * NS + NS + r] = wd;
+    }
+    __syncthreads();
+
+    // B. triangle contraction and point stage, one thread per (element, point)
+    for (int i = tid; i < ne * NQ; i += C::NTH) {
+      const int e = i / NQ, q = i - e * NQ, iz = q / NAB, iab = q - iz * NAB;
+      const T *w = sW + e * 2 * NS + iz * NT, *wd = w + NS;
+      const T *f0 = sTab + iab, *f1 = f0 + NT * NABP, *f2 = f1 + NT * NABP;
+      T u0 = 0, u1 = 0, u2 = 0, u3 = 0;
+#pragma unroll 4
+      for (int t = 0; t < NT; t++) {
+        const T a0 = w[t], a1 = wd[t], p0 = f0[t * NABP];
+        u0 = fma(p0, a0, u0);
+        u1 = fma(f1[t * NABP], a0, u1);
+        u2 = fma(f2[t * NABP], a0, u2);
+        u3 = fma(p0, a1, u3);
+      }
+      double adj[3][3];
+      const double det = jac_adj_tp(sZF + (e * N + iz) * kZf, sXF + (e * NAB + iab) * kXf, adj);
+      if (!(det > 0.0)) atomicOr(&sSt[e], FEM_ST_DET);
+      double v[4];
+      apply_point(adj, det, sWq[q], GC + e * C::NGC + 18, (double)u0, (double)u1, (double)u2, (double)u3, v);
+      T *vo = sV + e * 4 * NQ + q;
+      vo[0] = (T)v[0];
+      vo[NQ] = (T)v[1];
+      vo[2 * NQ] = (T)v[2];
+      vo[3 * NQ] = (T)v[3];
+    }
+    __syncthreads();
+
+    // C. transposed triangle contraction -> R, Rd (in place of W, Wd)
+    for (int i = tid; i < ne * NS; i += C::NTH) {
+      const int e = i / NS, r = i - e * NS, iz = r / NT, t = r - iz * NT;
+      const T *v = sV + e * 4 * NQ + iz * NAB;
+      const T *f0 = sTab + t * NABP, *f1 = f0 + NT * NABP, *f2 = f1 + NT * NABP;
+      T ra = 0, rb = 0, rd = 0;
+#pragma unroll 4
+      for (int iab = 0; iab < NAB; iab++) {
+        const T p0 = f0[iab];
+        ra = fma(p0, v[iab], ra);
+        rb = fma(f1[iab], v[NQ + iab], rb);
+        ra = fma(f2[iab], v[2 * NQ + iab], ra);
+        rd = fma(p0, v[3 * NQ + iab], rd);
+      }
+      sW[e * 2 * NS + r] = ra + rb;
+      sW[e * 2 * NS + NS + r] = rd;
+    }
+    __syncthreads();
+
+    // D. transposed zeta contraction -> y
+    T *yg = static_cast<T *>(a.y) + e0 * NS;
+    for (int i = tid; i < ne * NS; i += C::NTH) {
+      const int e = i / NS, r = i - e * NS, k = r / NT, t = r - k * NT;
+      const T *R = sW + e * 2 * NS + t, *Rd = R + NS;
+      T y = 0;
+#pragma unroll
+      for (int iz = 0; iz < N; iz++) {
+        y = fma(sL[iz * N + k], R[iz * NT], y);
+        y = fma(sD[iz * N + k], Rd[iz * NT], y);
+      }
+      yg[i] = y;
+    }
+    if (a.status != nullptr)
+      for (int e = tid; e < ne; e += C::NTH) a.status[e0 + e] = sSt[e];
+    // the next iteration's barrier (after its wait) orders these reads of
+    // sW and sSt before that iteration's phase A overwrites them
+  }
+}
+
+// P1 tetrahedra: one thread per element, J constant over the element.
+template <class T>
+__global__ void __launch_bounds__(256) apply_tet_kernel(const ApplyArgs a) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.n) return;
+  double X[12], cf[10];
+  int st = 0;
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    X[k] = a.coords[e * 12 + k];
+    if (!isfinite(X[k])) st = FEM_ST_NONFINITE;
+  }
+#pragma unroll
+  for (int k = 0; k < 11; k++) {
+    const double c = a.coeffs[k * a.cstride + e];
+    if (k < 10) cf[k] = c;
+    if (!isfinite(c)) st = FEM_ST_NONFINITE;
+  }
+  const T *xe = static_cast<const T *>(a.x) + e * 4;
+  const double x0 = (double)xe[0], x1 = (double)xe[1], x2 = (double)xe[2], x3 = (double)xe[3];
+  double adj[3][3];
+  const double det = jac_adj<FEM_TET4>(X, a.qp, adj);
+  if (!(det > 0.0)) st |= FEM_ST_DET;
+  const T *phi = static_cast<const T *>(a.tab);  // [4 NQ][4], row 4 q + d
+  double y[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    double u[4];
+#pragma unroll
+    for (int d = 0; d < 4; d++) {
+      const T *r = phi + (4 * q + d) * 4;
+      u[d] = (double)r[0] * x0 + (double)r[1] * x1 + (double)r[2] * x2 + (double)r[3] * x3;
+    }
+    double v[4];
+    apply_point(adj, det, a.qp[4 * q + 3], cf, u[0], u[1], u[2], u[3], v);
+#pragma unroll
+    for (int d = 0; d < 4; d++) {
+      const T *r = phi + (4 * q + d) * 4;
+#pragma unroll
+      for (int i = 0; i < 4; i++) y[i] += (double)r[i] * v[d];
+    }
+  }
+  T *ye = static_cast<T *>(a.y) + e * 4;
+#pragma unroll
+  for (int i = 0; i < 4; i++) ye[i] = (T)y[i];
+  if (a.status != nullptr) a.status[e] = st;
+}
+
+template <int P, class T>
+int launch_prism(const ApplyArgs &a, void *stream) {
+  using C = ApCfg<P, T>;
+  cudaError_t err =
+      cudaFuncSetAttribute(apply_prism_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  if (err != cudaSuccess) {
+    set_error(std::string("cudaFuncSetAttribute(apply_prism_kernel): ") + cudaGetErrorString(err));
+    return FEM_ECUDA;
+  }
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_prism_kernel<P, T>, C::NTH, C::SMEM);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t groups = (a.n + C::EB - 1) / C::EB;
+  const int64_t grid = groups < (int64_t)nsm * per_sm ? groups : (int64_t)nsm * per_sm;
+  apply_prism_kernel<P, T><<<(unsigned)grid, C::NTH, C::SMEM, (cudaStream_t)stream>>>(a);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) {
+    set_error(std::string("apply_prism_kernel launch: ") + cudaGetErrorString(err));
+    return FEM_ECUDA;
+  }
+  return FEM_OK;
+}
+
+template <class T>
+int launch_typed(int elem, int p, const ApplyArgs &a, void *stream) {
+  if (elem == FEM_TET4) {
+    const int64_t grid = (a.n + 255) / 256;
+    if (grid > 0x7fffffffLL) {
+      set_error("fem_apply: too many elements for one launch");
+      return FEM_EINVAL;
+    }
+    apply_tet_kernel<T><<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(a);
+    const cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) {
+      set_error(std::string("apply_tet_kernel launch: ") + cudaGetErrorString(err));
+      return FEM_ECUDA;
+    }
+    return FEM_OK;
+  }
+  switch (p) {
+    case 1: return launch_prism<1, T>(a, stream);
+    case 2: return launch_prism<2, T>(a, stream);
+    case 3: return launch_prism<3, T>(a, stream);
+    case 4: return launch_prism<4, T>(a, stream);
+    case 5: return launch_prism<5, T>(a, stream);
+    case 6: return launch_prism<6, T>(a, stream);
+    case 7: return launch_prism<7, T>(a, stream);
+  }
+  set_error("fem_apply: degree out of range");
+  return FEM_EINVAL;
+}
+
+}  // namespace
+
+int launch_apply(int elem, int p, bool f32, const ApplyArgs &a, void *stream) {
+  if (a.n == 0) return FEM_OK;
+  return f32 ? launch_typed<float>(elem, p, a, stream) : launch_typed<double>(elem, p, a, stream);
+}
+
+}  // namespace fem

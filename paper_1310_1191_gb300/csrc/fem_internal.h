@@ -33,6 +33,12 @@ struct HostRule {
 // Builds the quadrature rule and shape-function table; false if (elem,p) invalid.
 bool build_host_rule(int elem, int p, HostRule *out);
 
+// Factor tables of a prism rule for sum factorisation, FP64:
+// [3][NT][NAB | 1] triangle factors (value, d/dxi, d/deta; rows padded to an
+// odd length), then [N][N] Legendre values and [N][N] derivatives (row = zeta
+// level, column = degree); N = p + 1, NT = N (N + 1) / 2, NAB = N^2.
+void build_sf_tables(const HostRule &r, int p, std::vector<double> &out);
+
 // Device copies of one degree's tables.
 struct DevTable {
   int p = 0, ns = 0, nq = 0;
@@ -47,6 +53,9 @@ struct DevTable {
   // tensor-core operand images of Phi^T (hi | lo per K chunk), prisms only
   uint16_t *img_bf16 = nullptr;
   uint16_t *img_f16 = nullptr;
+  // sum-factorisation factors (build_sf_tables), prisms only
+  double *sf64 = nullptr;
+  float *sf32 = nullptr;
   float phimax = 0.f;  // max |Phi|
   int aphi_f16 = 0;    // power-of-two scale applied to the FP16 image
 };
@@ -135,6 +144,20 @@ struct TcLaunch {
   float box[4] = {0, 0, 0, 0};
 };
 int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *stream);
+
+// Matrix-free element-operator apply y_e = A_e x_e (constant coefficients).
+struct ApplyArgs {
+  int64_t n;
+  const double *coords;
+  const double *coeffs;
+  int64_t cstride;
+  const double *qp;   // [NQ][4]
+  const void *tab;    // prisms: sum-factorisation factors; tets: Phi [4 NQ][NS] (the precision's type)
+  const void *x;      // [n][NS]
+  void *y;            // [n][NS]
+  int32_t *status;
+};
+int launch_apply(int elem, int p, bool f32, const ApplyArgs &a, void *stream);
 void build_tc_image(int p, const std::vector<double> &phi, bool f16, int aphi, std::vector<uint16_t> &out);
 
 }  // namespace fem

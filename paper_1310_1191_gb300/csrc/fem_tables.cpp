@@ -222,4 +222,25 @@ bool build_host_rule(int elem, int p, HostRule *out) {
   return true;
 }
 
+// The prism basis is a triangle function times a Legendre polynomial in zeta
+// (DOF t + NT k) and the rule a collapsed triangle rule times a Gauss rule in
+// zeta (point iz NAB + iab), so the table factors.  The k = 0 DOFs at the
+// points of the first zeta level give the triangle factors (L_0 = 1), the
+// t = 0 DOFs at the first triangle point of each level the zeta factors (the
+// t = 0 triangle function is 1): both are read off the full table exactly.
+void build_sf_tables(const HostRule &r, int p, std::vector<double> &out) {
+  const int n = p + 1, nt = n * (n + 1) / 2, nab = n * n, nabp = nab | 1, ns = r.ns;
+  out.assign((size_t)3 * nt * nabp + 2 * n * n, 0.0);
+  for (int c = 0; c < 3; c++)
+    for (int t = 0; t < nt; t++)
+      for (int iab = 0; iab < nab; iab++)
+        out[((size_t)c * nt + t) * nabp + iab] = r.phi[((size_t)4 * iab + c) * ns + t];
+  const size_t lo = (size_t)3 * nt * nabp;
+  for (int iz = 0; iz < n; iz++)
+    for (int k = 0; k < n; k++) {
+      out[lo + iz * n + k] = r.phi[((size_t)4 * iz * nab + 0) * ns + nt * k];
+      out[lo + n * n + iz * n + k] = r.phi[((size_t)4 * iz * nab + 3) * ns + nt * k];
+    }
+}
+
 }  // namespace fem

@@ -285,6 +285,12 @@ def field_coefficients(E: int, ns: int, seed: int = SEED_COEF + 1,
     return np.stack([2.0 * draw_uniform(seed, idx, 100 + k) - 1.0 for k in range(ns)], axis=1)
 
 
+def dof_vectors(E: int, ns: int, seed: int = SEED_COEF + 3, first: int = 0) -> np.ndarray:
+    """Per-element coefficient vectors x_e ~ U[-1,1]^ns that the element
+    operators are applied to (the operator-apply workload); float64 [E][ns]."""
+    return field_coefficients(E, ns, seed=seed, first=first)
+
+
 def box_samples(n: int, box, seed: int = SEED_SURROGATE, first: int = 0) -> np.ndarray:
     """n points uniform in the box [u_min,u_max] x [g_min,g_max]; float64 [n][2]."""
     (u0, u1), (g0, g1) = box

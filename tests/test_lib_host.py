@@ -56,6 +56,29 @@ def test_tet_tables_match_oracle(lib, orc):
     assert np.max(np.abs(phi - orc.basis(0, 1, oxi))) < 1e-15
 
 
+@pytest.mark.parametrize("p", [1, 4, 7])
+def test_prism_table_factors(lib, p):
+    """The structure fem_apply's sum factorisation relies on, read off the
+    library's own table: DOF t + NT k at point iz NAB + iab is the triangle
+    factor of (iab, t) times the zeta factor of (iz, k), for the value and all
+    three reference derivatives (d/dzeta from the Legendre derivative)."""
+    _, _, phi = lib.fem_reference_rule(lib.FEM_PRISM6, p)
+    N = p + 1
+    NT, NAB = N * (N + 1) // 2, N * N
+    T = phi[:NAB, :3, :NT]                 # zeta level 0, k = 0 (L_0 = 1)
+    L = phi[::NAB, 0, ::NT][:N, :N]        # first triangle point, t = 0 (T_0 = 1)
+    dL = phi[::NAB, 3, ::NT][:N, :N]
+    q = np.arange(N * NAB)
+    iz, iab = q // NAB, q % NAB
+    dof = np.arange(NT * N)
+    k, t = dof // NT, dof % NT
+    for d in range(3):
+        ref = T[iab][:, d][:, t] * L[iz][:, k]
+        assert np.max(np.abs(phi[:, d, :] - ref)) <= 1e-13 * np.abs(phi[:, d, :]).max()
+    ref = T[iab][:, 0][:, t] * dL[iz][:, k]
+    assert np.max(np.abs(phi[:, 3, :] - ref)) <= 1e-13 * np.abs(phi[:, 3, :]).max()
+
+
 def test_sizes_and_strings(lib):
     assert lib.fem_matrix_size(lib.FEM_PRISM6, 7, lib.FEM_OUT_FULL) == 288 * 288
     assert lib.fem_matrix_size(lib.FEM_PRISM6, 3, lib.FEM_OUT_SYMPACKED) == 40 * 41 // 2
@@ -72,6 +95,8 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert ei.value.code == lib.FEM_EINVAL
     # NULL tables handle
     rc = so.fem_integrate(None, 2, 10, 8, 8, 10, lib.FEM_F64, lib.FEM_OUT_FULL, 16, None, None, None)
+    assert rc == lib.FEM_EINVAL and "tables" in lib.last_error()
+    rc = so.fem_apply(None, 2, 10, 8, 8, 10, lib.FEM_F64, 8, 16, None, None)
     assert rc == lib.FEM_EINVAL and "tables" in lib.last_error()
     # bad degree range for the builder
     h = ctypes.c_void_p()
