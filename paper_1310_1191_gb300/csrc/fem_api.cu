@@ -161,7 +161,7 @@ int fem_tables_build(int elem, int p_min, int p_max, fem_tables *out) {
       int ex = 0;
       std::frexp(mx, &ex);  // mx < 2^ex
       std::vector<double> sf;
-      build_sf_tables(r, p, sf);
+      build_sf_tables(p, sf);
       std::vector<float> sf32(sf.begin(), sf.end());
       rc = upload(&d.sf64, sf.data(), sf.size());
       if (rc == FEM_OK) rc = upload(&d.sf32, sf32.data(), sf32.size());

@@ -13,29 +13,37 @@
 // to forming them that Section 3 points to: 16 NQ NS flops per element
 // instead of 8 NQ NS^2 for A_e.
 //
-// Prisms use sum factorisation.  The basis is a triangle function T_t(xi, eta)
-// times a Legendre polynomial L_k(zeta) (DOF t + NT k) and the rule a
-// collapsed triangle rule times a Gauss rule in zeta (point iz NAB + iab), so
-// the field at the points comes out of two small contractions,
-//     W[iz][t]  = sum_k L[iz][k] x[k][t],   Wd[iz][t] = sum_k L'[iz][k] x[k][t],
-//     u   = sum_t T[iab][t]   W[iz][t],     u_xi  = sum_t T_xi[iab][t]  W[iz][t],
-//     u_eta = sum_t T_eta[iab][t] W[iz][t], u_zeta = sum_t T[iab][t]    Wd[iz][t],
-// the point stage v = G_Q u, and the transposed contractions in reverse order
-// give y.  That is 4 N NS + 8 NQ NT multiply-adds per element instead of
-// 8 NQ NS (7.5x fewer at p = 7), and the kernel is bound by HBM (x in, y out,
-// the element's coordinates and coefficients) at every degree.
+// Prisms use sum factorisation in all three directions.  The basis function
+// of DOF t + NT k is psi_t(a, b) L_k(zeta) with the Dubiner function
+// psi_(i,j) = P_i(a) h(b)^i Q_j(b) in collapsed coordinates, and the rule is a
+// tensor product of Gauss rules in a, b and zeta (point iz NAB + ia N + ib),
+// so every table entry is a product of 1D factors (build_sf_tables) and the
+// field at the points follows from three small contractions per direction:
+//   zeta:  W[iz][t] = sum_k L[iz][k] x[k][t]   (and Wd with L'),
+//   b:     G[i] = sum_j B[t(i,j)][ib] W[iz][t(i,j)]   per (iz, ib), for the
+//          factors Bq, Bx, By of the value and the two triangle derivatives,
+//   a:     u = sum_i P[ia][i] G[i]   per point (Pa, Px, Pe),
+// then the point stage v = G_Q u (FP64 adj J and det J from the element's
+// tensor-product geometry factors), and the transposed contractions in
+// reverse order give y.  Per element that is 4 N NS + 2 N (4 N NT + 5 N^3)
+// multiply-adds plus about 60 FP64 operations per point: at p = 7 about 100k
+// FP64 operations against 170M multiply-adds to form A_e.  The kernel moves
+// 2 NS values, 18 coordinates and 11 coefficients per element, so even then it
+// is bound by GB300's FP64 pipe, not by HBM, at every degree.
 //
 // Work decomposition: a CTA owns groups of EB elements (grid-stride over the
-// groups, one or two CTAs per SM), keeps the factor tables in shared memory
-// for the whole launch, and pipelines the groups: the next group's x,
-// coordinates and coefficients are fetched with cp.async while the current
-// one is computed.  Per group four phases separated by barriers:
-//   A. element status, tensor-product geometry factors, zeta contraction;
-//   B. triangle contraction + point stage (one thread per point);
-//   C. transposed triangle contraction;
-//   D. transposed zeta contraction, y written to global memory.
-// The geometry (J, adj J, det J and the point stage) is FP64 in both
-// precisions; the contractions run in the precision of x and y.
+// groups), keeps the factor tables in shared memory for the whole launch, and
+// pipelines the groups: the next group's x, coordinates and coefficients are
+// fetched with cp.async while the current one is computed.  Per group five
+// phases separated by barriers:
+//   A.  element status, geometry factors, zeta contraction;
+//   B.  per column (element, iz, ib): b-direction contraction, then for each of
+//       the column's N points the a-direction contraction and the point stage;
+//   C1. per column: transposed a-direction contraction, in place over v;
+//   C2. transposed b-direction contraction;
+//   D.  transposed zeta contraction, y written to global memory.
+// The FP64 path does everything in FP64; the FP32 path keeps adj J rows 0, 1
+// and det J in FP64 (rounded afterwards) and runs the rest in FP32.
 //
 // P1 tetrahedra (NS = NQ = 4, J constant) use one thread per element.
 #include "fem_geometry.cuh"
@@ -74,22 +82,26 @@ constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
 template <int P, class T>
 struct ApCfg {
-  static constexpr int N = P + 1, NT = N * (N + 1) / 2, NS = NT * N, NAB = N * N, NABP = NAB | 1, NQ = N * NAB;
+  static constexpr int N = P + 1, NT = N * (N + 1) / 2, NS = NT * N, NAB = N * N, NQ = N * NAB, NP = N | 1;
   static constexpr int NTH = 256;
-  static constexpr int EB = NTH / NAB > 1 ? NTH / NAB : 1;  // elements per group: about one point per thread
+  static constexpr int EB = NTH / NAB > 1 ? NTH / NAB : 1;  // elements per group: one (level, ib) column per thread
   static constexpr int NGC = 18 + 11;                       // coordinates + coefficients per element
-  static constexpr int NTAB = 3 * NT * NABP + 2 * N * N;    // triangle factors, L, L'
-  static constexpr int OL = 3 * NT * NABP, OD = OL + N * N;
+  // factor tables (type T): Pa, Px, Pe [N][N]; Bq, Bx, By [NT][NP]; L, dL [N][N]
+  static constexpr int OPA = 0, OPX = N * N, OPE = 2 * N * N, OBQ = 3 * N * N, OBX = OBQ + NT * NP,
+                       OBY = OBX + NT * NP, OL = OBY + NT * NP, OD = OL + N * N, NTAB = OD + N * N;
   // shared memory (bytes)
-  static constexpr size_t O_TAB = 0;                                         // T [NTAB]
-  static constexpr size_t O_WQ = al16(O_TAB + sizeof(T) * NTAB);             // double [NQ] weights
-  static constexpr size_t O_X = al16(O_WQ + sizeof(double) * NQ);            // T [2][EB][NS]
-  static constexpr size_t O_W = al16(O_X + sizeof(T) * 2 * EB * NS);         // T [EB][2][N][NT]
-  static constexpr size_t O_V = al16(O_W + sizeof(T) * EB * 2 * NS);         // T [EB][4][NQ]
-  static constexpr size_t O_GC = al16(O_V + sizeof(T) * EB * 4 * NQ);        // double [2][EB][NGC]
-  static constexpr size_t O_ZF = al16(O_GC + sizeof(double) * 2 * EB * NGC); // double [EB][N][9]
-  static constexpr size_t O_XF = al16(O_ZF + sizeof(double) * EB * N * kZf); // double [EB][NAB][3]
-  static constexpr size_t O_ST = al16(O_XF + sizeof(double) * EB * NAB * kXf);
+  static constexpr size_t O_TAB = 0;                                          // T [NTAB]
+  static constexpr size_t O_WQ = al16(O_TAB + sizeof(T) * NTAB);              // double [NQ] weights
+  static constexpr size_t O_TI = al16(O_WQ + sizeof(double) * NQ);            // int [NT]: i of DOF t
+  static constexpr size_t O_X = al16(O_TI + sizeof(int) * NT);                // T [2][EB][NS]
+  static constexpr size_t O_W = al16(O_X + sizeof(T) * 2 * EB * NS);          // T [EB][2][N][NT]
+  static constexpr size_t O_V = al16(O_W + sizeof(T) * EB * 2 * NS);          // T [EB][4][NQ]
+  static constexpr size_t O_GC = al16(O_V + sizeof(T) * EB * 4 * NQ);         // double [2][EB][NGC]
+  static constexpr size_t O_ZF = al16(O_GC + sizeof(double) * 2 * EB * NGC);  // double [EB][N][9]
+  static constexpr size_t O_XF = al16(O_ZF + sizeof(double) * EB * N * kZf);  // double [EB][NAB][3]
+  static constexpr size_t O_ZR = al16(O_XF + sizeof(double) * EB * NAB * kXf);// float [EB][N][3] (FP32 path)
+  static constexpr size_t O_CF = al16(O_ZR + sizeof(float) * EB * N * 3);     // float [EB][10] (FP32 path)
+  static constexpr size_t O_ST = al16(O_CF + sizeof(float) * EB * 10);
   static constexpr size_t SMEM = al16(O_ST + sizeof(int) * EB);
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -109,19 +121,44 @@ __device__ __forceinline__ void prefetch_group(const ApplyArgs &a, int64_t g, T 
   }
 }
 
+// Point stage in the FP32 path: adj J rows 0, 1 and det J in FP64 from the
+// tensor-product factors (then rounded), the rest in FP32.
+__device__ __forceinline__ void apply_point_f32(const double *zf, const float *zr, const double *xf, float w,
+                                                const float *cf, float u0, float u1, float u2, float u3,
+                                                float (&v)[4], double &det) {
+  float a[3][3];
+  det = adj_tp_f32(zf, zr, xf, a);
+  const float d = (float)det;
+  const float t0 = a[0][0] * u1 + a[1][0] * u2 + a[2][0] * u3;
+  const float t1 = a[0][1] * u1 + a[1][1] * u2 + a[2][1] * u3;
+  const float t2 = a[0][2] * u1 + a[1][2] * u2 + a[2][2] * u3;
+  const float s0 = cf[0] * t0 + cf[3] * t1 + cf[4] * t2;
+  const float s1 = cf[3] * t0 + cf[1] * t1 + cf[5] * t2;
+  const float s2 = cf[4] * t0 + cf[5] * t1 + cf[2] * t2;
+  const float sc = w / d;
+  v[1] = sc * (a[0][0] * s0 + a[0][1] * s1 + a[0][2] * s2);
+  v[2] = sc * (a[1][0] * s0 + a[1][1] * s1 + a[1][2] * s2);
+  v[3] = sc * (a[2][0] * s0 + a[2][1] * s1 + a[2][2] * s2);
+  v[0] = w * (d * cf[9] * u0 + cf[6] * t0 + cf[7] * t1 + cf[8] * t2);
+}
+
 template <int P, class T>
 __global__ void __launch_bounds__(256) apply_prism_kernel(const ApplyArgs a) {
   using C = ApCfg<P, T>;
-  constexpr int N = C::N, NT = C::NT, NS = C::NS, NAB = C::NAB, NABP = C::NABP, NQ = C::NQ, EB = C::EB;
+  constexpr int N = C::N, NT = C::NT, NS = C::NS, NAB = C::NAB, NQ = C::NQ, NP = C::NP, EB = C::EB;
+  constexpr bool F32 = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char smem[];
   T *sTab = reinterpret_cast<T *>(smem + C::O_TAB);
   double *sWq = reinterpret_cast<double *>(smem + C::O_WQ);
+  int *sTi = reinterpret_cast<int *>(smem + C::O_TI);
   T *sX = reinterpret_cast<T *>(smem + C::O_X);
   T *sW = reinterpret_cast<T *>(smem + C::O_W);
   T *sV = reinterpret_cast<T *>(smem + C::O_V);
   double *sGC = reinterpret_cast<double *>(smem + C::O_GC);
   double *sZF = reinterpret_cast<double *>(smem + C::O_ZF);
   double *sXF = reinterpret_cast<double *>(smem + C::O_XF);
+  float *sZR = reinterpret_cast<float *>(smem + C::O_ZR);
+  float *sCF = reinterpret_cast<float *>(smem + C::O_CF);
   int *sSt = reinterpret_cast<int *>(smem + C::O_ST);
   const int tid = threadIdx.x;
   const int64_t ngroups = (a.n + EB - 1) / EB;
@@ -131,8 +168,13 @@ __global__ void __launch_bounds__(256) apply_prism_kernel(const ApplyArgs a) {
   const T *tab = static_cast<const T *>(a.tab);
   for (int i = tid; i < C::NTAB; i += C::NTH) sTab[i] = tab[i];
   for (int q = tid; q < NQ; q += C::NTH) sWq[q] = a.qp[4 * q + 3];
+  if (tid == 0)
+    for (int m = 0, t = 0; m < N; m++)
+      for (int i = m; i >= 0; i--, t++) sTi[t] = i;
   prefetch_group<C>(a, g, sX, sGC);
   cp_commit();
+  const T *sPa = sTab + C::OPA, *sPx = sTab + C::OPX, *sPe = sTab + C::OPE;
+  const T *sBq = sTab + C::OBQ, *sBx = sTab + C::OBX, *sBy = sTab + C::OBY;
   const T *sL = sTab + C::OL, *sD = sTab + C::OD;
 
   for (int it = 0; g < ngroups; g += gridDim.x, it++) {
@@ -147,18 +189,26 @@ __global__ void __launch_bounds__(256) apply_prism_kernel(const ApplyArgs a) {
     const T *X = sX + cur * EB * NS;
     const double *GC = sGC + cur * EB * C::NGC;
 
-    // A. status, geometry factors, zeta contraction
+    // A. status, geometry factors, zeta contraction W = L x, Wd = L' x
     for (int e = tid; e < ne; e += C::NTH) {
       int st = 0;
       for (int k = 0; k < C::NGC; k++)
         if (!isfinite(GC[e * C::NGC + k])) st = FEM_ST_NONFINITE;
       sSt[e] = st;
+      if (F32)
+        for (int k = 0; k < 10; k++) sCF[e * 10 + k] = (float)GC[e * C::NGC + 18 + k];
     }
     for (int i = tid; i < ne * N; i += C::NTH) {
       const int e = i / N, iz = i - e * N;
       double ed[kEdgeRec];
       edge_record<FEM_PRISM6>(GC + e * C::NGC, ed);
-      prism_zf(ed, a.qp[4 * (iz * NAB) + 2], sZF + i * kZf);
+      double *zf = sZF + i * kZf;
+      prism_zf(ed, a.qp[4 * (iz * NAB) + 2], zf);
+      if (F32) {
+        sZR[i * 3 + 0] = (float)zf[6];
+        sZR[i * 3 + 1] = (float)zf[7];
+        sZR[i * 3 + 2] = (float)zf[8];
+      }
     }
     for (int i = tid; i < ne * NAB; i += C::NTH) {
       const int e = i / NAB, iab = i - e * NAB;
@@ -181,46 +231,114 @@ __global__ void __launch_bounds__(256) apply_prism_kernel(const ApplyArgs a) {
     }
     __syncthreads();
 
-    // B. triangle contraction and point stage, one thread per (element, point)
-    for (int i = tid; i < ne * NQ; i += C::NTH) {
-      const int e = i / NQ, q = i - e * NQ, iz = q / NAB, iab = q - iz * NAB;
+    // B. per column (element, level iz, point ib): the b-direction factors
+    // G[i] = sum_j B[t(i,j)][ib] W[t(i,j)], then for each of the column's N
+    // points (ia, ib) the a-direction sums and the point stage
+    for (int i = tid; i < ne * NAB; i += C::NTH) {
+      const int e = i / NAB, r = i - e * NAB, iz = r / N, ib = r - iz * N;
       const T *w = sW + e * 2 * NS + iz * NT, *wd = w + NS;
-      const T *f0 = sTab + iab, *f1 = f0 + NT * NABP, *f2 = f1 + NT * NABP;
-      T u0 = 0, u1 = 0, u2 = 0, u3 = 0;
-#pragma unroll 4
-      for (int t = 0; t < NT; t++) {
-        const T a0 = w[t], a1 = wd[t], p0 = f0[t * NABP];
-        u0 = fma(p0, a0, u0);
-        u1 = fma(f1[t * NABP], a0, u1);
-        u2 = fma(f2[t * NABP], a0, u2);
-        u3 = fma(p0, a1, u3);
+      T g0[N], gx[N], gy[N], gd[N];
+#pragma unroll
+      for (int ii = 0; ii < N; ii++) {
+        T s0 = 0, sx = 0, sy = 0, sd = 0;
+#pragma unroll 2
+        for (int j = 0; j < N - ii; j++) {
+          const int t = (ii + j) * (ii + j + 1) / 2 + j;  // DOF (ii, j)
+          const T wv = w[t], bq = sBq[t * NP + ib];
+          s0 = fma(bq, wv, s0);
+          sd = fma(bq, wd[t], sd);
+          sy = fma(sBy[t * NP + ib], wv, sy);
+          if (ii > 0) sx = fma(sBx[t * NP + ib], wv, sx);
+        }
+        g0[ii] = s0;
+        gx[ii] = sx;
+        gy[ii] = sy;
+        gd[ii] = sd;
       }
-      double adj[3][3];
-      const double det = jac_adj_tp(sZF + (e * N + iz) * kZf, sXF + (e * NAB + iab) * kXf, adj);
-      if (!(det > 0.0)) atomicOr(&sSt[e], FEM_ST_DET);
-      double v[4];
-      apply_point(adj, det, sWq[q], GC + e * C::NGC + 18, (double)u0, (double)u1, (double)u2, (double)u3, v);
-      T *vo = sV + e * 4 * NQ + q;
-      vo[0] = (T)v[0];
-      vo[NQ] = (T)v[1];
-      vo[2 * NQ] = (T)v[2];
-      vo[3 * NQ] = (T)v[3];
+      const int e_ = e;
+      const double *zf = sZF + (e_ * N + iz) * kZf;
+#pragma unroll 1
+      for (int ia = 0; ia < N; ia++) {
+        T u0 = 0, u1 = 0, u2 = 0, u3 = 0;
+#pragma unroll
+        for (int ii = 0; ii < N; ii++) {
+          const T pa = sPa[ia * N + ii];
+          u0 = fma(pa, g0[ii], u0);
+          u2 = fma(pa, gy[ii], u2);
+          u3 = fma(pa, gd[ii], u3);
+          if (ii > 0) {
+            u1 = fma(sPx[ia * N + ii], gx[ii], u1);
+            u2 = fma(sPe[ia * N + ii], gx[ii], u2);
+          }
+        }
+        const int iab = ia * N + ib, q = iz * NAB + iab;
+        const double *xf = sXF + (e_ * NAB + iab) * kXf;
+        T *vo = sV + e_ * 4 * NQ + q;
+        double det;
+        if constexpr (F32) {
+          float v[4];
+          apply_point_f32(zf, sZR + (e_ * N + iz) * 3, xf, (float)sWq[q], sCF + e_ * 10, u0, u1, u2, u3, v, det);
+          vo[0] = v[0];
+          vo[NQ] = v[1];
+          vo[2 * NQ] = v[2];
+          vo[3 * NQ] = v[3];
+        } else {
+          double adj[3][3];
+          det = jac_adj_tp(zf, xf, adj);
+          double v[4];
+          apply_point(adj, det, sWq[q], GC + e_ * C::NGC + 18, u0, u1, u2, u3, v);
+          vo[0] = v[0];
+          vo[NQ] = v[1];
+          vo[2 * NQ] = v[2];
+          vo[3 * NQ] = v[3];
+        }
+        if (!(det > 0.0)) atomicOr(&sSt[e_], FEM_ST_DET);
+      }
     }
     __syncthreads();
 
-    // C. transposed triangle contraction -> R, Rd (in place of W, Wd)
+    // C1. per column (element, level, ib): the transposed a-direction sums
+    // H[i] over the column's points, written over the column's v values
+    for (int i = tid; i < ne * NAB; i += C::NTH) {
+      const int e = i / NAB, r = i - e * NAB, iz = r / N, ib = r - iz * N;
+      T *col = sV + e * 4 * NQ + iz * NAB + ib;  // [c][ia] at col[c NQ + ia N]
+      T h0[N], hx[N], hy[N], hd[N];
+#pragma unroll
+      for (int c = 0; c < N; c++) h0[c] = hx[c] = hy[c] = hd[c] = 0;
+#pragma unroll 1
+      for (int ia = 0; ia < N; ia++) {
+        const T v0 = col[ia * N], v1 = col[NQ + ia * N], v2 = col[2 * NQ + ia * N], v3 = col[3 * NQ + ia * N];
+#pragma unroll
+        for (int ii = 0; ii < N; ii++) {
+          const T pa = sPa[ia * N + ii];
+          h0[ii] = fma(pa, v0, h0[ii]);
+          hy[ii] = fma(pa, v2, hy[ii]);
+          hd[ii] = fma(pa, v3, hd[ii]);
+          if (ii > 0) hx[ii] = fma(sPx[ia * N + ii], v1, fma(sPe[ia * N + ii], v2, hx[ii]));
+        }
+      }
+#pragma unroll
+      for (int ii = 0; ii < N; ii++) {
+        col[ii * N] = h0[ii];
+        col[NQ + ii * N] = hx[ii];
+        col[2 * NQ + ii * N] = hy[ii];
+        col[3 * NQ + ii * N] = hd[ii];
+      }
+    }
+    __syncthreads();
+
+    // C2. transposed b-direction sums -> R, Rd (in place of W, Wd)
     for (int i = tid; i < ne * NS; i += C::NTH) {
       const int e = i / NS, r = i - e * NS, iz = r / NT, t = r - iz * NT;
-      const T *v = sV + e * 4 * NQ + iz * NAB;
-      const T *f0 = sTab + t * NABP, *f1 = f0 + NT * NABP, *f2 = f1 + NT * NABP;
+      const T *h = sV + e * 4 * NQ + iz * NAB + sTi[t] * N;  // [c][ib] at h[c NQ + ib]
+      const T *bq = sBq + t * NP, *bx = sBx + t * NP, *by = sBy + t * NP;
       T ra = 0, rb = 0, rd = 0;
-#pragma unroll 4
-      for (int iab = 0; iab < NAB; iab++) {
-        const T p0 = f0[iab];
-        ra = fma(p0, v[iab], ra);
-        rb = fma(f1[iab], v[NQ + iab], rb);
-        ra = fma(f2[iab], v[2 * NQ + iab], ra);
-        rd = fma(p0, v[3 * NQ + iab], rd);
+#pragma unroll
+      for (int ib = 0; ib < N; ib++) {
+        ra = fma(bq[ib], h[ib], ra);
+        rb = fma(bx[ib], h[NQ + ib], rb);
+        ra = fma(by[ib], h[2 * NQ + ib], ra);
+        rd = fma(bq[ib], h[3 * NQ + ib], rd);
       }
       sW[e * 2 * NS + r] = ra + rb;
       sW[e * 2 * NS + NS + r] = rd;

@@ -33,11 +33,11 @@ struct HostRule {
 // Builds the quadrature rule and shape-function table; false if (elem,p) invalid.
 bool build_host_rule(int elem, int p, HostRule *out);
 
-// Factor tables of a prism rule for sum factorisation, FP64:
-// [3][NT][NAB | 1] triangle factors (value, d/dxi, d/deta; rows padded to an
-// odd length), then [N][N] Legendre values and [N][N] derivatives (row = zeta
-// level, column = degree); N = p + 1, NT = N (N + 1) / 2, NAB = N^2.
-void build_sf_tables(const HostRule &r, int p, std::vector<double> &out);
+// 1D factor tables of the prism rule and basis for sum factorisation, FP64:
+// Pa, Px, Pe [N][N] (point ia, index i), Bq, Bx, By [NT][N | 1] (triangle DOF
+// t, point ib; rows padded to an odd length), L, dL [N][N] (zeta level iz,
+// degree k); N = p + 1, NT = N (N + 1) / 2.  Definitions in fem_tables.cpp.
+void build_sf_tables(int p, std::vector<double> &out);
 
 // Device copies of one degree's tables.
 struct DevTable {

@@ -222,24 +222,57 @@ bool build_host_rule(int elem, int p, HostRule *out) {
   return true;
 }
 
-// The prism basis is a triangle function times a Legendre polynomial in zeta
-// (DOF t + NT k) and the rule a collapsed triangle rule times a Gauss rule in
-// zeta (point iz NAB + iab), so the table factors.  The k = 0 DOFs at the
-// points of the first zeta level give the triangle factors (L_0 = 1), the
-// t = 0 DOFs at the first triangle point of each level the zeta factors (the
-// t = 0 triangle function is 1): both are read off the full table exactly.
-void build_sf_tables(const HostRule &r, int p, std::vector<double> &out) {
-  const int n = p + 1, nt = n * (n + 1) / 2, nab = n * n, nabp = nab | 1, ns = r.ns;
-  out.assign((size_t)3 * nt * nabp + 2 * n * n, 0.0);
-  for (int c = 0; c < 3; c++)
-    for (int t = 0; t < nt; t++)
-      for (int iab = 0; iab < nab; iab++)
-        out[((size_t)c * nt + t) * nabp + iab] = r.phi[((size_t)4 * iab + c) * ns + t];
-  const size_t lo = (size_t)3 * nt * nabp;
+// Factors of the prism tables for sum factorisation.  The basis function
+// t = (i, j) x k is psi_ij(a, b) L_k(zeta) with psi_ij = P_i(a) h^i Q_j(b),
+// h = (1 - b)/2, Q_j = P_j^(2i+1,0), and the rule's point (iz, ia, ib) sits at
+// a = xa[ia], b = xb[ib], zeta = xa[iz], so every entry of the full table is a
+// product of 1D factors (the chain rule of the collapsed coordinates as in
+// prism_basis_point):
+//   value     Pa[ia][i]  Bq[t][ib] L[iz][k],   Pa = P_i(a),   Bq = h^i Q_j(b)
+//   d/dxi     Px[ia][i]  Bx[t][ib] L[iz][k],   Px = 2 P_i'(a), Bx = h^(i-1) Q_j(b)
+//   d/deta   (Pe[ia][i]  Bx[t][ib] + Pa[ia][i] By[t][ib]) L[iz][k],
+//            Pe = (1 + a) P_i'(a) - i P_i(a),  By = 2 h^i Q_j'(b)
+//   d/dzeta   Pa[ia][i]  Bq[t][ib] dL[iz][k]
+// (Bx = 0 for i = 0, where Px and Pe vanish).
+void build_sf_tables(int p, std::vector<double> &out) {
+  const int n = p + 1, nt = n * (n + 1) / 2, np_ = n | 1;
+  double xa[16], wa[16], xb[16], wb[16];
+  gauss_jacobi_gw(n, 0.0, 0.0, xa, wa);
+  gauss_jacobi_gw(n, 1.0, 0.0, xb, wb);
+  out.assign((size_t)5 * n * n + (size_t)3 * nt * np_, 0.0);
+  double *Pa = out.data(), *Px = Pa + n * n, *Pe = Px + n * n;
+  double *Bq = Pe + n * n, *Bx = Bq + nt * np_, *By = Bx + nt * np_;
+  double *L = By + nt * np_, *dL = L + n * n;
+  for (int ia = 0; ia < n; ia++)
+    for (int i = 0; i < n; i++) {
+      double P, dP;
+      jacobi_rec(i, 0.0, 0.0, xa[ia], &P, &dP);
+      Pa[ia * n + i] = P;
+      Px[ia * n + i] = 2.0 * dP;
+      Pe[ia * n + i] = (1.0 + xa[ia]) * dP - i * P;
+    }
+  int t = 0;
+  for (int m = 0; m <= p; m++)
+    for (int i = m; i >= 0; i--, t++) {
+      const int j = m - i;
+      for (int ib = 0; ib < n; ib++) {
+        const double b = xb[ib], h = 0.5 * (1.0 - b);
+        double Q, dQ;
+        jacobi_rec(j, 2.0 * i + 1.0, 0.0, b, &Q, &dQ);
+        double hi1 = 1.0;  // h^(i-1) for i >= 1
+        for (int k = 1; k < i; k++) hi1 *= h;
+        const double hi = i >= 1 ? hi1 * h : 1.0;
+        Bq[t * np_ + ib] = hi * Q;
+        Bx[t * np_ + ib] = i >= 1 ? hi1 * Q : 0.0;
+        By[t * np_ + ib] = 2.0 * hi * dQ;
+      }
+    }
   for (int iz = 0; iz < n; iz++)
     for (int k = 0; k < n; k++) {
-      out[lo + iz * n + k] = r.phi[((size_t)4 * iz * nab + 0) * ns + nt * k];
-      out[lo + n * n + iz * n + k] = r.phi[((size_t)4 * iz * nab + 3) * ns + nt * k];
+      double P, dP;
+      jacobi_rec(k, 0.0, 0.0, xa[iz], &P, &dP);
+      L[iz * n + k] = P;
+      dL[iz * n + k] = dP;
     }
 }
 
