@@ -425,6 +425,24 @@ def wl_elastic(lib, tables, stream, dev, reps, scale_down=1, degrees=range(1, 8)
             "per_degree": out}
 
 
+# FP64 pipe rate of GB300: 2 FP64 operations per clock per SM (a multiply-add
+# is one), 152 SMs at 2.07 GHz; the 1.26 TFLOP/s FP64 peak counts each
+# multiply-add as 2 flops
+FP64_PIPE_GOPS = 2 * 152 * 2.07
+
+
+def apply_fp64_ops(p):
+    """FP64 operations per element of the FP64 apply kernel (multiply-add = 1),
+    counted from its loops: zeta contractions and the transposed b-direction
+    sums (4 N NS each), the b-direction sums per column (N^2 (4 NT - N)), the
+    a-direction sums both ways (2 NQ (5 N - 2)), 57 per point for adj J, det J
+    and v = G_Q u, and the element's geometry factors (33 N + 18 N^2 + 29)."""
+    N = p + 1
+    NT, NQ = N * (N + 1) // 2, N ** 3
+    NS = NT * N
+    return 8 * N * NS + N * N * (4 * NT - N) + 2 * NQ * (5 * N - 2) + 57 * NQ + 33 * N + 18 * N * N + 29
+
+
 def wl_apply(lib, tables, stream, dev, reps, hbm, scale_down=1, degrees=range(1, 8)):
     """Matrix-free operator apply y_e = A_e x_e (fem_apply), prisms p = 1..7,
     about 1 GB of algorithmic FP64 traffic per degree (x and y, coordinates,
@@ -451,8 +469,12 @@ def wl_apply(lib, tables, stream, dev, reps, hbm, scale_down=1, degrees=range(1,
             nbytes = (2 * osz * n + 8 * 29 + 4) * E
             gbs = nbytes / ms / 1e6
             row[name] = {"ms": round(ms, 4), "elem_per_s": E / ms * 1e3, "gbs": round(gbs, 1),
-                         "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
-                                      "frac": round(gbs / hbm, 4)}}
+                         "hbm_frac": round(gbs / hbm, 4)}
+            if prec == lib.FEM_F64:
+                gops = apply_fp64_ops(p) * E / ms / 1e6
+                row[name]["fp64_ops_per_elem"] = apply_fp64_ops(p)
+                row[name]["roofline"] = {"bound": "alu", "achieved": round(gops, 1), "peak": FP64_PIPE_GOPS,
+                                         "unit": "G FP64 ops/s", "frac": round(gops / FP64_PIPE_GOPS, 4)}
             if y64 is None:
                 y64 = y[:S].clone()
                 A = torch.empty((S, n * n), dtype=torch.float64, device=dev)

@@ -42,8 +42,9 @@
 //   C1. per column: transposed a-direction contraction, in place over v;
 //   C2. transposed b-direction contraction;
 //   D.  transposed zeta contraction, y written to global memory.
-// The FP64 path does everything in FP64; the FP32 path keeps adj J rows 0, 1
-// and det J in FP64 (rounded afterwards) and runs the rest in FP32.
+// The FP64 path does everything in FP64.  The FP32 path computes the
+// element's geometry factors and det J at every point in FP64 and the rest
+// (adj J from the rounded factors, point stage, contractions) in FP32.
 //
 // P1 tetrahedra (NS = NQ = 4, J constant) use one thread per element.
 #include "fem_geometry.cuh"
@@ -99,8 +100,11 @@ struct ApCfg {
   static constexpr size_t O_GC = al16(O_V + sizeof(T) * EB * 4 * NQ);         // double [2][EB][NGC]
   static constexpr size_t O_ZF = al16(O_GC + sizeof(double) * 2 * EB * NGC);  // double [EB][N][9]
   static constexpr size_t O_XF = al16(O_ZF + sizeof(double) * EB * N * kZf);  // double [EB][NAB][3]
-  static constexpr size_t O_ZR = al16(O_XF + sizeof(double) * EB * NAB * kXf);// float [EB][N][3] (FP32 path)
-  static constexpr size_t O_CF = al16(O_ZR + sizeof(float) * EB * N * 3);     // float [EB][10] (FP32 path)
+  // FP32 path: float copies of the geometry factors, coefficients, weights
+  static constexpr size_t O_ZR = al16(O_XF + sizeof(double) * EB * NAB * kXf);// float [EB][N][9]
+  static constexpr size_t O_XR = al16(O_ZR + sizeof(float) * EB * N * kZf);   // float [EB][NAB][3]
+  static constexpr size_t O_WF = al16(O_XR + sizeof(float) * EB * NAB * kXf); // float [NQ]
+  static constexpr size_t O_CF = al16(O_WF + sizeof(float) * NQ);             // float [EB][10]
   static constexpr size_t O_ST = al16(O_CF + sizeof(float) * EB * 10);
   static constexpr size_t SMEM = al16(O_ST + sizeof(int) * EB);
   static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -121,14 +125,17 @@ __device__ __forceinline__ void prefetch_group(const ApplyArgs &a, int64_t g, T 
   }
 }
 
-// Point stage in the FP32 path: adj J rows 0, 1 and det J in FP64 from the
-// tensor-product factors (then rounded), the rest in FP32.
-__device__ __forceinline__ void apply_point_f32(const double *zf, const float *zr, const double *xf, float w,
-                                                const float *cf, float u0, float u1, float u2, float u3,
-                                                float (&v)[4], double &det) {
-  float a[3][3];
-  det = adj_tp_f32(zf, zr, xf, a);
-  const float d = (float)det;
+// Point stage in the FP32 path: adj J from FP32 copies of the element's
+// tensor-product factors (zr: J[:,0], J[:,1] and adj row 2 of the point's
+// zeta level; xr: J[:,2] of its triangle point), det J computed in FP64 by the
+// caller (its sign sets the status flag), the rest in FP32.
+__device__ __forceinline__ void apply_point_f32(const float *zr, const float *xr, float d, float w, const float *cf,
+                                                float u0, float u1, float u2, float u3, float (&v)[4]) {
+  const float c0x = zr[0], c0y = zr[1], c0z = zr[2], c1x = zr[3], c1y = zr[4], c1z = zr[5];
+  const float c2x = xr[0], c2y = xr[1], c2z = xr[2];
+  const float a[3][3] = {{c1y * c2z - c1z * c2y, c1z * c2x - c1x * c2z, c1x * c2y - c1y * c2x},
+                         {c2y * c0z - c2z * c0y, c2z * c0x - c2x * c0z, c2x * c0y - c2y * c0x},
+                         {zr[6], zr[7], zr[8]}};
   const float t0 = a[0][0] * u1 + a[1][0] * u2 + a[2][0] * u3;
   const float t1 = a[0][1] * u1 + a[1][1] * u2 + a[2][1] * u3;
   const float t2 = a[0][2] * u1 + a[1][2] * u2 + a[2][2] * u3;
@@ -158,6 +165,8 @@ __global__ void __launch_bounds__(256) apply_prism_kernel(const ApplyArgs a) {
   double *sZF = reinterpret_cast<double *>(smem + C::O_ZF);
   double *sXF = reinterpret_cast<double *>(smem + C::O_XF);
   float *sZR = reinterpret_cast<float *>(smem + C::O_ZR);
+  float *sXR = reinterpret_cast<float *>(smem + C::O_XR);
+  float *sWf = reinterpret_cast<float *>(smem + C::O_WF);
   float *sCF = reinterpret_cast<float *>(smem + C::O_CF);
   int *sSt = reinterpret_cast<int *>(smem + C::O_ST);
   const int tid = threadIdx.x;
@@ -167,7 +176,10 @@ __global__ void __launch_bounds__(256) apply_prism_kernel(const ApplyArgs a) {
 
   const T *tab = static_cast<const T *>(a.tab);
   for (int i = tid; i < C::NTAB; i += C::NTH) sTab[i] = tab[i];
-  for (int q = tid; q < NQ; q += C::NTH) sWq[q] = a.qp[4 * q + 3];
+  for (int q = tid; q < NQ; q += C::NTH) {
+    sWq[q] = a.qp[4 * q + 3];
+    if (F32) sWf[q] = (float)a.qp[4 * q + 3];
+  }
   if (tid == 0)
     for (int m = 0, t = 0; m < N; m++)
       for (int i = m; i >= 0; i--, t++) sTi[t] = i;
@@ -204,17 +216,17 @@ __global__ void __launch_bounds__(256) apply_prism_kernel(const ApplyArgs a) {
       edge_record<FEM_PRISM6>(GC + e * C::NGC, ed);
       double *zf = sZF + i * kZf;
       prism_zf(ed, a.qp[4 * (iz * NAB) + 2], zf);
-      if (F32) {
-        sZR[i * 3 + 0] = (float)zf[6];
-        sZR[i * 3 + 1] = (float)zf[7];
-        sZR[i * 3 + 2] = (float)zf[8];
-      }
+      if (F32)
+        for (int k = 0; k < kZf; k++) sZR[i * kZf + k] = (float)zf[k];
     }
     for (int i = tid; i < ne * NAB; i += C::NTH) {
       const int e = i / NAB, iab = i - e * NAB;
       double ed[kEdgeRec];
       edge_record<FEM_PRISM6>(GC + e * C::NGC, ed);
-      prism_xf(ed, a.qp[4 * iab], a.qp[4 * iab + 1], sXF + i * kXf);
+      double *xf = sXF + i * kXf;
+      prism_xf(ed, a.qp[4 * iab], a.qp[4 * iab + 1], xf);
+      if (F32)
+        for (int k = 0; k < kXf; k++) sXR[i * kXf + k] = (float)xf[k];
     }
     for (int i = tid; i < ne * NS; i += C::NTH) {
       const int e = i / NS, r = i - e * NS, iz = r / NT, t = r - iz * NT;
@@ -277,7 +289,9 @@ __global__ void __launch_bounds__(256) apply_prism_kernel(const ApplyArgs a) {
         double det;
         if constexpr (F32) {
           float v[4];
-          apply_point_f32(zf, sZR + (e_ * N + iz) * 3, xf, (float)sWq[q], sCF + e_ * 10, u0, u1, u2, u3, v, det);
+          det = xf[0] * zf[6] + xf[1] * zf[7] + xf[2] * zf[8];
+          apply_point_f32(sZR + (e_ * N + iz) * kZf, sXR + (e_ * NAB + iab) * kXf, (float)det, sWf[q],
+                          sCF + e_ * 10, u0, u1, u2, u3, v);
           vo[0] = v[0];
           vo[NQ] = v[1];
           vo[2 * NQ] = v[2];
