@@ -92,8 +92,8 @@ struct ApCfg {
                        OBY = OBX + NT * NP, OL = OBY + NT * NP, OD = OL + N * N, NTAB = OD + N * N;
   // shared memory (bytes)
   static constexpr size_t O_TAB = 0;                                          // T [NTAB]
-  static constexpr size_t O_WQ = al16(O_TAB + sizeof(T) * NTAB);              // double [NQ] weights
-  static constexpr size_t O_TI = al16(O_WQ + sizeof(double) * NQ);            // int [NT]: i of DOF t
+  static constexpr size_t O_WQ = al16(O_TAB + sizeof(T) * NTAB);              // double [NQ] weights (FP64 path)
+  static constexpr size_t O_TI = al16(O_WQ + (sizeof(T) == 8 ? sizeof(double) * NQ : 0));  // int [NT]: i of DOF t
   static constexpr size_t O_X = al16(O_TI + sizeof(int) * NT);                // T [2][EB][NS]
   static constexpr size_t O_W = al16(O_X + sizeof(T) * 2 * EB * NS);          // T [EB][2][N][NT]
   static constexpr size_t O_V = al16(O_W + sizeof(T) * EB * 2 * NS);          // T [EB][4][NQ]
@@ -177,8 +177,10 @@ __global__ void __launch_bounds__(256) apply_prism_kernel(const ApplyArgs a) {
   const T *tab = static_cast<const T *>(a.tab);
   for (int i = tid; i < C::NTAB; i += C::NTH) sTab[i] = tab[i];
   for (int q = tid; q < NQ; q += C::NTH) {
-    sWq[q] = a.qp[4 * q + 3];
-    if (F32) sWf[q] = (float)a.qp[4 * q + 3];
+    if (F32)
+      sWf[q] = (float)a.qp[4 * q + 3];
+    else
+      sWq[q] = a.qp[4 * q + 3];
   }
   if (tid == 0)
     for (int m = 0, t = 0; m < N; m++)
