@@ -28,8 +28,9 @@
 // reverse order give y.  Per element that is 4 N NS + 2 N (4 N NT + 5 N^3)
 // multiply-adds plus about 60 FP64 operations per point: at p = 7 about 100k
 // FP64 operations against 170M multiply-adds to form A_e.  The kernel moves
-// 2 NS values, 18 coordinates and 11 coefficients per element, so even then it
-// is bound by GB300's FP64 pipe, not by HBM, at every degree.
+// 2 NS values, 18 coordinates and 11 coefficients per element, so even then
+// the FP64 path is bound by GB300's FP64 pipe, not by HBM, at every degree;
+// the FP32 path is bound by latency (barriers and shared-memory loads).
 //
 // Work decomposition: a CTA owns groups of EB elements (grid-stride over the
 // groups), keeps the factor tables in shared memory for the whole launch, and
