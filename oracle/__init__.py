@@ -3,15 +3,18 @@
 Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product path (the CUDA library and
 its binding) never calls it.  The arithmetic lives in ``fem_oracle.c``, plain
-C with OpenMP over elements, which follows Algorithms 1/2 of the paper; this
-module compiles it with gcc on first use and wraps it with ctypes.
+C with OpenMP over elements, which writes out the quadrature sum of the weak
+form (Section 2, eq. sum_int); this module compiles it with gcc on first use
+and wraps it with ctypes.
 
 Parity status of each function (what pins it is in tests/test_oracle_*.py):
   rule, basis, integrate (constant coefficients), law_k, mlp_loss_grad,
   apply (the element operator applied to a coefficient vector): pinned;
-  integrate with law=2 (MLP coefficient): pinned through its parts (the MLP
-  forward is pinned by the finite-difference and closed-form tests, the
-  integration by the law=0 pins).
+  point_law (u, |grad u| and k at the points): pinned by a linear physical
+  field on a sheared affine prism (u, |grad u| and k in closed form);
+  integrate with law=1/2: pinned by the constant-field reduction (law 1) and
+  by a network that sees only |grad u|, constant for a linear field (law 2),
+  both against law=0 with D = k I.
 """
 from __future__ import annotations
 
@@ -70,6 +73,7 @@ def _load():
             lib.orc_mlp_loss_grad.argtypes = [i, P, P, i64, P, P, P, P]
             lib.orc_mlp_loss_grad.restype = d
             lib.orc_integrate_ex.argtypes = [i, i, i64, P, P, i64, i, P, i, P, P, P, P, P, i]
+            lib.orc_point_law.argtypes = [i, i, i64, P, P, i, i, P, P, P, P, P, P]
             lib.orc_integrate_elastic.argtypes = [i, i64, P, P, i64, P, P, P, i]
             lib.orc_jacobian_terms.argtypes = [i, i, i64, P, P, P]
             lib.orc_max_threads.argtypes = []
@@ -190,6 +194,29 @@ def integrate(elem: int, p: int, coords, coeffs, law: int = 0, ucoef=None, mlp=N
     if rc != 0:
         raise RuntimeError("oracle integrate failed")
     return A, b, st
+
+
+def point_law(elem: int, p: int, coords, ucoef, law: int = 1, mlp=None):
+    """The coefficient stage of ``integrate`` with law 1 or 2 at every
+    quadrature point: u [E][NQ], s = |grad u| [E][NQ], k [E][NQ], status [E]."""
+    coords = _f64(coords)
+    uc = _f64(ucoef)
+    E = coords.shape[0]
+    n = nq(elem, p)
+    if n < 0:
+        raise ValueError("unsupported element/degree")
+    H, th, box = (0, None, None) if mlp is None else (mlp[0], _f64(mlp[1]), _f64(mlp[2]))
+    if law == 2 and mlp is None:
+        raise ValueError("law 2 needs mlp")
+    u = np.zeros((E, n))
+    s = np.zeros((E, n))
+    k = np.zeros((E, n))
+    st = np.zeros(E, dtype=np.int32)
+    rc = _load().orc_point_law(elem, p, E, _ptr(coords), _ptr(uc), law, H, _ptr(th), _ptr(box),
+                               _ptr(u), _ptr(s), _ptr(k), _ptr(st))
+    if rc != 0:
+        raise RuntimeError("oracle point_law failed")
+    return u, s, k, st
 
 
 def apply(elem: int, p: int, coords, coeffs, x, nthreads: int = 0):

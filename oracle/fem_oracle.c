@@ -11,20 +11,19 @@
  * map derivatives come from the six vertex shape functions (the library uses
  * edge vectors).
  *
- * What it computes (Section 2, Algorithms 1 and 2):
- *   for each element, for each quadrature point iQ:
- *     phi^Q[iQ][iD][i]   reference shape functions (iD=0) and their
- *                        reference derivatives (iD=1..3),
- *     J, det J, J^{-1}   Jacobian of the reference->real map,
- *     psi^Q[iQ][iD][i]   physical derivatives by the chain rule (eq. sum_int):
- *                        d phi/d x_m = sum_k d phi/d xi_k * (J^{-1})[k][m],
- *     c^Q[iD][jD]        coefficients at the point,
- *     A^e[i][j] += det * w^Q * c^Q[iD][jD] * psi[iD][i] * psi[jD][j]
- *   for the non-zero entries of c (Algorithm 2 skips the zero ones).
+ * What it computes (Section 2, eq. sum_int): the quadrature sum of the weak
+ * form over each element, written out as its definition:
+ *   phi_Q[iD][i]  reference shape functions (iD=0) and their reference
+ *                 derivatives (iD=1..3) at quadrature point Q,
+ *   J_Q, det J_Q, J_Q^{-1}  Jacobian of the reference->real map,
+ *   psi_Q[iD][i]  physical table by the chain rule:
+ *                 d phi/d x_m = sum_k d phi/d xi_k * (J^{-1})[k][m],
+ *   C_Q[iD][jD]   4x4 coefficient matrix of the form at the point,
+ *   A^e = sum_Q w_Q det J_Q psi_Q^T C_Q psi_Q.
  * The generic second-order form is -div(D grad u) + b.grad u + c u = f, i.e.
- *   c[0][0] = c, c[0][1+m] = b_m, c[1+l][1+m] = D[l][m], c[1+l][0] = 0,
+ *   C[0][0] = c, C[0][1+m] = b_m, C[1+l][1+m] = D[l][m], C[1+l][0] = 0,
  * row i = test function, column j = trial function.  The load vector (not in
- * the paper, which integrates only A^e) is b^e[i] = sum_Q det w f psi[0][i].
+ * the paper, which integrates only A^e) is b^e[i] = sum_Q w det f psi[0][i].
  *
  * Readings where the paper is silent (it names a prism with complete
  * triangle polynomials times 1D polynomials and "Gaussian" quadrature,
@@ -399,9 +398,100 @@ double orc_mlp_loss_grad(int H, const double *th, const double *box, int64_t n, 
 }
 
 /* ------------------------------------------------ element integration */
-/* law: 0 constant coefficients; 1 exact nonlinear law with D = k(u, |grad u|^2) I;
- *      2 same with k = MLP(u, |grad u|) (theta, box, H) inside the box
- *        [u0,u1] x [s0,s1] and the exact law outside (status bit 8).
+/* Geometry at one reference point (Section 2, the reference-to-real map):
+ * J[i][k] = d x_i / d xi_k = sum_v x_v[i] dN_v/dxi_k, det J, and Ji = J^{-1}. */
+static double point_geometry(int elem, const double *X, const double *xi, double Ji[3][3]) {
+    int nv = elem == ORC_TET ? 4 : 6;
+    double dN[3][6], J[3][3];
+    map_derivs(elem, xi, dN);
+    for (int i = 0; i < 3; i++)
+        for (int k = 0; k < 3; k++) {
+            double s = 0.0;
+            for (int v = 0; v < nv; v++) s += X[3 * v + i] * dN[k][v];
+            J[i][k] = s;
+        }
+    double det = det3(J);
+    inv3(J, det, Ji);
+    return det;
+}
+
+/* Physical shape-function table at a point (eq. sum_int, chain rule):
+ * psi[0][i] = phi[0][i], psi[1+m][i] = sum_k (J^{-1})[k][m] phi[1+k][i]. */
+static void physical_table(int NS, const double *phi, const double Ji[3][3], double *psi) {
+    for (int i = 0; i < NS; i++) {
+        psi[i] = phi[i];
+        for (int m = 0; m < 3; m++) {
+            double s = 0.0;
+            for (int k = 0; k < 3; k++) s += Ji[k][m] * phi[(1 + k) * NS + i];
+            psi[(1 + m) * NS + i] = s;
+        }
+    }
+}
+
+/* Diffusion coefficient that depends on the previous solution (Section 2: the
+ * coefficients at a point may be computed from the old degrees of freedom).
+ * The field and its physical gradient at the point, from the element's
+ * coefficient vector U and the physical table psi:
+ *   u = sum_i U_i psi[0][i],  grad u = sum_i U_i psi[1..3][i],  s = |grad u|;
+ * law 1: k = law_k(u, s^2) (the exact law in the squared gradient);
+ * law 2: k = MLP(u, s) if (u, s) lies in the network's box, else the exact
+ * law and ORC_ST_FALLBACK.  Returns the status bits. */
+static int32_t point_law(int NS, const double *psi, const double *U, int law, int H,
+                         const double *theta, const double *box, double *u_out, double *s_out,
+                         double *k_out, double *h1, double *h2) {
+    double u = 0.0, gu[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < NS; i++) {
+        u += U[i] * psi[i];
+        for (int m = 0; m < 3; m++) gu[m] += U[i] * psi[(1 + m) * NS + i];
+    }
+    double g = gu[0] * gu[0] + gu[1] * gu[1] + gu[2] * gu[2];
+    double s = sqrt(g), k;
+    int32_t st = 0;
+    if (law == 2 && u >= box[0] && u <= box[1] && s >= box[2] && s <= box[3]) {
+        k = mlp_forward(H, theta, box, u, s, h1, h2);
+    } else {
+        k = orc_law_k(u, g);
+        if (law == 2) st |= ORC_ST_FALLBACK;
+    }
+    *u_out = u;
+    *s_out = s;
+    *k_out = k;
+    return st;
+}
+
+/* Coefficient matrix C[iD][jD] of the generic form at a point (Section 2,
+ * -div(D grad u) + b.grad u + c u = f; iD = 0 value, 1..3 derivatives, row =
+ * test function): C[0][0] = c, C[0][1+m] = b_m, C[1+l][1+m] = D[l][m]
+ * (D = k I when the law gives k), C[1+l][0] = 0. */
+static void coefficient_matrix(const double *cf, int law, double k, double C[4][4]) {
+    memset(C, 0, sizeof(double) * 16);
+    C[0][0] = cf[9];
+    for (int m = 0; m < 3; m++) C[0][1 + m] = cf[6 + m];
+    if (law == 0) {
+        double D[3][3] = {{cf[0], cf[3], cf[4]}, {cf[3], cf[1], cf[5]}, {cf[4], cf[5], cf[2]}};
+        for (int l = 0; l < 3; l++)
+            for (int m = 0; m < 3; m++) C[1 + l][1 + m] = D[l][m];
+    } else {
+        for (int l = 0; l < 3; l++) C[1 + l][1 + l] = k;
+    }
+}
+
+static int32_t nonfinite_inputs(const double *X, int nv, const double *cf, int ncf) {
+    int32_t st = 0;
+    for (int k = 0; k < nv * 3; k++)
+        if (!isfinite(X[k])) st |= ORC_ST_NONFINITE;
+    for (int k = 0; k < ncf; k++)
+        if (!isfinite(cf[k])) st |= ORC_ST_NONFINITE;
+    return st;
+}
+
+/* Element matrix and load vector by the quadrature sum of the weak form
+ * (eq. sum_int):
+ *   A^e[i][j] = sum_Q w_Q det J_Q sum_{iD,jD} psi_Q[iD][i] C_Q[iD][jD] psi_Q[jD][j],
+ *   b^e[i]    = sum_Q w_Q det J_Q f psi_Q[0][i]   (the load vector; the paper
+ *                                                  integrates only A^e).
+ * law: 0 constant coefficients; 1 exact nonlinear law, D = k I; 2 network
+ * inside its box [u0,u1] x [s0,s1], exact law outside (status bit 8).
  * coords [E][nv][3]; coeffs SoA [11][cstride]: Dxx Dyy Dzz Dxy Dxz Dyz bx by bz c f;
  * ucoef [E][NS] (law != 0); A [E][NS][NS]; b [E][NS]; status [E] (nullable). */
 int orc_integrate_ex(int elem, int p, int64_t E, const double *coords, const double *coeffs,
@@ -421,92 +511,48 @@ int orc_integrate_ex(int elem, int p, int64_t E, const double *coords, const dou
 #pragma omp parallel
     {
         double *psi = (double *)malloc(sizeof(double) * 4 * NS);
+        double *Cpsi = (double *)malloc(sizeof(double) * 4 * NS);
         double h1[256], h2[256];
 #pragma omp for schedule(dynamic, 1)
         for (int64_t e = 0; e < E; e++) {
-            /* Algorithm 1, element set-up: coefficients, geometry, old DOFs, init */
             const double *X = coords + (size_t)e * nv * 3;
             double cf[11];
             for (int k = 0; k < 11; k++) cf[k] = coeffs[(size_t)k * cstride + e];
-            int32_t st = 0;
-            for (int k = 0; k < 11; k++)
-                if (!isfinite(cf[k])) st |= ORC_ST_NONFINITE;
-            for (int k = 0; k < nv * 3; k++)
-                if (!isfinite(X[k])) st |= ORC_ST_NONFINITE;
-            const double *U = law ? ucoef + (size_t)e * NS : NULL;
+            int32_t st = nonfinite_inputs(X, nv, cf, 11);
             double *Ae = A + (size_t)e * NS * NS, *be = bvec + (size_t)e * NS;
             memset(Ae, 0, sizeof(double) * NS * NS);
             memset(be, 0, sizeof(double) * NS);
             for (int q = 0; q < NQ; q++) {
-                /* Algorithm 1, per point: shape functions at iQ; Jacobian, det, inverse */
-                const double *phi = phiQ + (size_t)q * 4 * NS;
-                double dN[3][6], J[3][3], Ji[3][3];
-                map_derivs(elem, xq + 3 * q, dN);
-                for (int i = 0; i < 3; i++)
-                    for (int k = 0; k < 3; k++) {
-                        double s = 0.0;
-                        for (int v = 0; v < nv; v++) s += X[3 * v + i] * dN[k][v];
-                        J[i][k] = s;
-                    }
-                double det = det3(J);
+                double Ji[3][3], C[4][4], k = 0.0;
+                double det = point_geometry(elem, X, xq + 3 * q, Ji);
                 if (!(det > 0.0)) st |= ORC_ST_DET;
-                inv3(J, det, Ji);
-                /* physical derivatives psi = J^{-T} grad_ref phi */
-                for (int i = 0; i < NS; i++) {
-                    psi[i] = phi[i];
-                    for (int m = 0; m < 3; m++) {
+                physical_table(NS, phiQ + (size_t)q * 4 * NS, Ji, psi);
+                if (law != 0) {
+                    double u, s;
+                    st |= point_law(NS, psi, ucoef + (size_t)e * NS, law, H, theta, box, &u, &s,
+                                    &k, h1, h2);
+                }
+                coefficient_matrix(cf, law, k, C);
+                double dw = wq[q] * det;
+                /* (C psi)[iD][j] = sum_jD C[iD][jD] psi[jD][j] */
+                for (int iD = 0; iD < 4; iD++)
+                    for (int j = 0; j < NS; j++) {
                         double s = 0.0;
-                        for (int k = 0; k < 3; k++) s += Ji[k][m] * phi[(1 + k) * NS + i];
-                        psi[(1 + m) * NS + i] = s;
+                        for (int jD = 0; jD < 4; jD++) s += C[iD][jD] * psi[jD * NS + j];
+                        Cpsi[iD * NS + j] = s;
                     }
-                }
-                /* coefficients at the point */
-                double c[4][4] = {{0}};
-                c[0][0] = cf[9];
-                c[0][1] = cf[6];
-                c[0][2] = cf[7];
-                c[0][3] = cf[8];
-                if (law == 0) {
-                    c[1][1] = cf[0];
-                    c[2][2] = cf[1];
-                    c[3][3] = cf[2];
-                    c[1][2] = c[2][1] = cf[3];
-                    c[1][3] = c[3][1] = cf[4];
-                    c[2][3] = c[3][2] = cf[5];
-                } else {
-                    double u = 0.0, gu[3] = {0, 0, 0};
-                    for (int i = 0; i < NS; i++) {
-                        u += U[i] * psi[i];
-                        for (int m = 0; m < 3; m++) gu[m] += U[i] * psi[(1 + m) * NS + i];
-                    }
-                    double g = gu[0] * gu[0] + gu[1] * gu[1] + gu[2] * gu[2];
-                    double sg = sqrt(g), k;
-                    int inbox = law == 2 && u >= box[0] && u <= box[1] && sg >= box[2] &&
-                                sg <= box[3];
-                    if (law == 2 && inbox) {
-                        k = mlp_forward(H, theta, box, u, sg, h1, h2);
-                    } else {
-                        k = orc_law_k(u, g);
-                        if (law == 2) st |= ORC_ST_FALLBACK;
-                    }
-                    c[1][1] = c[2][2] = c[3][3] = k;
-                }
-                double dw = det * wq[q];
-                /* Algorithm 1 innermost loops: update A^e for every DOF pair, non-zero c only */
                 for (int i = 0; i < NS; i++)
                     for (int j = 0; j < NS; j++) {
                         double s = 0.0;
-                        for (int iD = 0; iD < 4; iD++)
-                            for (int jD = 0; jD < 4; jD++)
-                                if (c[iD][jD] != 0.0)
-                                    s += dw * c[iD][jD] * psi[iD * NS + i] * psi[jD * NS + j];
-                        Ae[i * NS + j] += s;
+                        for (int iD = 0; iD < 4; iD++) s += psi[iD * NS + i] * Cpsi[iD * NS + j];
+                        Ae[i * NS + j] += dw * s;
                     }
                 for (int i = 0; i < NS; i++) be[i] += dw * cf[10] * psi[i];
             }
             if (status) status[e] = st;
         }
         free(psi);
+        free(Cpsi);
     }
     free(xq);
     free(wq);
@@ -514,14 +560,52 @@ int orc_integrate_ex(int elem, int p, int64_t E, const double *coords, const dou
     return 0;
 }
 
+/* The law's quantities at every quadrature point (the per-point stage of
+ * orc_integrate_ex with law 1 or 2): u [E][NQ], s = |grad u| [E][NQ] and the
+ * coefficient k [E][NQ]; status [E] (nullable) as in orc_integrate_ex. */
+int orc_point_law(int elem, int p, int64_t E, const double *coords, const double *ucoef, int law,
+                  int H, const double *theta, const double *box, double *u_out, double *s_out,
+                  double *k_out, int32_t *status) {
+    int NS = orc_ns(elem, p), NQ = orc_nq(elem, p);
+    if (NS < 0 || NQ < 0 || (law != 1 && law != 2)) return -1;
+    int nv = elem == ORC_TET ? 4 : 6;
+    double *xq = (double *)malloc(sizeof(double) * 3 * NQ);
+    double *wq = (double *)malloc(sizeof(double) * NQ);
+    double *phiQ = (double *)malloc(sizeof(double) * (size_t)NQ * 4 * NS);
+    double *psi = (double *)malloc(sizeof(double) * 4 * NS);
+    double h1[256], h2[256];
+    orc_rule(elem, p, xq, wq);
+    orc_basis(elem, p, NQ, xq, phiQ);
+    for (int64_t e = 0; e < E; e++) {
+        const double *X = coords + (size_t)e * nv * 3;
+        int32_t st = nonfinite_inputs(X, nv, NULL, 0);
+        for (int q = 0; q < NQ; q++) {
+            double Ji[3][3];
+            double det = point_geometry(elem, X, xq + 3 * q, Ji);
+            if (!(det > 0.0)) st |= ORC_ST_DET;
+            physical_table(NS, phiQ + (size_t)q * 4 * NS, Ji, psi);
+            size_t o = (size_t)e * NQ + q;
+            st |= point_law(NS, psi, ucoef + (size_t)e * NS, law, H, theta, box, u_out + o,
+                            s_out + o, k_out + o, h1, h2);
+        }
+        if (status) status[e] = st;
+    }
+    free(psi);
+    free(xq);
+    free(wq);
+    free(phiQ);
+    return 0;
+}
+
 /* ------------------------------------------ linear elastostatics (Section 5.1) */
-/* Isotropic elasticity, N_E = 3 (eq. strong_form, fes, sum_int): block (iE, jE)
- * of A^e, test component iE, trial component jE:
- *   A[iE][jE][s][r] = sum_Q det w sum_{iD,jD>=1} c[iE][jE][iD][jD] psi[iD][s] psi[jD][r],
- *   c[i][k][j][l] = c_ijkl = lam d_ij d_kl + mu (d_ik d_jl + d_il d_jk),
+/* Isotropic elasticity, N_E = 3 (Section 5.1, with eq. sum_int per pair of
+ * components): block (iE, jE) of A^e couples test component iE with trial
+ * component jE,
+ *   A[iE][jE][s][r] = sum_Q w_Q det J_Q sum_{l,m} psi_Q[1+l][s] c_{iE l jE m} psi_Q[1+m][r],
+ *   c_ijkl = lam d_ij d_kl + mu (d_ik d_jl + d_il d_jk),
  * lam = E nu / ((1 + nu)(1 - 2 nu)), mu = E / (2 (1 + nu)), constant per
  * element (the paper's material data: Young modulus and Poisson ratio); body
- * force load b[iE][s] = sum_Q det w f_iE psi[0][s].
+ * force load b[iE][s] = sum_Q w_Q det J_Q f_iE psi_Q[0][s].
  * coeffs SoA [5][cstride]: E, nu, fx, fy, fz.  A [E][3][3][NS][NS], b [E][3][NS]. */
 int orc_integrate_elastic(int p, int64_t E, const double *coords, const double *coeffs,
                           int64_t cstride, double *A, double *bvec, int32_t *status, int nthreads) {
@@ -542,64 +626,43 @@ int orc_integrate_elastic(int p, int64_t E, const double *coords, const double *
 #pragma omp for schedule(dynamic, 1)
         for (int64_t e = 0; e < E; e++) {
             const double *X = coords + (size_t)e * 18;
-            double Ey = coeffs[e], nu = coeffs[cstride + e];
-            double f[3] = {coeffs[2 * cstride + e], coeffs[3 * cstride + e], coeffs[4 * cstride + e]};
+            double cf[5];
+            for (int k = 0; k < 5; k++) cf[k] = coeffs[(size_t)k * cstride + e];
+            double Ey = cf[0], nu = cf[1];
             double lam = Ey * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = Ey / (2.0 * (1.0 + nu));
-            int32_t st = 0;
-            for (int k = 0; k < 18; k++)
-                if (!isfinite(X[k])) st |= ORC_ST_NONFINITE;
-            if (!isfinite(Ey) || !isfinite(nu) || !isfinite(f[0]) || !isfinite(f[1]) || !isfinite(f[2]))
-                st |= ORC_ST_NONFINITE;
-            /* c[iE][jE][iD][jD] for the derivative pairs (iD, jD >= 1) */
-            double c[3][3][4][4];
-            memset(c, 0, sizeof(c));
+            int32_t st = nonfinite_inputs(X, 6, cf, 5);
+            /* c[iE][jE][l][m] = c_{iE l jE m} */
+            double c[3][3][3][3];
             for (int i = 0; i < 3; i++)
                 for (int k = 0; k < 3; k++)
                     for (int j = 0; j < 3; j++)
                         for (int l = 0; l < 3; l++)
-                            c[i][k][1 + j][1 + l] = lam * (i == j) * (k == l) +
-                                                     mu * ((i == k) * (j == l) + (i == l) * (j == k));
+                            c[i][k][j][l] = lam * (i == j) * (k == l) +
+                                            mu * ((i == k) * (j == l) + (i == l) * (j == k));
             double *Ae = A + (size_t)e * 9 * NS * NS, *be = bvec + (size_t)e * 3 * NS;
             memset(Ae, 0, sizeof(double) * 9 * NS * NS);
             memset(be, 0, sizeof(double) * 3 * NS);
             for (int q = 0; q < NQ; q++) {
-                const double *phi = phiQ + (size_t)q * 4 * NS;
-                double dN[3][6], J[3][3], Ji[3][3];
-                map_derivs(elem, xq + 3 * q, dN);
-                for (int i = 0; i < 3; i++)
-                    for (int k = 0; k < 3; k++) {
-                        double sacc = 0.0;
-                        for (int v = 0; v < 6; v++) sacc += X[3 * v + i] * dN[k][v];
-                        J[i][k] = sacc;
-                    }
-                double det = det3(J);
+                double Ji[3][3];
+                double det = point_geometry(elem, X, xq + 3 * q, Ji);
                 if (!(det > 0.0)) st |= ORC_ST_DET;
-                inv3(J, det, Ji);
-                for (int i = 0; i < NS; i++) {
-                    psi[i] = phi[i];
-                    for (int m = 0; m < 3; m++) {
-                        double sacc = 0.0;
-                        for (int k = 0; k < 3; k++) sacc += Ji[k][m] * phi[(1 + k) * NS + i];
-                        psi[(1 + m) * NS + i] = sacc;
-                    }
-                }
-                double dw = det * wq[q];
-                /* Algorithm 1 with the N_E x N_E blocks, non-zero c only */
+                physical_table(NS, phiQ + (size_t)q * 4 * NS, Ji, psi);
+                double dw = wq[q] * det;
                 for (int iE = 0; iE < 3; iE++)
                     for (int jE = 0; jE < 3; jE++) {
                         double *blk = Ae + ((size_t)iE * 3 + jE) * NS * NS;
                         for (int s2 = 0; s2 < NS; s2++)
                             for (int r = 0; r < NS; r++) {
                                 double sacc = 0.0;
-                                for (int iD = 1; iD < 4; iD++)
-                                    for (int jD = 1; jD < 4; jD++)
-                                        if (c[iE][jE][iD][jD] != 0.0)
-                                            sacc += dw * c[iE][jE][iD][jD] * psi[iD * NS + s2] * psi[jD * NS + r];
-                                blk[s2 * NS + r] += sacc;
+                                for (int l = 0; l < 3; l++)
+                                    for (int m = 0; m < 3; m++)
+                                        sacc += psi[(1 + l) * NS + s2] * c[iE][jE][l][m] *
+                                                psi[(1 + m) * NS + r];
+                                blk[s2 * NS + r] += dw * sacc;
                             }
                     }
                 for (int iE = 0; iE < 3; iE++)
-                    for (int s2 = 0; s2 < NS; s2++) be[iE * NS + s2] += dw * f[iE] * psi[s2];
+                    for (int s2 = 0; s2 < NS; s2++) be[iE * NS + s2] += dw * cf[2 + iE] * psi[s2];
             }
             if (status) status[e] = st;
         }

@@ -507,3 +507,85 @@ def test_integrate_mlp_law_inside_and_outside_box(orc):
     A3, _, st3 = orc.integrate(PRISM, p, X, C, law=2, ucoef=U, mlp=(H, th, tiny))
     A1, _, _ = orc.integrate(PRISM, p, X, C, law=1, ucoef=U)
     assert _relF(A3, A1) < 1e-15 and np.all(st3 == 8)
+
+
+# ------------------------------------------- law with a non-zero field gradient
+
+
+def _sheared_affine_prism():
+    """An affine image x = M xi + t of the reference prism with a shear (M is
+    not symmetric, so J^{-1} and J^{-T} differ), det M > 0."""
+    M = np.array([[1.2, 0.35, -0.2], [-0.15, 0.9, 0.25], [0.3, -0.1, 0.6]])
+    t = np.array([0.4, -0.3, 1.1])
+    assert np.linalg.det(M) > 0
+    return M, t, REF_PRISM @ M.T + t
+
+
+def _linear_field_coefficients(orc, elem, p, X, M, t, a, c0):
+    """Dubiner coefficients of u(x) = a.x + c0 on the affine element, by
+    least squares over the oracle's quadrature points (u is linear in the
+    reference coordinates, so the fit is exact)."""
+    xi, _ = orc.rule(elem, p)
+    phi0 = orc.basis(elem, p, xi)[:, 0, :]
+    x = xi @ M.T + t
+    U, *_ = np.linalg.lstsq(phi0, x @ a + c0, rcond=None)
+    assert np.max(np.abs(phi0 @ U - (x @ a + c0))) < 1e-13
+    return U, x
+
+
+def _law_root(u, g):
+    from scipy.optimize import brentq
+    return brentq(lambda kk: kk - 1 - 0.5 * math.exp(-u * u) - 0.2 * math.log(1 + kk * g), 1.0,
+                  100.0, xtol=1e-15)
+
+
+@pytest.mark.parametrize("elem,p", [(PRISM, 1), (PRISM, 2), (PRISM, 3), (TET, 1)])
+def test_point_law_linear_field_closed_form(orc, elem, p):
+    """A linear physical field u = a.x + c0 on a sheared affine element: at
+    every quadrature point u = a.x(xi_Q) + c0, |grad u| = |a| exactly, and k
+    solves the law with g = |a|^2 (checked by a bracketing root finder).
+    |a| != 1 separates g from |grad u|; the shear separates J^{-T} from J^{-1}."""
+    M, t, X = _sheared_affine_prism()
+    if elem == TET:
+        X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float) @ M.T + t
+    a = np.array([1.3, -0.7, 2.1])
+    c0 = 0.25
+    U, x = _linear_field_coefficients(orc, elem, p, X, M, t, a, c0)
+    u, s, k, st = orc.point_law(elem, p, X[None], U[None], law=1)
+    assert st[0] == 0
+    assert np.max(np.abs(u[0] - (x @ a + c0))) < 1e-12
+    assert np.max(np.abs(s[0] - np.linalg.norm(a))) < 1e-12
+    g = float(a @ a)
+    kr = np.array([_law_root(uq, g) for uq in u[0]])
+    assert np.max(np.abs(k[0] - kr) / kr) < 1e-12
+
+
+def test_integrate_network_law_gradient_only_network(orc):
+    """law=2 on a linear field: a network whose first layer ignores u (zero
+    u-column) sees only |grad u| = |a|, constant over the element, so its
+    output k0 is constant and integrate(law=2) equals integrate(law=0) with
+    D = k0 I (b, c, f unchanged).  k0 comes from the network forward pass,
+    which is pinned against torch.nn."""
+    M, t, X = _sheared_affine_prism()
+    p = 3
+    a = np.array([1.3, -0.7, 2.1])
+    U, _ = _linear_field_coefficients(orc, PRISM, p, X, M, t, a, 0.25)
+    H = 8
+    rng = np.random.default_rng(21)
+    th = rng.standard_normal(orc.mlp_nparams(H)) * 0.4
+    th[0:2 * H:2] = 0.0  # W1[:, 0] = 0: the network ignores u
+    s0 = float(np.linalg.norm(a))
+    box = np.array([-1e3, 1e3, 0.5 * s0, 2.0 * s0])
+    k0 = float(orc.mlp_forward(H, th, box, np.array([0.0]), np.array([s0]))[0])
+    C = inputs.coefficients(1)
+    A2, b2, st2 = orc.integrate(PRISM, p, X[None], C, law=2, ucoef=U[None], mlp=(H, th, box))
+    assert st2[0] == 0
+    C0 = C.copy()
+    C0[0] = C0[1] = C0[2] = k0
+    C0[3:6] = 0
+    A0, b0, _ = orc.integrate(PRISM, p, X[None], C0)
+    # |grad u| at the points is |a| up to rounding (about 1e-13), hence 1e-12
+    assert _relF(A2, A0) < 1e-12 and _relF(b2, b0) < 1e-15
+    # the exact law at the same points (law=1) is not constant: it differs
+    A1, _, _ = orc.integrate(PRISM, p, X[None], C, law=1, ucoef=U[None])
+    assert _relF(A1, A0) > 1e-3
