@@ -39,15 +39,20 @@ sys.path.insert(0, ROOT)
 from paper_1310_1191_gb300 import inputs  # noqa: E402
 
 SWEEP_E = {1: 5952381, 2: 730994, 3: 152439, 4: 43860, 5: 15623, 6: 6475, 7: 3004}
-# oracle sample per degree for the CPU baseline (~1-3 s of host work each)
-CPU_SAMPLE = {1: 200000, 2: 20000, 3: 2000, 4: 300, 5: 48, 6: 16, 7: 16}
-# ALU peaks derived from unit counts and clocks (152 SMs x 2.07 GHz):
+# oracle sample per degree for the CPU baseline (at least four elements per
+# host core at every degree; a few seconds of host work each)
+CPU_SAMPLE = {1: 200000, 2: 20000, 3: 2000, 4: 300, 5: 64, 6: 64, 7: 64}
+# ALU peaks derived from unit counts and clocks (152 SMs x 2.07 GHz), used
+# only when the FMA probe cannot run:
 PEAK_F32 = 152 * 2.07e9 * 128 * 2 / 1e12   # 128 FP32 lanes per SM: 80.5 TFLOP/s
 PEAK_F64 = 152 * 2.07e9 * 2 * 2 / 1e12     # 2 FP64 FMA per SM per clock: 1.26 TFLOP/s
 HBM_FALLBACK, BF16_FALLBACK = 6800.0, 1900.0
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture of the full-size launch (profiles/fma_kernel_f64_p7_traffic.md)
+# capture of the full-size FP64 p = 7 launch (dram__bytes_read.sum +
+# dram__bytes_write.sum of fma_kernel<double>, 3004 prisms)
 TRAFFIC = {("f64", 7): 51.21e6 + 1.9624e9}
+TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
+                  "of the full-size FP64 p=7 launch (bench.py --only sweep --degrees 7)")
 
 
 def measured_peaks():
@@ -59,8 +64,41 @@ def measured_peaks():
         return HBM_FALLBACK, BF16_FALLBACK, "fallback"
 
 
+def measure_fma_peaks(lib, dev, stream):
+    """FP64 and FP32 multiply-add throughput (TFLOP/s, a multiply-add = 2
+    flops) measured with the library's FMA probe: 8 independent chains per
+    thread, 8 CTAs of 256 threads per SM, one launch of about 50 ms, best
+    of 3 after a warm-up launch, CUDA events on the launching stream."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    n = sms * 8 * 256
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    res = {}
+    for name, fp64, iters in (("f64", True, 12000), ("f32", False, 800000)):
+        best = 0.0
+        for rep in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lib.fem_probe_fma(fp64, iters, n, out, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if rep:
+                best = max(best, 2.0 * 8 * iters * n / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        res[name] = best
+    return res
+
+
 def ns_of(p):
     return (p + 1) ** 2 * (p + 2) // 2
+
+
+def geom_fp64_ops(p):
+    """FP64 operations (a multiply-add = 1) of the prism geometry per element
+    in the FP32 and tensor-core paths: adj J rows 0, 1 and det J per point
+    (15), the zeta-level factors J[:,0], J[:,1], adj row 2 (18 per level),
+    J[:,2] per triangle point (12) and the edge record (21)."""
+    N = p + 1
+    return 15 * N ** 3 + 18 * N + 12 * N * N + 21
 
 
 def nq_of(p):
@@ -221,7 +259,7 @@ def measure_sweep(lib, tables, sweep, data, prec, stream, steps, warmup, flush):
             for p, d in data.items():
                 if events is not None:
                     events[p][0].record(stream)
-                lib.fem_integrate(tables, p, sweep[p], d["X"], d["C"], sweep[p], prec,
+                lib.fem_integrate_uniform(tables, p, sweep[p], d["X"], d["C"], sweep[p], prec,
                                   lib.FEM_OUT_FULL, d["A"], d["b"], d["st"], stream)
                 if events is not None:
                     events[p][1].record(stream)
@@ -247,16 +285,22 @@ def measure_sweep(lib, tables, sweep, data, prec, stream, steps, warmup, flush):
     return step_ms, {p: statistics.mean(v) for p, v in per_p.items()}
 
 
-def per_degree_table(sweep, mean_p, osz, peak, hbm):
+def per_degree_table(sweep, mean_p, osz, peak, hbm, fp64_peak=None):
+    """Per degree: time, rate and the fraction of the roofline time, the
+    largest of the contraction at its ALU peak, the bytes at the HBM peak and
+    (FP32 path, fp64_peak given) the FP64 geometry at the FP64 pipe rate."""
     out = {}
     for p in sweep:
         t_s = mean_p[p] / 1e3
         tf = flops_per_elem(p) * sweep[p] / t_s / 1e12
         gbs = bytes_per_elem(p, osz) * sweep[p] / t_s / 1e9
-        t_roof = max(flops_per_elem(p) / (peak * 1e12), bytes_per_elem(p, osz) / (hbm * 1e9))
+        terms = {"alu": flops_per_elem(p) / (peak * 1e12), "hbm": bytes_per_elem(p, osz) / (hbm * 1e9)}
+        if fp64_peak:
+            terms["fp64_geometry"] = geom_fp64_ops(p) / (fp64_peak / 2 * 1e12)
+        bound = max(terms, key=terms.get)
         out[str(p)] = {"elements": sweep[p], "ms": round(mean_p[p], 4), "elem_per_s": sweep[p] / t_s,
                        "tflops": round(tf, 3), "gbs": round(gbs, 1),
-                       "roofline_frac": round(t_roof * sweep[p] / t_s, 4)}
+                       "roofline_frac": round(terms[bound] * sweep[p] / t_s, 4), "bound": bound}
     return out
 
 
@@ -342,14 +386,15 @@ def wl_tets(lib, stream, dev, reps):
     Xd, Cd = torch.from_numpy(X).to(dev), torch.from_numpy(C).to(dev)
     A = torch.empty((E, 16), dtype=torch.float64, device=dev)
     b = torch.empty((E, 4), dtype=torch.float64, device=dev)
-    ms = _timed(stream, lambda: lib.fem_integrate(t, 1, E, Xd, Cd, E, 0, 0, A, b, None, stream), reps, 3)
+    ms = _timed(stream, lambda: lib.fem_integrate_uniform(t, 1, E, Xd, Cd, E, 0, 0, A, b, None, stream), reps, 3)
     vol = float(b.sum().item())
     t.close()
     return {"workload": "P1 tets, unit cube 16^3 x 6 = 24576 elements, Laplace, FP64",
             "ms": round(ms, 4), "elem_per_s": E / ms * 1e3, "sum_b": vol}
 
 
-def wl_tensor(lib, tables, stream, dev, reps, bf16_peak, E=200000, degrees=(4, 5, 6, 7)):
+def wl_tensor(lib, tables, stream, dev, reps, bf16_peak, E=200000, degrees=(4, 5, 6, 7), hbm=HBM_FALLBACK,
+              fp64_peak=PEAK_F64):
     """Tensor-core forms at p = 4..7, 200k prisms each; errors against the GPU
     FP64 path (itself within 1e-12 of the oracle) on the first 512 elements."""
     import torch
@@ -361,24 +406,28 @@ def wl_tensor(lib, tables, stream, dev, reps, bf16_peak, E=200000, degrees=(4, 5
     for p in degrees:
         n = ns_of(p)
         A64 = torch.empty((S, n * n), dtype=torch.float64, device=dev)
-        lib.fem_integrate(tables, p, S, Xd, Cd, E, 0, 0, A64, None, None, stream)
+        lib.fem_integrate_uniform(tables, p, S, Xd, Cd, E, 0, 0, A64, None, None, stream)
         stream.synchronize()
         ref = A64.view(S, n, n)
         A = torch.empty((E, n * n), dtype=torch.float32, device=dev)
         b = torch.empty((E, n), dtype=torch.float32, device=dev)
         row = {}
         for name, prec in (("bf16x3", lib.FEM_BF16X3), ("f16x3", lib.FEM_F16X3)):
-            ms = _timed(stream, lambda: lib.fem_integrate(tables, p, E, Xd, Cd, E, prec, 0, A, b, None,
+            ms = _timed(stream, lambda: lib.fem_integrate_uniform(tables, p, E, Xd, Cd, E, prec, 0, A, b, None,
                                                           stream), reps)
             err = ((A[:S].double().view(S, n, n) - ref).flatten(1).norm(dim=1) /
                    ref.flatten(1).norm(dim=1)).cpu().numpy()
             fl = 8.0 * nq_of(p) * n * n * E
+            terms = {"tensor_x3": 3 * fl / (bf16_peak * 1e12), "hbm": bytes_per_elem(p, 4) * E / (hbm * 1e9),
+                     "fp64_geometry": geom_fp64_ops(p) * E / (fp64_peak / 2 * 1e12)}
+            bound = max(terms, key=terms.get)
             row[name] = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3,
                          "alg_tflops": round(fl / ms / 1e9, 1),
                          "hw_tflops_x3": round(3 * fl / ms / 1e9, 1),
                          "frac_of_bf16_peak_x3": round(3 * fl / ms / 1e9 / bf16_peak, 4),
+                         "roofline_frac": round(terms[bound] / (ms / 1e3), 4), "bound": bound,
                          "err_max": float(err.max()), "err_median": float(np.median(err))}
-        ms32 = _timed(stream, lambda: lib.fem_integrate(tables, p, E, Xd, Cd, E, 1, 0, A, b, None,
+        ms32 = _timed(stream, lambda: lib.fem_integrate_uniform(tables, p, E, Xd, Cd, E, 1, 0, A, b, None,
                                                         stream), 1)
         row["f32_fma"] = {"ms": round(ms32, 3), "elem_per_s": E / ms32 * 1e3}
         out[str(p)] = row
@@ -478,7 +527,7 @@ def wl_apply(lib, tables, stream, dev, reps, hbm, scale_down=1, degrees=range(1,
             if y64 is None:
                 y64 = y[:S].clone()
                 A = torch.empty((S, n * n), dtype=torch.float64, device=dev)
-                lib.fem_integrate(tables, p, S, Xd, Cd, E, lib.FEM_F64, lib.FEM_OUT_FULL, A, None, None, stream)
+                lib.fem_integrate_uniform(tables, p, S, Xd, Cd, E, lib.FEM_F64, lib.FEM_OUT_FULL, A, None, None, stream)
                 stream.synchronize()
                 yf = torch.bmm(A.view(S, n, n), xd[:S].unsqueeze(2)).squeeze(2)
                 row[name]["err_max_vs_formed"] = float(((y64 - yf).norm(dim=1) / yf.norm(dim=1)).max())
@@ -517,7 +566,7 @@ def wl_split(lib, tables, stream, dev, reps, scale_down=1, degrees=range(1, 8)):
         T = torch.empty((E, q, 10), dtype=torch.float64, device=dev)
         st = torch.empty((E,), dtype=torch.int32, device=dev)
         F, L = lib.FEM_F64, lib.FEM_OUT_FULL
-        fused = _timed(stream, lambda: lib.fem_integrate(tables, p, E, Xd, Cd, E, F, L, A, b, st, stream), reps)
+        fused = _timed(stream, lambda: lib.fem_integrate_uniform(tables, p, E, Xd, Cd, E, F, L, A, b, st, stream), reps)
         A_ref = A[:: max(1, E // 64)].clone()
         terms = _timed(stream, lambda: lib.fem_jacobian_terms(tables, p, E, Xd, T, st, stream), reps)
         nojac = _timed(stream, lambda: lib.fem_integrate_terms(tables, p, E, T, Cd, E, F, L, A, b, st, stream),
@@ -615,12 +664,12 @@ def wl_surrogate(lib, tables, stream, dev, reps, E=1000000):
     ref = A64.view(S, NS, NS)
     res = {}
     for name, fn in (
-            ("constant_D", lambda: lib.fem_integrate(tables, p, E, Xd, Cd, E, 1, 0, A, b, st, stream)),
+            ("constant_D", lambda: lib.fem_integrate_uniform(tables, p, E, Xd, Cd, E, 1, 0, A, b, st, stream)),
             ("exact_law", lambda: lib.fem_integrate_law(tables, p, E, Xd, Cd, E, Ud, lib.FEM_LAW_EXACT, None,
                                                         1, 0, A, b, st, stream)),
             ("network", lambda: lib.fem_integrate_law(tables, p, E, Xd, Cd, E, Ud, lib.FEM_LAW_MLP, m, 1, 0,
                                                       A, b, st, stream)),
-            ("constant_D_bf16x3", lambda: lib.fem_integrate(tables, p, E, Xd, Cd, E, lib.FEM_BF16X3, 0, A, b, st,
+            ("constant_D_bf16x3", lambda: lib.fem_integrate_uniform(tables, p, E, Xd, Cd, E, lib.FEM_BF16X3, 0, A, b, st,
                                                             stream)),
             ("exact_law_bf16x3", lambda: lib.fem_integrate_law(tables, p, E, Xd, Cd, E, Ud, lib.FEM_LAW_EXACT, None,
                                                                lib.FEM_BF16X3, 0, A, b, st, stream)),
@@ -657,13 +706,15 @@ def run_only(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
     hbm, bf16_peak, _ = measured_peaks()
+    fma = measure_fma_peaks(lib, dev, stream)
     tables = lib.fem_tables_build(lib.FEM_PRISM6, 1, 7)
     reps = args.steps
     if args.only == "tets":
         out = wl_tets(lib, stream, dev, reps)
     elif args.only == "tc":
         degs = tuple(int(x) for x in args.degrees.split(",")) if args.degrees else (4, 5, 6, 7)
-        out = wl_tensor(lib, tables, stream, dev, reps, bf16_peak, E=args.elements or 200000, degrees=degs)
+        out = wl_tensor(lib, tables, stream, dev, reps, bf16_peak, E=args.elements or 200000, degrees=degs,
+                        hbm=hbm, fp64_peak=fma["f64"])
     elif args.only == "mixed":
         out = wl_batched(lib, tables, stream, dev, reps, E=args.elements or 500000)
     elif args.only == "law":
@@ -686,9 +737,10 @@ def run_only(args):
         data = make_sweep_data(sweep, dev, dt)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         step_ms, mean_p = measure_sweep(lib, tables, sweep, data, prec, stream, reps, args.warmup, flush)
-        peak = PEAK_F64 if prec == lib.FEM_F64 else PEAK_F32
-        out = {"elem_per_s": sum(sweep.values()) * reps / (sum(step_ms) / 1e3),
-               "per_degree": per_degree_table(sweep, mean_p, 8 if prec == lib.FEM_F64 else 4, peak, hbm)}
+        peak = fma["f64"] if prec == lib.FEM_F64 else fma["f32"]
+        out = {"elem_per_s": sum(sweep.values()) * reps / (sum(step_ms) / 1e3), "fma_peaks": fma,
+               "per_degree": per_degree_table(sweep, mean_p, 8 if prec == lib.FEM_F64 else 4, peak, hbm,
+                                              None if prec == lib.FEM_F64 else fma["f64"])}
     print(json.dumps({"only": args.only, "result": out}), flush=True)
     tables.close()
 
@@ -710,12 +762,19 @@ def run_ours(args):
     _build.build()
     lib.load()
     hbm, bf16_peak, peak_src = measured_peaks()
+    stream = torch.cuda.Stream(device=dev)
+    with Clocks(torch.cuda.current_device()) as pclk:
+        try:
+            fma = measure_fma_peaks(lib, dev, stream)
+            fma_src = "measured"
+        except Exception:
+            fma, fma_src = {"f64": PEAK_F64, "f32": PEAK_F32}, "derived from unit counts x 2.07 GHz"
+    probe_clocks = pclk.summary()
     prec = lib.FEM_F64 if args.precision == "f64" else lib.FEM_F32
     dt = torch.float64 if prec == lib.FEM_F64 else torch.float32
     osz = 8 if prec == lib.FEM_F64 else 4
     sweep = {p: (max(1, SWEEP_E[p] // args.scale_down)) for p in range(1, 8)}
     tables = lib.fem_tables_build(lib.FEM_PRISM6, 1, 7)
-    stream = torch.cuda.Stream(device=dev)
     host_inputs = {}
     data = make_sweep_data(sweep, dev, dt, host_inputs, rank, world)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -734,10 +793,11 @@ def run_ours(args):
     units = sum(sweep.values()) * args.steps * world
     value = units / (total_ms / 1e3)
 
-    peak = PEAK_F64 if prec == lib.FEM_F64 else PEAK_F32
+    peak = fma["f64"] if prec == lib.FEM_F64 else fma["f32"]
     pdom = max(mean_p, key=mean_p.get)
     achieved = flops_per_elem(pdom) * sweep[pdom] / (mean_p[pdom] / 1e3) / 1e12
-    per_degree = per_degree_table(sweep, mean_p, osz, peak, hbm)
+    per_degree = per_degree_table(sweep, mean_p, osz, peak, hbm,
+                                  None if prec == lib.FEM_F64 else fma["f64"])
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(lib, tables, sweep, data, prec, args.e2e_steps, world)
@@ -751,10 +811,12 @@ def run_ours(args):
             d32 = make_sweep_data(sweep, dev, torch.float32, host_inputs)
             sm32, mp32 = measure_sweep(lib, tables, sweep, d32, lib.FEM_F32, stream, reps, 2, flush)
             workloads["sweep_f32"] = {"elem_per_s": sum(sweep.values()) * reps / (sum(sm32) / 1e3),
-                                      "per_degree": per_degree_table(sweep, mp32, 4, PEAK_F32, hbm)}
+                                      "per_degree": per_degree_table(sweep, mp32, 4, fma["f32"], hbm,
+                                                                     fma["f64"])}
             del d32
             torch.cuda.empty_cache()
-        workloads["tensor_core"] = wl_tensor(lib, tables, stream, dev, reps, bf16_peak)
+        workloads["tensor_core"] = wl_tensor(lib, tables, stream, dev, reps, bf16_peak, hbm=hbm,
+                                             fp64_peak=fma["f64"])
         workloads["mixed_degree"] = wl_batched(lib, tables, stream, dev, reps)
         workloads["nonlinear_law"] = wl_surrogate(lib, tables, stream, dev, reps)
         workloads["elasticity"] = wl_elastic(lib, tables, stream, dev, reps)
@@ -778,8 +840,13 @@ def run_ours(args):
                          "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
                          "frac": round(achieved / peak, 4),
                          "traffic": TRAFFIC.get((args.precision, pdom)),
-                         "peak_source": "%s ALU peak derived from unit counts x 2.07 GHz; HBM %s %.0f GB/s"
-                                        % (args.precision, peak_src, hbm)},
+                         "traffic_source": TRAFFIC_SOURCE if (args.precision, pdom) in TRAFFIC else None,
+                         "peak_source": "%s FMA peak %s (fem_probe_fma: 8 independent multiply-add "
+                                        "chains per thread, 8 CTAs x 256 threads per SM, best of 3 "
+                                        "launches of about 50 ms); HBM %s %.0f GB/s"
+                                        % (args.precision, fma_src, peak_src, hbm)},
+            "fma_peaks": {"f64_tflops": round(fma["f64"], 4), "f32_tflops": round(fma["f32"], 3),
+                          "source": fma_src, "clocks": probe_clocks},
             "flagged_elements": bad,
             "clocks": clocks,
             "e2e": e2e, "cpu_baseline": cb, "workloads": workloads,

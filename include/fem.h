@@ -88,15 +88,42 @@ int fem_reference_rule(int elem, int p, int *nq, int *ns, double *xi, double *w,
 int fem_tables_build(int elem, int p_min, int p_max, fem_tables *out);
 int fem_tables_destroy(fem_tables t);
 
-/* Per-element integration of a uniform-degree batch (Algorithms 3/4 of
- * Section 4.1 re-designed for sm_103a).
- *   t            : tables holding degree p of the element type;
- *   p            : polynomial degree (1..7; 1 for FEM_TET4);
+/* Coefficient law of fem_integrate: the diffusion coefficient at each
+ * quadrature point computed from the previous solution's degrees of freedom
+ * (Section 2: the coefficients may depend on the old solution; the law and
+ * the network are described with fem_integrate_law below).
+ *   law   : 0 constant coefficients (the rows of coeffs as given),
+ *           FEM_LAW_EXACT or FEM_LAW_MLP;
+ *   ucoef : device float [n_elem][NS], the field's coefficients per element;
+ *   mlp   : the network for FEM_LAW_MLP, else NULL. */
+typedef struct fem_mlp_s *fem_mlp;
+typedef struct fem_coef_law_s {
+  int law;
+  const float *ucoef;
+  fem_mlp mlp;
+} fem_coef_law;
+
+/* Per-element integration (Section 2; Algorithms 3/4 of Section 4.1 and the
+ * host's classification of elements by degree of Section 4.2, re-designed for
+ * sm_103a): element matrices A_e and load vectors b_e of n_elem elements.
+ *   t            : tables holding every degree used, of one element type;
  *   n_elem       : number of elements (0 is a no-op);
  *   coords       : device, double [n_elem][nv][3], nv = 4 (tet) or 6 (prism),
  *                  8-byte aligned; vertex order as in the reference element;
+ *   p_per_elem   : HOST int8 [n_elem] degree of each element, or NULL for a
+ *                  mesh of the single degree p_uniform.  With per-element
+ *                  degrees the elements are binned by degree on the host and
+ *                  run by a mixed-degree plan (fem_plan_create with
+ *                  FEM_PLAN_CONCURRENT) that the tables handle creates and
+ *                  keeps for the next call with the same degrees, precision
+ *                  and layout; the outputs are then the flat variable-size
+ *                  arrays of fem_output_offsets (elements in their order);
+ *   p_uniform    : the degree when p_per_elem is NULL (1..7; 1 for FEM_TET4);
  *   coeffs       : device, double SoA [11][coeff_stride]: Dxx Dyy Dzz Dxy Dxz
  *                  Dyz bx by bz c f, element e at column e; coeff_stride >= n_elem;
+ *   law          : NULL (constant coefficients) or a coefficient law
+ *                  (uniform degree only: per-element degrees with a law give
+ *                  FEM_EUNSUPPORTED; see fem_integrate_law for the precisions);
  *   prec         : FEM_F64 / FEM_F32 / FEM_BF16X3 / FEM_F16X3;
  *   layout       : FEM_OUT_FULL or FEM_OUT_SYMPACKED;
  *   A_out        : device, [n_elem][NS*NS] (full) or [n_elem][NS(NS+1)/2]
@@ -104,14 +131,41 @@ int fem_tables_destroy(fem_tables t);
  *   b_out        : device, [n_elem][NS] of the same type, or NULL to skip;
  *   status       : device int32 [n_elem] of FEM_ST_* bits, or NULL;
  *   stream       : cudaStream_t.
- * Returns FEM_EINVAL for null/misaligned pointers, n_elem < 0, p outside the
- * tables, unknown prec/layout; FEM_EUNSUPPORTED for a tensor-core precision
- * where no tensor-core kernel exists for (elem, p); FEM_ECUDA if a launch
- * fails.  Numerical problems of single elements never fail the call: they are
- * reported in status[]. */
-int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
-                  int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out,
-                  int32_t *status, void *stream);
+ * Returns FEM_EINVAL for null/misaligned pointers, n_elem < 0, a degree
+ * outside the tables, unknown prec/layout; FEM_EUNSUPPORTED for a
+ * combination no kernel provides (tensor-core precisions on tetrahedra);
+ * FEM_ECUDA if a launch fails.  Numerical problems of single elements
+ * (det J <= 0, non-finite input, packed output of a non-symmetric form) never
+ * fail the call: they are recorded in status[], and fem_sync_status turns
+ * them into FEM_EELEMENT.  The first call with new per-element degrees
+ * allocates the plan's device arrays and captures its graph; later calls
+ * with the same degrees and buffers replay it. */
+int fem_integrate(fem_tables t, int64_t n_elem, const double *coords, const int8_t *p_per_elem,
+                  int p_uniform, const double *coeffs, int64_t coeff_stride, const fem_coef_law *law,
+                  int prec, int layout, void *A_out, void *b_out, int32_t *status, void *stream);
+
+/* The uniform-degree, constant-coefficient case of fem_integrate, as one
+ * direct launch of the degree's kernel: fem_integrate(t, n_elem, coords,
+ * NULL, p, coeffs, coeff_stride, NULL, ...) calls it.  Same arguments and
+ * errors. */
+int fem_integrate_uniform(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
+                          int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out,
+                          int32_t *status, void *stream);
+
+/* Synchronous status query over the per-element flags of a finished or
+ * enqueued integration: waits for `stream`, reduces status[0..n_elem) on the
+ * device, and returns
+ *   FEM_ETIMEOUT  if a bounded device wait of these tables expired (the
+ *                 device error word of fem_error_flag, left as it is);
+ *   FEM_EELEMENT  if at least one element carries an error bit (FEM_ST_DET,
+ *                 FEM_ST_NONFINITE, FEM_ST_NONSYM or FEM_ST_TIMEOUT);
+ *   FEM_OK        otherwise (FEM_ST_FALLBACK is informational).
+ *   status : device int32 [n_elem], 4-byte aligned (NULL with n_elem = 0);
+ *   bits   : out, OR of every element's bits (nullable);
+ *   nflag  : out, number of elements with an error bit (nullable).
+ * FEM_EINVAL for bad arguments, FEM_ECUDA if a CUDA call fails. */
+int fem_sync_status(fem_tables t, const int32_t *status, int64_t n_elem, int32_t *bits, int64_t *nflag,
+                    void *stream);
 
 /* Linear elastostatics, the paper's model problem (Section 5.1, eqs.
  * strong_form / fes / sum_int): N_E = 3 components, isotropic
@@ -219,8 +273,6 @@ int fem_error_flag(fem_tables t, int clear);
  * outside the box the exact law is used and the element gets FEM_ST_FALLBACK. */
 #define FEM_LAW_EXACT 1
 #define FEM_LAW_MLP 2
-
-typedef struct fem_mlp_s *fem_mlp;
 
 /* Integration with the per-point law.  Arguments as fem_integrate, plus
  *   ucoef : device float [n_elem][NS] coefficients of the scalar field u in
@@ -368,6 +420,20 @@ int fem_integrate_mixed_noalloc(fem_tables t, int64_t n_elem, const int8_t *p_ho
  * releases its tensor memory and returns; the context stays usable.  Faults,
  * traps and unbounded waits are never used. */
 int fem_debug_stall_next(fem_tables t);
+
+/* ---- measurement ---- */
+/* Throughput probe of the multiply-add pipe that bounds the CUDA-core kernels
+ * (FP64 for fem_integrate's FEM_F64 path and every path's geometry, FP32 for
+ * the FP32 contractions): n_threads threads (a multiple of 256; the probe's
+ * grid is n_threads / 256 CTAs of 256) each run 8 independent chains of
+ * `iters` multiply-adds a <- a x + y and write one value to out.  The paper
+ * has no counterpart: its rooflines use vendor peaks; here the denominator
+ * is measured (the caller times the launch with CUDA events; flops =
+ * 2 * 8 * iters * n_threads).
+ *   fp64      : non-zero for double, zero for float;
+ *   out       : device [n_threads] of double or float, caller-owned, 8-byte aligned;
+ * FEM_EINVAL for bad arguments, FEM_ECUDA if the launch fails. */
+int fem_probe_fma(int fp64, int64_t iters, int64_t n_threads, void *out, void *stream);
 
 /* Number of output values per element for (elem, p, layout): NS*NS or NS(NS+1)/2;
  * -1 if invalid.  */

@@ -24,7 +24,8 @@ FEM_ST_DET, FEM_ST_NONFINITE, FEM_ST_NONSYM, FEM_ST_FALLBACK, FEM_ST_TIMEOUT = 1
 
 # every symbol include/fem.h declares (checked by the CPU tests)
 EXPORTS = (
-    "fem_reference_rule", "fem_tables_build", "fem_tables_destroy", "fem_integrate",
+    "fem_reference_rule", "fem_tables_build", "fem_tables_destroy", "fem_integrate", "fem_integrate_uniform",
+    "fem_sync_status", "fem_probe_fma",
     "fem_matrix_size", "fem_status_str", "fem_last_error", "fem_error_flag",
     "fem_output_offsets", "fem_plan_create", "fem_plan_execute", "fem_plan_variant",
     "fem_plan_destroy", "fem_integrate_mixed_noalloc",
@@ -59,7 +60,10 @@ def load():
     lib.fem_reference_rule.argtypes = [i, i, P, P, P, P, P]
     lib.fem_tables_build.argtypes = [i, i, i, P]
     lib.fem_tables_destroy.argtypes = [P]
-    lib.fem_integrate.argtypes = [P, i, i64, P, P, i64, i, i, P, P, P, P]
+    lib.fem_integrate.argtypes = [P, i64, P, P, i, P, i64, P, i, i, P, P, P, P]
+    lib.fem_integrate_uniform.argtypes = [P, i, i64, P, P, i64, i, i, P, P, P, P]
+    lib.fem_sync_status.argtypes = [P, P, i64, P, P, P]
+    lib.fem_probe_fma.argtypes = [i, i64, i64, P, P]
     lib.fem_matrix_size.argtypes = [i, i, i]
     lib.fem_matrix_size.restype = i64
     lib.fem_status_str.argtypes = [i]
@@ -185,12 +189,60 @@ def fem_tables_destroy(t: Tables) -> None:
     t.close()
 
 
-def fem_integrate(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_stride: int, prec: int,
-                  layout: int, A_out, b_out=None, status=None, stream=None) -> int:
-    """Enqueue the integration of n_elem elements of degree p (see fem.h)."""
+class CoefLaw(ctypes.Structure):
+    """fem_coef_law: law (0, FEM_LAW_EXACT, FEM_LAW_MLP), ucoef, mlp."""
+    _fields_ = [("law", ctypes.c_int), ("ucoef", ctypes.c_void_p), ("mlp", ctypes.c_void_p)]
+
+
+def coef_law(law: int, ucoef=None, mlp=None) -> CoefLaw:
+    """A coefficient law for fem_integrate (ucoef: device float [n][NS])."""
+    c = CoefLaw(law, _addr(ucoef), mlp.handle.value if mlp is not None else None)
+    c._keep = (ucoef, mlp)  # the buffers must outlive the call
+    return c
+
+
+def fem_integrate(t: Tables, n_elem: int, coords, p_per_elem, p_uniform: int, coeffs, coeff_stride: int,
+                  law, prec: int, layout: int, A_out, b_out=None, status=None, stream=None) -> int:
+    """Enqueue the integration of n_elem elements (see fem.h): p_per_elem a
+    host int8 array of degrees or None (then every element has p_uniform);
+    law None (constant coefficients) or a CoefLaw from coef_law()."""
+    pp = None
+    if p_per_elem is not None:
+        pp = np.ascontiguousarray(p_per_elem, dtype=np.int8)
+        if pp.shape[0] != n_elem:
+            raise ValueError("p_per_elem must have n_elem entries")
     return _check("fem_integrate", load().fem_integrate(
+        t.handle, n_elem, _addr(coords), pp.ctypes.data if pp is not None else None, p_uniform,
+        _addr(coeffs), coeff_stride, ctypes.byref(law) if law is not None else None, prec, layout,
+        _addr(A_out), _addr(b_out), _addr(status), _stream(stream)))
+
+
+def fem_probe_fma(fp64: bool, iters: int, n_threads: int, out, stream=None) -> int:
+    """Enqueue the FMA-pipe throughput probe (8 chains x iters multiply-adds per thread)."""
+    return _check("fem_probe_fma", load().fem_probe_fma(1 if fp64 else 0, iters, n_threads, _addr(out),
+                                                        _stream(stream)))
+
+
+def fem_integrate_uniform(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_stride: int, prec: int,
+                          layout: int, A_out, b_out=None, status=None, stream=None) -> int:
+    """Enqueue the integration of n_elem elements of degree p with constant
+    coefficients (one direct launch; see fem.h)."""
+    return _check("fem_integrate_uniform", load().fem_integrate_uniform(
         t.handle, p, n_elem, _addr(coords), _addr(coeffs), coeff_stride, prec, layout,
         _addr(A_out), _addr(b_out), _addr(status), _stream(stream)))
+
+
+def fem_sync_status(t: Tables, status, n_elem: int, stream=None):
+    """(code, bits, n_flagged): waits for the stream and reduces status[]; code
+    is FEM_OK, FEM_EELEMENT or FEM_ETIMEOUT (returned, not raised); other
+    codes raise FemError."""
+    bits = ctypes.c_int32()
+    nflag = ctypes.c_int64()
+    code = load().fem_sync_status(t.handle, _addr(status), n_elem, ctypes.byref(bits),
+                                  ctypes.byref(nflag), _stream(stream))
+    if code not in (FEM_OK, FEM_EELEMENT, FEM_ETIMEOUT):
+        raise FemError("fem_sync_status", code, last_error())
+    return code, bits.value, nflag.value
 
 
 def fem_apply(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_stride: int, prec: int, x, y,

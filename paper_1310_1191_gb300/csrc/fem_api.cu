@@ -46,14 +46,38 @@ static void free_table(DevTable &d) {
 }
 
 static void free_tables(fem_tables t) {
+  if (t->mixed) fem_plan_destroy(t->mixed);
+  t->mixed = nullptr;
   for (int p = 0; p <= kMaxP; p++) free_table(t->tab[p]);
   if (t->d_err) cudaFree(t->d_err);
   t->d_err = nullptr;
+  if (t->d_red) cudaFree(t->d_red);
+  t->d_red = nullptr;
   for (int i = 0; i < 2; i++) {
     if (t->stage[i]) cudaFree(t->stage[i]);
     if (t->hs[i]) cudaStreamDestroy(t->hs[i]);
     t->stage[i] = nullptr;
     t->hs[i] = nullptr;
+  }
+}
+
+// OR of the status words and number of elements with an error bit (every
+// bit but the informational FEM_ST_FALLBACK); red[0] = OR, red[1] = count.
+__global__ void status_reduce_kernel(const int32_t *__restrict__ st, int64_t n, unsigned long long *red) {
+  unsigned bits = 0, cnt = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned v = (unsigned)st[i];
+    bits |= v;
+    cnt += (v & ~(unsigned)FEM_ST_FALLBACK) != 0u;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bits) atomicOr(&red[0], (unsigned long long)bits);
+    if (cnt) atomicAdd(&red[1], (unsigned long long)cnt);
   }
 }
 
@@ -179,6 +203,7 @@ int fem_tables_build(int elem, int p_min, int p_max, fem_tables *out) {
   if (rc == FEM_OK) {
     cudaError_t e = cudaMalloc((void **)&t->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(t->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&t->d_red, 2 * sizeof(unsigned long long));
     if (e != cudaSuccess) rc = cuda_fail("cudaMalloc(error word)", e);
   }
   if (rc != FEM_OK) {
@@ -213,9 +238,30 @@ int fem_error_flag(fem_tables t, int clear) {
   return h ? FEM_ETIMEOUT : FEM_OK;
 }
 
-int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
-                  int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out,
-                  int32_t *status, void *stream) {
+int fem_integrate(fem_tables t, int64_t n_elem, const double *coords, const int8_t *p_per_elem,
+                  int p_uniform, const double *coeffs, int64_t coeff_stride, const fem_coef_law *law,
+                  int prec, int layout, void *A_out, void *b_out, int32_t *status, void *stream) {
+  if (!t) return invalid("fem_integrate: tables handle is NULL");
+  const int lw = law ? law->law : 0;
+  if (lw != 0 && lw != FEM_LAW_EXACT && lw != FEM_LAW_MLP) return invalid("fem_integrate: unknown coefficient law");
+  if (!p_per_elem) {
+    if (lw == 0)
+      return fem_integrate_uniform(t, p_uniform, n_elem, coords, coeffs, coeff_stride, prec, layout, A_out, b_out,
+                                   status, stream);
+    return fem_integrate_law(t, p_uniform, n_elem, coords, coeffs, coeff_stride, law->ucoef, lw, law->mlp, prec,
+                             layout, A_out, b_out, status, stream);
+  }
+  if (lw != 0) {
+    set_error("fem_integrate: a coefficient law needs a uniform degree (p_per_elem = NULL)");
+    return FEM_EUNSUPPORTED;
+  }
+  return integrate_mixed_cached(t, n_elem, p_per_elem, coords, coeffs, coeff_stride, prec, layout, A_out, b_out,
+                                status, stream);
+}
+
+int fem_integrate_uniform(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
+                          int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out,
+                          int32_t *status, void *stream) {
   if (!t) return invalid("fem_integrate: tables handle is NULL");
   if (p < t->p_min || p > t->p_max) return invalid("fem_integrate: degree not in the tables");
   if (n_elem < 0) return invalid("fem_integrate: n_elem < 0");
@@ -270,6 +316,40 @@ int fem_integrate(fem_tables t, int p, int64_t n_elem, const double *coords, con
       return launch_tc(p, prec == FEM_F16X3, d, l, stream);
     }
   }
+}
+
+int fem_sync_status(fem_tables t, const int32_t *status, int64_t n_elem, int32_t *bits, int64_t *nflag,
+                    void *stream) {
+  if (!t || !t->d_red) return invalid("fem_sync_status: tables handle is NULL");
+  if (n_elem < 0 || (n_elem > 0 && !status)) return invalid("fem_sync_status: bad n_elem or NULL status");
+  if ((uintptr_t)status & 3) return invalid("fem_sync_status: status misaligned");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != t->device) return invalid("fem_sync_status: tables live on another device");
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long h[2] = {0, 0};
+  int herr = 0;
+  cudaError_t e = cudaMemsetAsync(t->d_red, 0, 2 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess && n_elem > 0) {
+    const int grid = (int)std::min<int64_t>((n_elem + 255) / 256, 4 * 152);
+    status_reduce_kernel<<<grid, 256, 0, s>>>(status, n_elem, t->d_red);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, t->d_red, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, t->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail("fem_sync_status", e);
+  if (bits) *bits = (int32_t)h[0];
+  if (nflag) *nflag = (int64_t)h[1];
+  if (herr) {
+    set_error("fem_sync_status: a bounded device wait expired");
+    return FEM_ETIMEOUT;
+  }
+  if (h[1]) {
+    set_error("fem_sync_status: " + std::to_string(h[1]) + " element(s) flagged in status[]");
+    return FEM_EELEMENT;
+  }
+  return FEM_OK;
 }
 
 int fem_apply(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
@@ -487,8 +567,8 @@ int fem_integrate_host(fem_tables t, int p, int64_t n_elem, const double *coords
       rc = cuda_fail("fem_integrate_host: copy in", e);
       break;
     }
-    rc = fem_integrate(t, p, c, dX, dC, c, prec, layout, st + oA, b_out ? st + oB : nullptr,
-                       status ? reinterpret_cast<int32_t *>(st + oS) : nullptr, s);
+    rc = fem_integrate_uniform(t, p, c, dX, dC, c, prec, layout, st + oA, b_out ? st + oB : nullptr,
+                               status ? reinterpret_cast<int32_t *>(st + oS) : nullptr, s);
     if (rc != FEM_OK) break;
     e = cudaMemcpyAsync(static_cast<unsigned char *>(A_out) + (size_t)e0 * m * osz, st + oA, (size_t)c * m * osz,
                         cudaMemcpyDeviceToHost, s);

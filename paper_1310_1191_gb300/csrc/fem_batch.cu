@@ -161,6 +161,7 @@ static int launch_loop(int p, int v, const FmaArgs &a, void *stream) {
 // ---------------------------------------------------------------- plan object
 struct fem_plan_s {
   fem_tables t = nullptr;
+  int device = 0;  // the device current at creation (the tables' device)
   int prec = 0, layout = 0, flags = 0;
   int64_t n = 0;
   std::string cache;
@@ -561,6 +562,10 @@ int fem_integrate_mixed_noalloc(fem_tables t, int64_t n_elem, const int8_t *p_ho
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return plan_fail("cudaGetDevice", err);
+  if (dev != t->device) {
+    set_error("fem_integrate_mixed_noalloc: tables live on another device");
+    return FEM_EINVAL;
+  }
   if (dev < 0 || dev >= kNoAllocMaxDevices) {
     set_error("fem_integrate_mixed_noalloc: device index out of range");
     return FEM_EUNSUPPORTED;
@@ -673,6 +678,13 @@ int fem_plan_create(fem_tables t, int64_t n_elem, const int8_t *p_host, int prec
     set_error("fem_plan_create: unknown layout");
     return FEM_EINVAL;
   }
+  int dev = 0;
+  cudaError_t derr = cudaGetDevice(&dev);
+  if (derr != cudaSuccess) return plan_fail("cudaGetDevice", derr);
+  if (dev != t->device) {
+    set_error("fem_plan_create: tables live on another device");
+    return FEM_EINVAL;
+  }
   std::vector<int64_t> cnt(kMaxP + 2, 0);
   for (int64_t e = 0; e < n_elem; e++) {
     const int p = p_host[e];
@@ -685,6 +697,7 @@ int fem_plan_create(fem_tables t, int64_t n_elem, const int8_t *p_host, int prec
   fem_plan pl = new (std::nothrow) fem_plan_s();
   if (!pl) return FEM_ENOMEM;
   pl->t = t;
+  pl->device = dev;
   pl->prec = prec;
   pl->layout = layout;
   pl->flags = flags;
@@ -741,6 +754,13 @@ int fem_plan_execute(fem_plan pl, const double *coords, const double *coeffs, in
     return FEM_EINVAL;
   }
   if (pl->n == 0) return FEM_OK;
+  int dev = 0;
+  cudaError_t derr = cudaGetDevice(&dev);
+  if (derr != cudaSuccess) return plan_fail("cudaGetDevice", derr);
+  if (dev != pl->device) {
+    set_error("fem_plan_execute: the plan lives on another device");
+    return FEM_EINVAL;
+  }
   if (!coords || !coeffs || !A_out || coeff_stride < pl->n) {
     set_error("fem_plan_execute: NULL buffer or coeff_stride < n_elem");
     return FEM_EINVAL;
@@ -829,3 +849,37 @@ int fem_plan_destroy(fem_plan pl) {
 }
 
 }  // extern "C"
+
+namespace fem {
+
+// fem_integrate with per-element degrees (the host's classification of the
+// elements by degree, Section 4.2): the tables keep one per-degree
+// concurrent plan and rebuild it when the degrees, precision or layout of a
+// call differ from the ones it was made for.
+int integrate_mixed_cached(fem_tables t, int64_t n, const int8_t *p_host, const double *coords,
+                           const double *coeffs, int64_t cstride, int prec, int layout, void *A, void *b,
+                           int32_t *status, void *stream) {
+  if (n < 0) {
+    set_error("fem_integrate: n_elem < 0");
+    return FEM_EINVAL;
+  }
+  if (n == 0) return FEM_OK;
+  std::lock_guard<std::mutex> lock(t->mixed_mutex);
+  const bool same = t->mixed && t->mixed_prec == prec && t->mixed_layout == layout &&
+                    (int64_t)t->mixed_p.size() == n && std::memcmp(t->mixed_p.data(), p_host, (size_t)n) == 0;
+  if (!same) {
+    if (t->mixed) fem_plan_destroy(t->mixed);
+    t->mixed = nullptr;
+    t->mixed_p.clear();
+    fem_plan pl = nullptr;
+    const int rc = fem_plan_create(t, n, p_host, prec, layout, FEM_PLAN_CONCURRENT, nullptr, &pl);
+    if (rc != FEM_OK) return rc;
+    t->mixed = pl;
+    t->mixed_p.assign(p_host, p_host + n);
+    t->mixed_prec = prec;
+    t->mixed_layout = layout;
+  }
+  return fem_plan_execute(t->mixed, coords, coeffs, cstride, A, b, status, stream);
+}
+
+}  // namespace fem

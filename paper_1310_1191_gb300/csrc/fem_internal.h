@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -65,12 +66,19 @@ struct DevTable {
 struct fem_tables_s {
   int elem = 0, p_min = 0, p_max = 0, device = 0;
   int *d_err = nullptr;  // device error word (bounded waits that expired)
+  unsigned long long *d_red = nullptr;  // [2] status reduction of fem_sync_status (OR of bits, count)
   int stall_next = 0;    // test hook: the next tensor-core launch withholds its operand copies
   fem::DevTable tab[fem::kMaxP + 1];
   // staging for host-buffer integration (two pipeline slots)
   unsigned char *stage[2] = {nullptr, nullptr};
   size_t stage_bytes = 0;
   cudaStream_t hs[2] = {nullptr, nullptr};
+  // mixed-degree plan that fem_integrate keeps for per-element degrees (the
+  // degrees, precision and layout it was made for)
+  struct fem_plan_s *mixed = nullptr;
+  std::vector<int8_t> mixed_p;
+  int mixed_prec = -1, mixed_layout = -1;
+  std::mutex mixed_mutex;
 };
 
 namespace fem {
@@ -104,6 +112,12 @@ struct FmaArgs {
   float nrm[4] = {0, 0, 0, 0};   // input normalisation of the network
   float box[4] = {0, 0, 0, 0};   // u0, u1, s0, s1 (network used inside)
 };
+
+// fem_integrate with per-element degrees: runs (and keeps in t) a per-degree
+// concurrent plan for these degrees, precision and layout (fem_batch.cu).
+int integrate_mixed_cached(fem_tables t, int64_t n, const int8_t *p_host, const double *coords,
+                           const double *coeffs, int64_t cstride, int prec, int layout, void *A, void *b,
+                           int32_t *status, void *stream);
 
 // Launch the FP64 / FP32 FMA kernels for (elem, p); returns a fem status code.
 int launch_fma_f64(int elem, int p, const FmaArgs &a, void *stream);

@@ -278,6 +278,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
   if (warp == 0) {
     // ---------------- Phi^T image loader (TMA bulk copies) ----------------
     if (lane == 0) {
+      // issued[s]: 1 + the round of the last copy issued into stage s (0: none)
+      uint32_t issued[C::STAGES];
+#pragma unroll
+      for (int s = 0; s < C::STAGES; s++) issued[s] = 0;
       uint32_t g = 0;
       for (int64_t t = t_begin; t < t_end && !*sAbort; t++) {
         for (int c = 0; c < C::NCH; c++, g++) {
@@ -289,12 +293,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
           ptx::mbar_arrive_expect_tx(&bar_full[s], 2 * C::B_BYTES);
           ptx::bulk_g2s(dst, reinterpret_cast<const unsigned char *>(a.img) + (size_t)c * 2 * C::B_BYTES,
                         2 * C::B_BYTES, &bar_full[s]);
+          issued[s] = round + 1;
         }
       }
-      if (*sAbort) {  // let copies in flight land before the CTA leaves
-        const uint64_t t0 = ptx::globaltimer();
-        while (ptx::globaltimer() - t0 < 200000) {
-        }
+      if (*sAbort) {
+        // Let this CTA's copies in flight land before it leaves: the last copy
+        // into stage s completes phase issued[s] - 1 of full[s], and only this
+        // thread arms full[s], so that phase cannot be overtaken.  Each wait
+        // is bounded like every other.
+        for (int s = 0; s < C::STAGES; s++)
+          if (issued[s]) ptx::mbar_wait(&bar_full[s], (issued[s] - 1) & 1, kWaitLimitNs);
       }
     }
   } else if (warp == 1) {

@@ -59,8 +59,8 @@ def gpu_integrate(tables, elem, p, X, C, prec, layout=0, want_b=True, stream=Non
     A = torch.full((max(E, 1), m), float("nan"), dtype=dt, device=dev)
     b = torch.full((max(E, 1), ns(elem, p)), float("nan"), dtype=dt, device=dev) if want_b else None
     st = torch.full((max(E, 1),), -1, dtype=torch.int32, device=dev)
-    _lib.fem_integrate(tables, p, E, Xd, Cd, coeff_stride or C.shape[1], prec, layout, A,
-                       b, st, stream)
+    _lib.fem_integrate_uniform(tables, p, E, Xd, Cd, coeff_stride or C.shape[1], prec, layout, A,
+                               b, st, stream)
     torch.cuda.synchronize()
     if return_tensors:
         return A, b, st

@@ -135,14 +135,14 @@ def test_device_errors_are_reported(lib, prism_tables):
     Cd = torch.from_numpy(C).cuda()
     A = torch.zeros(4 * 324 + 2, dtype=torch.float64, device="cuda")
     with pytest.raises(lib.FemError) as ei:  # misaligned output
-        lib.fem_integrate(prism_tables, 2, 4, Xd, Cd, 4, 0, 0, A.data_ptr() + 8)
+        lib.fem_integrate_uniform(prism_tables, 2, 4, Xd, Cd, 4, 0, 0, A.data_ptr() + 8)
     assert ei.value.code == lib.FEM_EINVAL
     with pytest.raises(lib.FemError) as ei:  # degree outside the tables
         t = lib.fem_tables_build(lib.FEM_PRISM6, 1, 2)
-        lib.fem_integrate(t, 3, 4, Xd, Cd, 4, 0, 0, A)
+        lib.fem_integrate_uniform(t, 3, 4, Xd, Cd, 4, 0, 0, A)
     assert ei.value.code == lib.FEM_EINVAL
     with pytest.raises(lib.FemError) as ei:
-        lib.fem_integrate(prism_tables, 2, 4, Xd, Cd, 3, 0, 0, A)  # stride < n
+        lib.fem_integrate_uniform(prism_tables, 2, 4, Xd, Cd, 3, 0, 0, A)  # stride < n
     assert ei.value.code == lib.FEM_EINVAL
 
 

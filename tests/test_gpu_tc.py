@@ -139,7 +139,7 @@ def test_tc_tet_unsupported(lib):
     C = torch.zeros((11, 2), dtype=torch.float64, device="cuda")
     A = torch.zeros((2, 16), dtype=torch.float32, device="cuda")
     with pytest.raises(lib.FemError) as ei:
-        lib.fem_integrate(t, 1, 2, X, C, 2, lib.FEM_BF16X3, 0, A)
+        lib.fem_integrate_uniform(t, 1, 2, X, C, 2, lib.FEM_BF16X3, 0, A)
     assert ei.value.code == lib.FEM_EUNSUPPORTED
     t.close()
 

@@ -94,7 +94,13 @@ def test_invalid_arguments_rejected_on_host(lib):
         lib.fem_reference_rule(lib.FEM_PRISM6, 9)
     assert ei.value.code == lib.FEM_EINVAL
     # NULL tables handle
-    rc = so.fem_integrate(None, 2, 10, 8, 8, 10, lib.FEM_F64, lib.FEM_OUT_FULL, 16, None, None, None)
+    rc = so.fem_integrate(None, 10, 8, None, 2, 8, 10, None, lib.FEM_F64, lib.FEM_OUT_FULL, 16, None,
+                          None, None)
+    assert rc == lib.FEM_EINVAL and "tables" in lib.last_error()
+    rc = so.fem_integrate_uniform(None, 2, 10, 8, 8, 10, lib.FEM_F64, lib.FEM_OUT_FULL, 16, None, None,
+                                  None)
+    assert rc == lib.FEM_EINVAL and "tables" in lib.last_error()
+    rc = so.fem_sync_status(None, 8, 10, None, None, None)
     assert rc == lib.FEM_EINVAL and "tables" in lib.last_error()
     rc = so.fem_apply(None, 2, 10, 8, 8, 10, lib.FEM_F64, 8, 16, None, None)
     assert rc == lib.FEM_EINVAL and "tables" in lib.last_error()
