@@ -7,6 +7,11 @@ C with OpenMP over elements, which writes out the quadrature sum of the weak
 form (Section 2, eq. sum_int); this module compiles it with gcc on first use
 and wraps it with ctypes.
 
+Prism rules: elem PRISM uses the collapsed (p+1)^3-point rule; elem PRISM_T1
+the paper's point counts (Table 1), a fully symmetric triangle rule found by
+this oracle's own search (tri_search; stored in prism_rules_table1.txt by
+make_prism_rules.py) times Gauss-Legendre in zeta.
+
 Parity status of each function (what pins it is in tests/test_oracle_*.py):
   rule, basis, integrate (constant coefficients), law_k, mlp_loss_grad,
   apply (the element operator applied to a coefficient vector): pinned;
@@ -31,7 +36,9 @@ _SRC = os.path.join(_HERE, "fem_oracle.c")
 _SO = os.path.join(_BUILD, "libfem_oracle.so")
 
 TET, PRISM = 0, 1
+PRISM_T1 = 2  # prism with the paper's rule (Table 1 point counts)
 ST_DET, ST_NONFINITE, ST_FALLBACK = 1, 2, 8
+_RULES = os.path.join(_HERE, "prism_rules_table1.txt")
 
 _lib = None
 _lock = threading.Lock()
@@ -77,8 +84,51 @@ def _load():
             lib.orc_integrate_elastic.argtypes = [i, i64, P, P, i64, P, P, P, i]
             lib.orc_jacobian_terms.argtypes = [i, i, i64, P, P, P]
             lib.orc_max_threads.argtypes = []
+            lib.orc_tri_search.argtypes = [i, i64, ctypes.c_uint64, i, P, P]
+            lib.orc_tri_unknowns.argtypes = [i]
+            lib.orc_tri_points.argtypes = [i]
+            lib.orc_set_tri_rule.argtypes = [i, P]
+            lib.orc_tri_rule.argtypes = [i, P, P, P]
+            for p, params in read_tri_rules().items():
+                lib.orc_set_tri_rule(p, _f64(params).ctypes.data_as(ctypes.c_void_p))
             _lib = lib
     return _lib
+
+
+def read_tri_rules(path: str = _RULES) -> dict:
+    """{p: orbit parameters} of the stored symmetric triangle rules (the
+    oracle's own search, written by make_prism_rules.py); {} if absent."""
+    out = {}
+    if not os.path.exists(path):
+        return out
+    for line in open(path):
+        f = line.split()
+        if f and f[0] == "rule":
+            out[int(f[1])] = np.array([float(v) for v in f[7:]])
+    return out
+
+
+def tri_search(p: int, trials: int, seed: int = 1310, max_sol: int = 64):
+    """Distinct positive-interior symmetric triangle rules of degree 2p found
+    by `trials` continuation paths: (params [n][unknowns], smallest
+    barycentric coordinate [n]), the largest coordinate first."""
+    lib = _load()
+    nu = lib.orc_tri_unknowns(p)
+    sol = np.zeros((max_sol, nu))
+    mb = np.zeros(max_sol)
+    n = lib.orc_tri_search(p, trials, seed, max_sol, _ptr(sol), _ptr(mb))
+    if n < 0:
+        raise ValueError("bad degree")
+    return sol[:n], mb[:n]
+
+
+def tri_rule(p: int):
+    """(xi [n], eta [n], w [n]) of the stored symmetric triangle rule of degree 2p."""
+    x, y, w = np.zeros(64), np.zeros(64), np.zeros(64)
+    n = _load().orc_tri_rule(p, _ptr(x), _ptr(y), _ptr(w))
+    if n < 0:
+        raise ValueError("no stored triangle rule for p = %d" % p)
+    return x[:n], y[:n], w[:n]
 
 
 def _ptr(a):

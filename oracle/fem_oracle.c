@@ -50,6 +50,7 @@
 
 #define ORC_TET 0
 #define ORC_PRISM 1
+#define ORC_PRISM_T1 2 /* prism with the paper's rule (Table 1 point counts) */
 
 #define ORC_ST_DET 1      /* det J <= 0 at some quadrature point */
 #define ORC_ST_NONFINITE 2 /* non-finite geometry or coefficient input */
@@ -60,13 +61,16 @@ typedef long double ld;
 /* ------------------------------------------------------------------ sizes */
 int orc_ns(int elem, int p) {
     if (elem == ORC_TET) return p == 1 ? 4 : -1;
-    if (p < 1 || p > 7) return -1;
+    if ((elem != ORC_PRISM && elem != ORC_PRISM_T1) || p < 1 || p > 7) return -1;
     return (p + 1) * (p + 1) * (p + 2) / 2;
 }
 
+static const int orc_tri_count[8] = {0, 3, 6, 12, 16, 25, 33, 42};
+
 int orc_nq(int elem, int p) {
     if (elem == ORC_TET) return p == 1 ? 4 : -1;
-    if (p < 1 || p > 7) return -1;
+    if ((elem != ORC_PRISM && elem != ORC_PRISM_T1) || p < 1 || p > 7) return -1;
+    if (elem == ORC_PRISM_T1) return (p + 1) * orc_tri_count[p];
     return (p + 1) * (p + 1) * (p + 1);
 }
 
@@ -133,6 +137,8 @@ void orc_gauss_jacobi(int n, int a, int b, double *x, double *w) {
     }
 }
 
+int orc_tri_rule(int p, double *x, double *y, double *w);
+
 /* Quadrature rule on the reference element; returns NQ or -1.
  * xi: [NQ][3], w: [NQ]. */
 int orc_rule(int elem, int p, double *xi, double *w) {
@@ -147,11 +153,26 @@ int orc_rule(int elem, int p, double *xi, double *w) {
         }
         return 4;
     }
-    if (p < 1 || p > 7) return -1;
+    if (orc_nq(elem, p) < 0) return -1;
     int n = p + 1;
     double xa[16], wa[16], xb[16], wb[16];
     orc_gauss_jacobi(n, 0, 0, xa, wa);
     orc_gauss_jacobi(n, 1, 0, xb, wb);
+    if (elem == ORC_PRISM_T1) {
+        /* symmetric triangle rule x Gauss-Legendre: point q = iz * NT + it */
+        double tx[64], ty[64], tw[64];
+        int nt = orc_tri_rule(p, tx, ty, tw);
+        if (nt < 0) return -1;
+        for (int iz = 0; iz < n; iz++)
+            for (int it = 0; it < nt; it++) {
+                int q = iz * nt + it;
+                xi[3 * q + 0] = tx[it];
+                xi[3 * q + 1] = ty[it];
+                xi[3 * q + 2] = xa[iz];
+                w[q] = tw[it] * wa[iz];
+            }
+        return n * nt;
+    }
     int q = 0;
     for (int iz = 0; iz < n; iz++)
         for (int ia = 0; ia < n; ia++)
@@ -162,6 +183,424 @@ int orc_rule(int elem, int p, double *xi, double *w) {
                 w[q] = wa[ia] * wb[ib] * wa[iz] / 8.0;
             }
     return q;
+}
+
+/* ---------------------------------------- the paper's prism rules (Table 1) */
+/* Table 1 gives N_Q = 6, 18, 48, 80, 150, 231, 336 = (p + 1) x (3, 6, 12, 16,
+ * 25, 33, 42): a fully symmetric degree-2p triangle rule times (p + 1)-point
+ * Gauss-Legendre in zeta (the paper calls them Gaussian; the triangle rules
+ * are not printed).  Reading: with n0 centroids, n1 orbits (a, a, 1-2a) and n2
+ * orbits (a, b, 1-a-b) in barycentric coordinates, the point count and a
+ * square moment system fix (n0, n1, n2) = (0,1,0), (0,2,0), (0,2,1), (1,3,1),
+ * (1,2,3), (0,5,3), (0,6,4); the rule is the positive-interior solution of the
+ * moment equations, the one with the largest smallest barycentric coordinate
+ * where several exist.
+ *
+ * orc_tri_search finds the positive-interior solutions: from random starts,
+ * homotopy continuation that moves the target moments linearly from the
+ * start's own moments to the exact ones; the moments are those of every
+ * monomial xi^i eta^j, i + j <= 2p (closed form i! j! / (i + j + 2)!), an
+ * overdetermined but consistent system solved by Gauss-Newton steps; points
+ * stay strictly inside and weights positive through the parameters
+ * a = 1 / (2 (1 + e^-s)) (S21), (a, b, c) = softmax(s1, s2, 0) (S111),
+ * w = e^t.  Each solution is polished in long double and stored in canonical
+ * order (S21 by a; S111 as a < b < c, by (a, b)). */
+static const int orc_tri_shape[8][3] = {{0, 0, 0}, {0, 1, 0}, {0, 2, 0}, {0, 2, 1},
+                                        {1, 3, 1}, {1, 2, 3}, {0, 5, 3}, {0, 6, 4}};
+
+int orc_tri_points(int p) {
+    if (p < 1 || p > 7) return -1;
+    return orc_tri_shape[p][0] + 3 * orc_tri_shape[p][1] + 6 * orc_tri_shape[p][2];
+}
+
+int orc_tri_unknowns(int p) {
+    if (p < 1 || p > 7) return -1;
+    return orc_tri_shape[p][0] + 2 * orc_tri_shape[p][1] + 3 * orc_tri_shape[p][2];
+}
+
+/* barycentric points (l0, l1, l2) and weights of the orbits with natural
+ * parameters x (centroid w; S21 a, w; S111 a, b, w) */
+static int tri_expand(int p, const ld *x, ld (*l)[3], ld *w) {
+    int n = 0, k = 0;
+    for (int o = 0; o < orc_tri_shape[p][0]; o++, k++) {
+        l[n][0] = l[n][1] = l[n][2] = 1.0L / 3.0L;
+        w[n++] = x[k];
+    }
+    for (int o = 0; o < orc_tri_shape[p][1]; o++, k += 2) {
+        ld a = x[k], c = 1.0L - 2.0L * a;
+        ld pts[3][3] = {{a, a, c}, {a, c, a}, {c, a, a}};
+        for (int m = 0; m < 3; m++, n++) {
+            for (int d = 0; d < 3; d++) l[n][d] = pts[m][d];
+            w[n] = x[k + 1];
+        }
+    }
+    for (int o = 0; o < orc_tri_shape[p][2]; o++, k += 3) {
+        ld a = x[k], b = x[k + 1], c = 1.0L - a - b;
+        ld pts[6][3] = {{a, b, c}, {a, c, b}, {b, a, c}, {b, c, a}, {c, a, b}, {c, b, a}};
+        for (int m = 0; m < 6; m++, n++) {
+            for (int d = 0; d < 3; d++) l[n][d] = pts[m][d];
+            w[n] = x[k + 2];
+        }
+    }
+    return n;
+}
+
+/* exact monomial moments of the triangle, i! j! / (i + j + 2)!, i + j <= 2p */
+static void tri_exact(int p, double *ex) {
+    int m = 0;
+    for (int i = 0; i <= 2 * p; i++)
+        for (int j = 0; i + j <= 2 * p; j++, m++)
+            ex[m] = (double)(tgammal(i + 1) * tgammal(j + 1) / tgammal(i + j + 3));
+}
+
+/* natural parameters x from the free parameters z, and dx/dz (block diagonal:
+ * per orbit), see the search's description above */
+static void tri_natural(int p, const double *z, double *x, double (*dx)[40]) {
+    const int nu = orc_tri_unknowns(p);
+    for (int a = 0; a < nu; a++)
+        for (int b = 0; b < nu; b++) dx[a][b] = 0.0;
+    int k = 0;
+    for (int o = 0; o < orc_tri_shape[p][0]; o++, k++) x[k] = dx[k][k] = exp(z[k]);
+    for (int o = 0; o < orc_tri_shape[p][1]; o++, k += 2) {
+        double sg = 1.0 / (1.0 + exp(-z[k]));
+        x[k] = 0.5 * sg;
+        dx[k][k] = 0.5 * sg * (1.0 - sg);
+        x[k + 1] = dx[k + 1][k + 1] = exp(z[k + 1]);
+    }
+    for (int o = 0; o < orc_tri_shape[p][2]; o++, k += 3) {
+        double m = z[k] > z[k + 1] ? z[k] : z[k + 1];
+        m = m > 0.0 ? m : 0.0;
+        double e1 = exp(z[k] - m), e2 = exp(z[k + 1] - m), Z = e1 + e2 + exp(-m);
+        double a = e1 / Z, b = e2 / Z;
+        x[k] = a;
+        x[k + 1] = b;
+        dx[k][k] = a * (1.0 - a);
+        dx[k][k + 1] = -a * b;
+        dx[k + 1][k] = -a * b;
+        dx[k + 1][k + 1] = b * (1.0 - b);
+        x[k + 2] = dx[k + 2][k + 2] = exp(z[k + 2]);
+    }
+}
+
+/* moments (over the exact ones) of the rule with natural parameters x, and
+ * their derivatives d mom / d x (analytic) */
+static int tri_moments_d(int p, const double *x, const double *ex, double *mom, double (*J)[40]) {
+    const int nm = (2 * p + 1) * (2 * p + 2) / 2, nu = orc_tri_unknowns(p), d = 2 * p;
+    for (int m = 0; m < nm; m++) {
+        mom[m] = 0.0;
+        for (int a = 0; a < nu; a++) J[m][a] = 0.0;
+    }
+    /* TRI_POINT: one point (l1, l2) = (xi, eta) of weight w, Jacobian
+     * columns cw (its weight) and c0.. (its np position parameters, with
+     * d l1 / d param = d1[], d l2 / d param = d2[]) */
+    int k = 0;
+#define TRI_POINT(L1, L2, W, CW, C0, NP, D1, D2)                                                  \
+    do {                                                                                          \
+        double p1[16], p2[16];                                                                    \
+        p1[0] = p2[0] = 1.0;                                                                      \
+        for (int e = 1; e <= d; e++) {                                                            \
+            p1[e] = p1[e - 1] * (L1);                                                             \
+            p2[e] = p2[e - 1] * (L2);                                                             \
+        }                                                                                         \
+        int m_ = 0;                                                                               \
+        for (int i = 0; i <= d; i++)                                                              \
+            for (int j = 0; i + j <= d; j++, m_++) {                                              \
+                double v = p1[i] * p2[j] / ex[m_];                                                \
+                double g1 = i ? i * p1[i - 1] * p2[j] / ex[m_] : 0.0;                             \
+                double g2 = j ? j * p1[i] * p2[j - 1] / ex[m_] : 0.0;                             \
+                mom[m_] += (W) * v;                                                               \
+                J[m_][CW] += v;                                                                   \
+                for (int q_ = 0; q_ < (NP); q_++) J[m_][(C0) + q_] += (W) * (g1 * (D1)[q_] + g2 * (D2)[q_]); \
+            }                                                                                     \
+    } while (0)
+    for (int o = 0; o < orc_tri_shape[p][0]; o++, k++) {
+        const double z0[1] = {0.0};
+        TRI_POINT(1.0 / 3.0, 1.0 / 3.0, x[k], k, k, 0, z0, z0);
+    }
+    for (int o = 0; o < orc_tri_shape[p][1]; o++, k += 2) {
+        double a = x[k], c = 1.0 - 2.0 * a, w = x[k + 1];
+        /* (l1, l2) = (a, c), (c, a), (a, a); d/da */
+        const double da1[3] = {1.0, -2.0, 1.0}, da2[3] = {-2.0, 1.0, 1.0};
+        const double l1[3] = {a, c, a}, l2[3] = {c, a, a};
+        for (int m = 0; m < 3; m++) TRI_POINT(l1[m], l2[m], w, k + 1, k, 1, &da1[m], &da2[m]);
+    }
+    for (int o = 0; o < orc_tri_shape[p][2]; o++, k += 3) {
+        double a = x[k], b = x[k + 1], c = 1.0 - a - b, w = x[k + 2];
+        /* the six permutations (l0, l1, l2) of (a, b, c); (l1, l2) and d/d(a, b) */
+        const double l1[6] = {b, c, a, c, a, b}, l2[6] = {c, b, c, a, b, a};
+        const double d1[6][2] = {{0, 1}, {-1, -1}, {1, 0}, {-1, -1}, {1, 0}, {0, 1}};
+        const double d2[6][2] = {{-1, -1}, {0, 1}, {-1, -1}, {1, 0}, {0, 1}, {1, 0}};
+        for (int m = 0; m < 6; m++) TRI_POINT(l1[m], l2[m], w, k + 2, k, 2, d1[m], d2[m]);
+    }
+#undef TRI_POINT
+    return nm;
+}
+
+/* Gauss-Newton step: (J^T J) dz = -J^T r; 0 if singular */
+static int tri_gn_step(int nu, int nm, double (*J)[40], const double *r, double *dz) {
+    double A[40][41];
+    for (int a = 0; a < nu; a++) {
+        for (int b = 0; b < nu; b++) {
+            double s = 0.0;
+            for (int m = 0; m < nm; m++) s += J[m][a] * J[m][b];
+            A[a][b] = s;
+        }
+        double s = 0.0;
+        for (int m = 0; m < nm; m++) s -= J[m][a] * r[m];
+        A[a][nu] = s;
+    }
+    for (int c = 0; c < nu; c++) {
+        int pv = c;
+        for (int q = c + 1; q < nu; q++)
+            if (fabs(A[q][c]) > fabs(A[pv][c])) pv = q;
+        if (!(fabs(A[pv][c]) > 1e-300)) return 0;
+        for (int q = 0; q <= nu; q++) {
+            double t = A[c][q];
+            A[c][q] = A[pv][q];
+            A[pv][q] = t;
+        }
+        for (int q = c + 1; q < nu; q++) {
+            double f = A[q][c] / A[c][c];
+            for (int k = c; k <= nu; k++) A[q][k] -= f * A[c][k];
+        }
+    }
+    for (int q = nu - 1; q >= 0; q--) {
+        double s = A[q][nu];
+        for (int k = q + 1; k < nu; k++) s -= A[q][k] * dz[k];
+        dz[q] = s / A[q][q];
+    }
+    return 1;
+}
+
+static uint64_t orc_splitmix(uint64_t *s) {
+    uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static double orc_unif(uint64_t *s) { return (double)(orc_splitmix(s) >> 11) * (1.0 / 9007199254740992.0); }
+
+/* one continuation path from a seeded start; 1 and the natural parameters x on success */
+static int tri_path(int p, uint64_t seed, const double *ex, double *x) {
+    const int nu = orc_tri_unknowns(p), npt = orc_tri_points(p), nm = (2 * p + 1) * (2 * p + 2) / 2;
+    double z[40], m0[200], mom[200], r[200], Jx[200][40], Jz[200][40], dxz[40][40];
+    int k = 0;
+    for (int o = 0; o < orc_tri_shape[p][0]; o++) z[k++] = log(0.5 / npt) + 0.6 * (orc_unif(&seed) - 0.5);
+    for (int o = 0; o < orc_tri_shape[p][1]; o++) {
+        z[k++] = 6.0 * (orc_unif(&seed) - 0.5);
+        z[k++] = log(0.5 / npt) + 0.6 * (orc_unif(&seed) - 0.5);
+    }
+    for (int o = 0; o < orc_tri_shape[p][2]; o++) {
+        z[k++] = 5.0 * (orc_unif(&seed) - 0.5);
+        z[k++] = 5.0 * (orc_unif(&seed) - 0.5);
+        z[k++] = log(0.5 / npt) + 0.6 * (orc_unif(&seed) - 0.5);
+    }
+    tri_natural(p, z, x, dxz);
+    tri_moments_d(p, x, ex, m0, Jx);
+    double t = 0.0, dt = 0.02;
+    while (t < 1.0) {
+        double tn = t + dt > 1.0 ? 1.0 : t + dt, z2[40];
+        memcpy(z2, z, sizeof(double) * nu);
+        int good = 0;
+        for (int it = 0; it < 6; it++) {
+            tri_natural(p, z2, x, dxz);
+            tri_moments_d(p, x, ex, mom, Jx);
+            double nr = 0.0;
+            for (int m = 0; m < nm; m++) {
+                r[m] = mom[m] - ((1.0 - tn) * m0[m] + tn);
+                nr = fabs(r[m]) > nr ? fabs(r[m]) : nr;
+                for (int a = 0; a < nu; a++) {  /* chain rule through dx/dz */
+                    double s = 0.0;
+                    for (int b = 0; b < nu; b++) s += Jx[m][b] * dxz[b][a];
+                    Jz[m][a] = s;
+                }
+            }
+            if (!(nr == nr)) break;
+            if (nr < 1e-11) {
+                good = 1;
+                break;
+            }
+            double dz[40], mx = 0.0;
+            if (!tri_gn_step(nu, nm, Jz, r, dz)) break;
+            for (int a = 0; a < nu; a++) mx = fabs(dz[a]) > mx ? fabs(dz[a]) : mx;
+            if (mx > 2.0) break;
+            for (int a = 0; a < nu; a++) z2[a] += dz[a];
+        }
+        double mz = 0.0;
+        for (int a = 0; a < nu; a++) mz = fabs(z2[a]) > mz ? fabs(z2[a]) : mz;
+        if (good && mz < 40.0) {
+            memcpy(z, z2, sizeof(double) * nu);
+            t = tn;
+            dt = dt * 1.3 > 0.05 ? 0.05 : dt * 1.3;
+        } else {
+            dt *= 0.5;
+            if (dt < 1e-6) return 0;
+        }
+    }
+    tri_natural(p, z, x, dxz);
+    return 1;
+}
+
+/* exactness residual of the rule in long double: max over the monomials of
+ * |sum_q w_q xi^i eta^j / exact - 1| */
+static ld tri_residual_l(int p, const ld *x, ld *r) {
+    ld l[64][3], w[64], nr = 0.0L;
+    int n = tri_expand(p, x, l, w), m = 0;
+    for (int i = 0; i <= 2 * p; i++)
+        for (int j = 0; i + j <= 2 * p; j++, m++) {
+            ld ex = tgammal(i + 1) * tgammal(j + 1) / tgammal(i + j + 3), s = 0.0L;
+            for (int q = 0; q < n; q++) s += w[q] * ipow_l(l[q][1], i) * ipow_l(l[q][2], j);
+            r[m] = s / ex - 1.0L;
+            nr = fabsl(r[m]) > nr ? fabsl(r[m]) : nr;
+        }
+    return nr;
+}
+
+/* Gauss-Newton polish in the natural parameters: residual in long double,
+ * Jacobian in double (iterative refinement); 1 if it drops below 1e-17 */
+static int tri_polish(int p, const double *ex, ld *x) {
+    const int nu = orc_tri_unknowns(p), nm = (2 * p + 1) * (2 * p + 2) / 2;
+    ld rl[200];
+    double xd[40], mom[200], J[200][40], r[200], dx[40];
+    for (int it = 0; it < 10; it++) {
+        if (tri_residual_l(p, x, rl) < 1e-17L) return 1;
+        for (int a = 0; a < nu; a++) xd[a] = (double)x[a];
+        tri_moments_d(p, xd, ex, mom, J);
+        for (int m = 0; m < nm; m++) r[m] = (double)rl[m];
+        if (!tri_gn_step(nu, nm, J, r, dx)) return 0;
+        for (int a = 0; a < nu; a++) x[a] += (ld)dx[a];
+    }
+    return tri_residual_l(p, x, rl) < 1e-17L;
+}
+
+static void tri_canonical(int p, ld *x) {
+    int k = orc_tri_shape[p][0];
+    int n1 = orc_tri_shape[p][1], n2 = orc_tri_shape[p][2];
+    for (int i = 0; i < n1; i++)  /* S21 by a: insertion sort of (a, w) pairs */
+        for (int j = i + 1; j < n1; j++)
+            if (x[k + 2 * j] < x[k + 2 * i]) {
+                ld ta = x[k + 2 * i], tw = x[k + 2 * i + 1];
+                x[k + 2 * i] = x[k + 2 * j];
+                x[k + 2 * i + 1] = x[k + 2 * j + 1];
+                x[k + 2 * j] = ta;
+                x[k + 2 * j + 1] = tw;
+            }
+    k += 2 * n1;
+    for (int o = 0; o < n2; o++) {  /* a < b < c within each S111 orbit */
+        ld v[3] = {x[k + 3 * o], x[k + 3 * o + 1], 1.0L - x[k + 3 * o] - x[k + 3 * o + 1]};
+        for (int i = 0; i < 3; i++)
+            for (int j = i + 1; j < 3; j++)
+                if (v[j] < v[i]) {
+                    ld t = v[i];
+                    v[i] = v[j];
+                    v[j] = t;
+                }
+        x[k + 3 * o] = v[0];
+        x[k + 3 * o + 1] = v[1];
+    }
+    for (int i = 0; i < n2; i++)  /* S111 orbits by (a, b) */
+        for (int j = i + 1; j < n2; j++) {
+            ld *u = x + k + 3 * i, *v = x + k + 3 * j;
+            if (v[0] < u[0] || (v[0] == u[0] && v[1] < u[1]))
+                for (int q = 0; q < 3; q++) {
+                    ld t = u[q];
+                    u[q] = v[q];
+                    v[q] = t;
+                }
+        }
+}
+
+static ld tri_min_bary(int p, const ld *x) {
+    ld l[64][3], w[64], mb = 1.0L;
+    int n = tri_expand(p, x, l, w);
+    for (int q = 0; q < n; q++)
+        for (int d = 0; d < 3; d++) mb = l[q][d] < mb ? l[q][d] : mb;
+    return mb;
+}
+
+/* Runs `trials` seeded paths for degree 2p; stores up to max_sol distinct
+ * positive-interior solutions (natural parameters, canonical order, sorted by
+ * smallest barycentric coordinate, largest first) in sol[max_sol][unknowns]
+ * and that coordinate in minb[]; returns the number stored, -1 on bad input. */
+int orc_tri_search(int p, int64_t trials, uint64_t seed, int max_sol, double *sol, double *minb) {
+    const int nu = orc_tri_unknowns(p);
+    if (nu < 0 || max_sol < 1 || trials < 1) return -1;
+    ld *found = (ld *)malloc(sizeof(ld) * 40 * (size_t)max_sol);
+    int nfound = 0;
+    double ex[200];
+    tri_exact(p, ex);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t tr = 0; tr < trials; tr++) {
+        ld x[40];
+        double xd[40];
+        uint64_t s = seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(tr + 1));
+        orc_splitmix(&s);
+        if (!tri_path(p, s, ex, xd)) continue;
+        for (int a = 0; a < nu; a++) x[a] = xd[a];
+        if (!tri_polish(p, ex, x)) continue;
+        tri_canonical(p, x);
+        ld l[64][3], w[64];
+        int n = tri_expand(p, x, l, w), ok = tri_min_bary(p, x) > 1e-9L;
+        for (int q = 0; q < n; q++) ok = ok && w[q] > 0.0L;
+        if (!ok) continue;
+#pragma omp critical
+        {
+            int dup = 0;
+            for (int f = 0; f < nfound && !dup; f++) {
+                ld d = 0.0L;
+                for (int a = 0; a < nu; a++) d = fabsl(found[40 * f + a] - x[a]) > d ? fabsl(found[40 * f + a] - x[a]) : d;
+                dup = d < 1e-10L;
+            }
+            if (!dup && nfound < max_sol) {
+                memcpy(found + 40 * nfound, x, sizeof(ld) * nu);
+                nfound++;
+            }
+        }
+    }
+    /* sort by smallest barycentric coordinate, largest first */
+    for (int i = 0; i < nfound; i++)
+        for (int j = i + 1; j < nfound; j++)
+            if (tri_min_bary(p, found + 40 * j) > tri_min_bary(p, found + 40 * i))
+                for (int a = 0; a < 40; a++) {
+                    ld t = found[40 * i + a];
+                    found[40 * i + a] = found[40 * j + a];
+                    found[40 * j + a] = t;
+                }
+    for (int f = 0; f < nfound; f++) {
+        for (int a = 0; a < nu; a++) sol[(size_t)f * nu + a] = (double)found[40 * f + a];
+        minb[f] = (double)tri_min_bary(p, found + 40 * f);
+    }
+    free(found);
+    return nfound;
+}
+
+/* The triangle rules the oracle uses for the Table 1 prism rules, set once
+ * from the stored result of orc_tri_search (oracle/prism_rules_table1.txt). */
+static double orc_tri_params[8][40];
+static int orc_tri_set[8];
+
+int orc_set_tri_rule(int p, const double *params) {
+    if (p < 1 || p > 7) return -1;
+    memcpy(orc_tri_params[p], params, sizeof(double) * orc_tri_unknowns(p));
+    orc_tri_set[p] = 1;
+    return 0;
+}
+
+/* Points (xi, eta) = (l1, l2) and weights of the stored triangle rule of
+ * degree 2p (the orbits expanded as in tri_expand); returns the number of
+ * points, -1 if no rule is set for p. */
+int orc_tri_rule(int p, double *x, double *y, double *w) {
+    if (p < 1 || p > 7 || !orc_tri_set[p]) return -1;
+    ld xp[40], l[64][3], wl[64];
+    for (int a = 0; a < orc_tri_unknowns(p); a++) xp[a] = orc_tri_params[p][a];
+    int n = tri_expand(p, xp, l, wl);
+    for (int q = 0; q < n; q++) {
+        x[q] = (double)l[q][1];
+        y[q] = (double)l[q][2];
+        w[q] = (double)wl[q];
+    }
+    return n;
 }
 
 /* ---------------------------------------------------------- basis */

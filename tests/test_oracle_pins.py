@@ -42,11 +42,13 @@ def test_paper_table1_table2_sizes(orc):
     """N_sh and Table 2 array sizes printed in the paper (Tables 1, 2)."""
     rows = [l.split() for l in open(os.path.join(HERE, "golden", "paper_tables_1_2.txt"))
             if l.strip() and not l.startswith("#")][1:]
-    for p, nsh, per_pt, blocks in (map(int, r) for r in rows):
+    for p, nsh, per_pt, blocks, nq in (map(int, r) for r in rows):
         assert orc.ns(PRISM, p) == nsh
         assert 4 * orc.ns(PRISM, p) == per_pt
         assert orc.ns(PRISM, p) ** 2 == blocks
         assert orc.nq(PRISM, p) == (p + 1) ** 3
+        assert orc.nq(orc.PRISM_T1, p) == nq
+        assert orc.rule(orc.PRISM_T1, p)[0].shape == (nq, 3)
 
 
 def test_jacobi_vs_scipy(orc):
@@ -341,11 +343,13 @@ def _exact_reference_moments(p):
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("elem", [PRISM, 2])
 @pytest.mark.parametrize("p", [1, 2])
-def test_affine_prism_exact_rational(orc, p):
+def test_affine_prism_exact_rational(orc, p, elem):
     """Affine prism, constant coefficients: the integrand is a polynomial of
     degree <= 2p, so the oracle's quadrature sum equals the exact integral,
-    computed here with rationals from a symbolic basis."""
+    computed here with rationals from a symbolic basis; with the collapsed
+    rule and with the paper's rule (elem 2, Table 1 point counts)."""
     x0 = [Fraction(1, 3), Fraction(-1, 5), Fraction(2, 7)]
     e1 = [Fraction(3, 4), Fraction(1, 8), Fraction(-1, 6)]
     e2 = [Fraction(-1, 9), Fraction(2, 3), Fraction(1, 10)]
@@ -384,7 +388,7 @@ def test_affine_prism_exact_rational(orc, p):
                      for j in range(NS)] for i in range(NS)])
     X = np.array([[float(q) for q in row] for row in verts])[None]
     C = _coef(1, D=np.array(D, dtype=float), b=np.array(bb, dtype=float), c=float(c))
-    A, _, st = orc.integrate(PRISM, p, X, C)
+    A, _, st = orc.integrate(elem, p, X, C)
     assert st[0] == 0
     assert _relF(A[0], Aex) < 1e-14
 
