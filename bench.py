@@ -64,27 +64,40 @@ def measured_peaks():
         return HBM_FALLBACK, BF16_FALLBACK, "fallback"
 
 
-def measure_fma_peaks(lib, dev, stream):
-    """FP64 and FP32 multiply-add throughput (TFLOP/s, a multiply-add = 2
-    flops) measured with the library's FMA probe: 8 independent chains per
-    thread, 8 CTAs of 256 threads per SM, one launch of about 50 ms, best
-    of 3 after a warm-up launch, CUDA events on the launching stream."""
+def measure_fma_peaks(lib, dev, stream, sm_mhz=2070.0):
+    """FP64 and FP32 multiply-add throughput measured with the library's FMA
+    probe: 8 independent chains per thread, 8 CTAs of 256 threads per SM,
+    launches of about 50 ms (best of 3 after a warm-up launch, CUDA events on
+    the launching stream).  Each CTA records its SM clock cycles, so the
+    probe gives multiply-adds per SM per clock; the peak (TFLOP/s, a
+    multiply-add = 2 flops) is that rate at sm_mhz, the SM clock the
+    measured kernels ran at (the probe itself may run at a lower,
+    power-capped clock)."""
     import torch
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     n = sms * 8 * 256
     out = torch.empty(n, dtype=torch.float64, device=dev)
-    res = {}
+    clk = torch.zeros((n // 256, 2), dtype=torch.int64, device=dev)
+    res = {"sm_mhz_used": sm_mhz}
     for name, fp64, iters in (("f64", True, 12000), ("f32", False, 800000)):
-        best = 0.0
+        best = None
         for rep in range(4):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            lib.fem_probe_fma(fp64, iters, n, out, stream)
+            lib.fem_probe_fma(fp64, iters, n, out, clk, stream)
             e1.record(stream)
             e1.synchronize()
             if rep:
-                best = max(best, 2.0 * 8 * iters * n / (e0.elapsed_time(e1) / 1e3) / 1e12)
-        res[name] = best
+                s = e0.elapsed_time(e1) / 1e3
+                c = clk.double()
+                mhz = float((c[:, 0] / c[:, 1]).mean()) * 1e3
+                per_clk = 8.0 * iters * n / (s * mhz * 1e6) / sms
+                if best is None or per_clk > best[0]:
+                    best = (per_clk, 2.0 * 8 * iters * n / s / 1e12, mhz)
+        res[name] = 2.0 * best[0] * sms * sm_mhz * 1e6 / 1e12
+        res[name + "_fma_per_sm_clk"] = round(best[0], 3)
+        res[name + "_probe_tflops"] = round(best[1], 4)
+        res[name + "_probe_mhz"] = round(best[2], 1)
     return res
 
 
@@ -549,6 +562,62 @@ def _copy_ms(stream, pairs, reps=2):
     return _timed(stream, lambda: [d.copy_(s, non_blocking=True) for d, s in pairs], reps)
 
 
+NTRI_TABLE1 = {1: 3, 2: 6, 3: 12, 4: 16, 5: 25, 6: 33, 7: 42}
+
+
+def flops_per_elem_rule(p, nq):
+    """flops_per_elem with a rule of nq points."""
+    n = ns_of(p)
+    return 8 * nq * n * n + 2 * nq * n + 32 * nq * n + 150 * nq
+
+
+def wl_table1(lib, stream, dev, reps, fma, hbm, bf16_peak, scale_down=1, degrees=range(1, 8),
+              collapsed_ms=None):
+    """The paper's prism rules (Table 1: N_Q = (p+1) x 3 ... 42 points, a
+    symmetric degree-2p triangle rule x Gauss-Legendre) at the sweep's element
+    counts, FP64, FP32 and BF16x3, with the same roofline terms as the sweep
+    (counted with the rule's N_Q); collapsed_ms: {precision: {p: ms}} of the
+    collapsed rule's runs for the speed ratio."""
+    import torch
+    t1 = lib.fem_tables_build_ex(lib.FEM_PRISM6, lib.FEM_RULE_TABLE1, 1, 7)
+    out = {}
+    for p in degrees:
+        E = max(1, SWEEP_E[p] // scale_down)
+        n, q = ns_of(p), (p + 1) * NTRI_TABLE1[p]
+        X, C = inputs.prism_mesh(E), inputs.coefficients(E)
+        Xd, Cd = torch.from_numpy(X).to(dev), torch.from_numpy(C).to(dev)
+        row = {"elements": E, "nq": q, "nq_collapsed": (p + 1) ** 3,
+               "work_ratio_collapsed_over_table1": round((p + 1) ** 3 / q, 3)}
+        for name, prec, dt in (("f64", lib.FEM_F64, torch.float64), ("f32", lib.FEM_F32, torch.float32),
+                               ("bf16x3", lib.FEM_BF16X3, torch.float32)):
+            A = torch.empty((E, n * n), dtype=dt, device=dev)
+            b = torch.empty((E, n), dtype=dt, device=dev)
+            ms = _timed(stream, lambda: lib.fem_integrate_uniform(t1, p, E, Xd, Cd, E, prec, lib.FEM_OUT_FULL, A, b,
+                                                                  None, stream), reps)
+            fl = flops_per_elem_rule(p, q)
+            osz = 8 if prec == lib.FEM_F64 else 4
+            terms = {"hbm": bytes_per_elem(p, osz) * E / (hbm * 1e9)}
+            if name == "bf16x3":
+                terms["tensor_x3"] = 3 * 8.0 * q * n * n * E / (bf16_peak * 1e12)
+            else:
+                terms["alu"] = fl * E / ((fma["f64"] if name == "f64" else fma["f32"]) * 1e12)
+            if name != "f64":
+                terms["fp64_geometry"] = (15 * q + 18 * (p + 1) + 12 * NTRI_TABLE1[p] + 21) * E / (fma["f64"] / 2 * 1e12)
+            bound = max(terms, key=terms.get)
+            r = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3, "tflops": round(fl * E / ms / 1e9, 3),
+                 "roofline_frac": round(terms[bound] / (ms / 1e3), 4), "bound": bound}
+            if collapsed_ms and name in collapsed_ms and p in collapsed_ms[name]:
+                r["speedup_vs_collapsed"] = round(collapsed_ms[name][p] / ms, 3)
+            row[name] = r
+            del A, b
+        out[str(p)] = row
+        torch.cuda.empty_cache()
+    t1.close()
+    return {"workload": "prism degree sweep with the paper's rules (Table 1 N_Q = 6, 18, 48, 80, 150, 231, 336), "
+                        "same element counts, coefficients and outputs as the headline sweep",
+            "per_degree": out}
+
+
 def wl_split(lib, tables, stream, dev, reps, scale_down=1, degrees=range(1, 8)):
     """Split geometry (the paper's NOJAC variants: det J and J^{-1} per point
     stored, then read) against the fused kernels (JAC), FP64, at the sweep's
@@ -725,6 +794,9 @@ def run_only(args):
     elif args.only == "apply":
         degs = tuple(int(x) for x in args.degrees.split(",")) if args.degrees else range(1, 8)
         out = wl_apply(lib, tables, stream, dev, reps, hbm, args.scale_down, degs)
+    elif args.only == "table1":
+        degs = tuple(int(x) for x in args.degrees.split(",")) if args.degrees else range(1, 8)
+        out = wl_table1(lib, stream, dev, reps, fma, hbm, bf16_peak, args.scale_down, degs)
     elif args.only == "split":
         degs = tuple(int(x) for x in args.degrees.split(",")) if args.degrees else range(1, 8)
         out = wl_split(lib, tables, stream, dev, reps, args.scale_down, degs)
@@ -785,6 +857,13 @@ def run_ours(args):
         step_ms, mean_p = measure_sweep(lib, tables, sweep, data, prec, stream, args.steps,
                                         args.warmup, flush)
     torch.cuda.synchronize()
+    clocks = clk.summary()
+    if fma_src == "measured":  # the probe's rate per SM clock at the sweep's median SM clock
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        f_k = clocks.get("sm_mhz") or 2070.0
+        fma["sm_mhz_used"] = f_k
+        for k in ("f64", "f32"):
+            fma[k] = 2.0 * fma[k + "_fma_per_sm_clk"] * sms * f_k * 1e6 / 1e12
     bad = sum(int((d["st"] != 0).sum().item()) for d in data.values())
     total_ms = sum(step_ms)
     if world > 1:
@@ -802,6 +881,7 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = measure_e2e(lib, tables, sweep, data, prec, args.e2e_steps, world)
     workloads = {}
+    collapsed_ms = None
     if rank == 0 and not args.no_extras:
         del data
         torch.cuda.empty_cache()
@@ -813,10 +893,13 @@ def run_ours(args):
             workloads["sweep_f32"] = {"elem_per_s": sum(sweep.values()) * reps / (sum(sm32) / 1e3),
                                       "per_degree": per_degree_table(sweep, mp32, 4, fma["f32"], hbm,
                                                                      fma["f64"])}
+            collapsed_ms = {"f64": dict(mean_p), "f32": dict(mp32)}
             del d32
             torch.cuda.empty_cache()
         workloads["tensor_core"] = wl_tensor(lib, tables, stream, dev, reps, bf16_peak, hbm=hbm,
                                              fp64_peak=fma["f64"])
+        workloads["table1_rules"] = wl_table1(lib, stream, dev, reps, fma, hbm, bf16_peak,
+                                              collapsed_ms=collapsed_ms if prec == lib.FEM_F64 else None)
         workloads["mixed_degree"] = wl_batched(lib, tables, stream, dev, reps)
         workloads["nonlinear_law"] = wl_surrogate(lib, tables, stream, dev, reps)
         workloads["elasticity"] = wl_elastic(lib, tables, stream, dev, reps)
@@ -825,7 +908,6 @@ def run_ours(args):
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_baseline(sweep)
-    clocks = clk.summary()
     if rank == 0:
         line = {
             "metric": "element matrices/s (prism sweep p=1..7)", "value": value,
@@ -841,12 +923,12 @@ def run_ours(args):
                          "frac": round(achieved / peak, 4),
                          "traffic": TRAFFIC.get((args.precision, pdom)),
                          "traffic_source": TRAFFIC_SOURCE if (args.precision, pdom) in TRAFFIC else None,
-                         "peak_source": "%s FMA peak %s (fem_probe_fma: 8 independent multiply-add "
-                                        "chains per thread, 8 CTAs x 256 threads per SM, best of 3 "
-                                        "launches of about 50 ms); HBM %s %.0f GB/s"
-                                        % (args.precision, fma_src, peak_src, hbm)},
-            "fma_peaks": {"f64_tflops": round(fma["f64"], 4), "f32_tflops": round(fma["f32"], 3),
-                          "source": fma_src, "clocks": probe_clocks},
+                         "peak_source": "%s FMA peak %s: fem_probe_fma's multiply-adds per SM per clock "
+                                        "(8 independent chains per thread, 8 CTAs x 256 threads per SM, "
+                                        "best of 3 launches of about 50 ms, SM clock from clock64 and "
+                                        "globaltimer in every CTA) x SMs x the timed region's median SM "
+                                        "clock; HBM %s %.0f GB/s" % (args.precision, fma_src, peak_src, hbm)},
+            "fma_peaks": dict(fma, source=fma_src, nvidia_smi_clocks=probe_clocks),
             "flagged_elements": bad,
             "clocks": clocks,
             "e2e": e2e, "cpu_baseline": cb, "workloads": workloads,
@@ -869,7 +951,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--only", choices=["sweep", "tets", "tc", "mixed", "law", "elastic", "split", "apply"],
+    ap.add_argument("--only", choices=["sweep", "tets", "tc", "mixed", "law", "elastic", "split", "apply", "table1"],
                     help="run one workload alone (profiling); prints its own JSON")
     ap.add_argument("--elements", type=int, default=0, help="elements for --only tc/mixed/law")
     ap.add_argument("--degrees", default="", help="comma-separated degrees for --only sweep/tc")

@@ -16,8 +16,10 @@
  *
  * Elements: P1 tetrahedra (4 nodes, 4-point degree-2 rule) and straight-edged
  * 6-node prisms of degree p = 1..7 (Dubiner triangle x Legendre basis,
- * NS = (p+1)^2 (p+2)/2 shape functions, collapsed Gauss-Jacobi x Gauss-Legendre
- * rule with NQ = (p+1)^3 points, exact to degree 2p).
+ * NS = (p+1)^2 (p+2)/2 shape functions), integrated with a rule exact to
+ * degree 2p: by default the collapsed Gauss-Jacobi x Gauss-Legendre rule with
+ * NQ = (p+1)^3 points, or the paper's counts (Table 1, NQ = 6 ... 336) with
+ * fem_tables_build_ex(..., FEM_RULE_TABLE1, ...).
  *
  * Conventions for every entry point:
  *   - all functions return a status code (FEM_OK = 0) and never abort;
@@ -55,6 +57,11 @@ extern "C" {
 #define FEM_BF16X3 2  /* tensor cores, bf16 hi+lo split, FP32 accumulate; float */
 #define FEM_F16X3 3   /* tensor cores, fp16 hi+lo split, FP32 accumulate; float */
 
+/* ---- quadrature rules of the prism (tetrahedra: the 4-point degree-2 rule) ---- */
+#define FEM_RULE_COLLAPSED 0  /* (p+1)^3 points: Gauss-Legendre x Gauss-Jacobi(1,0) x Gauss-Legendre */
+#define FEM_RULE_TABLE1 1     /* the paper's point counts (Table 1, N_Q = 6, 18, 48, 80, 150, 231, 336):
+                                 a fully symmetric degree-2p triangle rule x (p+1) Gauss-Legendre points */
+
 /* ---- output layouts ---- */
 #define FEM_OUT_FULL 0       /* A [E][NS][NS] row-major, unpadded */
 #define FEM_OUT_SYMPACKED 1  /* upper triangle row by row, NS(NS+1)/2 per element */
@@ -77,6 +84,12 @@ typedef struct fem_tables_s *fem_tables;
  *             d/dxi, d/deta, d/dzeta (rows 1..3), or NULL.
  * Returns FEM_EINVAL for an unknown element or p outside 1..7 (tet: p = 1). */
 int fem_reference_rule(int elem, int p, int *nq, int *ns, double *xi, double *w, double *phi);
+/* The same for a chosen prism rule (FEM_RULE_COLLAPSED as fem_reference_rule,
+ * or FEM_RULE_TABLE1, the paper's point counts of Table 1; its prism points
+ * are ordered q = iz * NT + it, zeta level iz of the (p+1)-point Gauss-Legendre
+ * rule, point it of the NT-point triangle rule).  FEM_EINVAL for a rule the
+ * element does not have. */
+int fem_reference_rule_ex(int elem, int rule, int p, int *nq, int *ns, double *xi, double *w, double *phi);
 
 /* Build the device tables (quadrature points and weights, shape functions
  * and reference derivatives at all points, in FP64 and in the reduced
@@ -86,6 +99,12 @@ int fem_reference_rule(int elem, int p, int *nq, int *ns, double *xi, double *w,
  * they are built once and kept resident in HBM.
  *   out : receives a library-owned handle; release with fem_tables_destroy. */
 int fem_tables_build(int elem, int p_min, int p_max, fem_tables *out);
+/* fem_tables_build for a chosen prism quadrature rule.  Tables built with
+ * FEM_RULE_TABLE1 serve fem_integrate / fem_integrate_uniform (uniform degree,
+ * constant coefficients; every precision) and fem_integrate_host; the other
+ * compute entry points return FEM_EUNSUPPORTED for them.  FEM_EINVAL for an
+ * unknown rule or a rule the element does not have (tetrahedra). */
+int fem_tables_build_ex(int elem, int rule, int p_min, int p_max, fem_tables *out);
 int fem_tables_destroy(fem_tables t);
 
 /* Coefficient law of fem_integrate: the diffusion coefficient at each
@@ -429,11 +448,14 @@ int fem_debug_stall_next(fem_tables t);
  * `iters` multiply-adds a <- a x + y and write one value to out.  The paper
  * has no counterpart: its rooflines use vendor peaks; here the denominator
  * is measured (the caller times the launch with CUDA events; flops =
- * 2 * 8 * iters * n_threads).
+ * 2 * 8 * iters * n_threads).  The SM clock under this load can sit below
+ * the one the measured kernels run at (power cap), so each CTA also records
+ * its SM clock cycles and nanoseconds: the rate per clock follows.
  *   fp64      : non-zero for double, zero for float;
  *   out       : device [n_threads] of double or float, caller-owned, 8-byte aligned;
+ *   clk       : device int64 [n_threads / 256][2] (cycles, ns per CTA), or NULL;
  * FEM_EINVAL for bad arguments, FEM_ECUDA if the launch fails. */
-int fem_probe_fma(int fp64, int64_t iters, int64_t n_threads, void *out, void *stream);
+int fem_probe_fma(int fp64, int64_t iters, int64_t n_threads, void *out, int64_t *clk, void *stream);
 
 /* Number of output values per element for (elem, p, layout): NS*NS or NS(NS+1)/2;
  * -1 if invalid.  */

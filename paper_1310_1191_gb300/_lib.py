@@ -20,11 +20,13 @@ FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_ECUDA, FEM_EUNSUPPORTED, FEM_EELEMENT, FEM_E
 FEM_TET4, FEM_PRISM6 = 0, 1
 FEM_F64, FEM_F32, FEM_BF16X3, FEM_F16X3 = 0, 1, 2, 3
 FEM_OUT_FULL, FEM_OUT_SYMPACKED = 0, 1
+FEM_RULE_COLLAPSED, FEM_RULE_TABLE1 = 0, 1
 FEM_ST_DET, FEM_ST_NONFINITE, FEM_ST_NONSYM, FEM_ST_FALLBACK, FEM_ST_TIMEOUT = 1, 2, 4, 8, 16
 
 # every symbol include/fem.h declares (checked by the CPU tests)
 EXPORTS = (
-    "fem_reference_rule", "fem_tables_build", "fem_tables_destroy", "fem_integrate", "fem_integrate_uniform",
+    "fem_reference_rule", "fem_reference_rule_ex", "fem_tables_build", "fem_tables_build_ex",
+    "fem_tables_destroy", "fem_integrate", "fem_integrate_uniform",
     "fem_sync_status", "fem_probe_fma",
     "fem_matrix_size", "fem_status_str", "fem_last_error", "fem_error_flag",
     "fem_output_offsets", "fem_plan_create", "fem_plan_execute", "fem_plan_variant",
@@ -59,11 +61,13 @@ def load():
     i, i64, P = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
     lib.fem_reference_rule.argtypes = [i, i, P, P, P, P, P]
     lib.fem_tables_build.argtypes = [i, i, i, P]
+    lib.fem_reference_rule_ex.argtypes = [i, i, i, P, P, P, P, P]
+    lib.fem_tables_build_ex.argtypes = [i, i, i, i, P]
     lib.fem_tables_destroy.argtypes = [P]
     lib.fem_integrate.argtypes = [P, i64, P, P, i, P, i64, P, i, i, P, P, P, P]
     lib.fem_integrate_uniform.argtypes = [P, i, i64, P, P, i64, i, i, P, P, P, P]
     lib.fem_sync_status.argtypes = [P, P, i64, P, P, P]
-    lib.fem_probe_fma.argtypes = [i, i64, i64, P, P]
+    lib.fem_probe_fma.argtypes = [i, i64, i64, P, P, P]
     lib.fem_matrix_size.argtypes = [i, i, i]
     lib.fem_matrix_size.restype = i64
     lib.fem_status_str.argtypes = [i]
@@ -144,15 +148,20 @@ def _stream(stream):
 
 def fem_reference_rule(elem: int, p: int):
     """(xi [nq][3], w [nq], phi [nq][4][ns]) from the library's host tables."""
+    return fem_reference_rule_ex(elem, FEM_RULE_COLLAPSED, p)
+
+
+def fem_reference_rule_ex(elem: int, rule: int, p: int):
+    """fem_reference_rule for a chosen prism rule (FEM_RULE_COLLAPSED / FEM_RULE_TABLE1)."""
     lib = load()
     nq, ns = ctypes.c_int(), ctypes.c_int()
-    _check("fem_reference_rule", lib.fem_reference_rule(elem, p, ctypes.byref(nq),
-                                                        ctypes.byref(ns), None, None, None))
+    _check("fem_reference_rule_ex", lib.fem_reference_rule_ex(elem, rule, p, ctypes.byref(nq),
+                                                              ctypes.byref(ns), None, None, None))
     xi = np.zeros((nq.value, 3))
     w = np.zeros(nq.value)
     phi = np.zeros((nq.value, 4, ns.value))
-    _check("fem_reference_rule", lib.fem_reference_rule(elem, p, None, None, xi.ctypes.data,
-                                                        w.ctypes.data, phi.ctypes.data))
+    _check("fem_reference_rule_ex", lib.fem_reference_rule_ex(elem, rule, p, None, None, xi.ctypes.data,
+                                                              w.ctypes.data, phi.ctypes.data))
     return xi, w, phi
 
 
@@ -163,10 +172,10 @@ def fem_matrix_size(elem: int, p: int, layout: int) -> int:
 class Tables:
     """Owning wrapper of a fem_tables handle."""
 
-    def __init__(self, elem: int, p_min: int, p_max: int):
-        self.elem, self.p_min, self.p_max = elem, p_min, p_max
+    def __init__(self, elem: int, p_min: int, p_max: int, rule: int = FEM_RULE_COLLAPSED):
+        self.elem, self.p_min, self.p_max, self.rule = elem, p_min, p_max, rule
         h = ctypes.c_void_p()
-        _check("fem_tables_build", load().fem_tables_build(elem, p_min, p_max, ctypes.byref(h)))
+        _check("fem_tables_build_ex", load().fem_tables_build_ex(elem, rule, p_min, p_max, ctypes.byref(h)))
         self.handle = h
 
     def close(self):
@@ -183,6 +192,10 @@ class Tables:
 
 def fem_tables_build(elem: int, p_min: int, p_max: int) -> Tables:
     return Tables(elem, p_min, p_max)
+
+
+def fem_tables_build_ex(elem: int, rule: int, p_min: int, p_max: int) -> Tables:
+    return Tables(elem, p_min, p_max, rule)
 
 
 def fem_tables_destroy(t: Tables) -> None:
@@ -217,10 +230,11 @@ def fem_integrate(t: Tables, n_elem: int, coords, p_per_elem, p_uniform: int, co
         _addr(A_out), _addr(b_out), _addr(status), _stream(stream)))
 
 
-def fem_probe_fma(fp64: bool, iters: int, n_threads: int, out, stream=None) -> int:
-    """Enqueue the FMA-pipe throughput probe (8 chains x iters multiply-adds per thread)."""
+def fem_probe_fma(fp64: bool, iters: int, n_threads: int, out, clk=None, stream=None) -> int:
+    """Enqueue the FMA-pipe throughput probe (8 chains x iters multiply-adds
+    per thread; clk: optional int64 [n_threads / 256][2] cycles and ns per CTA)."""
     return _check("fem_probe_fma", load().fem_probe_fma(1 if fp64 else 0, iters, n_threads, _addr(out),
-                                                        _stream(stream)))
+                                                        _addr(clk), _stream(stream)))
 
 
 def fem_integrate_uniform(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_stride: int, prec: int,

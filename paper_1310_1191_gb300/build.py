@@ -34,6 +34,7 @@ def _flags():
 
 def _headers_mtime() -> float:
     hs = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
+        glob.glob(os.path.join(CSRC, "*.inc")) + \
         glob.glob(os.path.join(ROOT, "include", "*.h"))
     return max(os.path.getmtime(h) for h in hs) if hs else 0.0
 

@@ -38,6 +38,7 @@ static void free_table(DevTable &d) {
   if (d.phi32) cudaFree(d.phi32);
   if (d.phiT64) cudaFree(d.phiT64);
   if (d.phiT32) cudaFree(d.phiT32);
+  if (d.phiq32) cudaFree(d.phiq32);
   if (d.sf64) cudaFree(d.sf64);
   if (d.sf32) cudaFree(d.sf32);
   if (d.img_bf16) cudaFree(d.img_bf16);
@@ -124,8 +125,13 @@ int64_t fem_matrix_size(int elem, int p, int layout) {
 }
 
 int fem_reference_rule(int elem, int p, int *nq, int *ns, double *xi, double *w, double *phi) {
+  return fem_reference_rule_ex(elem, FEM_RULE_COLLAPSED, p, nq, ns, xi, w, phi);
+}
+
+int fem_reference_rule_ex(int elem, int rule, int p, int *nq, int *ns, double *xi, double *w, double *phi) {
   HostRule r;
-  if (!build_host_rule(elem, p, &r)) return invalid("fem_reference_rule: unknown element or degree");
+  if (!build_host_rule(elem, p, &r, rule))
+    return invalid("fem_reference_rule: unknown element, rule or degree");
   if (nq) *nq = r.nq;
   if (ns) *ns = r.ns;
   if (xi) std::memcpy(xi, r.xi.data(), r.xi.size() * sizeof(double));
@@ -135,27 +141,38 @@ int fem_reference_rule(int elem, int p, int *nq, int *ns, double *xi, double *w,
 }
 
 int fem_tables_build(int elem, int p_min, int p_max, fem_tables *out) {
+  return fem_tables_build_ex(elem, FEM_RULE_COLLAPSED, p_min, p_max, out);
+}
+
+int fem_tables_build_ex(int elem, int rule, int p_min, int p_max, fem_tables *out) {
   if (!out) return invalid("fem_tables_build: out is NULL");
   *out = nullptr;
   if (elem == FEM_TET4) {
     if (p_min != 1 || p_max != 1) return invalid("fem_tables_build: tetrahedra have p = 1 only");
+    if (rule != FEM_RULE_COLLAPSED) return invalid("fem_tables_build: tetrahedra have the 4-point rule only");
   } else if (elem != FEM_PRISM6 || p_min < 1 || p_max > kMaxP || p_min > p_max) {
     return invalid("fem_tables_build: bad element type or degree range");
   }
+  if (rule != FEM_RULE_COLLAPSED && rule != FEM_RULE_TABLE1) return invalid("fem_tables_build: unknown rule");
   fem_tables t = new (std::nothrow) fem_tables_s();
   if (!t) return FEM_ENOMEM;
   t->elem = elem;
+  t->rule = rule;
   t->p_min = p_min;
   t->p_max = p_max;
   cudaGetDevice(&t->device);
   int rc = FEM_OK;
   for (int p = p_min; p <= p_max && rc == FEM_OK; p++) {
     HostRule r;
-    build_host_rule(elem, p, &r);
+    if (!build_host_rule(elem, p, &r, rule)) {
+      rc = invalid("fem_tables_build: the rule's reference data failed its exactness check");
+      break;
+    }
     DevTable &d = t->tab[p];
     d.p = p;
     d.ns = r.ns;
     d.nq = r.nq;
+    d.rule = rule;
     std::vector<double> qp(4 * (size_t)r.nq);
     for (int q = 0; q < r.nq; q++) {
       qp[4 * q + 0] = r.xi[3 * q + 0];
@@ -166,36 +183,40 @@ int fem_tables_build(int elem, int p_min, int p_max, fem_tables *out) {
     std::vector<float> phi32(r.phi.size());
     for (size_t i = 0; i < r.phi.size(); i++) phi32[i] = (float)r.phi[i];
     std::vector<double> phiT64(r.phi.size());
-    std::vector<float> phiT32(r.phi.size());
+    std::vector<float> phiT32(r.phi.size()), phiq32(r.phi.size());
     for (int q = 0; q < r.nq; q++)
       for (int dd = 0; dd < 4; dd++)
         for (int i = 0; i < r.ns; i++) {
           const size_t src = ((size_t)(4 * q + dd)) * r.ns + i, dst = ((size_t)i * r.nq + q) * 4 + dd;
           phiT64[dst] = r.phi[src];
           phiT32[dst] = phi32[src];
+          phiq32[((size_t)q * r.ns + i) * 4 + dd] = phi32[src];
         }
     rc = upload(&d.qp, qp.data(), qp.size());
     if (rc == FEM_OK) rc = upload(&d.phi64, r.phi.data(), r.phi.size());
     if (rc == FEM_OK) rc = upload(&d.phi32, phi32.data(), phi32.size());
     if (rc == FEM_OK) rc = upload(&d.phiT64, phiT64.data(), phiT64.size());
     if (rc == FEM_OK) rc = upload(&d.phiT32, phiT32.data(), phiT32.size());
+    if (rc == FEM_OK) rc = upload(&d.phiq32, phiq32.data(), phiq32.size());
     if (rc == FEM_OK && elem == FEM_PRISM6) {
       double mx = 0.0;
       for (double v : r.phi) mx = std::fmax(mx, std::fabs(v));
       int ex = 0;
       std::frexp(mx, &ex);  // mx < 2^ex
-      std::vector<double> sf;
-      build_sf_tables(p, sf);
-      std::vector<float> sf32(sf.begin(), sf.end());
-      rc = upload(&d.sf64, sf.data(), sf.size());
-      if (rc == FEM_OK) rc = upload(&d.sf32, sf32.data(), sf32.size());
+      if (rule == FEM_RULE_COLLAPSED) {  // 1D factors of the collapsed rule (operator apply)
+        std::vector<double> sf;
+        build_sf_tables(p, sf);
+        std::vector<float> sf32(sf.begin(), sf.end());
+        rc = upload(&d.sf64, sf.data(), sf.size());
+        if (rc == FEM_OK) rc = upload(&d.sf32, sf32.data(), sf32.size());
+      }
       d.phimax = (float)mx;
       d.aphi_f16 = 14 - ex;  // scaled magnitudes below 2^14
       std::vector<uint16_t> img;
-      build_tc_image(p, r.phi, false, 0, img);
-      rc = upload(&d.img_bf16, img.data(), img.size());
+      build_tc_image(p, rule, r.phi, false, 0, img);
+      if (rc == FEM_OK) rc = upload(&d.img_bf16, img.data(), img.size());
       if (rc == FEM_OK) {
-        build_tc_image(p, r.phi, true, d.aphi_f16, img);
+        build_tc_image(p, rule, r.phi, true, d.aphi_f16, img);
         rc = upload(&d.img_f16, img.data(), img.size());
       }
     }
@@ -289,13 +310,14 @@ int fem_integrate_uniform(fem_tables t, int p, int64_t n_elem, const double *coo
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev != t->device) return invalid("fem_integrate: tables live on another device");
+  const bool t1 = t->rule == FEM_RULE_TABLE1;
   switch (prec) {
     case FEM_F64:
       a.phi = d.phi64;
-      return launch_fma_f64(t->elem, p, a, stream);
+      return t1 ? launch_fma_t1_f64(p, a, stream) : launch_fma_f64(t->elem, p, a, stream);
     case FEM_F32:
       a.phi = d.phi32;
-      return launch_fma_f32(t->elem, p, a, stream);
+      return t1 ? launch_fma_t1_f32(p, a, stream) : launch_fma_f32(t->elem, p, a, stream);
     default: {
       if (t->elem != FEM_PRISM6) {
         set_error("fem_integrate: tensor-core precisions are provided for prisms only");
@@ -354,6 +376,7 @@ int fem_sync_status(fem_tables t, const int32_t *status, int64_t n_elem, int32_t
 
 int fem_apply(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
               int64_t coeff_stride, int prec, const void *x, void *y, int32_t *status, void *stream) {
+  if (rule_check(t, "fem_apply") != FEM_OK) return FEM_EUNSUPPORTED;
   if (!t) return invalid("fem_apply: tables handle is NULL");
   if (p < t->p_min || p > t->p_max) return invalid("fem_apply: degree not in the tables");
   if (n_elem < 0) return invalid("fem_apply: n_elem < 0");
@@ -395,6 +418,7 @@ int fem_apply(fem_tables t, int p, int64_t n_elem, const double *coords, const d
 int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
                           int64_t coeff_stride, int prec, void *A_out, void *b_out, int32_t *status,
                           void *stream) {
+  if (rule_check(t, "fem_integrate_elastic") != FEM_OK) return FEM_EUNSUPPORTED;
   if (!t || t->elem != FEM_PRISM6) return invalid("fem_integrate_elastic: needs prism tables");
   if (p < t->p_min || p > t->p_max || n_elem < 0) return invalid("fem_integrate_elastic: bad degree or n_elem");
   if (prec != FEM_F64 && prec != FEM_F32 && prec != FEM_BF16X3 && prec != FEM_F16X3) {
@@ -444,6 +468,7 @@ int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coo
 int fem_integrate_terms(fem_tables t, int p, int64_t n_elem, const double *terms, const double *coeffs,
                         int64_t coeff_stride, int prec, int layout, void *A_out, void *b_out,
                         int32_t *status, void *stream) {
+  if (rule_check(t, "fem_integrate_terms") != FEM_OK) return FEM_EUNSUPPORTED;
   if (!t) return invalid("fem_integrate_terms: tables handle is NULL");
   if (p < t->p_min || p > t->p_max || n_elem < 0) return invalid("fem_integrate_terms: bad degree or n_elem");
   if (prec != FEM_F64 && prec != FEM_F32) {
@@ -481,6 +506,7 @@ int fem_integrate_terms(fem_tables t, int p, int64_t n_elem, const double *terms
 int fem_integrate_elastic_terms(fem_tables t, int p, int64_t n_elem, const double *terms, const double *coeffs,
                                 int64_t coeff_stride, int prec, void *A_out, void *b_out, int32_t *status,
                                 void *stream) {
+  if (rule_check(t, "fem_integrate_elastic_terms") != FEM_OK) return FEM_EUNSUPPORTED;
   if (!t || t->elem != FEM_PRISM6) return invalid("fem_integrate_elastic_terms: needs prism tables");
   if (p < t->p_min || p > t->p_max || n_elem < 0) return invalid("fem_integrate_elastic_terms: bad degree or n_elem");
   if (prec != FEM_F64 && prec != FEM_F32) {

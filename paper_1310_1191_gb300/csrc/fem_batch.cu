@@ -523,6 +523,7 @@ extern "C" {
 int fem_integrate_mixed_noalloc(fem_tables t, int64_t n_elem, const int8_t *p_host, const double *coords,
                                 const double *coeffs, int64_t coeff_stride, int prec, int layout, void *A_out,
                                 void *b_out, int32_t *status, void *stream) {
+  if (rule_check(t, "fem_integrate_mixed_noalloc") != FEM_OK) return FEM_EUNSUPPORTED;
   if (!t || t->elem != FEM_PRISM6) {
     set_error("fem_integrate_mixed_noalloc: needs prism tables");
     return FEM_EINVAL;
@@ -652,6 +653,7 @@ int fem_output_offsets(int elem, const int8_t *p_host, int64_t n, int layout, in
 
 int fem_plan_create(fem_tables t, int64_t n_elem, const int8_t *p_host, int prec, int layout, int flags,
                     const char *tune_cache, fem_plan *out) {
+  if (rule_check(t, "fem_plan_create") != FEM_OK) return FEM_EUNSUPPORTED;
   if (!out) {
     set_error("fem_plan_create: out is NULL");
     return FEM_EINVAL;

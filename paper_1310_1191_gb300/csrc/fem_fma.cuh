@@ -30,10 +30,12 @@ namespace fem {
 
 // ND_ = rows of K per point: 4 (value + 3 derivatives, scalar form) or 3
 // (derivatives only, one 3x3 block of linear elastostatics per virtual element).
-template <int ELEM_, int P_, int BM_, int TM_, int TN_, int EPB_, int QC_, int ND_ = 4>
+// RULE_: the prism rule (FEM_RULE_COLLAPSED or FEM_RULE_TABLE1); both are
+// (p+1) zeta levels x NAB triangle points, point q = iz NAB + iab.
+template <int ELEM_, int P_, int BM_, int TM_, int TN_, int EPB_, int QC_, int ND_ = 4, int RULE_ = FEM_RULE_COLLAPSED>
 struct FmaCfg {
-  static constexpr int ELEM = ELEM_, P = P_, ND = ND_;
-  static constexpr int NS = ns_of(ELEM_, P_), NQ = nq_of(ELEM_, P_), NV = nv_of(ELEM_);
+  static constexpr int ELEM = ELEM_, P = P_, ND = ND_, RULE = RULE_;
+  static constexpr int NS = ns_of(ELEM_, P_), NQ = nq_of(ELEM_, P_, RULE_), NV = nv_of(ELEM_);
   static constexpr int BM = BM_, BN = BM_, TM = TM_, TN = TN_;
   static constexpr int TY = BM / TM, TX = BN / TN, TPE = TX * TY;
   static constexpr int EPB = EPB_, NT = EPB * TPE;
@@ -41,8 +43,8 @@ struct FmaCfg {
   static constexpr int QC = QC_, KC = ND * QC, NCH = (NQ + QC - 1) / QC;
   static constexpr int NREC = NV * 3 + 11;  // coords + coefficients per element
   static constexpr int NEDGE = kEdgeRec;    // FP64 edge record per element
-  static constexpr int NZ = ELEM_ == FEM_PRISM6 ? P_ + 1 : 0;  // zeta levels of the rule
-  static constexpr int NAB = NZ * NZ;                           // (xi, eta) points per level
+  static constexpr int NZ = ELEM_ == FEM_PRISM6 ? P_ + 1 : 0;                 // zeta levels of the rule
+  static constexpr int NAB = ELEM_ == FEM_PRISM6 ? ntri_of(P_, RULE_) : 0;     // (xi, eta) points per level
   static_assert(BM % TM == 0 && BN % TN == 0, "tile must split into micro-tiles");
   static_assert(NT <= 1024, "too many threads");
 
@@ -664,6 +666,25 @@ int launch_fma_elastic(int p, const FmaArgs &a, void *stream) {
     case 5: return launch_fma_cfg<T, typename FmaShapeE<T, 5>::type, 0, SPLIT>(v, stream);
     case 6: return launch_fma_cfg<T, typename FmaShapeE<T, 6>::type, 0, SPLIT>(v, stream);
     case 7: return launch_fma_cfg<T, typename FmaShapeE<T, 7>::type, 0, SPLIT>(v, stream);
+  }
+  return FEM_EINVAL;
+}
+
+// The paper's prism rule (Table 1's point counts): the collapsed rule's
+// shapes with its points (constant coefficients).
+template <class S>
+using Table1Cfg = FmaCfg<S::ELEM, S::P, S::BM, S::TM, S::TN, S::EPB, S::QC, S::ND, FEM_RULE_TABLE1>;
+
+template <class T>
+int launch_fma_table1(int p, const FmaArgs &a, void *stream) {
+  switch (p) {
+    case 1: return launch_fma_cfg<T, Table1Cfg<typename FmaShape<T, FEM_PRISM6, 1>::type>>(a, stream);
+    case 2: return launch_fma_cfg<T, Table1Cfg<typename FmaShape<T, FEM_PRISM6, 2>::type>>(a, stream);
+    case 3: return launch_fma_cfg<T, Table1Cfg<typename FmaShape<T, FEM_PRISM6, 3>::type>>(a, stream);
+    case 4: return launch_fma_cfg<T, Table1Cfg<typename FmaShape<T, FEM_PRISM6, 4>::type>>(a, stream);
+    case 5: return launch_fma_cfg<T, Table1Cfg<typename FmaShape<T, FEM_PRISM6, 5>::type>>(a, stream);
+    case 6: return launch_fma_cfg<T, Table1Cfg<typename FmaShape<T, FEM_PRISM6, 6>::type>>(a, stream);
+    case 7: return launch_fma_cfg<T, Table1Cfg<typename FmaShape<T, FEM_PRISM6, 7>::type>>(a, stream);
   }
   return FEM_EINVAL;
 }

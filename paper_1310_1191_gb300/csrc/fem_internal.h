@@ -18,8 +18,16 @@ constexpr int kMaxP = 7;
 __host__ __device__ constexpr int ns_of(int elem, int p) {
   return elem == FEM_TET4 ? 4 : (p + 1) * (p + 1) * (p + 2) / 2;
 }
-__host__ __device__ constexpr int nq_of(int elem, int p) {
-  return elem == FEM_TET4 ? 4 : (p + 1) * (p + 1) * (p + 1);
+// Triangle points of a prism rule: (p+1)^2 for the collapsed rule, the
+// fully symmetric triangle rule's 3, 6, 12, 16, 25, 33, 42 points for the
+// paper's rule (Table 1: N_Q = that times p + 1).
+__host__ __device__ constexpr int ntri_of(int p, int rule = FEM_RULE_COLLAPSED) {
+  return rule == FEM_RULE_TABLE1
+             ? (p == 1 ? 3 : p == 2 ? 6 : p == 3 ? 12 : p == 4 ? 16 : p == 5 ? 25 : p == 6 ? 33 : 42)
+             : (p + 1) * (p + 1);
+}
+__host__ __device__ constexpr int nq_of(int elem, int p, int rule = FEM_RULE_COLLAPSED) {
+  return elem == FEM_TET4 ? 4 : (p + 1) * ntri_of(p, rule);
 }
 __host__ __device__ constexpr int nv_of(int elem) { return elem == FEM_TET4 ? 4 : 6; }
 
@@ -31,8 +39,10 @@ struct HostRule {
   std::vector<double> phi;  // [nq][4][ns]
 };
 
-// Builds the quadrature rule and shape-function table; false if (elem,p) invalid.
-bool build_host_rule(int elem, int p, HostRule *out);
+// Builds the quadrature rule and shape-function table; false if (elem, p,
+// rule) is invalid (the paper's rule exists for prisms only).  Prism points
+// are ordered q = iz * ntri_of(p, rule) + it: zeta level iz, triangle point it.
+bool build_host_rule(int elem, int p, HostRule *out, int rule = FEM_RULE_COLLAPSED);
 
 // 1D factor tables of the prism rule and basis for sum factorisation, FP64:
 // Pa, Px, Pe [N][N] (point ia, index i), Bq, Bx, By [NT][N | 1] (triangle DOF
@@ -42,7 +52,7 @@ void build_sf_tables(int p, std::vector<double> &out);
 
 // Device copies of one degree's tables.
 struct DevTable {
-  int p = 0, ns = 0, nq = 0;
+  int p = 0, ns = 0, nq = 0, rule = FEM_RULE_COLLAPSED;
   double *qp = nullptr;     // [nq][4]: xi, eta, zeta, w (FP64)
   double *phi64 = nullptr;  // [4 nq][ns] row k = 4 q + d (FP64)
   float *phi32 = nullptr;   // same, FP32
@@ -51,6 +61,10 @@ struct DevTable {
   // consecutive 4-vectors when they evaluate a field at their points
   double *phiT64 = nullptr;
   float *phiT32 = nullptr;
+  // [nq][ns][4] FP32 (the 4 values of function i at point q contiguous, then
+  // the next function): the tensor-core producers, whose threads own
+  // consecutive functions, load one float4 per point
+  float *phiq32 = nullptr;
   // tensor-core operand images of Phi^T (hi | lo per K chunk), prisms only
   uint16_t *img_bf16 = nullptr;
   uint16_t *img_f16 = nullptr;
@@ -65,6 +79,7 @@ struct DevTable {
 
 struct fem_tables_s {
   int elem = 0, p_min = 0, p_max = 0, device = 0;
+  int rule = FEM_RULE_COLLAPSED;  // quadrature rule of every degree in the tables
   int *d_err = nullptr;  // device error word (bounded waits that expired)
   unsigned long long *d_red = nullptr;  // [2] status reduction of fem_sync_status (OR of bits, count)
   int stall_next = 0;    // test hook: the next tensor-core launch withholds its operand copies
@@ -85,6 +100,17 @@ namespace fem {
 
 // thread-local last-error text
 void set_error(const std::string &msg);
+
+// FEM_EUNSUPPORTED (with a message naming fn) for tables built with the
+// paper's rule: the entry points other than fem_integrate / fem_integrate_uniform
+// / fem_integrate_host have kernels for the collapsed rule only.
+inline int rule_check(const fem_tables_s *t, const char *fn) {
+  if (t && t->rule != FEM_RULE_COLLAPSED) {
+    set_error(std::string(fn) + ": tables with the paper's rule (FEM_RULE_TABLE1) serve fem_integrate only");
+    return FEM_EUNSUPPORTED;
+  }
+  return FEM_OK;
+}
 
 // Kernel launch arguments of the FMA path.
 struct FmaArgs {
@@ -122,6 +148,9 @@ int integrate_mixed_cached(fem_tables t, int64_t n, const int8_t *p_host, const 
 // Launch the FP64 / FP32 FMA kernels for (elem, p); returns a fem status code.
 int launch_fma_f64(int elem, int p, const FmaArgs &a, void *stream);
 int launch_fma_f32(int elem, int p, const FmaArgs &a, void *stream);
+// the same for prisms with the paper's rule (FEM_RULE_TABLE1), constant coefficients
+int launch_fma_t1_f64(int p, const FmaArgs &a, void *stream);
+int launch_fma_t1_f32(int p, const FmaArgs &a, void *stream);
 // linear elastostatics: a.n real elements, 9 blocks each
 int launch_fma_elastic_f64(int p, const FmaArgs &a, void *stream);
 // split geometry (a.terms set, a.coords unused): scalar form and elastostatics
@@ -172,6 +201,6 @@ struct ApplyArgs {
   int32_t *status;
 };
 int launch_apply(int elem, int p, bool f32, const ApplyArgs &a, void *stream);
-void build_tc_image(int p, const std::vector<double> &phi, bool f16, int aphi, std::vector<uint16_t> &out);
+void build_tc_image(int p, int rule, const std::vector<double> &phi, bool f16, int aphi, std::vector<uint16_t> &out);
 
 }  // namespace fem

@@ -314,6 +314,7 @@ int fem_law_samples(int64_t n, const double *box, uint64_t seed, float *us, floa
 
 int fem_field_samples(fem_tables t, int p, int64_t n, const double *coords, const float *ucoef, float *us,
                       void *stream) {
+  if (rule_check(t, "fem_field_samples") != FEM_OK) return FEM_EUNSUPPORTED;
   if (!t || t->elem != FEM_PRISM6 || p < t->p_min || p > t->p_max || n < 0 ||
       (n > 0 && (!coords || !ucoef || !us))) {
     set_error("fem_field_samples: bad arguments");
@@ -590,6 +591,7 @@ int fem_mlp_load(const char *path, fem_mlp *out) {
 int fem_integrate_law(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
                       int64_t coeff_stride, const float *ucoef, int law, fem_mlp mlp, int prec, int layout,
                       void *A_out, void *b_out, int32_t *status, void *stream) {
+  if (rule_check(t, "fem_integrate_law") != FEM_OK) return FEM_EUNSUPPORTED;
   if (!t) {
     set_error("fem_integrate_law: tables handle is NULL");
     return FEM_EINVAL;

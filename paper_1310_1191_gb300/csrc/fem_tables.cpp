@@ -23,6 +23,7 @@
 //   d psi/d eta = h^(i-1) [(1+a) P_i'(a) - i P_i(a)] Q_j(b) + 2 h^i P_i(a) Q_j'(b)
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "fem_internal.h"
 
@@ -172,11 +173,68 @@ void prism_basis_point(int p, double xi, double eta, double zeta, double *phi, i
   }
 }
 
+// Fully symmetric positive-interior triangle rules of degree 2p behind the
+// paper's prism rules (Table 1), as orbit parameters in barycentric
+// coordinates; written by tri_rules_gen.cpp (which documents how they are
+// found and chosen).
+struct TriRuleRow {
+  int p, n0, n1, n2;
+  double v[24];
+};
+const TriRuleRow kTriRules[] = {
+#include "fem_tri_rules.inc"
+};
+
+// Points (xi, eta) = (l1, l2) and weights of the degree-2p symmetric
+// triangle rule: the centroid, then each S21 orbit (a, a, c), (a, c, a),
+// (c, a, a), then each S111 orbit in the six permutations of (a, b, c).
+// Checks exactness on every monomial xi^i eta^j, i + j <= 2p, against
+// i! j! / (i + j + 2)!; false if a table row is missing or inexact.
+bool tri_rule_table1(int p, std::vector<double> &x, std::vector<double> &y, std::vector<double> &w) {
+  const TriRuleRow *r = nullptr;
+  for (const TriRuleRow &row : kTriRules)
+    if (row.p == p) r = &row;
+  if (!r) return false;
+  x.clear();
+  y.clear();
+  w.clear();
+  auto add = [&](double l1, double l2, double wt) {
+    x.push_back(l1);
+    y.push_back(l2);
+    w.push_back(wt);
+  };
+  int k = 0;
+  for (int o = 0; o < r->n0; o++, k++) add(1.0 / 3.0, 1.0 / 3.0, r->v[k]);
+  for (int o = 0; o < r->n1; o++, k += 2) {
+    const double a = r->v[k], c = 1.0 - 2.0 * a, wt = r->v[k + 1];
+    add(a, c, wt);  // (l0, l1, l2) = (a, a, c)
+    add(c, a, wt);  // (a, c, a)
+    add(a, a, wt);  // (c, a, a)
+  }
+  for (int o = 0; o < r->n2; o++, k += 3) {
+    const double a = r->v[k], b = r->v[k + 1], c = 1.0 - a - b, wt = r->v[k + 2];
+    const double l[6][3] = {{a, b, c}, {a, c, b}, {b, a, c}, {b, c, a}, {c, a, b}, {c, b, a}};
+    for (int m = 0; m < 6; m++) add(l[m][1], l[m][2], wt);
+  }
+  if ((int)w.size() != ntri_of(p, FEM_RULE_TABLE1)) return false;
+  for (int i = 0; i <= 2 * p; i++)
+    for (int j = 0; i + j <= 2 * p; j++) {
+      long double sum = 0.0L, ex = 1.0L;
+      for (int m = 2; m <= i; m++) ex *= m;
+      for (int m = 2; m <= j; m++) ex *= m;
+      for (int m = 2; m <= i + j + 2; m++) ex /= m;
+      for (size_t q = 0; q < w.size(); q++)
+        sum += (long double)w[q] * std::pow((long double)x[q], i) * std::pow((long double)y[q], j);
+      if (std::fabs((double)(sum / ex - 1.0L)) > 1e-13) return false;
+    }
+  return true;
+}
+
 }  // namespace
 
-bool build_host_rule(int elem, int p, HostRule *out) {
+bool build_host_rule(int elem, int p, HostRule *out, int rule) {
   if (elem == FEM_TET4) {
-    if (p != 1) return false;
+    if (p != 1 || rule != FEM_RULE_COLLAPSED) return false;
     out->nq = 4;
     out->ns = 4;
     // 4-point degree-2 rule: barycentric (al, be, be, be) and permutations
@@ -198,7 +256,8 @@ bool build_host_rule(int elem, int p, HostRule *out) {
     return true;
   }
   if (elem != FEM_PRISM6 || p < 1 || p > kMaxP) return false;
-  const int n = p + 1, nq = n * n * n, ns = ns_of(elem, p);
+  if (rule != FEM_RULE_COLLAPSED && rule != FEM_RULE_TABLE1) return false;
+  const int n = p + 1, nq = nq_of(elem, p, rule), ns = ns_of(elem, p);
   double xa[16], wa[16], xb[16], wb[16];
   gauss_jacobi_gw(n, 0.0, 0.0, xa, wa);
   gauss_jacobi_gw(n, 1.0, 0.0, xb, wb);
@@ -207,6 +266,22 @@ bool build_host_rule(int elem, int p, HostRule *out) {
   out->xi.resize(3 * nq);
   out->w.resize(nq);
   out->phi.resize((size_t)nq * 4 * ns);
+  if (rule == FEM_RULE_TABLE1) {
+    // the paper's prism rule: symmetric triangle rule x Gauss-Legendre in zeta
+    std::vector<double> tx, ty, tw;
+    if (!tri_rule_table1(p, tx, ty, tw)) return false;
+    const int nt = (int)tw.size();
+    for (int iz = 0; iz < n; iz++)
+      for (int it = 0; it < nt; it++) {
+        const int q = iz * nt + it;
+        out->xi[3 * q + 0] = tx[it];
+        out->xi[3 * q + 1] = ty[it];
+        out->xi[3 * q + 2] = xa[iz];
+        out->w[q] = tw[it] * wa[iz];
+        prism_basis_point(p, tx[it], ty[it], xa[iz], &out->phi[(size_t)q * 4 * ns], ns);
+      }
+    return true;
+  }
   int q = 0;
   for (int iz = 0; iz < n; iz++)
     for (int ia = 0; ia < n; ia++)

@@ -38,6 +38,8 @@
 // Every mbarrier wait is bounded (about a second); a CTA whose wait expires
 // sets the library's device error word, marks its elements FEM_ST_TIMEOUT,
 // waits for its own copies and MMAs, frees TMEM and returns.
+#pragma once
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -51,9 +53,9 @@
 
 namespace fem {
 
-template <int P, bool ELAS = false, int LAW = 0>
+template <int P, bool ELAS = false, int LAW = 0, int RULE = FEM_RULE_COLLAPSED>
 struct TcCfg {
-  static constexpr int NS = ns_of(FEM_PRISM6, P), NQ = nq_of(FEM_PRISM6, P);
+  static constexpr int NS = ns_of(FEM_PRISM6, P), NQ = nq_of(FEM_PRISM6, P, RULE);
   static constexpr int L = NS + 1;  // MMA rows per element
   static constexpr int BM = 128;
   static constexpr int KC = 32;     // K per stage: 8 points x 4 derivatives
@@ -79,7 +81,7 @@ struct TcCfg {
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int SBO = (KC / 8) * 128;   // 8-row group stride in a stage tile
   static constexpr int NREC = 18 + (ELAS ? 5 : 11);  // coordinates + coefficients
-  static constexpr int NZ = P + 1, NAB = NZ * NZ;  // tensor-product factors of J per element
+  static constexpr int NZ = P + 1, NAB = ntri_of(P, RULE);  // zeta levels x triangle points (J factors)
   // Each CTA owns a contiguous range of tiles, so consecutive tiles share
   // elements; point records live in a ring of RING element slots (slot =
   // element mod RING) and every element's geometry is computed once per CTA.
@@ -125,7 +127,7 @@ struct TcArgs {
   const double *coeffs;
   int64_t cstride;
   const double *qp;
-  const float *phi32;
+  const float *phiq;     // Phi as [NQ][NS][4] float4 (value + 3 derivatives of function j at point q)
   const uint16_t *img;  // Phi^T hi/lo image per K chunk
   float phimax;         // max |Phi| (FP32 table)
   int aphi;             // power-of-two exponent applied to the image (FP16)
@@ -178,9 +180,9 @@ __device__ __forceinline__ uint32_t split_pack(float x0, float x1, uint32_t &lo_
 // in the geometry warps -- u and grad u from the element's field
 // coefficients, k from the exact law or from the network (its 64x64 layer on
 // warp-level MMAs, the exact law outside its box), D = k I.
-template <int P, bool F16, bool ELAS = false, int LAW = 0>
+template <int P, bool F16, bool ELAS = false, int LAW = 0, int RULE = FEM_RULE_COLLAPSED>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
-  using C = TcCfg<P, ELAS, LAW>;
+  using C = TcCfg<P, ELAS, LAW, RULE>;
   static_assert(LAW == 0 || (!F16 && !ELAS), "the law runs in the BF16 scalar form");
   constexpr int VPE = ELAS ? 9 : 1;  // row blocks (virtual elements) per element
   extern __shared__ unsigned char smem_raw[];
@@ -388,11 +390,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
         for (int qq = 0; qq < QH; qq++) {
           const int q = c * C::QC + half * QH + qq;
           if (arow && q < C::NQ) {
-            const float *ph = a.phi32 + (size_t)(4 * q) * C::NS + j;
-            f[qq][0] = __ldg(ph);
-            f[qq][1] = __ldg(ph + C::NS);
-            f[qq][2] = __ldg(ph + 2 * C::NS);
-            f[qq][3] = __ldg(ph + 3 * C::NS);
+            // one 16-byte load; the rows j of a warp read consecutive float4s
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(a.phiq) + (size_t)q * C::NS + j);
+            f[qq][0] = v.x;
+            f[qq][1] = v.y;
+            f[qq][2] = v.z;
+            f[qq][3] = v.w;
           } else {
             f[qq][0] = f[qq][1] = f[qq][2] = f[qq][3] = 0.f;
           }
@@ -819,12 +822,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
 
 // ---------------------------------------------------------------- host side
 
-template <int P, bool F16, bool ELAS, int LAW = 0>
+template <int P, bool F16, bool ELAS, int LAW = 0, int RULE = FEM_RULE_COLLAPSED>
 static int launch_tc_p(const TcArgs &a, void *stream) {
-  using C = TcCfg<P, ELAS, LAW>;
+  using C = TcCfg<P, ELAS, LAW, RULE>;
   if (a.n == 0) return FEM_OK;
-  cudaError_t err =
-      cudaFuncSetAttribute(tc_kernel<P, F16, ELAS, LAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  cudaError_t err = cudaFuncSetAttribute(tc_kernel<P, F16, ELAS, LAW, RULE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   if (err != cudaSuccess) {
     set_error(std::string("cudaFuncSetAttribute(tc_kernel): ") + cudaGetErrorString(err));
     return FEM_ECUDA;
@@ -836,7 +839,7 @@ static int launch_tc_p(const TcArgs &a, void *stream) {
   const int64_t ntiles = (a.n * (ELAS ? 9 : 1) * C::L + C::BM - 1) / C::BM;
   int64_t grid = nsm;
   if (grid > ntiles) grid = ntiles;
-  tc_kernel<P, F16, ELAS, LAW><<<(unsigned)grid, kTcThreads, C::SMEM, (cudaStream_t)stream>>>(a);
+  tc_kernel<P, F16, ELAS, LAW, RULE><<<(unsigned)grid, kTcThreads, C::SMEM, (cudaStream_t)stream>>>(a);
   err = cudaGetLastError();
   if (err != cudaSuccess) {
     set_error(std::string("tc_kernel launch: ") + cudaGetErrorString(err));
@@ -845,112 +848,25 @@ static int launch_tc_p(const TcArgs &a, void *stream) {
   return FEM_OK;
 }
 
-template <bool F16, bool ELAS, int LAW = 0>
+template <bool F16, bool ELAS, int LAW = 0, int RULE = FEM_RULE_COLLAPSED>
 static int launch_tc_any(int p, const TcArgs &a, void *stream) {
   switch (p) {
-    case 1: return launch_tc_p<1, F16, ELAS, LAW>(a, stream);
-    case 2: return launch_tc_p<2, F16, ELAS, LAW>(a, stream);
-    case 3: return launch_tc_p<3, F16, ELAS, LAW>(a, stream);
-    case 4: return launch_tc_p<4, F16, ELAS, LAW>(a, stream);
-    case 5: return launch_tc_p<5, F16, ELAS, LAW>(a, stream);
-    case 6: return launch_tc_p<6, F16, ELAS, LAW>(a, stream);
-    case 7: return launch_tc_p<7, F16, ELAS, LAW>(a, stream);
+    case 1: return launch_tc_p<1, F16, ELAS, LAW, RULE>(a, stream);
+    case 2: return launch_tc_p<2, F16, ELAS, LAW, RULE>(a, stream);
+    case 3: return launch_tc_p<3, F16, ELAS, LAW, RULE>(a, stream);
+    case 4: return launch_tc_p<4, F16, ELAS, LAW, RULE>(a, stream);
+    case 5: return launch_tc_p<5, F16, ELAS, LAW, RULE>(a, stream);
+    case 6: return launch_tc_p<6, F16, ELAS, LAW, RULE>(a, stream);
+    case 7: return launch_tc_p<7, F16, ELAS, LAW, RULE>(a, stream);
   }
   return FEM_EINVAL;
 }
 
-int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *stream) {
-  TcArgs a;
-  a.n = l.n;
-  a.coords = l.coords;
-  a.coeffs = l.coeffs;
-  a.cstride = l.cstride;
-  a.qp = d.qp;
-  a.phi32 = d.phi32;
-  a.img = f16 ? d.img_f16 : d.img_bf16;
-  a.phimax = d.phimax;
-  a.aphi = f16 ? d.aphi_f16 : 0;
-  a.A = l.A;
-  a.b = l.b;
-  a.status = l.status;
-  a.layout = l.layout;
-  a.err = l.err;
-  a.stall = l.stall;
-  a.perm = l.perm;
-  a.offA = l.offA;
-  a.offb = l.offb;
-  a.ucoef = l.ucoef;
-  a.phiT = d.phiT32;
-  a.mlpw = l.mlpw;
-  a.mlpw2 = l.mlpw2;
-  for (int i = 0; i < 4; i++) {
-    a.nrm[i] = l.nrm[i];
-    a.box[i] = l.box[i];
-  }
-  if (l.elastic && (a.perm || a.offA || a.offb)) {
-    set_error("tensor-core elasticity takes dense outputs only");
-    return FEM_EINVAL;
-  }
-  if (!a.img) {
-    set_error("tensor-core tables missing for this degree");
-    return FEM_EUNSUPPORTED;
-  }
-  if (l.elastic) return f16 ? launch_tc_any<true, true>(p, a, stream) : launch_tc_any<false, true>(p, a, stream);
-  if (l.law != 0) {
-    if (f16 || !a.ucoef || (l.law == 2 && (!a.mlpw || !a.mlpw2))) {
-      set_error("tensor-core law integration: BF16x3 with field coefficients (and a network) only");
-      return FEM_EINVAL;
-    }
-    return l.law == 1 ? launch_tc_any<false, false, 1>(p, a, stream) : launch_tc_any<false, false, 2>(p, a, stream);
-  }
-  return f16 ? launch_tc_any<true, false>(p, a, stream) : launch_tc_any<false, false>(p, a, stream);
-}
-
-// Image of Phi^T for the B operand: per K chunk of 32, [hi | lo] blocks of
-// NP x 32 16-bit values in the canonical K-major core-matrix layout
-// (8 rows x 8 values = 128 bytes per core matrix; K-adjacent core matrices
-// 128 bytes apart, 8-row groups (KC/8)*128 bytes apart).  Rows i >= NS and
-// k >= 4 NQ are zero.
-template <int P>
-static void build_image_p(const std::vector<double> &phi, bool f16, int aphi, std::vector<uint16_t> &out) {
-  using C = TcCfg<P>;
-  out.assign((size_t)C::NCH * 2 * C::NP * C::KC, 0);
-  const double scale = std::ldexp(1.0, aphi);
-  for (int c = 0; c < C::NCH; c++) {
-    uint16_t *hi = out.data() + (size_t)c * 2 * C::NP * C::KC;
-    uint16_t *lo = hi + (size_t)C::NP * C::KC;
-    for (int i = 0; i < C::NS; i++)
-      for (int kl = 0; kl < C::KC; kl++) {
-        const int k = c * C::KC + kl;
-        if (k >= 4 * C::NQ) continue;
-        const double x = phi[(size_t)k * C::NS + i] * scale;
-        uint16_t h, l;
-        if (f16) {
-          __half hh = __double2half((double)x);
-          h = __half_as_ushort(hh);
-          l = __half_as_ushort(__double2half(x - (double)__half2float(hh)));
-        } else {
-          __nv_bfloat16 hh = __double2bfloat16(x);
-          h = __bfloat16_as_ushort(hh);
-          l = __bfloat16_as_ushort(__double2bfloat16(x - (double)__bfloat162float(hh)));
-        }
-        const size_t off = ((size_t)(i >> 3) * (C::KC / 8) + (kl >> 3)) * 64 + (i & 7) * 8 + (kl & 7);
-        hi[off] = h;
-        lo[off] = l;
-      }
-  }
-}
-
-void build_tc_image(int p, const std::vector<double> &phi, bool f16, int aphi, std::vector<uint16_t> &out) {
-  switch (p) {
-    case 1: build_image_p<1>(phi, f16, aphi, out); break;
-    case 2: build_image_p<2>(phi, f16, aphi, out); break;
-    case 3: build_image_p<3>(phi, f16, aphi, out); break;
-    case 4: build_image_p<4>(phi, f16, aphi, out); break;
-    case 5: build_image_p<5>(phi, f16, aphi, out); break;
-    case 6: build_image_p<6>(phi, f16, aphi, out); break;
-    case 7: build_image_p<7>(phi, f16, aphi, out); break;
-  }
-}
+// Per-TU instantiations (fem_tc_*.cu), dispatched by launch_tc (fem_tc.cu).
+int launch_tc_scalar_bf16(int p, const TcArgs &a, void *stream);
+int launch_tc_scalar_f16(int p, const TcArgs &a, void *stream);
+int launch_tc_scalar_t1(int p, bool f16, const TcArgs &a, void *stream);
+int launch_tc_elastic(int p, bool f16, const TcArgs &a, void *stream);
+int launch_tc_law(int p, int law, const TcArgs &a, void *stream);
 
 }  // namespace fem

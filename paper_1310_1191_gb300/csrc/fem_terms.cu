@@ -115,6 +115,7 @@ using namespace fem;
 
 extern "C" int fem_jacobian_terms(fem_tables t, int p, int64_t n_elem, const double *coords, double *terms,
                                   int32_t *status, void *stream) {
+  if (rule_check(t, "fem_jacobian_terms") != FEM_OK) return FEM_EUNSUPPORTED;
   if (!t) {
     set_error("fem_jacobian_terms: tables handle is NULL");
     return FEM_EINVAL;

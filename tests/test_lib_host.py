@@ -49,6 +49,26 @@ def test_prism_tables_match_oracle(lib, orc, p):
     assert np.max(np.abs(phi - ophi) / scale) < 1e-14
 
 
+@pytest.mark.parametrize("p", range(1, 8))
+def test_table1_prism_rule_matches_oracle(lib, orc, p):
+    """The paper's prism rule (Table 1 point counts): the library's triangle
+    rules (tri_rules_gen.cpp: continuation on the symmetric invariants e2, e3
+    in its own parameters) and the oracle's (its own search on the monomial
+    moments) are the same point set with the same weights, in the same order;
+    the tables' shape functions at those points agree.  The orbit parameters
+    of the degree-14 rule are determined by its moments only to about 1e-13
+    (the system's condition number times the rounding of the moments), hence
+    the tolerances."""
+    xi, w, phi = lib.fem_reference_rule_ex(lib.FEM_PRISM6, lib.FEM_RULE_TABLE1, p)
+    oxi, ow = orc.rule(orc.PRISM_T1, p)
+    assert xi.shape == oxi.shape
+    assert np.max(np.abs(xi - oxi)) < 1e-12
+    assert np.max(np.abs(w - ow) / ow) < 1e-11
+    ophi = orc.basis(1, p, oxi)
+    scale = np.abs(ophi).max(axis=(0, 2), keepdims=True)
+    assert np.max(np.abs(phi - ophi) / scale) < 1e-11
+
+
 def test_tet_tables_match_oracle(lib, orc):
     xi, w, phi = lib.fem_reference_rule(lib.FEM_TET4, 1)
     oxi, ow = orc.rule(0, 1)
@@ -104,6 +124,13 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert rc == lib.FEM_EINVAL and "tables" in lib.last_error()
     rc = so.fem_apply(None, 2, 10, 8, 8, 10, lib.FEM_F64, 8, 16, None, None)
     assert rc == lib.FEM_EINVAL and "tables" in lib.last_error()
+    # unknown rule, or the paper's rule on tetrahedra
+    with pytest.raises(lib.FemError) as ei:
+        lib.fem_reference_rule_ex(lib.FEM_PRISM6, 5, 2)
+    assert ei.value.code == lib.FEM_EINVAL
+    with pytest.raises(lib.FemError) as ei:
+        lib.fem_reference_rule_ex(lib.FEM_TET4, lib.FEM_RULE_TABLE1, 1)
+    assert ei.value.code == lib.FEM_EINVAL
     # bad degree range for the builder
     h = ctypes.c_void_p()
     assert so.fem_tables_build(lib.FEM_PRISM6, 3, 2, ctypes.byref(h)) == lib.FEM_EINVAL
