@@ -753,6 +753,30 @@ def wl_surrogate(lib, tables, stream, dev, reps, E=1000000):
         if name.startswith("network"):
             row["fallback_elements"] = int(((st & 8) != 0).sum().item())
         res[name] = row
+    # the law's cost against the network's: the exact law with more Newton
+    # steps (k unchanged once converged), and the network with the hardware
+    # tanh approximation; the crossover is the step count at which the
+    # exact law costs as much as the network (linear in the steps)
+    for prec, tag in ((1, ""), (lib.FEM_BF16X3, "_bf16x3")):
+        steps_ms = {8: res["exact_law" + tag]["ms"]}
+        for steps in (16, 32):
+            law = lib.coef_law(lib.FEM_LAW_EXACT, Ud, newton_steps=steps)
+            ms = _timed(stream, lambda: lib.fem_integrate(tables, E, Xd, None, p, Cd, E, law, prec, 0, A, b, st,
+                                                          stream), reps)
+            steps_ms[steps] = ms
+            res["exact_law_newton%d%s" % (steps, tag)] = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3}
+        law = lib.coef_law(lib.FEM_LAW_MLP, Ud, m, hw_tanh=True)
+        ms = _timed(stream, lambda: lib.fem_integrate(tables, E, Xd, None, p, Cd, E, law, prec, 0, A, b, st, stream),
+                    reps)
+        err = ((A[:S].double().view(S, NS, NS) - ref).flatten(1).norm(dim=1) /
+               ref.flatten(1).norm(dim=1)).cpu().numpy()
+        res["network_hw_tanh" + tag] = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3,
+                                        "err_max": float(err.max()), "err_median": float(np.median(err))}
+        slope = (steps_ms[32] - steps_ms[8]) / 24.0  # ms per Newton step
+        for net in ("network", "network_hw_tanh"):
+            t_net = res[net + tag]["ms"]
+            res["crossover_newton_steps_" + net + tag] = (round(8 + (t_net - steps_ms[8]) / slope, 1)
+                                                          if slope > 0 else None)
     m.close()
     return {"workload": "1000000 prisms p=3, FP32, D = k(u, |grad u|) I per point, 40 field "
                         "coefficients per element", "box": [float(x) for x in box],

@@ -111,15 +111,24 @@ int fem_tables_destroy(fem_tables t);
  * quadrature point computed from the previous solution's degrees of freedom
  * (Section 2: the coefficients may depend on the old solution; the law and
  * the network are described with fem_integrate_law below).
- *   law   : 0 constant coefficients (the rows of coeffs as given),
- *           FEM_LAW_EXACT or FEM_LAW_MLP;
- *   ucoef : device float [n_elem][NS], the field's coefficients per element;
- *   mlp   : the network for FEM_LAW_MLP, else NULL. */
+ *   law          : 0 constant coefficients (the rows of coeffs as given),
+ *                  FEM_LAW_EXACT or FEM_LAW_MLP;
+ *   ucoef        : device float [n_elem][NS], the field's coefficients per element;
+ *   mlp          : the network for FEM_LAW_MLP, else NULL;
+ *   newton_steps : Newton steps of the exact law (0: the law's 8; up to 1024
+ *                  -- more steps leave k unchanged once converged and only
+ *                  make the law costlier, to compare its cost with the
+ *                  network's);
+ *   hw_tanh      : non-zero: the network's activations from the hardware
+ *                  approximation tanh.approx.f32 (one special-function
+ *                  operation instead of two, larger error). */
 typedef struct fem_mlp_s *fem_mlp;
 typedef struct fem_coef_law_s {
   int law;
   const float *ucoef;
   fem_mlp mlp;
+  int newton_steps;
+  int hw_tanh;
 } fem_coef_law;
 
 /* Per-element integration (Section 2; Algorithms 3/4 of Section 4.1 and the

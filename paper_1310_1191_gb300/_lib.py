@@ -203,13 +203,16 @@ def fem_tables_destroy(t: Tables) -> None:
 
 
 class CoefLaw(ctypes.Structure):
-    """fem_coef_law: law (0, FEM_LAW_EXACT, FEM_LAW_MLP), ucoef, mlp."""
-    _fields_ = [("law", ctypes.c_int), ("ucoef", ctypes.c_void_p), ("mlp", ctypes.c_void_p)]
+    """fem_coef_law: law (0, FEM_LAW_EXACT, FEM_LAW_MLP), ucoef, mlp,
+    newton_steps (0: 8), hw_tanh."""
+    _fields_ = [("law", ctypes.c_int), ("ucoef", ctypes.c_void_p), ("mlp", ctypes.c_void_p),
+                ("newton_steps", ctypes.c_int), ("hw_tanh", ctypes.c_int)]
 
 
-def coef_law(law: int, ucoef=None, mlp=None) -> CoefLaw:
+def coef_law(law: int, ucoef=None, mlp=None, newton_steps: int = 0, hw_tanh: bool = False) -> CoefLaw:
     """A coefficient law for fem_integrate (ucoef: device float [n][NS])."""
-    c = CoefLaw(law, _addr(ucoef), mlp.handle.value if mlp is not None else None)
+    c = CoefLaw(law, _addr(ucoef), mlp.handle.value if mlp is not None else None, newton_steps,
+                1 if hw_tanh else 0)
     c._keep = (ucoef, mlp)  # the buffers must outlive the call
     return c
 

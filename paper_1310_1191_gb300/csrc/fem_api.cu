@@ -269,8 +269,9 @@ int fem_integrate(fem_tables t, int64_t n_elem, const double *coords, const int8
     if (lw == 0)
       return fem_integrate_uniform(t, p_uniform, n_elem, coords, coeffs, coeff_stride, prec, layout, A_out, b_out,
                                    status, stream);
-    return fem_integrate_law(t, p_uniform, n_elem, coords, coeffs, coeff_stride, law->ucoef, lw, law->mlp, prec,
-                             layout, A_out, b_out, status, stream);
+    return integrate_law_opts(t, p_uniform, n_elem, coords, coeffs, coeff_stride, law->ucoef, lw, law->mlp,
+                              law->newton_steps > 0 ? law->newton_steps : 8, law->hw_tanh, prec, layout, A_out,
+                              b_out, status, stream);
   }
   if (lw != 0) {
     set_error("fem_integrate: a coefficient law needs a uniform degree (p_per_elem = NULL)");

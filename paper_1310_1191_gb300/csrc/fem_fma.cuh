@@ -340,7 +340,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
       const float gg = gx * gx + gy * gy + gz * gz;
       float kq = 1.f;
       if (LAW == 1) {
-        kq = law_exact<float>(u, gg);
+        kq = law_exact<float>(u, gg, a.law_iters);
       } else {
         const float sf = sqrtf(gg);
         if (u >= a.box[0] && u <= a.box[1] && sf >= a.box[2] && sf <= a.box[3]) {
@@ -348,7 +348,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
           sNet[2 * idx] = fmaf(u, a.nrm[0], a.nrm[1]);
           sNet[2 * idx + 1] = fmaf(logf(sf), a.nrm[2], a.nrm[3]);
         } else {
-          kq = law_exact<float>(u, gg);
+          kq = law_exact<float>(u, gg, a.law_iters);
           st |= FEM_ST_FALLBACK;
         }
       }
@@ -385,7 +385,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
       const T gg = (T)(gx * gx + gy * gy + gz * gz);
       T kq = (T)1;
       if (LAW == 1) {
-        kq = law_exact<T>(u, gg);
+        kq = law_exact<T>(u, gg, a.law_iters);
       } else {
         // inside the box the network gives k after this stage (the record is
         // built with k = 1 and its diffusion block scaled then); outside, the
@@ -396,7 +396,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
           sNet[2 * idx] = fmaf(uf, a.nrm[0], a.nrm[1]);
           sNet[2 * idx + 1] = fmaf(logf(sf), a.nrm[2], a.nrm[3]);
         } else {
-          kq = law_exact<T>(u, gg);
+          kq = law_exact<T>(u, gg, a.law_iters);
           st |= FEM_ST_FALLBACK;
         }
       }
@@ -426,7 +426,8 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
           T *r = sG + (size_t)pt * kGStride;
 #pragma unroll
           for (int m = G11; m <= G33; m++) r[m] *= (T)k;
-        });
+        },
+        -1, 0, a.hw_tanh != 0);
     __syncthreads();
   }
 

@@ -137,6 +137,8 @@ struct FmaArgs {
   const uint32_t *mlpw2 = nullptr;  // the network's W2 as BF16 pairs, [H][H/2] words
   float nrm[4] = {0, 0, 0, 0};   // input normalisation of the network
   float box[4] = {0, 0, 0, 0};   // u0, u1, s0, s1 (network used inside)
+  int law_iters = 8;             // Newton steps of the exact law
+  int hw_tanh = 0;               // network activations from tanh.approx.f32
 };
 
 // fem_integrate with per-element degrees: runs (and keeps in t) a per-degree
@@ -185,8 +187,15 @@ struct TcLaunch {
   const uint32_t *mlpw2 = nullptr;
   float nrm[4] = {0, 0, 0, 0};
   float box[4] = {0, 0, 0, 0};
+  int law_iters = 8;
+  int hw_tanh = 0;
 };
 int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *stream);
+
+// fem_integrate_law with the law's options (Newton steps, hardware tanh)
+int integrate_law_opts(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
+                       int64_t coeff_stride, const float *ucoef, int law, fem_mlp mlp, int newton_steps,
+                       int hw_tanh, int prec, int layout, void *A_out, void *b_out, int32_t *status, void *stream);
 
 // Matrix-free element-operator apply y_e = A_e x_e (constant coefficients).
 struct ApplyArgs {

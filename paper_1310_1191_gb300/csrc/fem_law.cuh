@@ -22,15 +22,17 @@ constexpr int kMlpH = 64;
 __host__ __device__ constexpr int mlp_nparams(int H) { return 2 * H + H + H * H + H + H + 1; }
 constexpr int kMlpP = mlp_nparams(kMlpH);  // 4481
 
+// iters: Newton steps (the law's 8; more only to make the law costlier when
+// its cost is compared with the surrogate's)
 template <class R>
-__device__ __forceinline__ R law_exact(R u, R g);
+__device__ __forceinline__ R law_exact(R u, R g, int iters = 8);
 
 template <>
-__device__ __forceinline__ float law_exact<float>(float u, float g) {
+__device__ __forceinline__ float law_exact<float>(float u, float g, int iters) {
   const float e = 0.5f * expf(-u * u);
   float k = 1.f + e;
-#pragma unroll
-  for (int it = 0; it < 8; it++) {
+#pragma unroll 8
+  for (int it = 0; it < iters; it++) {
     const float kg1 = 1.f + k * g;
     const float F = k - 1.f - e - 0.2f * logf(kg1);
     const float Fp = 1.f - 0.2f * g / kg1;
@@ -40,11 +42,11 @@ __device__ __forceinline__ float law_exact<float>(float u, float g) {
 }
 
 template <>
-__device__ __forceinline__ double law_exact<double>(double u, double g) {
+__device__ __forceinline__ double law_exact<double>(double u, double g, int iters) {
   const double e = 0.5 * exp(-u * u);
   double k = 1.0 + e;
-#pragma unroll
-  for (int it = 0; it < 8; it++) {
+#pragma unroll 8
+  for (int it = 0; it < iters; it++) {
     const double kg1 = 1.0 + k * g;
     const double F = k - 1.0 - e - 0.2 * log(kg1);
     const double Fp = 1.0 - 0.2 * g / kg1;
@@ -93,6 +95,15 @@ __device__ __forceinline__ float tanh_fast(float x) {
   return fmaf(-2.f, r, 1.f);
 }
 
+// tanh as the single hardware approximation tanh.approx.f32 (one MUFU
+// operation instead of two; a larger error than tanh_fast, measured against
+// the oracle's network in the tests)
+__device__ __forceinline__ float tanh_hw(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // D (16x8, FP32) += A (16x16, BF16, row-major) * B (16x8, BF16, column-major),
 // one warp (PTX mma.sync m16n8k16; fragment layout of the PTX ISA).
 __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
@@ -127,9 +138,12 @@ constexpr int kMlpSmemBytes = kMlpSmall * 4 + kMlpH * kW2Stride * 2;
 // [npts][2]; pending(p) -> whether point p uses the network; apply(p, k)
 // consumes its output.  warp / nwarp: this warp's index among the nwarp
 // whole warps that share the points (negative: all whole warps of the block).
+// hw: tanh from tanh_hw instead of tanh_fast.
 template <class Pending, class Apply>
 __device__ __forceinline__ void mlp_points_mma(const float *sp, const uint32_t *w2, const float *xin, int npts,
-                                               Pending pending, Apply apply, int warp = -1, int nwarp = 0) {
+                                               Pending pending, Apply apply, int warp = -1, int nwarp = 0,
+                                               bool hw = false) {
+  auto act = [hw](float x) { return hw ? tanh_hw(x) : tanh_fast(x); };
   constexpr int H = kMlpH;
   const float *W1 = sp, *b1 = W1 + 2 * H, *b2 = b1 + H, *W3 = b2 + H;
   const float b3 = W3[H];
@@ -154,10 +168,10 @@ __device__ __forceinline__ void mlp_points_mma(const float *sp, const uint32_t *
         const int n = ks * 16 + hh * 8 + 2 * t4;  // neurons n, n + 1 (K columns of the A fragment)
         const float wa0 = W1[2 * n], wa1 = W1[2 * n + 1], wb0 = W1[2 * n + 2], wb1 = W1[2 * n + 3];
         const float ca = b1[n], cb = b1[n + 1];
-        const float h00 = tanh_fast(fmaf(wa0, x00, fmaf(wa1, x01, ca)));
-        const float h01 = tanh_fast(fmaf(wb0, x00, fmaf(wb1, x01, cb)));
-        const float h10 = tanh_fast(fmaf(wa0, x10, fmaf(wa1, x11, ca)));
-        const float h11 = tanh_fast(fmaf(wb0, x10, fmaf(wb1, x11, cb)));
+        const float h00 = act(fmaf(wa0, x00, fmaf(wa1, x01, ca)));
+        const float h01 = act(fmaf(wb0, x00, fmaf(wb1, x01, cb)));
+        const float h10 = act(fmaf(wa0, x10, fmaf(wa1, x11, ca)));
+        const float h11 = act(fmaf(wb0, x10, fmaf(wb1, x11, cb)));
         ah[ks][2 * hh] = bf16x2_split(h00, h01, al[ks][2 * hh]);          // row g
         ah[ks][2 * hh + 1] = bf16x2_split(h10, h11, al[ks][2 * hh + 1]);  // row g + 8
       }
@@ -178,10 +192,10 @@ __device__ __forceinline__ void mlp_points_mma(const float *sp, const uint32_t *
 #pragma unroll
     for (int nt = 0; nt < 8; nt++) {
       const int n = nt * 8 + 2 * t4;
-      y0 = fmaf(W3[n], tanh_fast(acc[nt][0] + b2[n]), y0);
-      y0 = fmaf(W3[n + 1], tanh_fast(acc[nt][1] + b2[n + 1]), y0);
-      y1 = fmaf(W3[n], tanh_fast(acc[nt][2] + b2[n]), y1);
-      y1 = fmaf(W3[n + 1], tanh_fast(acc[nt][3] + b2[n + 1]), y1);
+      y0 = fmaf(W3[n], act(acc[nt][0] + b2[n]), y0);
+      y0 = fmaf(W3[n + 1], act(acc[nt][1] + b2[n + 1]), y0);
+      y1 = fmaf(W3[n], act(acc[nt][2] + b2[n]), y1);
+      y1 = fmaf(W3[n + 1], act(acc[nt][3] + b2[n + 1]), y1);
     }
     y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
     y0 += __shfl_xor_sync(0xffffffffu, y0, 2);

@@ -591,7 +591,22 @@ int fem_mlp_load(const char *path, fem_mlp *out) {
 int fem_integrate_law(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
                       int64_t coeff_stride, const float *ucoef, int law, fem_mlp mlp, int prec, int layout,
                       void *A_out, void *b_out, int32_t *status, void *stream) {
+  return integrate_law_opts(t, p, n_elem, coords, coeffs, coeff_stride, ucoef, law, mlp, 8, 0, prec, layout, A_out,
+                            b_out, status, stream);
+}
+
+}  // extern "C"
+
+namespace fem {
+
+int integrate_law_opts(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
+                       int64_t coeff_stride, const float *ucoef, int law, fem_mlp mlp, int newton_steps,
+                       int hw_tanh, int prec, int layout, void *A_out, void *b_out, int32_t *status, void *stream) {
   if (rule_check(t, "fem_integrate_law") != FEM_OK) return FEM_EUNSUPPORTED;
+  if (newton_steps < 1 || newton_steps > 1024) {
+    set_error("fem_integrate_law: Newton steps must be in 1..1024");
+    return FEM_EINVAL;
+  }
   if (!t) {
     set_error("fem_integrate_law: tables handle is NULL");
     return FEM_EINVAL;
@@ -644,6 +659,8 @@ int fem_integrate_law(fem_tables t, int p, int64_t n_elem, const double *coords,
     l.stall = 0;
     l.law = law;
     l.ucoef = ucoef;
+    l.law_iters = newton_steps;
+    l.hw_tanh = hw_tanh;
     if (law == FEM_LAW_MLP) {
       l.mlpw = mlp->wc;
       l.mlpw2 = mlp->w2img;
@@ -667,6 +684,8 @@ int fem_integrate_law(fem_tables t, int p, int64_t n_elem, const double *coords,
   a.status = status;
   a.layout = layout;
   a.ucoef = ucoef;
+  a.law_iters = newton_steps;
+  a.hw_tanh = hw_tanh;
   if (law == FEM_LAW_MLP) {
     a.mlpw2 = mlp->w2img;
     a.mlpw = mlp->wc;
@@ -679,4 +698,4 @@ int fem_integrate_law(fem_tables t, int p, int64_t n_elem, const double *coords,
                          : launch_fma_law_f32(t->elem, p, law, a, stream);
 }
 
-}  // extern "C"
+}  // namespace fem

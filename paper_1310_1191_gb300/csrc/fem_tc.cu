@@ -34,6 +34,8 @@ int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *strea
     a.nrm[i] = l.nrm[i];
     a.box[i] = l.box[i];
   }
+  a.law_iters = l.law_iters;
+  a.hw_tanh = l.hw_tanh;
   if (l.elastic && (a.perm || a.offA || a.offb)) {
     set_error("tensor-core elasticity takes dense outputs only");
     return FEM_EINVAL;

@@ -149,6 +149,8 @@ struct TcArgs {
   const float *mlpw;      // network parameters (FP32 values of BF16 weights)
   const uint32_t *mlpw2;  // its W2 as BF16 pairs
   float nrm[4], box[4];
+  int law_iters;  // Newton steps of the exact law
+  int hw_tanh;    // network activations from tanh.approx.f32
 };
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
@@ -624,7 +626,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                 float kq = 1.f;
                 bool pend = false;
                 if (LAW == 1) {
-                  kq = law_exact<float>(u, gg);
+                  kq = law_exact<float>(u, gg, a.law_iters);
                 } else {
                   const float sf = sqrtf(gg);
                   if (u >= a.box[0] && u <= a.box[1] && sf >= a.box[2] && sf <= a.box[3]) {
@@ -632,7 +634,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                     sXin[2 * idx] = fmaf(u, a.nrm[0], a.nrm[1]);
                     sXin[2 * idx + 1] = fmaf(logf(sf), a.nrm[2], a.nrm[3]);
                   } else {
-                    kq = law_exact<float>(u, gg);
+                    kq = law_exact<float>(u, gg, a.law_iters);
                     atomicOr(&sSt[sl], FEM_ST_FALLBACK);
                   }
                 }
@@ -689,7 +691,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
 #pragma unroll
                   for (int m = G11; m <= G33; m++) r[m] *= k;
                 },
-                gt >> 5, kNGeo / 32);
+                gt >> 5, kNGeo / 32, a.hw_tanh != 0);
           }
           gbar();
         }

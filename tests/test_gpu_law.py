@@ -250,6 +250,70 @@ def test_tensor_core_network_vs_oracle(orc, lib, tables):
         m.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_law_more_newton_steps_converged(orc, lib, tables, prec):
+    """The exact law with 16 and 32 Newton steps through fem_integrate's law
+    descriptor: 8 steps have converged (residual <= 1e-12, pinned on the CPU),
+    so the element matrices match the oracle's 8-step law within the
+    precision's tolerance."""
+    import torch
+    E = 30
+    X = inputs.prism_mesh(E)
+    C = inputs.coefficients(E)
+    U = _field(E, NS3)
+    dt = torch.float64 if prec == 0 else torch.float32
+    RA, _, Rst = orc.integrate(PRISM, P3, X, C, law=1, ucoef=U.astype(np.float64))
+    tol = {0: 1e-12, 1: 1e-5, 2: TOL_TC}[prec]
+    for steps in (16, 32):
+        A = torch.empty((E, NS3 * NS3), dtype=dt, device="cuda")
+        st = torch.empty(E, dtype=torch.int32, device="cuda")
+        law = lib.coef_law(lib.FEM_LAW_EXACT, torch.from_numpy(U).cuda(), newton_steps=steps)
+        lib.fem_integrate(tables, E, torch.from_numpy(X).cuda(), None, P3, torch.from_numpy(C).cuda(), E, law, prec,
+                          0, A, None, st)
+        torch.cuda.synchronize()
+        assert rel_frob(A.double().cpu().numpy().reshape(E, NS3, NS3), RA).max() <= tol, steps
+        assert np.array_equal(st.cpu().numpy(), Rst)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_network_hardware_tanh_within_its_bound(orc, lib, tables, prec):
+    """The network with tanh.approx.f32 activations against the oracle's
+    network (FP64, exact tanh).  With an activation error of at most eps
+    the output moves by at most sum_n |W3_n| (1 + sum_m |W2_nm|) eps, so the
+    element matrices (linear in k in their diffusion part) move by at most
+    that over the smallest k, plus the kernel's own tolerance; eps = 2^-10.5
+    is taken as the approximation's bound."""
+    import torch
+    E = 40
+    X = inputs.prism_mesh(E)
+    C = inputs.coefficients(E)
+    U = _field(E, NS3)
+    box = np.array([-1e3, 1e3, 1e-3, 1e6])
+    m = lib.fem_mlp_create(box, 11)
+    _, wc, _ = m.params()
+    H = 64
+    W2 = wc[3 * H:3 * H + H * H].reshape(H, H)
+    W3 = wc[3 * H + H * H + H:3 * H + H * H + 2 * H]
+    eps = 2.0 ** -10.5
+    dk = float(np.sum(np.abs(W3) * (1.0 + np.abs(W2).sum(1)))) * eps
+    dt = torch.float32
+    A = torch.empty((E, NS3 * NS3), dtype=dt, device="cuda")
+    st = torch.empty(E, dtype=torch.int32, device="cuda")
+    law = lib.coef_law(lib.FEM_LAW_MLP, torch.from_numpy(U).cuda(), m, hw_tanh=True)
+    lib.fem_integrate(tables, E, torch.from_numpy(X).cuda(), None, P3, torch.from_numpy(C).cuda(), E, law, prec, 0,
+                      A, None, st)
+    torch.cuda.synchronize()
+    RA, _, Rst = orc.integrate(PRISM, P3, X, C, law=2, ucoef=U.astype(np.float64),
+                               mlp=(64, wc.astype(np.float64), box))
+    _, _, kref, _ = orc.point_law(PRISM, P3, X, U.astype(np.float64), law=2, mlp=(64, wc.astype(np.float64), box))
+    bound = dk / np.abs(kref).min() + (1e-5 if prec == 1 else TOL_TC)
+    err = rel_frob(A.cpu().numpy().reshape(E, NS3, NS3), RA)
+    print("hardware tanh, prec %d: max %.2e (bound %.2e)" % (prec, err.max(), bound))
+    assert err.max() <= bound
+    assert np.array_equal(st.cpu().numpy(), Rst)
+    m.close()
+
+
 @pytest.mark.slow
 def test_surrogate_gain_measured(orc, lib, tables):
     """What the trained network gains over the exact law on the nonlinear
@@ -278,8 +342,12 @@ def test_surrogate_gain_measured(orc, lib, tables):
     times, errs = {}, {}
     idx = np.arange(0, E, E // 48)[:48]
     RA, _, _ = orc.integrate(PRISM, P3, X[idx], C[:, idx], law=1, ucoef=U[idx].astype(np.float64))
-    for name, law, mm in (("exact", lib.FEM_LAW_EXACT, None), ("network", lib.FEM_LAW_MLP, m)):
-        run = lambda: lib.fem_integrate_law(tables, P3, E, Xd, Cd, E, Ud, law, mm, 1, 0, A, None, st)
+    for name, law, mm, steps, hw in (("exact", lib.FEM_LAW_EXACT, None, 8, False),
+                                     ("exact32", lib.FEM_LAW_EXACT, None, 32, False),
+                                     ("network", lib.FEM_LAW_MLP, m, 0, False),
+                                     ("network_hw", lib.FEM_LAW_MLP, m, 0, True)):
+        cl = lib.coef_law(law, Ud, mm, newton_steps=steps, hw_tanh=hw)
+        run = lambda: lib.fem_integrate(tables, E, Xd, None, P3, Cd, E, cl, 1, 0, A, None, st)
         run()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -296,6 +364,11 @@ def test_surrogate_gain_measured(orc, lib, tables):
           "time ratio network/exact %.2f | fallback elements %.1f%%"
           % (times["exact"], errs["exact"].max(), times["network"], errs["network"].max(),
              np.median(errs["network"]), times["network"] / times["exact"], 100.0 * fb / E))
-    assert errs["exact"].max() <= 1e-5
-    assert errs["network"].max() <= 5e-3
+    slope = (times["exact32"] - times["exact"]) / 24.0
+    for net in ("network", "network_hw"):
+        cross = 8 + (times[net] - times["exact"]) / slope if slope > 0 else float("inf")
+        print("%s: %.2f ms, err max %.2e; the exact law costs as much at about %.0f Newton steps"
+              % (net, times[net], errs[net].max(), cross))
+    assert errs["exact"].max() <= 1e-5 and errs["exact32"].max() <= 1e-5
+    assert errs["network"].max() <= 5e-3 and errs["network_hw"].max() <= 5e-3
     m.close()
