@@ -612,10 +612,33 @@ def wl_table1(lib, stream, dev, reps, fma, hbm, bf16_peak, scale_down=1, degrees
             del A, b
         out[str(p)] = row
         torch.cuda.empty_cache()
+    # the paper's model problem with its own rule: linear elastostatics, about
+    # 2 GB of FP64 output per degree; GFLOP/s also in the paper's count (63
+    # flops per 3x3 block and point, 63 N_Q NS^2 per element)
+    el = {}
+    for p in degrees:
+        n, q = ns_of(p), (p + 1) * NTRI_TABLE1[p]
+        E = max(1, round(2e9 / (8 * (9 * n * n + 3 * n))) // scale_down)
+        X, C = inputs.prism_mesh(E), inputs.elastic_coefficients(E)
+        Xd, Cd = torch.from_numpy(X).to(dev), torch.from_numpy(C).to(dev)
+        row = {"elements": E, "nq": q}
+        for name, prec, dt in (("f64", lib.FEM_F64, torch.float64), ("f32", lib.FEM_F32, torch.float32),
+                               ("bf16x3", lib.FEM_BF16X3, torch.float32)):
+            A = torch.empty((E, 9 * n * n), dtype=dt, device=dev)
+            b = torch.empty((E, 3 * n), dtype=dt, device=dev)
+            ms = _timed(stream, lambda: lib.fem_integrate_elastic(t1, p, E, Xd, Cd, E, prec, A, b, None, stream),
+                        reps)
+            row[name] = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3,
+                         "tflops": round(9 * 6.0 * q * n * n * E / ms / 1e9, 3),
+                         "paper_count_gflops": round(63.0 * q * n * n * E / ms / 1e6, 1)}
+            del A, b
+        el[str(p)] = row
+        torch.cuda.empty_cache()
     t1.close()
     return {"workload": "prism degree sweep with the paper's rules (Table 1 N_Q = 6, 18, 48, 80, 150, 231, 336), "
-                        "same element counts, coefficients and outputs as the headline sweep",
-            "per_degree": out}
+                        "same element counts, coefficients and outputs as the headline sweep; and linear "
+                        "elastostatics with that rule (about 2 GB of FP64 output per degree)",
+            "per_degree": out, "elasticity": el}
 
 
 def wl_split(lib, tables, stream, dev, reps, scale_down=1, degrees=range(1, 8)):

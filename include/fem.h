@@ -101,8 +101,9 @@ int fem_reference_rule_ex(int elem, int rule, int p, int *nq, int *ns, double *x
 int fem_tables_build(int elem, int p_min, int p_max, fem_tables *out);
 /* fem_tables_build for a chosen prism quadrature rule.  Tables built with
  * FEM_RULE_TABLE1 serve fem_integrate / fem_integrate_uniform (uniform degree,
- * constant coefficients; every precision) and fem_integrate_host; the other
- * compute entry points return FEM_EUNSUPPORTED for them.  FEM_EINVAL for an
+ * constant coefficients; every precision), fem_integrate_elastic (every
+ * precision) and fem_integrate_host; the other compute entry points return
+ * FEM_EUNSUPPORTED for them.  FEM_EINVAL for an
  * unknown rule or a rule the element does not have (tetrahedra). */
 int fem_tables_build_ex(int elem, int rule, int p_min, int p_max, fem_tables *out);
 int fem_tables_destroy(fem_tables t);

@@ -82,6 +82,7 @@ def _load():
             lib.orc_integrate_ex.argtypes = [i, i, i64, P, P, i64, i, P, i, P, P, P, P, P, i]
             lib.orc_point_law.argtypes = [i, i, i64, P, P, i, i, P, P, P, P, P, P]
             lib.orc_integrate_elastic.argtypes = [i, i64, P, P, i64, P, P, P, i]
+            lib.orc_integrate_elastic_ex.argtypes = [i, i, i64, P, P, i64, P, P, P, i]
             lib.orc_jacobian_terms.argtypes = [i, i, i64, P, P, P]
             lib.orc_max_threads.argtypes = []
             lib.orc_tri_search.argtypes = [i, i64, ctypes.c_uint64, i, P, P]
@@ -301,10 +302,11 @@ def jacobian_terms(elem: int, p: int, coords):
     return terms, st
 
 
-def integrate_elastic(p: int, coords, coeffs, nthreads: int = 0):
+def integrate_elastic(p: int, coords, coeffs, nthreads: int = 0, elem: int = PRISM):
     """Linear elastostatics on prisms: A [E][3][3][NS][NS], b [E][3][NS], status.
 
-    coeffs SoA [5][E]: Young modulus, Poisson ratio, body force fx, fy, fz."""
+    coeffs SoA [5][E]: Young modulus, Poisson ratio, body force fx, fy, fz;
+    elem PRISM (collapsed rule) or PRISM_T1 (the paper's rule)."""
     coords = _f64(coords)
     coeffs = _f64(coeffs)
     E = coords.shape[0]
@@ -312,8 +314,8 @@ def integrate_elastic(p: int, coords, coeffs, nthreads: int = 0):
     A = np.zeros((E, 3, 3, n, n))
     b = np.zeros((E, 3, n))
     st = np.zeros(E, dtype=np.int32)
-    rc = _load().orc_integrate_elastic(p, E, _ptr(coords), _ptr(coeffs), coeffs.shape[1], _ptr(A),
-                                       _ptr(b), _ptr(st), nthreads)
+    rc = _load().orc_integrate_elastic_ex(elem, p, E, _ptr(coords), _ptr(coeffs), coeffs.shape[1], _ptr(A),
+                                          _ptr(b), _ptr(st), nthreads)
     if rc != 0:
         raise RuntimeError("oracle integrate_elastic failed")
     return A, b, st

@@ -1045,10 +1045,11 @@ int orc_point_law(int elem, int p, int64_t E, const double *coords, const double
  * lam = E nu / ((1 + nu)(1 - 2 nu)), mu = E / (2 (1 + nu)), constant per
  * element (the paper's material data: Young modulus and Poisson ratio); body
  * force load b[iE][s] = sum_Q w_Q det J_Q f_iE psi_Q[0][s].
- * coeffs SoA [5][cstride]: E, nu, fx, fy, fz.  A [E][3][3][NS][NS], b [E][3][NS]. */
-int orc_integrate_elastic(int p, int64_t E, const double *coords, const double *coeffs,
-                          int64_t cstride, double *A, double *bvec, int32_t *status, int nthreads) {
-    const int elem = ORC_PRISM;
+ * coeffs SoA [5][cstride]: E, nu, fx, fy, fz.  A [E][3][3][NS][NS], b [E][3][NS].
+ * elem: ORC_PRISM (collapsed rule) or ORC_PRISM_T1 (the paper's rule). */
+int orc_integrate_elastic_ex(int elem, int p, int64_t E, const double *coords, const double *coeffs,
+                             int64_t cstride, double *A, double *bvec, int32_t *status, int nthreads) {
+    if (elem != ORC_PRISM && elem != ORC_PRISM_T1) return -1;
     int NS = orc_ns(elem, p), NQ = orc_nq(elem, p);
     if (NS < 0 || NQ < 0) return -1;
     double *xq = (double *)malloc(sizeof(double) * 3 * NQ);
@@ -1111,6 +1112,12 @@ int orc_integrate_elastic(int p, int64_t E, const double *coords, const double *
     free(wq);
     free(phiQ);
     return 0;
+}
+
+/* elasticity on prisms with the collapsed rule */
+int orc_integrate_elastic(int p, int64_t E, const double *coords, const double *coeffs,
+                          int64_t cstride, double *A, double *bvec, int32_t *status, int nthreads) {
+    return orc_integrate_elastic_ex(ORC_PRISM, p, E, coords, coeffs, cstride, A, bvec, status, nthreads);
 }
 
 int orc_integrate(int elem, int p, int64_t E, const double *coords, const double *coeffs,

@@ -419,7 +419,6 @@ int fem_apply(fem_tables t, int p, int64_t n_elem, const double *coords, const d
 int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coords, const double *coeffs,
                           int64_t coeff_stride, int prec, void *A_out, void *b_out, int32_t *status,
                           void *stream) {
-  if (rule_check(t, "fem_integrate_elastic") != FEM_OK) return FEM_EUNSUPPORTED;
   if (!t || t->elem != FEM_PRISM6) return invalid("fem_integrate_elastic: needs prism tables");
   if (p < t->p_min || p > t->p_max || n_elem < 0) return invalid("fem_integrate_elastic: bad degree or n_elem");
   if (prec != FEM_F64 && prec != FEM_F32 && prec != FEM_BF16X3 && prec != FEM_F16X3) {
@@ -463,6 +462,8 @@ int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coo
   a.b = b_out;
   a.status = status;
   a.layout = FEM_OUT_FULL;
+  if (t->rule == FEM_RULE_TABLE1)
+    return prec == FEM_F64 ? launch_fma_t1_elastic_f64(p, a, stream) : launch_fma_t1_elastic_f32(p, a, stream);
   return prec == FEM_F64 ? launch_fma_elastic_f64(p, a, stream) : launch_fma_elastic_f32(p, a, stream);
 }
 

@@ -690,6 +690,23 @@ int launch_fma_table1(int p, const FmaArgs &a, void *stream) {
   return FEM_EINVAL;
 }
 
+// linear elastostatics with the paper's rule (a.n real elements, 9 blocks each)
+template <class T>
+int launch_fma_elastic_table1(int p, const FmaArgs &a, void *stream) {
+  FmaArgs v = a;
+  v.n = 9 * a.n;  // virtual elements
+  switch (p) {
+    case 1: return launch_fma_cfg<T, Table1Cfg<typename FmaShapeE<T, 1>::type>>(v, stream);
+    case 2: return launch_fma_cfg<T, Table1Cfg<typename FmaShapeE<T, 2>::type>>(v, stream);
+    case 3: return launch_fma_cfg<T, Table1Cfg<typename FmaShapeE<T, 3>::type>>(v, stream);
+    case 4: return launch_fma_cfg<T, Table1Cfg<typename FmaShapeE<T, 4>::type>>(v, stream);
+    case 5: return launch_fma_cfg<T, Table1Cfg<typename FmaShapeE<T, 5>::type>>(v, stream);
+    case 6: return launch_fma_cfg<T, Table1Cfg<typename FmaShapeE<T, 6>::type>>(v, stream);
+    case 7: return launch_fma_cfg<T, Table1Cfg<typename FmaShapeE<T, 7>::type>>(v, stream);
+  }
+  return FEM_EINVAL;
+}
+
 template <class T, int LAW = 0, bool SPLIT = false>
 int launch_fma_any(int elem, int p, const FmaArgs &a, void *stream) {
   if (elem == FEM_TET4) return launch_fma_cfg<T, typename FmaShape<T, FEM_TET4, 1>::type, LAW, SPLIT>(a, stream);

@@ -103,7 +103,8 @@ void set_error(const std::string &msg);
 
 // FEM_EUNSUPPORTED (with a message naming fn) for tables built with the
 // paper's rule: the entry points other than fem_integrate / fem_integrate_uniform
-// / fem_integrate_host have kernels for the collapsed rule only.
+// / fem_integrate_elastic / fem_integrate_host have kernels for the collapsed
+// rule only.
 inline int rule_check(const fem_tables_s *t, const char *fn) {
   if (t && t->rule != FEM_RULE_COLLAPSED) {
     set_error(std::string(fn) + ": tables with the paper's rule (FEM_RULE_TABLE1) serve fem_integrate only");
@@ -153,6 +154,8 @@ int launch_fma_f32(int elem, int p, const FmaArgs &a, void *stream);
 // the same for prisms with the paper's rule (FEM_RULE_TABLE1), constant coefficients
 int launch_fma_t1_f64(int p, const FmaArgs &a, void *stream);
 int launch_fma_t1_f32(int p, const FmaArgs &a, void *stream);
+int launch_fma_t1_elastic_f64(int p, const FmaArgs &a, void *stream);
+int launch_fma_t1_elastic_f32(int p, const FmaArgs &a, void *stream);
 // linear elastostatics: a.n real elements, 9 blocks each
 int launch_fma_elastic_f64(int p, const FmaArgs &a, void *stream);
 // split geometry (a.terms set, a.coords unused): scalar form and elastostatics

@@ -44,13 +44,8 @@ int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *strea
     set_error("tensor-core tables missing for this degree");
     return FEM_EUNSUPPORTED;
   }
-  if (l.elastic) {
-    if (d.rule != FEM_RULE_COLLAPSED) {
-      set_error("tensor-core elasticity: collapsed-rule tables only");
-      return FEM_EUNSUPPORTED;
-    }
-    return launch_tc_elastic(p, f16, a, stream);
-  }
+  if (l.elastic)
+    return d.rule == FEM_RULE_TABLE1 ? launch_tc_elastic_t1(p, f16, a, stream) : launch_tc_elastic(p, f16, a, stream);
   if (l.law != 0) {
     if (f16 || !a.ucoef || (l.law == 2 && (!a.mlpw || !a.mlpw2))) {
       set_error("tensor-core law integration: BF16x3 with field coefficients (and a network) only");

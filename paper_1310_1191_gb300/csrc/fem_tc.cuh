@@ -24,17 +24,19 @@
 // each), the value row of T is zero, and the blocks (i, 0) carry the load
 // vector b^e[i] in their extra row (see the producers).
 //
-// CTA roles (512 threads, one CTA per SM, each CTA owns a contiguous range of
-// M tiles):
+// CTA roles (one CTA per SM, each CTA owns a contiguous range of M tiles;
+// 512 threads, or 768 where TcCfg gives 16 producer warps):
 //   warp 0, lane 0   : bulk-copies the Phi^T hi/lo image of each K chunk (TMA);
 //   warp 1, lane 0   : issues tcgen05.mma and commits (warp 1 owns TMEM);
-//   warps 6..13      : build the A tiles (T^T hi/lo) of each K chunk from the
-//                      point records, two threads per row;
-//   warps 2..5, 14, 15 : FP64 geometry of the elements each tile brings in ->
-//                      point records in a ring of element slots (consecutive
-//                      tiles share elements, so each element is computed once);
-//                      warps 2..5 then drain TMEM and write A_e / b_e of the
-//                      previous tile (warp w reads TMEM lanes 32 (w % 4) ..).
+//   warps 6..        : the producers, PRODW warps: build the A tiles (T^T hi/lo)
+//                      of each K chunk from the point records, 2 or 4 threads
+//                      per row;
+//   warps 2..5 and the last two : FP64 geometry of the elements each tile
+//                      brings in -> point records in a ring of element slots
+//                      (consecutive tiles share elements, so each element is
+//                      computed once); warps 2..5 then drain TMEM and write
+//                      A_e / b_e of the previous tile (warp w reads TMEM lanes
+//                      32 (w % 4) ..).
 // Every mbarrier wait is bounded (about a second); a CTA whose wait expires
 // sets the library's device error word, marks its elements FEM_ST_TIMEOUT,
 // waits for its own copies and MMAs, frees TMEM and returns.
@@ -74,8 +76,17 @@ struct TcCfg {
   // operand stages: as many as shared memory holds (the Phi^T copies come
   // from L2, partly across the die boundary, so deep rings hide their latency)
   static constexpr int STAGES = (P == 7 ? 3 : P == 6 ? 4 : P == 5 ? 5 : P == 4 ? 7 : 8) - (LAW != 0 && P >= 4 ? 1 : 0);
+  // producer warps: 8 (two threads per tile row, 4 points of each chunk
+  // each) or 16 (four threads per row, 2 points each); the CTA is
+  // 6 + PRODW + 2 warps (loader, MMA, 4 epilogue/geometry, producers,
+  // 2 geometry), so 16 producer warps make a 768-thread CTA with a budget of
+  // 85 registers per thread
+  static constexpr int PRODW = (P >= 3 && LAW == 0) ? 16 : 8;
+  static constexpr int THREADS = (8 + PRODW) * 32;
+  static constexpr int NPROD = PRODW * 32, PPR = NPROD / BM, QH = QC / PPR;
+  static constexpr int GEOW0 = 6 + PRODW;  // first geometry-only warp
   // chunks of Phi values the producers keep in flight (registers)
-  static constexpr int PD = 3;
+  static constexpr int PD = PRODW == 16 ? 2 : 3;
   static constexpr int A_BYTES = BM * KC * 2;  // one half (hi or lo)
   static constexpr int B_BYTES = NP * KC * 2;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
@@ -115,11 +126,12 @@ struct TcCfg {
 };
 
 // warp roles of the 512-thread CTA
-constexpr int kTcThreads = 512;
+// warp roles of the CTA (C::THREADS threads): warp 0 loader, warp 1 MMA,
+// warps 2..5 epilogue and geometry, warps 6 .. 6 + PRODW - 1 producers, the
+// last two warps (C::GEOW0, C::GEOW0 + 1) geometry only
 constexpr int kEpiWarp0 = 2;    // 4 warps: TMEM lanes 32 (w % 4) .. + 31; also geometry
-constexpr int kProdWarp0 = 6;   // 8 warps: 256 producer threads
-constexpr int kGeoWarp0 = 14;   // 2 warps: geometry only
-constexpr int kNProd = 256, kNEpi = 128, kNGeo = 192;  // geometry: warps 2..5 and 14..15
+constexpr int kProdWarp0 = 6;
+constexpr int kNEpi = 128, kNGeo = 192;  // geometry: warps 2..5 and the last two
 
 struct TcArgs {
   int64_t n;
@@ -183,7 +195,7 @@ __device__ __forceinline__ uint32_t split_pack(float x0, float x1, uint32_t &lo_
 // coefficients, k from the exact law or from the network (its 64x64 layer on
 // warp-level MMAs, the exact law outside its box), D = k I.
 template <int P, bool F16, bool ELAS = false, int LAW = 0, int RULE = FEM_RULE_COLLAPSED>
-__global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kernel(const TcArgs a) {
   using C = TcCfg<P, ELAS, LAW, RULE>;
   static_assert(LAW == 0 || (!F16 && !ELAS), "the law runs in the BF16 scalar form");
   constexpr int VPE = ELAS ? 9 : 1;  // row blocks (virtual elements) per element
@@ -240,14 +252,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
 
   if (tid == 0) {
     for (int s = 0; s < C::STAGES; s++) {
-      ptx::mbar_init(&bar_full[s], kNProd / 32 + 1);  // one arrival per producer warp + the loader
+      ptx::mbar_init(&bar_full[s], C::PRODW + 1);  // one arrival per producer warp + the loader
       ptx::mbar_init(&bar_empty[s], 1);
     }
     for (int i = 0; i < 2; i++) {
       ptx::mbar_init(&bar_accf[i], 1);
       ptx::mbar_init(&bar_acce[i], kNEpi / 32);
       ptx::mbar_init(&bar_gfull[i], 1);
-      ptx::mbar_init(&bar_gempty[i], (kNProd + kNEpi) / 32);
+      ptx::mbar_init(&bar_gempty[i], C::PRODW + kNEpi / 32);
     }
     ptx::mbar_init(bar_fin, 1);
     *sAbort = 0;
@@ -354,12 +366,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
       ptx::mma_commit(bar_fin);
       ptx::mbar_wait(bar_fin, 0, kWaitLimitNs);
     }
-  } else if (warp >= kProdWarp0 && warp < kGeoWarp0) {
+  } else if (warp >= kProdWarp0 && warp < C::GEOW0) {
     // ---------------- producers: A tiles (T^T hi/lo) of each K chunk ----------------
     const int pt = tid - kProdWarp0 * 32;
     const int rl = pt & 127;       // tile row
-    const int half = pt >> 7;      // points 4 half .. 4 half + 3 of each chunk
-    constexpr int QH = C::QC / 2;
+    const int half = pt >> 7;      // points QH half .. QH half + QH - 1 of each chunk
+    constexpr int QH = C::QH;
     uint32_t tt = 0;
     for (int64_t t = t_begin; t < t_end; t++, tt++) {
       const int b = tt & 1;
@@ -504,7 +516,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
     // tt - 1.  All 192 threads run every iteration and every named barrier
     // (work is skipped after an abort), so none can be left waiting on barrier 2.
     const bool epi = warp < kProdWarp0;
-    const int gt = epi ? tid - kEpiWarp0 * 32 : 128 + tid - kGeoWarp0 * 32;
+    const int gt = epi ? tid - kEpiWarp0 * 32 : 128 + tid - C::GEOW0 * 32;
     int64_t e_done = -1;  // last element whose records are in the ring
     uint32_t tt = 0;
     auto gbar = [] { asm volatile("bar.sync 2, 192;" ::: "memory"); };
@@ -841,7 +853,7 @@ static int launch_tc_p(const TcArgs &a, void *stream) {
   const int64_t ntiles = (a.n * (ELAS ? 9 : 1) * C::L + C::BM - 1) / C::BM;
   int64_t grid = nsm;
   if (grid > ntiles) grid = ntiles;
-  tc_kernel<P, F16, ELAS, LAW, RULE><<<(unsigned)grid, kTcThreads, C::SMEM, (cudaStream_t)stream>>>(a);
+  tc_kernel<P, F16, ELAS, LAW, RULE><<<(unsigned)grid, C::THREADS, C::SMEM, (cudaStream_t)stream>>>(a);
   err = cudaGetLastError();
   if (err != cudaSuccess) {
     set_error(std::string("tc_kernel launch: ") + cudaGetErrorString(err));
@@ -869,6 +881,7 @@ int launch_tc_scalar_bf16(int p, const TcArgs &a, void *stream);
 int launch_tc_scalar_f16(int p, const TcArgs &a, void *stream);
 int launch_tc_scalar_t1(int p, bool f16, const TcArgs &a, void *stream);
 int launch_tc_elastic(int p, bool f16, const TcArgs &a, void *stream);
+int launch_tc_elastic_t1(int p, bool f16, const TcArgs &a, void *stream);
 int launch_tc_law(int p, int law, const TcArgs &a, void *stream);
 
 }  // namespace fem

@@ -97,8 +97,8 @@ def test_table1_rule_sympacked_and_flags(orc, lib, t1):
 
 def test_table1_rule_other_entry_points_refuse(lib, t1):
     """The paper's rule has kernels for the constant-coefficient scalar form
-    only: the law, elasticity, split-geometry, apply and mixed-degree entry
-    points give FEM_EUNSUPPORTED with these tables, before any launch."""
+    and for elasticity only: the law, split-geometry, apply and mixed-degree
+    entry points give FEM_EUNSUPPORTED with these tables, before any launch."""
     import torch
     E, p = 4, 2
     X = torch.from_numpy(inputs.prism_mesh(E)).cuda()
@@ -107,7 +107,6 @@ def test_table1_rule_other_entry_points_refuse(lib, t1):
     U = torch.zeros((E, 18), dtype=torch.float32, device="cuda")
     calls = [
         lambda: lib.fem_integrate_law(t1, p, E, X, C, E, U, lib.FEM_LAW_EXACT, None, 0, 0, A),
-        lambda: lib.fem_integrate_elastic(t1, p, E, X, C, E, 0, A),
         lambda: lib.fem_jacobian_terms(t1, p, E, X, A),
         lambda: lib.fem_apply(t1, p, E, X, C, E, 0, A, A[E * 18:]),
         lambda: lib.fem_plan_create(t1, np.full(E, p, dtype=np.int8), 0),
@@ -143,3 +142,29 @@ def test_table1_rule_full_size_sampled(orc, lib, t1, p, prec):
     Ah = A[torch.from_numpy(idx).cuda()].double().cpu().numpy().reshape(len(idx), n, n)
     assert rel_frob(Ah, RA).max() <= TOL_ALL[prec]
     assert int((st != 0).sum().item()) == 0
+
+
+E_EL = {1: 64, 2: 40, 3: 24, 4: 12, 5: 6, 6: 4, 7: 3}
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("p", range(1, 8))
+def test_table1_rule_elasticity_parity(orc, lib, t1, p, prec):
+    """Linear elastostatics (the paper's model problem, Section 5.1) with the
+    paper's own rule: every element and block against the oracle's
+    elasticity with the same rule."""
+    import torch
+    E = E_EL[p]
+    X, C = inputs.prism_mesh(E), inputs.elastic_coefficients(E)
+    n = ns(1, p)
+    dt = torch.float64 if prec == 0 else torch.float32
+    A = torch.full((E, 9 * n * n), float("nan"), dtype=dt, device="cuda")
+    b = torch.full((E, 3 * n), float("nan"), dtype=dt, device="cuda")
+    st = torch.full((E,), -1, dtype=torch.int32, device="cuda")
+    lib.fem_integrate_elastic(t1, p, E, torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda(), E, prec, A, b, st)
+    torch.cuda.synchronize()
+    RA, Rb, Rst = orc.integrate_elastic(p, X, C, elem=T1)
+    err = rel_frob(A.double().cpu().numpy().reshape(E, 9 * n * n), RA.reshape(E, -1))
+    assert err.max() <= TOL_ALL[prec], (p, prec, err.max())
+    assert rel_frob(b.double().cpu().numpy(), Rb.reshape(E, -1)).max() <= TOL_ALL[prec]
+    assert np.array_equal(st.cpu().numpy(), Rst)

@@ -21,12 +21,14 @@ def _relF(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("elem", [PRISM, 2])
 @pytest.mark.parametrize("p", [1, 2, 4])
-def test_block_symmetry_translations_load(orc, p):
+def test_block_symmetry_translations_load(orc, p, elem):
+    """(elem 2: the paper's prism rule, Table 1 point counts)"""
     E = 6
     X = inputs.prism_mesh(E, dims=(2, 2, 1))[:E]
     C = inputs.elastic_coefficients(E)
-    A, b, st = orc.integrate_elastic(p, X, C)
+    A, b, st = orc.integrate_elastic(p, X, C, elem=elem)
     assert np.all(st == 0)
     s = np.abs(A).max()
     for i in range(3):
@@ -37,7 +39,7 @@ def test_block_symmetry_translations_load(orc, p):
     # load vector: b[i][0] = f_i V_e (phi_0 = 1); volumes from the scalar oracle
     Cs = np.zeros((11, E))
     Cs[9] = 1.0
-    M, _, _ = orc.integrate(PRISM, p, X, Cs)
+    M, _, _ = orc.integrate(elem, p, X, Cs)
     V = M[:, 0, 0]
     assert np.allclose(b[:, :, 0], C[2:5].T * V[:, None], rtol=1e-13, atol=0)
 
@@ -52,14 +54,15 @@ def _map(Xe, pts):
     return out
 
 
+@pytest.mark.parametrize("elem", [PRISM, 2])
 @pytest.mark.parametrize("p", [1, 3])
-def test_rigid_rotations_in_kernel(orc, p):
+def test_rigid_rotations_in_kernel(orc, p, elem):
     """u = w x x has zero strain: its coefficient vectors (fitted exactly in the
-    basis, which contains the map) are annihilated by A^e."""
+    basis, which contains the map) are annihilated by A^e, with either rule."""
     E = 4
     X = inputs.prism_mesh(E, dims=(2, 1, 1))[:E]
     C = inputs.elastic_coefficients(E)
-    A, _, _ = orc.integrate_elastic(p, X, C)
+    A, _, _ = orc.integrate_elastic(p, X, C, elem=elem)
     rng = np.random.default_rng(1)
     pts = []
     while len(pts) < 400:
@@ -81,17 +84,18 @@ def test_rigid_rotations_in_kernel(orc, p):
             assert np.linalg.norm(r) < 1e-11 * np.linalg.norm(Ae) * np.linalg.norm(U)
 
 
+@pytest.mark.parametrize("elem", [PRISM, 2])
 @pytest.mark.parametrize("p", [2, 5])
-def test_trace_is_scaled_laplacian(orc, p):
+def test_trace_is_scaled_laplacian(orc, p, elem):
     """sum_i A^{ii} = (lam + 4 mu) times the scalar stiffness with D = I."""
     E = 3
     X = inputs.prism_mesh(E, dims=(2, 1, 1))[:E]
     C = inputs.elastic_coefficients(E)
-    A, _, _ = orc.integrate_elastic(p, X, C)
+    A, _, _ = orc.integrate_elastic(p, X, C, elem=elem)
     lam, mu = _lame(C[0], C[1])
     Cs = np.zeros((11, E))
     Cs[0:3] = (lam + 4 * mu)[None, :]
-    K, _, _ = orc.integrate(PRISM, p, X, Cs)
+    K, _, _ = orc.integrate(elem, p, X, Cs)
     assert _relF(A[:, 0, 0] + A[:, 1, 1] + A[:, 2, 2], K) < 1e-13
 
 
