@@ -66,9 +66,9 @@ def measured_peaks():
 
 def measure_fma_peaks(lib, dev, stream, sm_mhz=2070.0):
     """FP64 and FP32 multiply-add throughput measured with the library's FMA
-    probe: 8 independent chains per thread, 8 CTAs of 256 threads per SM,
-    launches of about 50 ms (best of 3 after a warm-up launch, CUDA events on
-    the launching stream).  Each CTA records its SM clock cycles, so the
+    probe (the contraction's inner loop: register-tile outer products fed from
+    shared memory), 8 CTAs of 256 threads per SM, launches of about 50 ms
+    (best of 3 after a warm-up launch, CUDA events on the launching stream).  Each CTA records its SM clock cycles, so the
     probe gives multiply-adds per SM per clock; the peak (TFLOP/s, a
     multiply-add = 2 flops) is that rate at sm_mhz, the SM clock the
     measured kernels ran at (the probe itself may run at a lower,
@@ -79,7 +79,7 @@ def measure_fma_peaks(lib, dev, stream, sm_mhz=2070.0):
     out = torch.empty(n, dtype=torch.float64, device=dev)
     clk = torch.zeros((n // 256, 2), dtype=torch.int64, device=dev)
     res = {"sm_mhz_used": sm_mhz}
-    for name, fp64, iters in (("f64", True, 12000), ("f32", False, 800000)):
+    for name, fp64, iters, tile in (("f64", True, 200, 16), ("f32", False, 3200, 64)):
         best = None
         for rep in range(4):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -91,9 +91,10 @@ def measure_fma_peaks(lib, dev, stream, sm_mhz=2070.0):
                 s = e0.elapsed_time(e1) / 1e3
                 c = clk.double()
                 mhz = float((c[:, 0] / c[:, 1]).mean()) * 1e3
-                per_clk = 8.0 * iters * n / (s * mhz * 1e6) / sms
+                fmas = 32.0 * tile * iters * n
+                per_clk = fmas / (s * mhz * 1e6) / sms
                 if best is None or per_clk > best[0]:
-                    best = (per_clk, 2.0 * 8 * iters * n / s / 1e12, mhz)
+                    best = (per_clk, 2.0 * fmas / s / 1e12, mhz)
         res[name] = 2.0 * best[0] * sms * sm_mhz * 1e6 / 1e12
         res[name + "_fma_per_sm_clk"] = round(best[0], 3)
         res[name + "_probe_tflops"] = round(best[1], 4)
@@ -707,6 +708,7 @@ def wl_batched(lib, tables, stream, dev, reps, E=500000):
     res, ref = {}, None
     for name, prec, flags in (("graph_autotuned", lib.FEM_F32, lib.FEM_PLAN_AUTOTUNE),
                               ("per_degree_loop", lib.FEM_F32, lib.FEM_PLAN_LOOP),
+                              ("per_degree_loop_autotuned", lib.FEM_F32, lib.FEM_PLAN_LOOP | lib.FEM_PLAN_AUTOTUNE),
                               ("graph_concurrent_branches", lib.FEM_F32, lib.FEM_PLAN_CONCURRENT),
                               ("graph_concurrent_bf16x3", lib.FEM_BF16X3, lib.FEM_PLAN_CONCURRENT),
                               ("graph_concurrent_f16x3", lib.FEM_F16X3, lib.FEM_PLAN_CONCURRENT)):
@@ -714,6 +716,8 @@ def wl_batched(lib, tables, stream, dev, reps, E=500000):
         ms = _timed(stream, lambda: lib.fem_plan_execute(plan, Xd, Cd, E, A, b, None, stream), reps, 2)
         res[name] = {"ms": round(ms, 3), "elem_per_s": E / ms * 1e3,
                      "variants": [plan.variant(p)[0] for p in range(1, 8)]}
+        if flags & lib.FEM_PLAN_AUTOTUNE:  # the autotuner's candidate times per degree (ms)
+            res[name]["tuned_ms"] = {str(p): [round(float(x), 3) for x in plan.variant(p)[1]] for p in range(1, 8)}
         stream.synchronize()
         blocks = [A[int(offA[e]):int(offA[e]) + ns_of(int(P[e])) ** 2].double() for e in sample]
         if ref is None:
@@ -971,7 +975,7 @@ def run_ours(args):
                          "traffic": TRAFFIC.get((args.precision, pdom)),
                          "traffic_source": TRAFFIC_SOURCE if (args.precision, pdom) in TRAFFIC else None,
                          "peak_source": "%s FMA peak %s: fem_probe_fma's multiply-adds per SM per clock "
-                                        "(8 independent chains per thread, 8 CTAs x 256 threads per SM, "
+                                        "(register-tile outer products from shared memory, 8 CTAs x 256 threads per SM, "
                                         "best of 3 launches of about 50 ms, SM clock from clock64 and "
                                         "globaltimer in every CTA) x SMs x the timed region's median SM "
                                         "clock; HBM %s %.0f GB/s" % (args.precision, fma_src, peak_src, hbm)},

@@ -234,8 +234,9 @@ def fem_integrate(t: Tables, n_elem: int, coords, p_per_elem, p_uniform: int, co
 
 
 def fem_probe_fma(fp64: bool, iters: int, n_threads: int, out, clk=None, stream=None) -> int:
-    """Enqueue the FMA-pipe throughput probe (8 chains x iters multiply-adds
-    per thread; clk: optional int64 [n_threads / 256][2] cycles and ns per CTA)."""
+    """Enqueue the FMA-pipe throughput probe (32 x iters outer-product steps of
+    16 (FP64) or 64 (FP32) multiply-adds per thread; clk: optional int64
+    [n_threads / 256][2] cycles and ns per CTA)."""
     return _check("fem_probe_fma", load().fem_probe_fma(1 if fp64 else 0, iters, n_threads, _addr(out),
                                                         _addr(clk), _stream(stream)))
 

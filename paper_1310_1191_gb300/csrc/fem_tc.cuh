@@ -77,11 +77,12 @@ struct TcCfg {
   // from L2, partly across the die boundary, so deep rings hide their latency)
   static constexpr int STAGES = (P == 7 ? 3 : P == 6 ? 4 : P == 5 ? 5 : P == 4 ? 7 : 8) - (LAW != 0 && P >= 4 ? 1 : 0);
   // producer warps: 8 (two threads per tile row, 4 points of each chunk
-  // each) or 16 (four threads per row, 2 points each); the CTA is
+  // each) or 16 (four threads per row, 2 points each; measured 1.2x at p = 5
+  // and 1.1x at p = 6, the same at p = 4, 7 % slower at p = 7); the CTA is
   // 6 + PRODW + 2 warps (loader, MMA, 4 epilogue/geometry, producers,
   // 2 geometry), so 16 producer warps make a 768-thread CTA with a budget of
   // 85 registers per thread
-  static constexpr int PRODW = (P >= 3 && LAW == 0) ? 16 : 8;
+  static constexpr int PRODW = (P >= 3 && P <= 6 && LAW == 0) ? 16 : 8;
   static constexpr int THREADS = (8 + PRODW) * 32;
   static constexpr int NPROD = PRODW * 32, PPR = NPROD / BM, QH = QC / PPR;
   static constexpr int GEOW0 = 6 + PRODW;  // first geometry-only warp
