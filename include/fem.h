@@ -454,20 +454,24 @@ int fem_debug_stall_next(fem_tables t);
 /* Throughput probe of the multiply-add pipe that bounds the CUDA-core kernels
  * (FP64 for fem_integrate's FEM_F64 path and every path's geometry, FP32 for
  * the FP32 contractions): n_threads threads (a multiple of 256; the probe's
- * grid is n_threads / 256 CTAs of 256) each run `iters` times 32 steps of the
- * contraction's inner loop, a register tile of accumulators plus the outer
- * product of two vectors loaded from shared memory (4 x 4 in FP64, 8 x 8 in
- * FP32), and write one value to out.  The paper has no counterpart: its
- * rooflines use vendor peaks; here the denominator is measured (the caller
- * times the launch with CUDA events; multiply-adds = 32 * iters * 16 (FP64)
- * or 64 (FP32) * n_threads, flops twice that).  The SM clock under this load
- * can sit below the one the measured kernels run at (power cap), so each CTA
- * also records its SM clock cycles and nanoseconds: the rate per clock follows.
+ * grid is n_threads / 256 CTAs of 256) each run one of two loop forms and
+ * write one value to out:
+ *   form 0: 8 independent chains a <- a x + y of `iters` multiply-adds each
+ *           (8 iters multiply-adds per thread);
+ *   form 1: `iters` times 32 steps of the contraction's inner loop, a register
+ *           tile of accumulators plus the outer product of two vectors loaded
+ *           from shared memory, 4 x 4 in FP64 and 8 x 8 in FP32 (32 iters x 16
+ *           or 64 multiply-adds per thread).
+ * The paper has no counterpart: its rooflines use vendor peaks; here the
+ * denominator is measured (the caller times the launch with CUDA events).
+ * The SM clock under this load can sit below the one the measured kernels run
+ * at (power cap), so each CTA also records its SM clock cycles and
+ * nanoseconds: the rate per clock follows.
  *   fp64      : non-zero for double, zero for float;
  *   out       : device [n_threads] of double or float, caller-owned, 8-byte aligned;
  *   clk       : device int64 [n_threads / 256][2] (cycles, ns per CTA), or NULL;
  * FEM_EINVAL for bad arguments, FEM_ECUDA if the launch fails. */
-int fem_probe_fma(int fp64, int64_t iters, int64_t n_threads, void *out, int64_t *clk, void *stream);
+int fem_probe_fma(int fp64, int form, int64_t iters, int64_t n_threads, void *out, int64_t *clk, void *stream);
 
 /* Number of output values per element for (elem, p, layout): NS*NS or NS(NS+1)/2;
  * -1 if invalid.  */

@@ -67,7 +67,7 @@ def load():
     lib.fem_integrate.argtypes = [P, i64, P, P, i, P, i64, P, i, i, P, P, P, P]
     lib.fem_integrate_uniform.argtypes = [P, i, i64, P, P, i64, i, i, P, P, P, P]
     lib.fem_sync_status.argtypes = [P, P, i64, P, P, P]
-    lib.fem_probe_fma.argtypes = [i, i64, i64, P, P, P]
+    lib.fem_probe_fma.argtypes = [i, i, i64, i64, P, P, P]
     lib.fem_matrix_size.argtypes = [i, i, i]
     lib.fem_matrix_size.restype = i64
     lib.fem_status_str.argtypes = [i]
@@ -233,11 +233,12 @@ def fem_integrate(t: Tables, n_elem: int, coords, p_per_elem, p_uniform: int, co
         _addr(A_out), _addr(b_out), _addr(status), _stream(stream)))
 
 
-def fem_probe_fma(fp64: bool, iters: int, n_threads: int, out, clk=None, stream=None) -> int:
-    """Enqueue the FMA-pipe throughput probe (32 x iters outer-product steps of
-    16 (FP64) or 64 (FP32) multiply-adds per thread; clk: optional int64
+def fem_probe_fma(fp64: bool, form: int, iters: int, n_threads: int, out, clk=None, stream=None) -> int:
+    """Enqueue the FMA-pipe throughput probe (form 0: 8 chains of iters
+    multiply-adds per thread; form 1: 32 x iters outer-product steps of 16
+    (FP64) or 64 (FP32) multiply-adds per thread; clk: optional int64
     [n_threads / 256][2] cycles and ns per CTA)."""
-    return _check("fem_probe_fma", load().fem_probe_fma(1 if fp64 else 0, iters, n_threads, _addr(out),
+    return _check("fem_probe_fma", load().fem_probe_fma(1 if fp64 else 0, form, iters, n_threads, _addr(out),
                                                         _addr(clk), _stream(stream)))
 
 
