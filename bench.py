@@ -716,6 +716,8 @@ def wl_batched(lib, tables, stream, dev, reps, E=500000):
                               ("per_degree_loop_autotuned", lib.FEM_F32, lib.FEM_PLAN_LOOP | lib.FEM_PLAN_AUTOTUNE),
                               ("graph_concurrent_branches", lib.FEM_F32, lib.FEM_PLAN_CONCURRENT),
                               ("graph_concurrent_bf16x3", lib.FEM_BF16X3, lib.FEM_PLAN_CONCURRENT),
+                              ("graph_concurrent_bf16x3_autotuned", lib.FEM_BF16X3,
+                               lib.FEM_PLAN_CONCURRENT | lib.FEM_PLAN_AUTOTUNE),
                               ("graph_concurrent_f16x3", lib.FEM_F16X3, lib.FEM_PLAN_CONCURRENT)):
         plan = lib.fem_plan_create(tables, P, prec, 0, flags, None)
         ms = _timed(stream, lambda: lib.fem_plan_execute(plan, Xd, Cd, E, A, b, None, stream), reps, 2)

@@ -46,6 +46,7 @@ extern "C" {
 #define FEM_EUNSUPPORTED 4  /* valid but not provided combination */
 #define FEM_EELEMENT 5      /* at least one element flagged in status[] */
 #define FEM_ETIMEOUT 6      /* a bounded device wait gave up */
+#define FEM_ECHECKED 7      /* checked build: a kernel's index check failed (access skipped) */
 
 /* ---- element types ---- */
 #define FEM_TET4 0
@@ -287,7 +288,11 @@ int fem_apply(fem_tables t, int p, int64_t n_elem, const double *coords, const d
 
 /* Device error word of the tables' kernels: FEM_ETIMEOUT if a bounded wait
  * inside a tensor-core launch expired since the last clear (the affected
- * elements also carry FEM_ST_TIMEOUT), else FEM_OK.  Synchronises the device.
+ * elements also carry FEM_ST_TIMEOUT); in the checked build
+ * (libfem_gb300_checked.so, compiled with FEM_CHECKED: the kernels check the
+ * element ids of permutations and the output offsets of mixed-degree plans
+ * against their extents and skip a failing access) FEM_ECHECKED if a check
+ * failed; else FEM_OK.  Synchronises the device.
  *   clear : non-zero resets the word. */
 int fem_error_flag(fem_tables t, int clear);
 
@@ -441,6 +446,13 @@ int fem_plan_destroy(fem_plan plan);
 int fem_integrate_mixed_noalloc(fem_tables t, int64_t n_elem, const int8_t *p_host, const double *coords,
                                 const double *coeffs, int64_t coeff_stride, int prec, int layout,
                                 void *A_out, void *b_out, int32_t *status, void *stream);
+
+/* Test hook of the checked build: the plan's next execution takes A_out as
+ * one value shorter than fem_output_offsets says, so the element whose block
+ * ends there fails the output-offset check and is skipped (its values are
+ * not written), and fem_error_flag returns FEM_ECHECKED; no access leaves the
+ * caller's buffer.  FEM_EUNSUPPORTED in the normal build. */
+int fem_debug_shrink_bound(fem_plan plan);
 
 /* Failure-detection test hook: the next tensor-core launch on these tables
  * withholds its operand copies, so its pipeline waits run out after their

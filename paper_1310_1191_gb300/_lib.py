@@ -15,8 +15,11 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfem_gb300.so")
+# the checked variant (kernel index checks; build.build(checked=True)), loaded
+# instead when the environment sets FEM_GB300_CHECKED=1
+LIB_PATH_CHECKED = os.path.join(HERE, "libfem_gb300_checked.so")
 
-FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_ECUDA, FEM_EUNSUPPORTED, FEM_EELEMENT, FEM_ETIMEOUT = range(7)
+FEM_OK, FEM_EINVAL, FEM_ENOMEM, FEM_ECUDA, FEM_EUNSUPPORTED, FEM_EELEMENT, FEM_ETIMEOUT, FEM_ECHECKED = range(8)
 FEM_TET4, FEM_PRISM6 = 0, 1
 FEM_F64, FEM_F32, FEM_BF16X3, FEM_F16X3 = 0, 1, 2, 3
 FEM_OUT_FULL, FEM_OUT_SYMPACKED = 0, 1
@@ -34,7 +37,7 @@ EXPORTS = (
     "fem_integrate_law", "fem_field_samples", "fem_box_from_samples", "fem_law_samples",
     "fem_mlp_create", "fem_mlp_destroy", "fem_mlp_nparams", "fem_mlp_forward", "fem_mlp_loss_grad",
     "fem_mlp_train", "fem_mlp_get", "fem_mlp_set", "fem_mlp_save", "fem_mlp_load",
-    "fem_integrate_host", "fem_integrate_elastic", "fem_debug_stall_next",
+    "fem_integrate_host", "fem_integrate_elastic", "fem_debug_stall_next", "fem_debug_shrink_bound",
     "fem_jacobian_terms", "fem_integrate_terms", "fem_integrate_elastic_terms", "fem_apply",
 )
 FEM_LAW_EXACT, FEM_LAW_MLP = 1, 2
@@ -50,14 +53,18 @@ class FemError(RuntimeError):
 
 
 def load():
-    """Load libfem_gb300.so; raises if it was not built (no CPU fallback)."""
+    """Load libfem_gb300.so (libfem_gb300_checked.so when FEM_GB300_CHECKED=1);
+    raises if it was not built (no CPU fallback)."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError("libfem_gb300.so is not built: run paper_1310_1191_gb300.build.build() "
-                           "(or __graft_entry__.build()) first")
-    lib = ctypes.CDLL(LIB_PATH)
+    checked = os.environ.get("FEM_GB300_CHECKED", "") == "1"
+    path = LIB_PATH_CHECKED if checked else LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("%s is not built: run paper_1310_1191_gb300.build.build(%s) "
+                           "(or __graft_entry__.build()) first"
+                           % (os.path.basename(path), "checked=True" if checked else ""))
+    lib = ctypes.CDLL(path)
     i, i64, P = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
     lib.fem_reference_rule.argtypes = [i, i, P, P, P, P, P]
     lib.fem_tables_build.argtypes = [i, i, i, P]
@@ -103,6 +110,7 @@ def load():
     lib.fem_integrate_terms.argtypes = [P, i, i64, P, P, i64, i, i, P, P, P, P]
     lib.fem_integrate_elastic_terms.argtypes = [P, i, i64, P, P, i64, i, P, P, P, P]
     lib.fem_debug_stall_next.argtypes = [P]
+    lib.fem_debug_shrink_bound.argtypes = [P]
     _lib = lib
     return lib
 
@@ -273,7 +281,9 @@ def fem_apply(t: Tables, p: int, n_elem: int, coords, coeffs, coeff_stride: int,
 
 
 def fem_error_flag(t: Tables, clear: bool = True) -> int:
-    """FEM_ETIMEOUT if a bounded device wait expired since the last clear (synchronises)."""
+    """FEM_ETIMEOUT if a bounded device wait expired since the last clear,
+    FEM_ECHECKED if a kernel index check of the checked build failed, else
+    FEM_OK (synchronises)."""
     return load().fem_error_flag(t.handle, 1 if clear else 0)
 
 
@@ -511,6 +521,12 @@ def fem_integrate_elastic_terms(t: Tables, p: int, n_elem: int, terms, coeffs, c
     return _check("fem_integrate_elastic_terms", load().fem_integrate_elastic_terms(
         t.handle, p, n_elem, _addr(terms), _addr(coeffs), coeff_stride, prec, _addr(A_out),
         _addr(b_out), _addr(status), _stream(stream)))
+
+
+def fem_debug_shrink_bound(plan) -> int:
+    """Checked-build test hook: the plan's next execution takes A_out as one
+    value shorter, so the last block fails its offset check (see fem.h)."""
+    return _check("fem_debug_shrink_bound", load().fem_debug_shrink_bound(plan.handle))
 
 
 def fem_debug_stall_next(t: Tables) -> int:

@@ -3,6 +3,13 @@
 Each translation unit under ``csrc/`` is compiled in parallel into
 ``_build/`` and linked into a shared library next to this file.  The build is
 incremental (an object is rebuilt when its source or any header is newer).
+
+``build(checked=True)`` makes the checked variant ``libfem_gb300_checked.so``
+(objects in ``_build_checked/``, compiled with ``-DFEM_CHECKED``): the same
+entry points, with index checks in the kernels (element ids taken from
+permutations, output offsets of mixed-degree plans) that skip a failing access
+and report FEM_ECHECKED through ``fem_error_flag``.  ``_lib.load()`` picks it
+when the environment sets ``FEM_GB300_CHECKED=1``.
 """
 from __future__ import annotations
 
@@ -17,6 +24,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfem_gb300.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libfem_gb300_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,16 +48,18 @@ def _headers_mtime() -> float:
     return max(os.path.getmtime(h) for h in hs) if hs else 0.0
 
 
-def build(verbose: bool = False, jobs: int = 0, extra_flags=None) -> str:
-    """Compile every source under csrc/ and link libfem_gb300.so; returns its path."""
+def build(verbose: bool = False, jobs: int = 0, extra_flags=None, checked: bool = False) -> str:
+    """Compile every source under csrc/ and link libfem_gb300.so (with
+    ``checked``: libfem_gb300_checked.so); returns its path."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    bdir, lib_path = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    os.makedirs(bdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     hdr_t = _headers_mtime()
-    flags = _flags() + list(extra_flags or [])
+    flags = _flags() + (["-DFEM_CHECKED"] if checked else []) + list(extra_flags or [])
 
     def obj_of(s):
-        return os.path.join(BUILD, os.path.basename(s) + ".o")
+        return os.path.join(bdir, os.path.basename(s) + ".o")
 
     def compile_one(s):
         o = obj_of(s)
@@ -71,17 +82,17 @@ def build(verbose: bool = False, jobs: int = 0, extra_flags=None) -> str:
             if log.strip():
                 print(log)
     objs = [o for o, _ in results]
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if not os.path.exists(lib_path) or os.path.getmtime(lib_path) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib_path + ".tmp%d" % os.getpid()
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \
             ["-Xlinker", "-rpath,/usr/local/cuda/lib64"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
     import sys
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, checked="--checked" in sys.argv))

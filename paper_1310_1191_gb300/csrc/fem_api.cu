@@ -110,6 +110,7 @@ const char *fem_status_str(int s) {
     case FEM_EUNSUPPORTED: return "unsupported combination";
     case FEM_EELEMENT: return "element flagged";
     case FEM_ETIMEOUT: return "device wait timed out";
+    case FEM_ECHECKED: return "kernel index check failed (checked build)";
   }
   return "unknown status";
 }
@@ -256,7 +257,12 @@ int fem_error_flag(fem_tables t, int clear) {
   if (e == cudaSuccess) e = cudaMemcpy(&h, t->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && clear) e = cudaMemset(t->d_err, 0, sizeof(int));
   if (e != cudaSuccess) return cuda_fail("fem_error_flag", e);
-  return h ? FEM_ETIMEOUT : FEM_OK;
+  if (h & kErrTimeout) return FEM_ETIMEOUT;
+  if (h & kErrCheck) {
+    set_error("fem_error_flag: a kernel index check of the checked build failed");
+    return FEM_ECHECKED;
+  }
+  return FEM_OK;
 }
 
 int fem_integrate(fem_tables t, int64_t n_elem, const double *coords, const int8_t *p_per_elem,
@@ -308,6 +314,7 @@ int fem_integrate_uniform(fem_tables t, int p, int64_t n_elem, const double *coo
   a.b = b_out;
   a.status = status;
   a.layout = layout;
+  a.err = t->d_err;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev != t->device) return invalid("fem_integrate: tables live on another device");
@@ -462,6 +469,7 @@ int fem_integrate_elastic(fem_tables t, int p, int64_t n_elem, const double *coo
   a.b = b_out;
   a.status = status;
   a.layout = FEM_OUT_FULL;
+  a.err = t->d_err;
   if (t->rule == FEM_RULE_TABLE1)
     return prec == FEM_F64 ? launch_fma_t1_elastic_f64(p, a, stream) : launch_fma_t1_elastic_f32(p, a, stream);
   return prec == FEM_F64 ? launch_fma_elastic_f64(p, a, stream) : launch_fma_elastic_f32(p, a, stream);
@@ -501,6 +509,7 @@ int fem_integrate_terms(fem_tables t, int p, int64_t n_elem, const double *terms
   a.b = b_out;
   a.status = status;
   a.layout = layout;
+  a.err = t->d_err;
   a.phi = prec == FEM_F64 ? (const void *)d.phi64 : (const void *)d.phi32;
   return launch_fma_terms(t->elem, p, prec, a, stream);
 }
@@ -537,6 +546,7 @@ int fem_integrate_elastic_terms(fem_tables t, int p, int64_t n_elem, const doubl
   a.b = b_out;
   a.status = status;
   a.layout = FEM_OUT_FULL;
+  a.err = t->d_err;
   return launch_fma_elastic_terms(p, prec, a, stream);
 }
 

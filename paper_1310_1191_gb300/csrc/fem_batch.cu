@@ -163,6 +163,8 @@ struct fem_plan_s {
   fem_tables t = nullptr;
   int device = 0;  // the device current at creation (the tables' device)
   int prec = 0, layout = 0, flags = 0;
+  int64_t totA = 0, totb = 0;  // values of A_out and b_out
+  int shrink_next = 0;         // test hook of checked builds (fem_debug_shrink_bound)
   int64_t n = 0;
   std::string cache;
   int64_t bin_off[fem::kMaxP + 2] = {0};  // sorted positions of each degree's bin
@@ -323,6 +325,9 @@ static int launch_bin(const fem_plan_s *pl, int p, int v, const FmaArgs &base, c
     l.perm = pl->perm + k0;
     l.offA = base.offA;
     l.offb = base.offb;
+    l.limA = base.limA;
+    l.limb = base.limb;
+    l.nmesh = base.nmesh;
     return launch_tc(p, pl->prec == FEM_F16X3, d, l, s);
   }
   FmaArgs a = base;
@@ -582,7 +587,8 @@ int fem_integrate_mixed_noalloc(fem_tables t, int64_t n_elem, const int8_t *p_ho
   // host side: counting sort by degree, output offsets, work list (default shapes)
   for (int p = 0; p <= kMaxP + 1; p++) cur[p] = bin_off[p];
   for (int64_t e = 0; e < n_elem; e++) g_noalloc_h_perm[cur[p_host[e]]++] = e;
-  int rc = fem_output_offsets(FEM_PRISM6, p_host, n_elem, layout, g_noalloc_h_offA, g_noalloc_h_offb, nullptr);
+  int64_t tot[2] = {0, 0};
+  int rc = fem_output_offsets(FEM_PRISM6, p_host, n_elem, layout, g_noalloc_h_offA, g_noalloc_h_offb, tot);
   if (rc != FEM_OK) return rc;
   int variant[kMaxP + 1] = {0};
   std::vector<int4> items;
@@ -618,6 +624,10 @@ int fem_integrate_mixed_noalloc(fem_tables t, int64_t n_elem, const int8_t *p_ho
   a.perm = reinterpret_cast<const int64_t *>(base + kNoAllocOffPerm);
   a.offA = reinterpret_cast<const int64_t *>(base + kNoAllocOffA);
   a.offb = reinterpret_cast<const int64_t *>(base + kNoAllocOffB);
+  a.err = t->d_err;
+  a.nmesh = n_elem;
+  a.limA = tot[0];
+  a.limb = tot[1];
   BatchArgs b = batch_args_raw(t, prec, a, reinterpret_cast<const int4 *>(base + kNoAllocOffItems),
                                (int)items.size(), reinterpret_cast<unsigned *>(base));
   return launch_batch_raw(prec == FEM_F64, b, s);  // zeroes the counter, then launches
@@ -716,6 +726,8 @@ int fem_plan_create(fem_tables t, int64_t n_elem, const int8_t *p_host, int prec
   for (int64_t e = 0; e < n_elem; e++) perm[cur[p_host[e]]++] = e;
   int64_t tot[2];
   int rc = fem_output_offsets(FEM_PRISM6, p_host, n_elem, layout, offA.data(), offb.data(), tot);
+  pl->totA = tot[0];
+  pl->totb = tot[1];
   auto up = [&](int64_t **dst, const std::vector<int64_t> &src) -> int {
     cudaError_t e = cudaMalloc((void **)dst, sizeof(int64_t) * src.size());
     if (e == cudaSuccess) e = cudaMemcpy(*dst, src.data(), sizeof(int64_t) * src.size(), cudaMemcpyHostToDevice);
@@ -786,7 +798,22 @@ int fem_plan_execute(fem_plan pl, const double *coords, const double *coeffs, in
   base.perm = pl->perm;
   base.offA = pl->offA;
   base.offb = pl->offb;
+  // checked builds: element ids and output offsets against the plan's extents
+  base.err = pl->t->d_err;
+  base.nmesh = pl->n;
+  base.limA = pl->totA;
+  base.limb = pl->totb;
   int rc = FEM_OK;
+  if (pl->shrink_next) {
+    // test hook of checked builds: A_out taken as one value shorter than it
+    // is, so the block that ends there is refused by the checks; a direct
+    // launch (no graph), the next execution is normal again
+    pl->shrink_next = 0;
+    base.limA = pl->totA - 1;
+    if (pl->flags & FEM_PLAN_LOOP) return launch_per_p_loop(pl, base, s);
+    if (pl->flags & FEM_PLAN_CONCURRENT) return launch_concurrent(pl, base, s);
+    return launch_batch(pl, batch_args(pl, base), s);
+  }
   if ((pl->flags & FEM_PLAN_AUTOTUNE) && !pl->tuned) {
     rc = autotune(pl, base, s);
     if (rc != FEM_OK) return rc;
@@ -822,6 +849,19 @@ int fem_plan_execute(fem_plan pl, const double *coords, const double *coeffs, in
   }
   cudaError_t e = cudaGraphLaunch(pl->exec, s);
   if (e != cudaSuccess) return plan_fail("cudaGraphLaunch", e);
+  return FEM_OK;
+}
+
+int fem_debug_shrink_bound(fem_plan pl) {
+  if (!pl) {
+    set_error("fem_debug_shrink_bound: plan is NULL");
+    return FEM_EINVAL;
+  }
+  if (!kChecked) {
+    set_error("fem_debug_shrink_bound: a hook of the checked build (libfem_gb300_checked.so)");
+    return FEM_EUNSUPPORTED;
+  }
+  pl->shrink_next = 1;
   return FEM_OK;
 }
 

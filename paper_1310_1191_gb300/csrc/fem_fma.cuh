@@ -147,7 +147,9 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
 
   for (int le = tid; le < C::EPB; le += nthr) {
     const int64_t k = k0 + le;
-    sE[le] = k < k_end ? (a.perm ? a.perm[k] : k) : -1;
+    int64_t v = k < k_end ? (a.perm ? a.perm[k] : k) : -1;
+    if (v >= 0 && a.perm && a.nmesh >= 0 && !fem_chk(v < a.nmesh, a.err)) v = -1;  // checked builds
+    sE[le] = v;
     sSt[le] = 0;
   }
   __syncthreads();
@@ -509,7 +511,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
         const T *g = sG + (size_t)l2 * C::NQ * kGStride + SLOT;
         for (int q = 0; q < C::NQ; q++) s = fma(g[q * kGStride], phi[(size_t)(4 * q) * C::NS + row], s);
         const int64_t boff = ELAST ? (e / 3) * (int64_t)C::NS : (a.offb ? a.offb[e] : e * (int64_t)C::NS);
-        bo[boff + row] = s;
+        if (fem_chk(a.limb < 0 || (boff >= 0 && boff + C::NS <= a.limb), a.err)) bo[boff + row] = s;
       }
     }
   }
@@ -518,8 +520,10 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   const int64_t e = owner ? sE[le] : -1;
   if (e >= 0) {
     T *Ao = static_cast<T *>(a.A);
-    if (a.layout == FEM_OUT_FULL) {
-      T *Ae = Ao + (a.offA ? a.offA[e] : e * (int64_t)NSZ);
+    const int64_t oA = a.offA ? a.offA[e] : e * (int64_t)(a.layout == FEM_OUT_FULL ? NSZ : NPK);
+    const bool okA = fem_chk(a.limA < 0 || (oA >= 0 && oA + (a.layout == FEM_OUT_FULL ? NSZ : NPK) <= a.limA), a.err);
+    if (okA && a.layout == FEM_OUT_FULL) {
+      T *Ae = Ao + oA;
 #pragma unroll
       for (int i = 0; i < C::TM; i++) {
         const int row = ti * C::BM + ty * C::TM + i;
@@ -530,8 +534,8 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
           if (col < C::NS) Ae[row * C::NS + col] = acc[i][j];
         }
       }
-    } else {
-      T *Ae = Ao + (a.offA ? a.offA[e] : e * (int64_t)NPK);
+    } else if (okA) {
+      T *Ae = Ao + oA;
 #pragma unroll
       for (int i = 0; i < C::TM; i++) {
         const int row = ti * C::BM + ty * C::TM + i;

@@ -15,6 +15,29 @@ namespace fem {
 
 constexpr int kMaxP = 7;
 
+// Checked builds (-DFEM_CHECKED, libfem_gb300_checked.so): the kernels check
+// the element ids and output offsets that come from permutations and offset
+// tables against the launch's bounds; a failed check skips the access and
+// sets bit 2 of the device error word (fem_error_flag then returns
+// FEM_ECHECKED).  In normal builds every check is compiled out.
+#ifdef FEM_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+constexpr int kErrTimeout = 1, kErrCheck = 2;
+
+#ifdef __CUDACC__
+__device__ __forceinline__ bool fem_chk(bool ok, int *err) {
+  if constexpr (kChecked) {
+    if (!ok && err) atomicOr(err, kErrCheck);
+    return ok;
+  } else {
+    return true;
+  }
+}
+#endif
+
 __host__ __device__ constexpr int ns_of(int elem, int p) {
   return elem == FEM_TET4 ? 4 : (p + 1) * (p + 1) * (p + 2) / 2;
 }
@@ -140,6 +163,11 @@ struct FmaArgs {
   float box[4] = {0, 0, 0, 0};   // u0, u1, s0, s1 (network used inside)
   int law_iters = 8;             // Newton steps of the exact law
   int hw_tanh = 0;               // network activations from tanh.approx.f32
+  // checked builds: device error word and the values of A and b the outputs
+  // hold (negative: not checked)
+  int *err = nullptr;
+  int64_t limA = -1, limb = -1;
+  int64_t nmesh = -1;  // checked builds: element ids from perm lie below it (negative: not checked)
 };
 
 // fem_integrate with per-element degrees: runs (and keeps in t) a per-degree
@@ -192,6 +220,8 @@ struct TcLaunch {
   float box[4] = {0, 0, 0, 0};
   int law_iters = 8;
   int hw_tanh = 0;
+  int64_t limA = -1, limb = -1;  // checked builds: values of A and b (negative: not checked)
+  int64_t nmesh = -1;            // checked builds: element ids from perm lie below it
 };
 int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *stream);
 

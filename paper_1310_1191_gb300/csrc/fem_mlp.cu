@@ -683,6 +683,7 @@ int integrate_law_opts(fem_tables t, int p, int64_t n_elem, const double *coords
   a.b = b_out;
   a.status = status;
   a.layout = layout;
+  a.err = t->d_err;
   a.ucoef = ucoef;
   a.law_iters = newton_steps;
   a.hw_tanh = hw_tanh;

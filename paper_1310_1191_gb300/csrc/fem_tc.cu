@@ -36,6 +36,9 @@ int launch_tc(int p, bool f16, const DevTable &d, const TcLaunch &l, void *strea
   }
   a.law_iters = l.law_iters;
   a.hw_tanh = l.hw_tanh;
+  a.limA = l.limA;
+  a.limb = l.limb;
+  a.nmesh = l.nmesh;
   if (l.elastic && (a.perm || a.offA || a.offb)) {
     set_error("tensor-core elasticity takes dense outputs only");
     return FEM_EINVAL;

@@ -164,6 +164,8 @@ struct TcArgs {
   float nrm[4], box[4];
   int law_iters;  // Newton steps of the exact law
   int hw_tanh;    // network activations from tanh.approx.f32
+  int64_t limA, limb;  // checked builds: values of A and b (negative: not checked)
+  int64_t nmesh;       // checked builds: element ids from perm lie below it (negative: not checked)
 };
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
@@ -543,7 +545,10 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
             const int el = idx / C::NREC, k = idx % C::NREC;
             const int64_t e = e_new + el;
             const int64_t eg = a.perm ? a.perm[e] : e;  // element of the mesh
-            sX[idx] = k < 18 ? a.coords[eg * 18 + k] : a.coeffs[(k - 18) * a.cstride + eg];
+            if (fem_chk(!a.perm || a.nmesh < 0 || (eg >= 0 && eg < a.nmesh), a.err))  // checked builds
+              sX[idx] = k < 18 ? a.coords[eg * 18 + k] : a.coeffs[(k - 18) * a.cstride + eg];
+            else
+              sX[idx] = 0.0;
           }
           if (LAW != 0)
             for (int idx = gt; idx < nnew * C::NS; idx += kNGeo) {
@@ -766,28 +771,32 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
           const int64_t ve = valid ? r / C::L : 0;  // virtual element (the element for the scalar form)
           const int64_t e = ve / VPE;
           const int64_t eg = a.perm && valid ? a.perm[e] : e;  // element of the mesh
+          // checked builds: an element id outside the mesh skips the row's stores
+          const bool egok = !valid || fem_chk(!a.perm || a.nmesh < 0 || (eg >= 0 && eg < a.nmesh), a.err);
           const int j = valid ? (int)(r % C::L) : 0;
           const int sl = (int)(e % C::RING);
           const float inv = valid ? (j < C::NS ? sInv[sl] : sInvB[sl]) : 0.f;
           const uint32_t tbase = tmem + ab * C::NP + ((uint32_t)(32 * lq) << 16);
-#pragma unroll 1
-          for (int c0 = 0; c0 < C::NP; c0 += 16) {
-            uint32_t v[16];
-            ptx::tmem_ld16(tbase + c0, v);
-            ptx::tmem_ld_wait();
-            if (valid) {
+          constexpr int NPK = C::NS * (C::NS + 1) / 2;
+          // columns c0 .. c0 + 15 of the accumulator row (v[0..15]) -> A_e / b_e
+          auto store16 = [&](int c0, const uint32_t (&v)[16]) {
+            if (valid && egok) {
               if (j < C::NS) {
-                if (a.layout == FEM_OUT_FULL) {
+                const int64_t oA = a.offA ? a.offA[eg] : (a.layout == FEM_OUT_FULL ? ve * (int64_t)(C::NS * C::NS)
+                                                                               : e * (int64_t)NPK);
+                const int64_t mA = a.layout == FEM_OUT_FULL ? (int64_t)C::NS * C::NS : NPK;
+                if (!fem_chk(a.limA < 0 || (oA >= 0 && oA + mA <= a.limA), a.err)) {
+                  // checked builds: the element's block lies outside A; skipped
+                } else if (a.layout == FEM_OUT_FULL) {
                   // elasticity: block-major A^e[i][k][s][r] = block ve's [s][r]
-                  float *Ae = static_cast<float *>(a.A) + (a.offA ? a.offA[eg] : ve * (int64_t)(C::NS * C::NS)) + j;
+                  float *Ae = static_cast<float *>(a.A) + oA + j;
 #pragma unroll
                   for (int u = 0; u < 16; u++) {
                     const int i = c0 + u;
                     if (i < C::NS) Ae[(size_t)i * C::NS] = __uint_as_float(v[u]) * inv;
                   }
                 } else {
-                  constexpr int NPK = C::NS * (C::NS + 1) / 2;
-                  float *Ae = static_cast<float *>(a.A) + (a.offA ? a.offA[eg] : e * (int64_t)NPK);
+                  float *Ae = static_cast<float *>(a.A) + oA;
 #pragma unroll
                   for (int u = 0; u < 16; u++) {
                     const int i = c0 + u;
@@ -796,14 +805,28 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
                 }
               } else if (a.b != nullptr && (!ELAS || ve % 3 == 0)) {
                 // elasticity: the blocks (i, 0) carry b^e[i] (index 3 e + i = ve / 3)
-                float *be = static_cast<float *>(a.b) + (a.offb ? a.offb[eg] : (ELAS ? ve / 3 : e) * (int64_t)C::NS);
+                const int64_t ob = a.offb ? a.offb[eg] : (ELAS ? ve / 3 : e) * (int64_t)C::NS;
+                if (fem_chk(a.limb < 0 || (ob >= 0 && ob + C::NS <= a.limb), a.err)) {
+                  float *be = static_cast<float *>(a.b) + ob;
 #pragma unroll
-                for (int u = 0; u < 16; u++) {
-                  const int i = c0 + u;
-                  if (i < C::NS) be[i] = __uint_as_float(v[u]) * inv;
+                  for (int u = 0; u < 16; u++) {
+                    const int i = c0 + u;
+                    if (i < C::NS) be[i] = __uint_as_float(v[u]) * inv;
+                  }
                 }
               }
             }
+          };
+          // two 16-column loads in flight per wait
+#pragma unroll 1
+          for (int c0 = 0; c0 < C::NP; c0 += 32) {
+            uint32_t v0[16], v1[16];
+            const bool two = c0 + 16 < C::NP;  // warp-uniform
+            ptx::tmem_ld16(tbase + c0, v0);
+            if (two) ptx::tmem_ld16(tbase + c0 + 16, v1);
+            ptx::tmem_ld_wait();
+            store16(c0, v0);
+            if (two) store16(c0 + 16, v1);
           }
           ptx::tc_fence_before();
           __syncwarp();
@@ -818,7 +841,7 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
 
   __syncthreads();
   if (*sAbort) {
-    if (tid == 0 && a.err) atomicExch(a.err, 1);
+    if (tid == 0 && a.err) atomicOr(a.err, kErrTimeout);
     // flag the elements of this CTA's tiles that may be incomplete
     if (a.status) {
       for (int64_t t = t_begin; t < t_end; t++) {
