@@ -110,7 +110,8 @@ struct TcCfg {
   static constexpr size_t OFF_ZR = OFF_XF + (size_t)MAXEL * NAB * kXf * 8;     // float [MAXEL][NZ][4]
   static constexpr size_t OFF_CF = OFF_ZR + (size_t)MAXEL * NZ * 16;           // float [MAXEL][12]
   static constexpr size_t OFF_W = OFF_CF + (size_t)MAXEL * 48;                 // float [NQP] weights
-  static constexpr size_t OFF_RS = OFF_W + (size_t)NQP * 4;                    // per slot: 7 x [RING] words
+  static constexpr size_t OFF_QZ = OFF_W + (size_t)NQP * 4;                    // double [NZ] zeta, [NAB][2] (xi, eta)
+  static constexpr size_t OFF_RS = OFF_QZ + (size_t)(NZ + 2 * NAB) * 8;        // per slot: 7 x [RING] words
   static constexpr size_t OFF_EC = (OFF_RS + 28 * (size_t)RING + 15) / 16 * 16;   // float [RING][8] (elasticity)
   // coefficient law: field coefficients of the pass's new elements; network
   // weights and the inputs of the pass's points (network only)
@@ -212,6 +213,7 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
   float *sZR = reinterpret_cast<float *>(sm + C::OFF_ZR);        // [MAXEL][NZ][4] adj row 2, FP32
   float *sCF = reinterpret_cast<float *>(sm + C::OFF_CF);        // [MAXEL][12] coefficients, FP32
   float *sW = reinterpret_cast<float *>(sm + C::OFF_W);          // [NQP] quadrature weights, FP32
+  double *sQZ = reinterpret_cast<double *>(sm + C::OFF_QZ);      // [NZ] zeta levels, then [NAB][2] (xi, eta)
   float *sEC = reinterpret_cast<float *>(sm + C::OFF_EC);        // [RING][8] lambda, mu, f (elasticity)
   float *sUC = reinterpret_cast<float *>(sm + C::OFF_UC);        // [MAXEL][NS] field coefficients (law)
   float *sMP = reinterpret_cast<float *>(sm + C::OFF_MLP);       // network: FP32 W1 b1 b2 W3 b3 (law 2)
@@ -241,6 +243,9 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
   const int64_t t_begin = (int64_t)blockIdx.x * ntiles / gridDim.x;
   const int64_t t_end = ((int64_t)blockIdx.x + 1) * ntiles / gridDim.x;
   for (int q = tid; q < C::NQP; q += blockDim.x) sW[q] = q < C::NQ ? (float)a.qp[4 * q + 3] : 0.f;
+  // the rule's zeta levels and triangle points (point q = iz NAB + iab)
+  for (int k = tid; k < C::NZ + 2 * C::NAB; k += blockDim.x)
+    sQZ[k] = k < C::NZ ? a.qp[4 * (k * C::NAB) + 2] : a.qp[4 * ((k - C::NZ) / 2) + (k - C::NZ) % 2];
   if (LAW == 2) {  // network parameters (layout of the CUDA-core law kernels)
     constexpr int H = kMlpH;
     for (int idx = tid; idx < kMlpSmall; idx += blockDim.x) {
@@ -564,26 +569,39 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
         }
         gbar();
         if (go) {
-          for (int idx = gt; idx < nnew * C::NREC; idx += kNGeo)
-            if (!isfinite(sX[idx])) atomicOr(&sSt[(e_new + idx / C::NREC) % C::RING], FEM_ST_NONFINITE);
-          if (gt < nnew) {
-            const double *cf = sX + gt * C::NREC + 18;
-            edge_record<FEM_PRISM6>(sX + gt * C::NREC, sEd + gt * kEdgeRec);
-            if (ELAS) {  // E, nu, f -> lambda, mu, f of the element's slot
-              const double Ey = cf[0], nu = cf[1];
-              float *ec = sEC + ((e_new + gt) % C::RING) * 8;
-              ec[0] = (float)(Ey * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
-              ec[1] = (float)(Ey / (2.0 * (1.0 + nu)));
-              ec[2] = (float)cf[2];
-              ec[3] = (float)cf[3];
-              ec[4] = (float)cf[4];
-            } else {
-              if (a.layout == FEM_OUT_SYMPACKED && (cf[6] != 0.0 || cf[7] != 0.0 || cf[8] != 0.0))
-                atomicOr(&sSt[(e_new + gt) % C::RING], FEM_ST_NONSYM);
-              float *cfl = sCF + gt * 12;  // D00 D11 D22 D01 D02 D12 b0 b1 b2 c f
-#pragma unroll
-              for (int k = 0; k < 11; k++) cfl[k] = (float)cf[k];
+          // one value per thread: the non-finite check of each input, the
+          // element's edge record (21 differences of vertex coordinates, as
+          // edge_record forms them) and its FP32 coefficients (a chain of FP64
+          // operations on one thread per element was the slowest step here)
+          for (int idx = gt; idx < nnew * C::NREC; idx += kNGeo) {
+            const int el = idx / C::NREC, k = idx % C::NREC;
+            const double *xe = sX + el * C::NREC;
+            const double v = xe[k];
+            if (!isfinite(v)) atomicOr(&sSt[(e_new + el) % C::RING], FEM_ST_NONFINITE);
+            if (k < kEdgeRec) {
+              // value k = 3 m + i of vertex pair m: (1,0) (4,3) (2,0) (5,3) (3,0) (4,1) (5,2)
+              constexpr unsigned kVa = 1u | 4u << 4 | 2u << 8 | 5u << 12 | 3u << 16 | 4u << 20 | 5u << 24;
+              constexpr unsigned kVb = 0u | 3u << 4 | 0u << 8 | 3u << 12 | 0u << 16 | 1u << 20 | 2u << 24;
+              const int m = k / 3, i = k % 3;
+              const int va = (kVa >> (4 * m)) & 15, vb = (kVb >> (4 * m)) & 15;
+              sEd[el * kEdgeRec + k] = xe[3 * va + i] - xe[3 * vb + i];
             }
+            if (!ELAS && k >= 18) {
+              const int kc = k - 18;  // D00 D11 D22 D01 D02 D12 b0 b1 b2 c f
+              sCF[el * 12 + kc] = (float)v;
+              if (kc >= 6 && kc <= 8 && a.layout == FEM_OUT_SYMPACKED && v != 0.0)
+                atomicOr(&sSt[(e_new + el) % C::RING], FEM_ST_NONSYM);
+            }
+          }
+          if (ELAS && gt < nnew) {  // E, nu, f -> lambda, mu, f of the element's slot
+            const double *cf = sX + gt * C::NREC + 18;
+            const double Ey = cf[0], nu = cf[1];
+            float *ec = sEC + ((e_new + gt) % C::RING) * 8;
+            ec[0] = (float)(Ey * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+            ec[1] = (float)(Ey / (2.0 * (1.0 + nu)));
+            ec[2] = (float)cf[2];
+            ec[3] = (float)cf[3];
+            ec[4] = (float)cf[4];
           }
         }
         gbar();
@@ -593,13 +611,14 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
             const double *ed = sEd + el * kEdgeRec;
             if (r < C::NZ) {
               double *zf = sZF + (el * C::NZ + r) * kZf;
-              prism_zf(ed, a.qp[4 * (r * C::NAB) + 2], zf);
+              prism_zf(ed, sQZ[r], zf);
               float *zr = sZR + (el * C::NZ + r) * 4;
               zr[0] = (float)zf[6];
               zr[1] = (float)zf[7];
               zr[2] = (float)zf[8];
             } else {
-              prism_xf(ed, a.qp[4 * (r - C::NZ)], a.qp[4 * (r - C::NZ) + 1], sXF + (el * C::NAB + r - C::NZ) * kXf);
+              const double *xe = sQZ + C::NZ + 2 * (r - C::NZ);
+              prism_xf(ed, xe[0], xe[1], sXF + (el * C::NAB + r - C::NZ) * kXf);
             }
           }
         }
