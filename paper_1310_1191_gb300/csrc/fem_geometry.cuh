@@ -147,6 +147,27 @@ __device__ __forceinline__ void prism_zf(const double *ed, double zeta, double *
   zf[8] = c0[0] * c1[1] - c0[1] * c1[0];
 }
 
+// The same two factors from the level's (lo, hi) and the triangle point's
+// (h0, h1, h2), computed once per rule.
+__device__ __forceinline__ void prism_zf_lh(const double *ed, double lo, double hi, double *zf) {
+  double c0[3], c1[3];
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    c0[i] = fma(lo, ed[0 + i], hi * ed[3 + i]);
+    c1[i] = fma(lo, ed[6 + i], hi * ed[9 + i]);
+  }
+  zf[0] = c0[0], zf[1] = c0[1], zf[2] = c0[2];
+  zf[3] = c1[0], zf[4] = c1[1], zf[5] = c1[2];
+  zf[6] = c0[1] * c1[2] - c0[2] * c1[1];
+  zf[7] = c0[2] * c1[0] - c0[0] * c1[2];
+  zf[8] = c0[0] * c1[1] - c0[1] * c1[0];
+}
+
+__device__ __forceinline__ void prism_xf_h(const double *ed, double h0, double h1, double h2, double *xf) {
+#pragma unroll
+  for (int i = 0; i < 3; i++) xf[i] = fma(h0, ed[12 + i], fma(h1, ed[15 + i], h2 * ed[18 + i]));
+}
+
 __device__ __forceinline__ void prism_xf(const double *ed, double xi, double eta, double *xf) {
   const double h0 = 0.5 * (1.0 - xi - eta), h1 = 0.5 * xi, h2 = 0.5 * eta;
 #pragma unroll

@@ -69,8 +69,13 @@ struct TcCfg {
   static constexpr int NSPLIT = NP > 256 ? 2 : 1;
   static constexpr int NH = NP / NSPLIT;
   static constexpr int MAXEL = (BM - 1 + L - 1) / L + 1;
-  static constexpr int NACC = 2 * NP <= 512 ? 2 : 1;  // TMEM accumulator buffers
-  static constexpr int TCOLS_NEED = NACC * NP;
+  // accumulators per tile: with KACC = 2 the two K steps of each chunk go to
+  // two accumulators whose MMAs alternate (no MMA waits for the one before
+  // it on the same accumulator), summed in FP32 by the epilogue; where TMEM
+  // holds four (p <= 5), else one (p = 7 alternates its two N halves)
+  static constexpr int KACC = 4 * NP <= 512 ? 2 : 1;
+  static constexpr int NACC = 2 * KACC * NP <= 512 ? 2 : 1;  // TMEM accumulator buffers (tiles in flight)
+  static constexpr int TCOLS_NEED = NACC * KACC * NP;
   static constexpr int TMEM_COLS = TCOLS_NEED <= 32 ? 32 : TCOLS_NEED <= 64 ? 64 : TCOLS_NEED <= 128 ? 128
                                    : TCOLS_NEED <= 256 ? 256 : 512;
   // operand stages: as many as shared memory holds (the Phi^T copies come
@@ -86,6 +91,11 @@ struct TcCfg {
   static constexpr int THREADS = (8 + PRODW) * 32;
   static constexpr int NPROD = PRODW * 32, PPR = NPROD / BM, QH = QC / PPR;
   static constexpr int GEOW0 = 6 + PRODW;  // first geometry-only warp
+  // p <= 4: the geometry pass bounds the kernel (tiles have few K chunks), so
+  // the inputs of its next pass are fetched ahead (cp.async), its J factors
+  // go one value per thread and its point records are spread evenly over the
+  // SM sub-partitions; above, the plain forms measured faster
+  static constexpr bool GEO_FINE = P <= 4;
   // chunks of Phi values the producers keep in flight (registers)
   static constexpr int PD = PRODW == 16 ? 2 : 3;
   static constexpr int A_BYTES = BM * KC * 2;  // one half (hi or lo)
@@ -103,15 +113,15 @@ struct TcCfg {
   static constexpr int GSLOT = NQP * 12;  // floats of point records per element
   // shared layout (bytes from a 1024-aligned base)
   static constexpr size_t OFF_G = (size_t)STAGES * STAGE_BYTES;                // float [RING][NQP][12]
-  static constexpr size_t OFF_X = OFF_G + (size_t)RING * GSLOT * 4;            // double [MAXEL][NREC]
-  static constexpr size_t OFF_ED = OFF_X + (size_t)MAXEL * NREC * 8;           // double [MAXEL][21]
+  static constexpr size_t OFF_X = OFF_G + (size_t)RING * GSLOT * 4;            // double [2][MAXEL][NREC]
+  static constexpr size_t OFF_ED = OFF_X + (size_t)2 * MAXEL * NREC * 8;       // double [MAXEL][21]
   static constexpr size_t OFF_ZF = OFF_ED + (size_t)MAXEL * kEdgeRec * 8;      // double [MAXEL][NZ][9]
   static constexpr size_t OFF_XF = OFF_ZF + (size_t)MAXEL * NZ * kZf * 8;      // double [MAXEL][NAB][3]
   static constexpr size_t OFF_ZR = OFF_XF + (size_t)MAXEL * NAB * kXf * 8;     // float [MAXEL][NZ][4]
   static constexpr size_t OFF_CF = OFF_ZR + (size_t)MAXEL * NZ * 16;           // float [MAXEL][12]
   static constexpr size_t OFF_W = OFF_CF + (size_t)MAXEL * 48;                 // float [NQP] weights
-  static constexpr size_t OFF_QZ = OFF_W + (size_t)NQP * 4;                    // double [NZ] zeta, [NAB][2] (xi, eta)
-  static constexpr size_t OFF_RS = OFF_QZ + (size_t)(NZ + 2 * NAB) * 8;        // per slot: 7 x [RING] words
+  static constexpr size_t OFF_QF = OFF_W + (size_t)NQP * 4;                    // double [NZ][2], [NAB][3] rule factors
+  static constexpr size_t OFF_RS = OFF_QF + (size_t)(2 * NZ + 3 * NAB) * 8;    // per slot: 7 x [RING] words
   static constexpr size_t OFF_EC = (OFF_RS + 28 * (size_t)RING + 15) / 16 * 16;   // float [RING][8] (elasticity)
   // coefficient law: field coefficients of the pass's new elements; network
   // weights and the inputs of the pass's points (network only)
@@ -206,14 +216,17 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
   extern __shared__ unsigned char smem_raw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float *sG = reinterpret_cast<float *>(sm + C::OFF_G);          // [RING][NQP][12] point records
-  double *sX = reinterpret_cast<double *>(sm + C::OFF_X);        // [MAXEL][NREC] new elements of a pass
+  double *sX = reinterpret_cast<double *>(sm + C::OFF_X);        // [2][MAXEL][NREC] new elements of a pass
   double *sEd = reinterpret_cast<double *>(sm + C::OFF_ED);      // [MAXEL][21]
   double *sZF = reinterpret_cast<double *>(sm + C::OFF_ZF);      // [MAXEL][NZ][9]
   double *sXF = reinterpret_cast<double *>(sm + C::OFF_XF);      // [MAXEL][NAB][3]
   float *sZR = reinterpret_cast<float *>(sm + C::OFF_ZR);        // [MAXEL][NZ][4] adj row 2, FP32
   float *sCF = reinterpret_cast<float *>(sm + C::OFF_CF);        // [MAXEL][12] coefficients, FP32
   float *sW = reinterpret_cast<float *>(sm + C::OFF_W);          // [NQP] quadrature weights, FP32
-  double *sQZ = reinterpret_cast<double *>(sm + C::OFF_QZ);      // [NZ] zeta levels, then [NAB][2] (xi, eta)
+  // per zeta level (lo, hi) = ((1 - zeta) / 2, (1 + zeta) / 2), then per
+  // triangle point (h0, h1, h2) = ((1 - xi - eta) / 2, xi / 2, eta / 2):
+  // the weights of the edge vectors in J (see edge_record)
+  double *sQF = reinterpret_cast<double *>(sm + C::OFF_QF);
   float *sEC = reinterpret_cast<float *>(sm + C::OFF_EC);        // [RING][8] lambda, mu, f (elasticity)
   float *sUC = reinterpret_cast<float *>(sm + C::OFF_UC);        // [MAXEL][NS] field coefficients (law)
   float *sMP = reinterpret_cast<float *>(sm + C::OFF_MLP);       // network: FP32 W1 b1 b2 W3 b3 (law 2)
@@ -244,8 +257,18 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
   const int64_t t_end = ((int64_t)blockIdx.x + 1) * ntiles / gridDim.x;
   for (int q = tid; q < C::NQP; q += blockDim.x) sW[q] = q < C::NQ ? (float)a.qp[4 * q + 3] : 0.f;
   // the rule's zeta levels and triangle points (point q = iz NAB + iab)
-  for (int k = tid; k < C::NZ + 2 * C::NAB; k += blockDim.x)
-    sQZ[k] = k < C::NZ ? a.qp[4 * (k * C::NAB) + 2] : a.qp[4 * ((k - C::NZ) / 2) + (k - C::NZ) % 2];
+  for (int k = tid; k < C::NZ; k += blockDim.x) {
+    const double ze = a.qp[4 * (k * C::NAB) + 2];
+    sQF[2 * k] = 0.5 * (1.0 - ze);
+    sQF[2 * k + 1] = 0.5 * (1.0 + ze);
+  }
+  for (int k = tid; k < C::NAB; k += blockDim.x) {
+    const double xi = a.qp[4 * k], eta = a.qp[4 * k + 1];
+    double *h = sQF + 2 * C::NZ + 3 * k;
+    h[0] = 0.5 * (1.0 - xi - eta);
+    h[1] = 0.5 * xi;
+    h[2] = 0.5 * eta;
+  }
   if (LAW == 2) {  // network parameters (layout of the CUDA-core law kernels)
     constexpr int H = kMlpH;
     for (int idx = tid; idx < kMlpSmall; idx += blockDim.x) {
@@ -338,7 +361,7 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
         const uint32_t ab = C::NACC == 2 ? (tt & 1) : 0, use = tt / C::NACC;
         if (!wait(&bar_acce[ab], (use & 1) ^ 1)) break;
         ptx::tc_fence_after();
-        const uint32_t dacc = tmem + ab * C::NP;
+        const uint32_t dacc = tmem + ab * C::KACC * C::NP;
         bool ok = true;
         for (int c = 0; c < C::NCH; c++, g++) {
           const int s = g % C::STAGES;
@@ -350,19 +373,40 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
           ptx::tc_fence_after();
           const uint32_t aH = stage0 + s * C::STAGE_BYTES, aL = aH + C::A_BYTES;
           const uint32_t bH = aL + C::A_BYTES, bL = bH + C::B_BYTES;
+          if constexpr (C::KACC == 2) {
+            // K step ks into accumulator ks; the products alternate between
+            // the two: hi.hi (0), hi.hi (1), hi.lo (0), hi.lo (1), lo.hi (0), lo.hi (1)
+            static_assert(C::KC / 16 == 2 && C::NSPLIT == 1, "two K steps, one N part");
+            uint64_t adH[2], adL[2], bdH[2], bdL[2];
 #pragma unroll
-          for (int ks = 0; ks < C::KC / 16; ks++) {
-            const uint64_t adH = ptx::smem_desc(aH + ks * 256, 128, C::SBO);
-            const uint64_t adL = ptx::smem_desc(aL + ks * 256, 128, C::SBO);
+            for (int ks = 0; ks < 2; ks++) {
+              adH[ks] = ptx::smem_desc(aH + ks * 256, 128, C::SBO);
+              adL[ks] = ptx::smem_desc(aL + ks * 256, 128, C::SBO);
+              bdH[ks] = ptx::smem_desc(bH + ks * 256, 128, C::SBO);
+              bdL[ks] = ptx::smem_desc(bL + ks * 256, 128, C::SBO);
+            }
+            const uint32_t acc0 = c > 0 ? 1u : 0u;
 #pragma unroll
-            for (int h = 0; h < C::NSPLIT; h++) {
-              const uint32_t boff = h * (C::NH / 8) * C::SBO + ks * 256;
-              const uint64_t bdH = ptx::smem_desc(bH + boff, 128, C::SBO);
-              const uint64_t bdL = ptx::smem_desc(bL + boff, 128, C::SBO);
-              const uint32_t d = dacc + h * C::NH;
-              ptx::mma_f16(d, adH, bdH, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-              ptx::mma_f16(d, adH, bdL, idesc, 1u);
-              ptx::mma_f16(d, adL, bdH, idesc, 1u);
+            for (int ks = 0; ks < 2; ks++) ptx::mma_f16(dacc + ks * C::NP, adH[ks], bdH[ks], idesc, acc0);
+#pragma unroll
+            for (int ks = 0; ks < 2; ks++) ptx::mma_f16(dacc + ks * C::NP, adH[ks], bdL[ks], idesc, 1u);
+#pragma unroll
+            for (int ks = 0; ks < 2; ks++) ptx::mma_f16(dacc + ks * C::NP, adL[ks], bdH[ks], idesc, 1u);
+          } else {
+#pragma unroll
+            for (int ks = 0; ks < C::KC / 16; ks++) {
+              const uint64_t adH = ptx::smem_desc(aH + ks * 256, 128, C::SBO);
+              const uint64_t adL = ptx::smem_desc(aL + ks * 256, 128, C::SBO);
+#pragma unroll
+              for (int h = 0; h < C::NSPLIT; h++) {
+                const uint32_t boff = h * (C::NH / 8) * C::SBO + ks * 256;
+                const uint64_t bdH = ptx::smem_desc(bH + boff, 128, C::SBO);
+                const uint64_t bdL = ptx::smem_desc(bL + boff, 128, C::SBO);
+                const uint32_t d = dacc + h * C::NH;
+                ptx::mma_f16(d, adH, bdH, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                ptx::mma_f16(d, adH, bdL, idesc, 1u);
+                ptx::mma_f16(d, adL, bdH, idesc, 1u);
+              }
             }
           }
           ptx::mma_commit(&bar_empty[s]);
@@ -528,6 +572,35 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
     int64_t e_done = -1;  // last element whose records are in the ring
     uint32_t tt = 0;
     auto gbar = [] { asm volatile("bar.sync 2, 192;" ::: "memory"); };
+    // coordinates and coefficients of a pass's new elements, copied
+    // asynchronously (cp.async) into buffer (pass & 1) one pass ahead, so the
+    // loads from memory overlap the previous pass and its drain
+    auto fetch = [&](int64_t e_new, int nnew, double *dst) {
+      for (int idx = gt; idx < nnew * C::NREC; idx += kNGeo) {
+        const int el = idx / C::NREC, k = idx % C::NREC;
+        const int64_t e = e_new + el;
+        const int64_t eg = a.perm ? a.perm[e] : e;  // element of the mesh
+        if (fem_chk(!a.perm || a.nmesh < 0 || (eg >= 0 && eg < a.nmesh), a.err))  // checked builds
+          ptx::cp_async8(dst + idx, k < 18 ? a.coords + eg * 18 + k : a.coeffs + (k - 18) * a.cstride + eg);
+        else
+          dst[idx] = 0.0;
+      }
+      ptx::cp_async_commit();
+    };
+    // the new elements of tile t (elements above e_done)
+    auto new_elems = [&](int64_t t, int64_t &e_new, int &nnew) {
+      int64_t e_first;
+      int nel;
+      tile_elems(t, e_first, nel);
+      e_new = e_first > e_done + 1 ? e_first : e_done + 1;
+      nnew = (int)(e_first + nel - 1 - e_new + 1);
+    };
+    if (C::GEO_FINE && t_begin < t_end) {
+      int64_t e0;
+      int n0;
+      new_elems(t_begin, e0, n0);
+      fetch(e0, n0, sX);
+    }
     for (int64_t t = t_begin; t <= t_end; t++, tt++) {
       if (t < t_end) {
         const int b = tt & 1;
@@ -540,21 +613,24 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
         const int64_t e_new = e_first > e_done + 1 ? e_first : e_done + 1;
         const int nnew = (int)(e_last - e_new + 1);  // 0 .. MAXEL
         e_done = e_last;
+        double *sXp = sX + (size_t)(tt & 1) * C::MAXEL * C::NREC;  // this pass's inputs
         // tile tt - 2 is finished by the producers and the epilogue: its
         // elements that tiles tt - 1 and tt do not share may be overwritten
         if (gt == 0) wait(&bar_gempty[b], (use & 1) ^ 1);
+        ptx::cp_async_wait_all();  // this thread's copies of the pass's inputs have landed
         gbar();
         const bool go = !*sAbort;
         if (go) {
-          for (int idx = gt; idx < nnew * C::NREC; idx += kNGeo) {
-            const int el = idx / C::NREC, k = idx % C::NREC;
-            const int64_t e = e_new + el;
-            const int64_t eg = a.perm ? a.perm[e] : e;  // element of the mesh
-            if (fem_chk(!a.perm || a.nmesh < 0 || (eg >= 0 && eg < a.nmesh), a.err))  // checked builds
-              sX[idx] = k < 18 ? a.coords[eg * 18 + k] : a.coeffs[(k - 18) * a.cstride + eg];
-            else
-              sX[idx] = 0.0;
-          }
+          if (!C::GEO_FINE)  // the pass's inputs, loaded here
+            for (int idx = gt; idx < nnew * C::NREC; idx += kNGeo) {
+              const int el = idx / C::NREC, k = idx % C::NREC;
+              const int64_t e = e_new + el;
+              const int64_t eg = a.perm ? a.perm[e] : e;  // element of the mesh
+              if (fem_chk(!a.perm || a.nmesh < 0 || (eg >= 0 && eg < a.nmesh), a.err))  // checked builds
+                sXp[idx] = k < 18 ? a.coords[eg * 18 + k] : a.coeffs[(k - 18) * a.cstride + eg];
+              else
+                sXp[idx] = 0.0;
+            }
           if (LAW != 0)
             for (int idx = gt; idx < nnew * C::NS; idx += kNGeo) {
               const int64_t e = e_new + idx / C::NS;
@@ -575,7 +651,7 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
           // operations on one thread per element was the slowest step here)
           for (int idx = gt; idx < nnew * C::NREC; idx += kNGeo) {
             const int el = idx / C::NREC, k = idx % C::NREC;
-            const double *xe = sX + el * C::NREC;
+            const double *xe = sXp + el * C::NREC;
             const double v = xe[k];
             if (!isfinite(v)) atomicOr(&sSt[(e_new + el) % C::RING], FEM_ST_NONFINITE);
             if (k < kEdgeRec) {
@@ -594,7 +670,7 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
             }
           }
           if (ELAS && gt < nnew) {  // E, nu, f -> lambda, mu, f of the element's slot
-            const double *cf = sX + gt * C::NREC + 18;
+            const double *cf = sXp + gt * C::NREC + 18;
             const double Ey = cf[0], nu = cf[1];
             float *ec = sEC + ((e_new + gt) % C::RING) * 8;
             ec[0] = (float)(Ey * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
@@ -605,26 +681,68 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
           }
         }
         gbar();
-        if (go) {  // tensor-product factors of J
-          for (int idx = gt; idx < nnew * (C::NZ + C::NAB); idx += kNGeo) {
-            const int el = idx / (C::NZ + C::NAB), r = idx % (C::NZ + C::NAB);
-            const double *ed = sEd + el * kEdgeRec;
-            if (r < C::NZ) {
-              double *zf = sZF + (el * C::NZ + r) * kZf;
-              prism_zf(ed, sQZ[r], zf);
-              float *zr = sZR + (el * C::NZ + r) * 4;
-              zr[0] = (float)zf[6];
-              zr[1] = (float)zf[7];
-              zr[2] = (float)zf[8];
-            } else {
-              const double *xe = sQZ + C::NZ + 2 * (r - C::NZ);
-              prism_xf(ed, xe[0], xe[1], sXF + (el * C::NAB + r - C::NZ) * kXf);
+        if constexpr (C::GEO_FINE) {
+          if (go) {  // tensor-product factors of J, one value per thread
+            // J[:,0] and J[:,1] of each zeta level (6 values), J[:,2] of each
+            // triangle point (3 values), as prism_zf / prism_xf form them
+            constexpr int NZV = 6 * C::NZ, NXV = 3 * C::NAB;
+            for (int idx = gt; idx < nnew * (NZV + NXV); idx += kNGeo) {
+              const int el = idx / (NZV + NXV), r = idx % (NZV + NXV);
+              const double *ed = sEd + el * kEdgeRec;
+              if (r < NZV) {
+                const int iz = r / 6, j = r % 6, o = j < 3 ? j : j + 3;  // edges (0, 3) or (6, 9)
+                sZF[(el * C::NZ + iz) * kZf + j] = fma(sQF[2 * iz], ed[o], sQF[2 * iz + 1] * ed[o + 3]);
+              } else {
+                const int iab = (r - NZV) / 3, i = (r - NZV) % 3;
+                const double *h = sQF + 2 * C::NZ + 3 * iab;
+                sXF[(el * C::NAB + iab) * kXf + i] = fma(h[0], ed[12 + i], fma(h[1], ed[15 + i], h[2] * ed[18 + i]));
+              }
+            }
+          }
+          gbar();
+          if (go) {  // adj row 2 of each level: J[:,0] x J[:,1] (FP64, and its FP32 copy)
+            for (int idx = gt; idx < nnew * C::NZ * 3; idx += kNGeo) {
+              const int el = idx / (3 * C::NZ), iz = (idx / 3) % C::NZ, j = idx % 3;
+              const int j1 = j == 2 ? 0 : j + 1, j2 = j == 0 ? 2 : j - 1;  // (j + 1) mod 3, (j + 2) mod 3
+              double *zf = sZF + (el * C::NZ + iz) * kZf;
+              const double v = zf[j1] * zf[3 + j2] - zf[j2] * zf[3 + j1];
+              zf[6 + j] = v;
+              sZR[(el * C::NZ + iz) * 4 + j] = (float)v;
+            }
+          }
+        } else {
+          if (go) {  // tensor-product factors of J, one zeta level or triangle point per thread
+            for (int idx = gt; idx < nnew * (C::NZ + C::NAB); idx += kNGeo) {
+              const int el = idx / (C::NZ + C::NAB), r = idx % (C::NZ + C::NAB);
+              const double *ed = sEd + el * kEdgeRec;
+              if (r < C::NZ) {
+                double *zf = sZF + (el * C::NZ + r) * kZf;
+                prism_zf_lh(ed, sQF[2 * r], sQF[2 * r + 1], zf);
+                float *zr = sZR + (el * C::NZ + r) * 4;
+                zr[0] = (float)zf[6];
+                zr[1] = (float)zf[7];
+                zr[2] = (float)zf[8];
+              } else {
+                const double *h = sQF + 2 * C::NZ + 3 * (r - C::NZ);
+                prism_xf_h(ed, h[0], h[1], h[2], sXF + (el * C::NAB + r - C::NZ) * kXf);
+              }
             }
           }
         }
         gbar();
         if (go) {
-          for (int idx = gt; idx < nnew * C::NQP; idx += kNGeo) {
+          // points spread evenly over the four SM sub-partitions (their FP64
+          // units bound this loop): warps 4 and 5 are alone on theirs and
+          // take two slots of 32 points per round of 256, warps 2, 3 and the
+          // last two share the other two sub-partitions and take one each
+          // (p <= 4; above, one point per thread in order)
+          const int wl = gt >> 5;
+          const int nslot = !C::GEO_FINE ? 1 : (wl == 2 || wl == 3) ? 2 : 1;
+          const int step = C::GEO_FINE ? 256 : kNGeo;
+          for (int base = 0; base < nnew * C::NQP; base += step)
+          for (int sv = 0; sv < nslot; sv++) {
+            const int idx = C::GEO_FINE ? base + (sv ? wl + 4 : wl) * 32 + (gt & 31) : base + gt;
+            if (idx >= nnew * C::NQP) continue;
             const int el = idx / C::NQP, q = idx % C::NQP;
             const int sl = (int)((e_new + el) % C::RING);
             float *gr = sG + (size_t)sl * C::GSLOT + q * 12;
@@ -773,6 +891,12 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
         }
         gbar();  // the pass is complete for the whole group before the drain reads it
         if (gt == 0) ptx::mbar_arrive(&bar_gfull[b]);  // arrives even after an abort
+        if (C::GEO_FINE && t + 1 < t_end && !*sAbort) {  // the next pass's inputs, into the other buffer
+          int64_t en;
+          int nn;
+          new_elems(t + 1, en, nn);
+          fetch(en, nn, sX + (size_t)((tt + 1) & 1) * C::MAXEL * C::NREC);
+        }
       }
       if (epi && t > t_begin) {
         // ---------------- epilogue of tile t - 1: TMEM -> columns of A_e / b_e ----------------
@@ -795,7 +919,7 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
           const int j = valid ? (int)(r % C::L) : 0;
           const int sl = (int)(e % C::RING);
           const float inv = valid ? (j < C::NS ? sInv[sl] : sInvB[sl]) : 0.f;
-          const uint32_t tbase = tmem + ab * C::NP + ((uint32_t)(32 * lq) << 16);
+          const uint32_t tbase = tmem + ab * C::KACC * C::NP + ((uint32_t)(32 * lq) << 16);
           constexpr int NPK = C::NS * (C::NS + 1) / 2;
           // columns c0 .. c0 + 15 of the accumulator row (v[0..15]) -> A_e / b_e
           auto store16 = [&](int c0, const uint32_t (&v)[16]) {
@@ -836,16 +960,30 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
               }
             }
           };
-          // two 16-column loads in flight per wait
+          if constexpr (C::KACC == 2) {
+            // the two accumulators' columns c0 .. c0 + 15, summed in FP32
 #pragma unroll 1
-          for (int c0 = 0; c0 < C::NP; c0 += 32) {
-            uint32_t v0[16], v1[16];
-            const bool two = c0 + 16 < C::NP;  // warp-uniform
-            ptx::tmem_ld16(tbase + c0, v0);
-            if (two) ptx::tmem_ld16(tbase + c0 + 16, v1);
-            ptx::tmem_ld_wait();
-            store16(c0, v0);
-            if (two) store16(c0 + 16, v1);
+            for (int c0 = 0; c0 < C::NP; c0 += 16) {
+              uint32_t v0[16], v1[16];
+              ptx::tmem_ld16(tbase + c0, v0);
+              ptx::tmem_ld16(tbase + C::NP + c0, v1);
+              ptx::tmem_ld_wait();
+#pragma unroll
+              for (int u = 0; u < 16; u++) v0[u] = __float_as_uint(__uint_as_float(v0[u]) + __uint_as_float(v1[u]));
+              store16(c0, v0);
+            }
+          } else {
+            // two 16-column loads in flight per wait
+#pragma unroll 1
+            for (int c0 = 0; c0 < C::NP; c0 += 32) {
+              uint32_t v0[16], v1[16];
+              const bool two = c0 + 16 < C::NP;  // warp-uniform
+              ptx::tmem_ld16(tbase + c0, v0);
+              if (two) ptx::tmem_ld16(tbase + c0 + 16, v1);
+              ptx::tmem_ld_wait();
+              store16(c0, v0);
+              if (two) store16(c0 + 16, v1);
+            }
           }
           ptx::tc_fence_before();
           __syncwarp();
@@ -858,6 +996,7 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
     }
   }
 
+  ptx::cp_async_wait_all();  // no copy into shared memory outlives the CTA
   __syncthreads();
   if (*sAbort) {
     if (tid == 0 && a.err) atomicOr(a.err, kErrTimeout);
