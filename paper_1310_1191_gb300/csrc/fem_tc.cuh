@@ -133,6 +133,7 @@ struct TcCfg {
   static constexpr size_t OFF_MISC = OFF_BAR + 8 * NBAR;
   static constexpr size_t SMEM = OFF_MISC + 16 + 1024;
   static_assert(NH % 16 == 0 && NH >= 16 && NH <= 256, "MMA N out of range");
+  static constexpr bool PAIRS = STAGES >= 4;  // producers hand chunks over in pairs
   static_assert(NQP >= NQ, "padding");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -542,9 +543,20 @@ __global__ void __launch_bounds__(TcCfg<P, ELAS, LAW, RULE>::THREADS, 1) tc_kern
           *reinterpret_cast<uint4 *>(aH + off) = make_uint4(hw[4 * k2], hw[4 * k2 + 1], hw[4 * k2 + 2], hw[4 * k2 + 3]);
           *reinterpret_cast<uint4 *>(aL + off) = make_uint4(lw[4 * k2], lw[4 * k2 + 1], lw[4 * k2 + 2], lw[4 * k2 + 3]);
         }
-        ptx::fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&bar_full[s]);
+        // with 4 or more stages chunks are handed over in pairs: one proxy
+        // fence (it waits for the shared-memory writes to reach the tensor
+        // cores' view, about 5 % of the kernel when issued per chunk) covers
+        // both, then both stages arrive.  The stage the second chunk waits for
+        // was released by a chunk at least two back, already handed over, so
+        // this cannot stall; with 3 stages (p = 7) pairs starve the MMAs.
+        if (!C::PAIRS || (c & 1) || c == C::NCH - 1) {
+          ptx::fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) {
+            if (C::PAIRS && (c & 1)) ptx::mbar_arrive(&bar_full[(g - 1) % C::STAGES]);
+            ptx::mbar_arrive(&bar_full[s]);
+          }
+        }
         return true;
       };
       for (int c0 = 0; c0 < C::NCH && ok; c0 += C::PD) {
