@@ -489,10 +489,28 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
         T av[C::TM], bv[C::TN];
         lds_vec<T, C::TM, ALA>(pa + k * C::BM, av);
         lds_vec<T, C::TN, ALB>(pb + k * C::BN, bv);
+        if constexpr (sizeof(T) == 4) {
+          // FP32: two multiply-adds per instruction (fma.rn.f32x2; the same
+          // round-to-nearest fused multiply-add on each lane as fmaf, so the
+          // results are unchanged).  The kernel is issue-bound, and this
+          // halves the issue slots of the multiply-adds.
 #pragma unroll
-        for (int i = 0; i < C::TM; i++)
+          for (int i = 0; i < C::TM; i++) {
+            const float2 a2 = make_float2(av[i], av[i]);
 #pragma unroll
-          for (int j = 0; j < C::TN; j++) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+            for (int j = 0; j + 1 < C::TN; j += 2) {
+              const float2 c = __ffma2_rn(a2, make_float2(bv[j], bv[j + 1]), make_float2(acc[i][j], acc[i][j + 1]));
+              acc[i][j] = c.x;
+              acc[i][j + 1] = c.y;
+            }
+            if (C::TN & 1) acc[i][C::TN - 1] = fma(av[i], bv[C::TN - 1], acc[i][C::TN - 1]);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < C::TM; i++)
+#pragma unroll
+            for (int j = 0; j < C::TN; j++) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
       }
     }
     __syncthreads();
