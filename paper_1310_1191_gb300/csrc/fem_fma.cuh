@@ -489,11 +489,13 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
         T av[C::TM], bv[C::TN];
         lds_vec<T, C::TM, ALA>(pa + k * C::BM, av);
         lds_vec<T, C::TN, ALB>(pb + k * C::BN, bv);
-        if constexpr (sizeof(T) == 4) {
+        if constexpr (sizeof(T) == 4 && C::NT <= 512) {
           // FP32: two multiply-adds per instruction (fma.rn.f32x2; the same
           // round-to-nearest fused multiply-add on each lane as fmaf, so the
           // results are unchanged).  The kernel is issue-bound, and this
-          // halves the issue slots of the multiply-adds.
+          // halves the issue slots of the multiply-adds.  Not in the one-tile
+          // p = 6 shapes (625 threads, 96 registers): there the register
+          // pairs spill (elasticity p = 6 measured 12 % slower).
 #pragma unroll
           for (int i = 0; i < C::TM; i++) {
             const float2 a2 = make_float2(av[i], av[i]);
