@@ -568,16 +568,20 @@ int fem_integrate_host(fem_tables t, int p, int64_t n_elem, const double *coords
   if (chunk > n_elem) chunk = n_elem;
   const size_t need = (size_t)chunk * per + 5 * 256;
   if (t->stage_bytes < need) {
+    // at least the default chunk's 256 MB, so that calls of other degrees
+    // (other per-element sizes) reuse the slots: a reallocation frees the
+    // old slots, which synchronises the device
+    const size_t alloc = std::max(need, ((size_t)256 << 20) + 5 * 256);
     for (int i = 0; i < 2; i++) {
       if (t->stage[i]) cudaFree(t->stage[i]);
       t->stage[i] = nullptr;
-      cudaError_t e = cudaMalloc((void **)&t->stage[i], need);
+      cudaError_t e = cudaMalloc((void **)&t->stage[i], alloc);
       if (e != cudaSuccess) {
         t->stage_bytes = 0;
         return cuda_fail("fem_integrate_host: staging allocation", e);
       }
     }
-    t->stage_bytes = need;
+    t->stage_bytes = alloc;
   }
   for (int i = 0; i < 2; i++)
     if (!t->hs[i]) {
