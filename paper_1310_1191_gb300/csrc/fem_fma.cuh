@@ -104,9 +104,38 @@ constexpr size_t law_smem_bytes(int law) {
   return law == 0 ? 0 : (size_t)C::EPB * C::NS * 4 + 16 + (law == 2 ? (size_t)kMlpSmemBytes + 16 : 0);
 }
 
+// Mirrored tile pairs.  Diffusion and reaction make a symmetric part S of
+// A_e (G[1..3][1..3] is symmetric, G[1..3][0] = 0); only the convection part
+// Cv[i][j] = sum_Q phi_0[Q][i] V[Q][j], V[Q][j] = sum_{d=1..3} G[0][d]
+// phi_d[Q][j], is not.  So the tile below the diagonal follows from the one
+// above it: A[j][i] = A[i][j] + sum_Q (phi_0[Q][j] V[Q][i] - phi_0[Q][i]
+// V[Q][j]), a contraction over 2 NQ instead of 4 NQ.  With several output
+// tiles per element (TILES >= 2) a CTA takes the tile pair (ti, tj), ti <= tj:
+// the upper tile as before, then, for ti < tj, the correction into the same
+// registers and the transposed write.  Work per element: TILES (TILES + 1) / 2
+// full tiles and TILES (TILES - 1) / 2 half tiles instead of TILES^2 full ones
+// (p = 7, three tiles: 0.83; two tiles: 0.875).  Scalar form with constant
+// coefficients only.
+template <class C, int LAW, bool SPLIT>
+constexpr bool fma_mirror() {
+  return C::TILES >= 2 && C::ND == 4 && LAW == 0 && !SPLIT;
+}
+
+// tile pair pr (0 .. TILES (TILES + 1) / 2 - 1) -> (ti, tj), ti <= tj, row by row
+template <int TILES>
+__device__ __forceinline__ void pair_tiles(int pr, int &ti, int &tj) {
+  ti = 0;
+  while (pr >= TILES - ti) {
+    pr -= TILES - ti;
+    ti++;
+  }
+  tj = ti + pr;
+}
+
 // SPLIT: the Jacobian terms (det J, J^{-1} per point) are read from a.terms
 // instead of computed from a.coords (the paper's NOJAC variants).
-template <class T, class C, int LAW = 0, bool SPLIT = false>
+// MIRROR (fma_mirror): (ti, tj) is a tile pair, see above.
+template <class T, class C, int LAW = 0, bool SPLIT = false, bool MIRROR = false>
 __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, const T *phi, int64_t k0,
                                          int64_t k_end, int ti, int tj, unsigned char *smem) {
   T *sPA = reinterpret_cast<T *>(smem);                 // [KC][BM]
@@ -518,8 +547,8 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
     __syncthreads();
   }
 
-  // 3. load vector rows of this tile
-  if (tj == 0 && a.b != nullptr) {
+  // 3. load vector rows of this tile (mirrored pairs: by the diagonal tile)
+  if ((MIRROR ? ti == tj : tj == 0) && a.b != nullptr) {
     T *bo = static_cast<T *>(a.b);
     constexpr int SLOT = ELAST ? 9 : GS;
     for (int idx = tid; idx < C::EPB * C::BM; idx += nthr) {
@@ -569,6 +598,77 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
       }
     }
   }
+  // 5. mirrored pair: the tile (tj, ti) below the diagonal from the upper one
+  //    (full layout; the upper-packed layout keeps only the upper tiles)
+  if constexpr (MIRROR) {
+    if (ti < tj && a.layout == FEM_OUT_FULL) {
+      static_assert(2 * C::QC * C::BM <= C::KC * C::BM && 2 * C::QC * C::BN <= C::KC * C::BN, "staging");
+      T *sP0i = sPA, *sP0j = sPA + C::QC * C::BM;            // phi_0 rows of tiles ti, tj: [QC][BM]
+      T *sVi = sT, *sVj = sT + C::EPB * C::QC * C::BM;       // V of tiles ti, tj: [EPB][QC][BM]
+      for (int ch = 0; ch < C::NCH; ch++) {
+        const int q0 = ch * C::QC;
+        for (int idx = tid; idx < 2 * C::QC * C::BM; idx += nthr) {
+          const int h = idx / (C::QC * C::BM), r2 = idx % (C::QC * C::BM);
+          const int qq = r2 / C::BM, i = r2 % C::BM, q = q0 + qq;
+          const int row = (h ? tj : ti) * C::BM + i;
+          sPA[idx] = (row < C::NS && q < C::NQ) ? phi[(size_t)(4 * q) * C::NS + row] : (T)0;
+        }
+        for (int idx = tid; idx < 2 * C::EPB * C::QC * C::BM; idx += nthr) {
+          const int h = idx / (C::EPB * C::QC * C::BM), r2 = idx % (C::EPB * C::QC * C::BM);
+          const int l2 = r2 / (C::QC * C::BM), r3 = r2 % (C::QC * C::BM);
+          const int qq = r3 / C::BM, i = r3 % C::BM, q = q0 + qq;
+          const int col = (h ? tj : ti) * C::BM + i;
+          T v = 0;
+          if (q < C::NQ && col < C::NS) {
+            const T *ph = phi + (size_t)(4 * q) * C::NS + col;
+            const T *g = sG + ((size_t)l2 * C::NQ + q) * kGStride;
+            v = g[G01] * ph[C::NS] + g[G02] * ph[2 * C::NS] + g[G03] * ph[3 * C::NS];
+          }
+          sT[idx] = v;
+        }
+        __syncthreads();
+        if (owner) {
+          const T *pi = sP0i + ty * C::TM, *pj = sP0j + tx * C::TN;
+          const T *vi = sVi + (size_t)le * C::QC * C::BM + ty * C::TM;
+          const T *vj = sVj + (size_t)le * C::QC * C::BN + tx * C::TN;
+          // element offsets of the four operands from the 16-byte aligned shared base
+          constexpr int ALPI = cgcd(C::BM, C::TM);
+          constexpr int ALPJ = cgcd(cgcd(C::QC * C::BM, C::BN), C::TN);
+          constexpr int ALVI = cgcd(cgcd(C::KC * C::BM, C::QC * C::BM), ALPI);
+          constexpr int ALVJ = cgcd(cgcd(C::KC * C::BM + C::EPB * C::QC * C::BM, C::QC * C::BN), cgcd(C::BN, C::TN));
+#pragma unroll 2
+          for (int k = 0; k < C::QC; k++) {
+            T api[C::TM], avi[C::TM], bpj[C::TN], bvj[C::TN];
+            lds_vec<T, C::TM, ALPI>(pi + k * C::BM, api);
+            lds_vec<T, C::TM, ALVI>(vi + k * C::BM, avi);
+            lds_vec<T, C::TN, ALPJ>(pj + k * C::BN, bpj);
+            lds_vec<T, C::TN, ALVJ>(vj + k * C::BN, bvj);
+#pragma unroll
+            for (int i = 0; i < C::TM; i++)
+#pragma unroll
+              for (int j = 0; j < C::TN; j++) acc[i][j] = fma(bpj[j], avi[i], fma(-api[i], bvj[j], acc[i][j]));
+          }
+        }
+        __syncthreads();
+      }
+      if (e >= 0) {
+        const int64_t oA = a.offA ? a.offA[e] : e * (int64_t)NSZ;
+        if (fem_chk(a.limA < 0 || (oA >= 0 && oA + NSZ <= a.limA), a.err)) {
+          T *Ae = static_cast<T *>(a.A) + oA;
+#pragma unroll
+          for (int i = 0; i < C::TM; i++) {
+            const int row = ti * C::BM + ty * C::TM + i;
+            if (row >= C::NS) continue;
+#pragma unroll
+            for (int j = 0; j < C::TN; j++) {
+              const int col = tj * C::BN + tx * C::TN + j;
+              if (col < C::NS) Ae[col * C::NS + row] = acc[i][j];
+            }
+          }
+        }
+      }
+    }
+  }
   if (a.status != nullptr && ti == 0 && tj == 0)
     for (int l2 = tid; l2 < C::EPB; l2 += nthr) {
       const int64_t v = sE[l2];
@@ -577,15 +677,40 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   __syncthreads();  // shared memory is reused by the next work item
 }
 
+// the block's element group and output tile (or tile pair)
+template <class T, class C, int LAW, bool SPLIT>
+__device__ __forceinline__ void fma_block(const FmaArgs &a, unsigned char *smem) {
+  long long blk = blockIdx.x;
+  constexpr bool mirror = fma_mirror<C, LAW, SPLIT>();
+  int ti, tj;
+  if constexpr (mirror) {
+    constexpr int NPAIR = C::TILES * (C::TILES + 1) / 2;
+    pair_tiles<C::TILES>((int)(blk % NPAIR), ti, tj);
+    blk /= NPAIR;
+  } else {
+    tj = (int)(blk % C::TILES);
+    blk /= C::TILES;
+    ti = (int)(blk % C::TILES);
+    blk /= C::TILES;
+  }
+  fma_body<T, C, LAW, SPLIT, mirror>(a, a.qp, static_cast<const T *>(a.phi), blk * (int64_t)C::EPB, a.n, ti, tj,
+                                     smem);
+}
+
 template <class T, class C, int LAW = 0, bool SPLIT = false>
 __global__ void __launch_bounds__(C::NT) fma_kernel(const FmaArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  long long blk = blockIdx.x;
-  const int tj = (int)(blk % C::TILES);
-  blk /= C::TILES;
-  const int ti = (int)(blk % C::TILES);
-  blk /= C::TILES;
-  fma_body<T, C, LAW, SPLIT>(a, a.qp, static_cast<const T *>(a.phi), blk * (int64_t)C::EPB, a.n, ti, tj, smem);
+  fma_block<T, C, LAW, SPLIT>(a, smem);
+}
+
+// FP64 mirrored tile pairs on CTAs of at most 256 threads, held to two CTAs
+// per SM: at p = 7 the correction pass took the kernel to 138 registers and
+// one CTA per SM (722 ms per 3,004 prisms); at 128 registers two CTAs run
+// (710 ms).
+template <class T, class C>
+__global__ void __launch_bounds__(C::NT, 2) fma_kernel_pair2(const FmaArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  fma_block<T, C, 0, false>(a, smem);
 }
 
 // FP32 kernels with the network stage: the MMA fragments and activations keep
@@ -615,9 +740,12 @@ int launch_fma_cfg(const FmaArgs &a, void *stream) {
   if (a.n == 0) return FEM_OK;
   const size_t smem = C::template smem_bytes<T>() + law_smem_bytes<C>(LAW);
   constexpr bool net = LAW == 2 && sizeof(T) == 4 && net_min_blocks<C>() >= 2;
+  constexpr bool pair2 = !net && sizeof(T) == 8 && fma_mirror<C, LAW, SPLIT>() && C::NT <= 256;
   void (*kern)(const FmaArgs);
   if constexpr (net)
     kern = fma_kernel_net<T, C, SPLIT>;
+  else if constexpr (pair2)
+    kern = fma_kernel_pair2<T, C>;
   else
     kern = fma_kernel<T, C, LAW, SPLIT>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -626,7 +754,7 @@ int launch_fma_cfg(const FmaArgs &a, void *stream) {
     return FEM_ECUDA;
   }
   const int64_t groups = (a.n + C::EPB - 1) / C::EPB;
-  const int64_t grid = groups * C::TILES * C::TILES;
+  const int64_t grid = groups * (fma_mirror<C, LAW, SPLIT>() && !net ? C::TILES * (C::TILES + 1) / 2 : C::TILES * C::TILES);
   if (grid > 0x7fffffffLL) {
     set_error("too many elements for one launch");
     return FEM_EINVAL;
