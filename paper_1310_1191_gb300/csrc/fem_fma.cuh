@@ -32,12 +32,18 @@ namespace fem {
 // (derivatives only, one 3x3 block of linear elastostatics per virtual element).
 // RULE_: the prism rule (FEM_RULE_COLLAPSED or FEM_RULE_TABLE1); both are
 // (p+1) zeta levels x NAB triangle points, point q = iz NAB + iab.
-template <int ELEM_, int P_, int BM_, int TM_, int TN_, int EPB_, int QC_, int ND_ = 4, int RULE_ = FEM_RULE_COLLAPSED>
+// MM_: mirrored micro-tiles (one output tile per element, square micro-tiles):
+// a thread per micro-tile on or above the diagonal, see fma_mirror.
+template <int ELEM_, int P_, int BM_, int TM_, int TN_, int EPB_, int QC_, int ND_ = 4, int RULE_ = FEM_RULE_COLLAPSED,
+          bool MM_ = false>
 struct FmaCfg {
   static constexpr int ELEM = ELEM_, P = P_, ND = ND_, RULE = RULE_;
+  static constexpr bool MM = MM_;
   static constexpr int NS = ns_of(ELEM_, P_), NQ = nq_of(ELEM_, P_, RULE_), NV = nv_of(ELEM_);
   static constexpr int BM = BM_, BN = BM_, TM = TM_, TN = TN_;
-  static constexpr int TY = BM / TM, TX = BN / TN, TPE = TX * TY;
+  static constexpr int TY = BM / TM, TX = BN / TN, TPE = MM_ ? TY * (TY + 1) / 2 : TX * TY;
+  // the same shape with a thread per micro-tile (paths that do not mirror)
+  using Plain = FmaCfg<ELEM_, P_, BM_, TM_, TN_, EPB_, QC_, ND_, RULE_, false>;
   static constexpr int EPB = EPB_, NT = EPB * TPE;
   static constexpr int TILES = (NS + BM - 1) / BM;
   static constexpr int QC = QC_, KC = ND * QC, NCH = (NQ + QC - 1) / QC;
@@ -47,6 +53,7 @@ struct FmaCfg {
   static constexpr int NAB = ELEM_ == FEM_PRISM6 ? ntri_of(P_, RULE_) : 0;     // (xi, eta) points per level
   static_assert(BM % TM == 0 && BN % TN == 0, "tile must split into micro-tiles");
   static_assert(NT <= 1024, "too many threads");
+  static_assert(!MM_ || (TM_ == TN_ && BM_ >= ns_of(ELEM_, P_)), "mirrored micro-tiles: square, one tile");
 
   template <class T>
   static constexpr size_t smem_bytes() {
@@ -114,11 +121,14 @@ constexpr size_t law_smem_bytes(int law) {
 // the upper tile as before, then, for ti < tj, the correction into the same
 // registers and the transposed write.  Work per element: TILES (TILES + 1) / 2
 // full tiles and TILES (TILES - 1) / 2 half tiles instead of TILES^2 full ones
-// (p = 7, three tiles: 0.83; two tiles: 0.875).  Scalar form with constant
-// coefficients only.
+// (p = 7, three tiles: 0.83; two tiles: 0.875).  With one tile per element
+// the same holds for micro-tiles (C::MM): a thread per micro-tile (ty, tx),
+// ty <= tx, the diagonal ones last (whole warps of them skip the correction);
+// with 21 x 21 micro-tiles (p = 5) 0.76 of the dense work.  Scalar form with
+// constant coefficients only.
 template <class C, int LAW, bool SPLIT>
 constexpr bool fma_mirror() {
-  return C::TILES >= 2 && C::ND == 4 && LAW == 0 && !SPLIT;
+  return (C::TILES >= 2 || C::MM) && C::ND == 4 && LAW == 0 && !SPLIT;
 }
 
 // tile pair pr (0 .. TILES (TILES + 1) / 2 - 1) -> (ti, tj), ti <= tj, row by row
@@ -464,7 +474,24 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
 
   // 2. contraction over chunks of points
   const bool owner = tid < C::NT;
-  const int le = owner ? tid / C::TPE : 0, r = tid % C::TPE, tx = r % C::TX, ty = r / C::TX;
+  const int le = owner ? tid / C::TPE : 0, r = tid % C::TPE;
+  int tx = r % C::TX, ty = r / C::TX;
+  if constexpr (C::MM) {
+    // micro-tile pairs: first the TY (TY - 1) / 2 above the diagonal, row by
+    // row, then the TY diagonal ones
+    constexpr int NOFF = C::TY * (C::TY - 1) / 2;
+    if (r >= NOFF) {
+      ty = tx = r - NOFF;
+    } else {
+      int rr = r;
+      ty = 0;
+      while (rr >= C::TY - 1 - ty) {
+        rr -= C::TY - 1 - ty;
+        ty++;
+      }
+      tx = ty + 1 + rr;
+    }
+  }
   T acc[C::TM][C::TN];
 #pragma unroll
   for (int i = 0; i < C::TM; i++)
@@ -601,7 +628,9 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
   // 5. mirrored pair: the tile (tj, ti) below the diagonal from the upper one
   //    (full layout; the upper-packed layout keeps only the upper tiles)
   if constexpr (MIRROR) {
-    if (ti < tj && a.layout == FEM_OUT_FULL) {
+    // pairs of tiles (ti < tj), or, with one tile, of micro-tiles (ty < tx)
+    const bool mine = !C::MM || ty < tx;
+    if ((C::MM || ti < tj) && a.layout == FEM_OUT_FULL) {
       static_assert(2 * C::QC * C::BM <= C::KC * C::BM && 2 * C::QC * C::BN <= C::KC * C::BN, "staging");
       T *sP0i = sPA, *sP0j = sPA + C::QC * C::BM;            // phi_0 rows of tiles ti, tj: [QC][BM]
       T *sVi = sT, *sVj = sT + C::EPB * C::QC * C::BM;       // V of tiles ti, tj: [EPB][QC][BM]
@@ -627,7 +656,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
           sT[idx] = v;
         }
         __syncthreads();
-        if (owner) {
+        if (owner && mine) {
           const T *pi = sP0i + ty * C::TM, *pj = sP0j + tx * C::TN;
           const T *vi = sVi + (size_t)le * C::QC * C::BM + ty * C::TM;
           const T *vj = sVj + (size_t)le * C::QC * C::BN + tx * C::TN;
@@ -651,7 +680,7 @@ __device__ __forceinline__ void fma_body(const FmaArgs &a, const double *qp, con
         }
         __syncthreads();
       }
-      if (e >= 0) {
+      if (e >= 0 && mine) {
         const int64_t oA = a.offA ? a.offA[e] : e * (int64_t)NSZ;
         if (fem_chk(a.limA < 0 || (oA >= 0 && oA + NSZ <= a.limA), a.err)) {
           T *Ae = static_cast<T *>(a.A) + oA;
@@ -737,6 +766,7 @@ __global__ void __launch_bounds__(C::NT, (net_min_blocks<C>() >= 2 ? net_min_blo
 
 template <class T, class C, int LAW = 0, bool SPLIT = false>
 int launch_fma_cfg(const FmaArgs &a, void *stream) {
+  if constexpr (C::MM && !(LAW == 0 && !SPLIT)) return launch_fma_cfg<T, typename C::Plain, LAW, SPLIT>(a, stream);
   if (a.n == 0) return FEM_OK;
   const size_t smem = C::template smem_bytes<T>() + law_smem_bytes<C>(LAW);
   constexpr bool net = LAW == 2 && sizeof(T) == 4 && net_min_blocks<C>() >= 2;
@@ -783,7 +813,9 @@ template <> struct FmaShape<double, FEM_PRISM6, 1> { using type = FmaCfg<FEM_PRI
 template <> struct FmaShape<double, FEM_PRISM6, 2> { using type = FmaCfg<FEM_PRISM6, 2, 18, 3, 6, 14, 3>; };
 template <> struct FmaShape<double, FEM_PRISM6, 3> { using type = FmaCfg<FEM_PRISM6, 3, 40, 5, 8, 4, 8>; };
 template <> struct FmaShape<double, FEM_PRISM6, 4> { using type = FmaCfg<FEM_PRISM6, 4, 75, 3, 5, 1, 5>; };
-template <> struct FmaShape<double, FEM_PRISM6, 5> { using type = FmaCfg<FEM_PRISM6, 5, 126, 6, 6, 1, 6>; };
+template <> struct FmaShape<double, FEM_PRISM6, 5> {
+  using type = FmaCfg<FEM_PRISM6, 5, 126, 6, 6, 1, 6, 4, FEM_RULE_COLLAPSED, true>;
+};
 template <> struct FmaShape<double, FEM_PRISM6, 6> { using type = FmaCfg<FEM_PRISM6, 6, 98, 2, 7, 1, 7>; };
 template <> struct FmaShape<double, FEM_PRISM6, 7> { using type = FmaCfg<FEM_PRISM6, 7, 96, 6, 6, 1, 8>; };
 template <> struct FmaShape<float, FEM_TET4, 1> { using type = FmaCfg<FEM_TET4, 1, 4, 1, 4, 64, 4>; };
@@ -826,7 +858,7 @@ int launch_fma_elastic(int p, const FmaArgs &a, void *stream) {
 // The paper's prism rule (Table 1's point counts): the collapsed rule's
 // shapes with its points (constant coefficients).
 template <class S>
-using Table1Cfg = FmaCfg<S::ELEM, S::P, S::BM, S::TM, S::TN, S::EPB, S::QC, S::ND, FEM_RULE_TABLE1>;
+using Table1Cfg = FmaCfg<S::ELEM, S::P, S::BM, S::TM, S::TN, S::EPB, S::QC, S::ND, FEM_RULE_TABLE1, S::MM>;
 
 template <class T>
 int launch_fma_table1(int p, const FmaArgs &a, void *stream) {
