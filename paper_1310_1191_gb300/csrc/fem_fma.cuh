@@ -812,7 +812,9 @@ template <> struct FmaShape<double, FEM_TET4, 1> { using type = FmaCfg<FEM_TET4,
 template <> struct FmaShape<double, FEM_PRISM6, 1> { using type = FmaCfg<FEM_PRISM6, 1, 6, 1, 6, 42, 4>; };
 template <> struct FmaShape<double, FEM_PRISM6, 2> { using type = FmaCfg<FEM_PRISM6, 2, 18, 3, 6, 14, 3>; };
 template <> struct FmaShape<double, FEM_PRISM6, 3> { using type = FmaCfg<FEM_PRISM6, 3, 40, 5, 8, 4, 8>; };
-template <> struct FmaShape<double, FEM_PRISM6, 4> { using type = FmaCfg<FEM_PRISM6, 4, 75, 3, 5, 1, 5>; };
+template <> struct FmaShape<double, FEM_PRISM6, 4> {
+  using type = FmaCfg<FEM_PRISM6, 4, 75, 3, 3, 1, 5, 4, FEM_RULE_COLLAPSED, true>;
+};
 template <> struct FmaShape<double, FEM_PRISM6, 5> {
   using type = FmaCfg<FEM_PRISM6, 5, 126, 6, 6, 1, 6, 4, FEM_RULE_COLLAPSED, true>;
 };
@@ -838,6 +840,9 @@ struct FmaShapeE {
 // slower for the nine-block elasticity (5.5 -> 8.4 ms and 8.3 -> 9.6 ms)
 template <> struct FmaShapeE<float, 2> { using type = FmaCfg<FEM_PRISM6, 2, 18, 6, 6, 28, 3, 3>; };
 template <> struct FmaShapeE<float, 4> { using type = FmaCfg<FEM_PRISM6, 4, 75, 5, 5, 1, 5, 3>; };
+// FP64 p = 4: the 3 x 5 micro-tiles of the scalar form before its mirrored
+// 3 x 3 micro-tiles (elasticity does not mirror)
+template <> struct FmaShapeE<double, 4> { using type = FmaCfg<FEM_PRISM6, 4, 75, 3, 5, 1, 5, 3>; };
 
 template <class T, bool SPLIT = false>
 int launch_fma_elastic(int p, const FmaArgs &a, void *stream) {
