@@ -136,9 +136,9 @@ def flops_per_elem(p):
 # Output tiles (or, with one tile, micro-tiles) per side of the FMA kernels'
 # shapes that take mirrored pairs (the tile below the diagonal from the one
 # above it plus the antisymmetric convection part, a contraction over 2 NQ
-# instead of 4 NQ): FP64 p = 5 (21 x 21 micro-tiles of one tile), p = 6 (two
-# tiles of 98) and p = 7 (three of 96), FP32 p = 7.
-MIRROR_TILES = {8: {5: 21, 6: 2, 7: 3}, 4: {7: 3}}
+# instead of 4 NQ): FP64 p = 4 and 5 (25 x 25 and 21 x 21 micro-tiles of one
+# tile), p = 6 (two tiles of 98) and p = 7 (three of 96), FP32 p = 7.
+MIRROR_TILES = {8: {4: 25, 5: 21, 6: 2, 7: 3}, 4: {7: 3}}
 
 
 def executed_flops_per_elem(p, osz):
