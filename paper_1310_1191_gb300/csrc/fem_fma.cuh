@@ -18,7 +18,10 @@
 //      weighted T columns of the tile for each element, then accumulate the
 //      outer products in registers;
 //   3. the column-0 tiles also form the load vector b = sum_Q S_Q phi[Q][0];
-//   4. write the unpadded micro-tiles (full or upper-packed rows).
+//   4. write the unpadded micro-tiles (full or upper-packed rows);
+//   5. mirrored pairs (see fma_mirror): the tile or micro-tile below the
+//      diagonal from the one above it and the convection part, written
+//      transposed.
 #pragma once
 
 #include <cuda_runtime.h>
